@@ -1,0 +1,357 @@
+#!/usr/bin/env python
+"""Benchmark of the per-frame atlasing path (one JSON line on rank 0).
+
+Workload: 200 displaced icospheres at subdivision 5 (4,096,000 triangles,
+2,048,400 vertices), a 1920x1080 view from a seeded camera at the edge of the 50^3
+box, texel-to-pixel ratio 1.0, 2048^2 atlas, 64 candidate scales, edge charts.
+A step is one whole frame: visibility (depth pre-pass + marking), chartify,
+boxes + footprints, order + pack + select, UVs.  Inputs are resident in HBM; the
+L2 is flushed (256 MiB write) between steps, outside the per-step CUDA events.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+N > 1 runs N independent replicas (one per rank, launched by torch.distributed.run);
+the work per GPU is fixed (weak scaling) and there is no collective on the data path.
+--impl reference times the CPU oracle on the host cores on the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "atlased frames/s at 1080p/2K atlas (% HBM roofline)"
+FLUSH_BYTES = 256 << 20
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--ratio", type=float, default=1.0)
+    ap.add_argument("--mode", type=int, default=0, help="0 edge charts, 1 vertex charts")
+    ap.add_argument("--seed", type=int, default=1)
+    ap.add_argument("--spheres", type=int, default=200)
+    ap.add_argument("--no-graph", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"icospheres{a.spheres}_sub5_1920x1080_atlas2048_ratio{a.ratio:g}_"
+            f"{'vertex' if a.mode else 'edge'}charts_64scales")
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.p = None
+        self.path = os.path.join("/tmp", f"fa_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.f = open(self.path, "w")
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.close()
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        if not sm:
+            return None
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# algorithmic (compulsory) bytes per launch, by kernel
+def algorithmic_bytes(kernel, T, V, W, H, T_vis, C):
+    vt = (T + 31) // 32 * 4
+    table = {
+        # read indices + positions once, read-modify-write the depth buffer, write the queue bits
+        "k_raster_depth": 12 * T + 12 * V + 4 * W * H + vt,
+        # read indices + positions once, read the depth buffer, write the VT words
+        "k_raster_mark": 12 * T + 12 * V + 4 * W * H + 2 * vt,
+        "k_clear": 4 * W * H,
+        "k_uf_init": vt + 12 * T_vis + 4 * T_vis,
+        "k_uf_hook": vt + 12 * T_vis + 8 * T_vis,
+        "k_uf_flatten": vt + 8 * T_vis,
+        "k_tri_chart": vt + 4 * T + 8 * T_vis,
+        "k_bbox": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis,
+        "k_uv": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis + 24 * T_vis,
+        "k_number": vt + 4 * T_vis,
+        "k_pack": 64 * 8 * C,
+    }
+    return table.get(kernel)
+
+
+def run_reference(a):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle as O
+    from paper_2502_17712_gb300 import scenes as S
+    sc, M, p = S.icosphere_frame(a.seed, a.spheres, a.ratio)
+    W, H, L = p["width"], p["height"], p["atlas_log2"]
+
+    def frame():
+        O.atlas_frame(M, sc.pos, sc.idx, W, H, a.ratio, L, mode=a.mode)
+
+    for _ in range(a.warmup):
+        frame()
+    t0 = time.perf_counter()
+    for _ in range(a.steps):
+        frame()
+    dt = time.perf_counter() - t0
+    v = a.steps / dt
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "frames/s", "n_gpus": a.gpus,
+            "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * dt / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "triangles": sc.T, "parallelism": "host, 1 thread"},
+            "cpu_baseline": {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
+                             "sample": f"{a.steps} full frames of the workload"},
+            "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def cpu_baseline(a, sc, M, p):
+    import oracle as O
+    W, H, L = p["width"], p["height"], p["atlas_log2"]
+    n, t0 = 0, time.perf_counter()
+    while True:
+        O.atlas_frame(M, sc.pos, sc.idx, W, H, a.ratio, L, mode=a.mode)
+        n += 1
+        if time.perf_counter() - t0 > 10.0 or n >= 3:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+            "sample": f"{n} full frame(s) of the workload, single-threaded oracle"}
+
+
+def run_ours(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+    from paper_2502_17712_gb300 import build as B
+    from paper_2502_17712_gb300 import fastatlas as F
+    from paper_2502_17712_gb300 import scenes as S
+
+    rank, world, local = dist_env()
+    if world > 1:
+        dist.init_process_group("nccl", init_method="env://")
+    torch.cuda.set_device(local)
+    if rank == 0 or world == 1:
+        B.build()
+    if world > 1:
+        dist.barrier()
+    F.load()
+    sc, M, p = S.icosphere_frame(a.seed, a.spheres, a.ratio)
+    W, H, L = p["width"], p["height"], p["atlas_log2"]
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 17, max_width=W, max_height=H,
+                    max_atlas_log2=L, device=local)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts)
+    flush = torch.empty(FLUSH_BYTES // 4, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def frame():
+        F.atlas_frame(ctx, mesh, bufs, M, W, H, a.ratio, L, a.mode)
+
+    for _ in range(max(a.warmup, 1)):
+        frame()
+    torch.cuda.synchronize()
+    st = ctx.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} after warm-up")
+    n0 = ctx.launches
+    frame()
+    torch.cuda.synchronize()
+    launches_per_frame = ctx.launches - n0
+    C = int(bufs.count[0])
+    T_vis = int(np.unpackbits(bufs.vt.cpu().numpy().view(np.uint8)).sum())
+
+    # one frame captured as a CUDA graph (the library is allocation- and sync-free)
+    F.fa_profile_enable(ctx.handle, True)
+    frame()
+    torch.cuda.synchronize()
+    graph = None
+    if not a.no_graph:
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            frame()
+        for _ in range(a.warmup):
+            graph.replay()
+        torch.cuda.synchronize()
+    run = graph.replay if graph is not None else frame
+
+    clocks = Clocks(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    per_kernel = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    time.sleep(0.3)
+    for i in range(a.steps):
+        flush.fill_(i)
+        ev[i][0].record(stream)
+        run()
+        ev[i][1].record(stream)
+        for name, ms in F.fa_profile_read(ctx.handle):
+            per_kernel.setdefault(name, []).append(ms)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        dist.barrier()
+    step_ms = [s.elapsed_time(e) for s, e in ev]
+    total_ms = float(sum(step_ms))
+    if world > 1:
+        t = torch.tensor([total_ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    st = ctx.device_status()
+    if st != 0:
+        raise RuntimeError(f"device status {st} in the timed region")
+    F.fa_profile_enable(ctx.handle, False)
+
+    # end to end through the C ABI with host buffers: H2D positions + matrix from
+    # pinned memory, the frame, D2H of the pack result and the placements
+    e2e = None
+    if not a.no_e2e:
+        h_pos = torch.as_tensor(sc.pos).pin_memory()
+        h_res = torch.empty(5, dtype=torch.int32).pin_memory()
+        h_place = torch.empty(max(C, 1), 4, dtype=torch.int32).pin_memory()
+        h2d = h_pos.numel() * 4 + 64
+        d2h = h_res.numel() * 4 + h_place.numel() * 4
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        for _ in range(2):
+            mesh.pos.copy_(h_pos, non_blocking=True)
+            frame()
+            h_res.copy_(bufs.result, non_blocking=True)
+            h_place.copy_(bufs.place[:max(C, 1)], non_blocking=True)
+        torch.cuda.synchronize()
+        e_ms = 0.0
+        for i in range(a.steps):
+            flush.fill_(i)
+            e0.record(stream)
+            mesh.pos.copy_(h_pos, non_blocking=True)
+            frame()  # the view matrix travels as a kernel argument (64 B)
+            h_res.copy_(bufs.result, non_blocking=True)
+            h_place.copy_(bufs.place[:max(C, 1)], non_blocking=True)
+            e1.record(stream)
+            e1.synchronize()
+            e_ms += e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([e_ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e_ms = float(t.item())
+        e2e = {"value": world * a.steps / (e_ms / 1e3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
+
+    if rank != 0:
+        if world > 1:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
+    # roofline of the dominant kernel (largest share of the traced frame time)
+    tot = {k: float(np.sum(v)) for k, v in per_kernel.items()}
+    frame_ms = sum(tot.values())
+    dom = max(tot, key=tot.get) if tot else None
+    peak, peak_kind = peaks()
+    roof = None
+    if dom:
+        avg_ms = tot[dom] / len(per_kernel[dom])
+        ab = algorithmic_bytes(dom, sc.T, sc.V, W, H, T_vis, C)
+        traffic = None
+        try:
+            with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+                traffic = json.load(f).get(dom)
+        except Exception:
+            pass
+        if ab is not None:
+            ach = ab / (avg_ms * 1e-3) / 1e9
+            roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                    "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
+                    "algorithmic_bytes": ab, "avg_launch_ms": avg_ms,
+                    "share": tot[dom] / frame_ms if frame_ms else None}
+    value = world * a.steps / (total_ms / 1e3)
+    line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": workload_name(a), "triangles": sc.T, "vertices": sc.V,
+                       "visible_triangles": T_vis, "charts": C, "cuda_graph": graph is not None,
+                       "l2": "flushed between steps (256 MiB write), outside the step events",
+                       "parallelism": f"replicas x{world}"},
+            "gpu_launches": launches_per_frame * a.steps,
+            "kernels_ms_per_frame": {k: tot[k] / len(per_kernel[k]) for k in sorted(tot, key=tot.get, reverse=True)},
+            "roofline": roof, "e2e": e2e, "clocks": clk}
+    if world == 1 and not a.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(a, sc, M, p)
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)
+
+
+if __name__ == "__main__":
+    main()

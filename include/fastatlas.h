@@ -1,0 +1,270 @@
+/*
+ * fastatlas.h - C ABI of the GB300 (sm_103a) per-frame atlasing path of
+ * FastAtlas (Vining et al., "FastAtlas: Real-Time Compact Atlases for Texture
+ * Space Shading", EG 2025).
+ *
+ * One frame: find the visible triangles (Sec. 5.1, App. A), group them into
+ * charts (connected components, Sec. 5.1, Alg. 1), give each chart a
+ * conservative projected box and quantized footprint (Sec. 5.2, Sec. 4.1), pack
+ * the footprints into an omega x omega atlas by the 64-scale prefix-sum fold /
+ * push search (Sec. 4.2, 4.3), and map every visible corner into its chart's
+ * atlas box (Sec. 3, App. A "Shading and Rasterization").
+ *
+ * Conventions shared by every call:
+ *  - Pointers named d_* are DEVICE pointers owned by the caller; host pointers
+ *    are read before the call returns.  The library never frees caller memory.
+ *  - Scratch memory is owned by the context and allocated once in fa_create
+ *    for the configured maxima; no per-frame call allocates, synchronizes or
+ *    copies to the host, so the calls may be captured in a CUDA graph.
+ *  - Every call is asynchronous and stream ordered on `stream` (a cudaStream_t;
+ *    NULL is the legacy default stream).  Argument errors the host can see are
+ *    returned immediately and nothing is launched.  Errors found on the device
+ *    (too many charts, no fitting scale, an iteration cap hit) are written to the
+ *    context's sticky device status word and, for packing, to
+ *    fa_pack_result.status; later kernels of the same context see the word and
+ *    skip their work.  fa_last_device_status reads and clears it.
+ *  - A context is not thread safe: use one context per stream / session.
+ *  - Matrices are row major float[16]; clip = M . [x, y, z, 1].  OpenGL
+ *    conventions: the near plane is z_clip = -w_clip, screen y points up, front
+ *    faces are counter-clockwise on screen.
+ */
+#ifndef FASTATLAS_H_
+#define FASTATLAS_H_
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st* fa_stream_t; /* same type as cudaStream_t */
+
+typedef enum {
+  FA_OK = 0,
+  FA_E_INVALID_ARG = 1,   /* bad pointer, size or parameter; nothing launched   */
+  FA_E_OUT_OF_MEMORY = 2, /* fa_create / fa_mesh_register could not allocate      */
+  FA_E_CAPACITY = 3,      /* a configured maximum was exceeded (charts, frontline) */
+  FA_E_PACK_FAILED = 4,   /* no candidate scale fits the atlas (Sec. 4.2)          */
+  FA_E_TIMEOUT = 5,       /* a device loop hit its iteration cap                   */
+  FA_E_CUDA = 6           /* a CUDA runtime call failed                           */
+} fa_status;
+
+typedef enum {
+  FA_CHARTS_EDGE = 0,   /* components under shared edges (Sec. 5.1)                  */
+  FA_CHARTS_VERTEX = 1  /* components under shared vertices: the vertex merge that
+                           gives every vertex one chart (App. A, Alg. 1)              */
+} fa_chart_mode;
+
+typedef enum {
+  FA_SELECT_EFFECTIVE = 0, /* largest effective scale (k/n) * omega / Omega        */
+  FA_SELECT_LARGEST_K = 1  /* largest fitting candidate k (Sec. 4.2 literal)         */
+} fa_select_mode;
+
+/* Context maxima.  Scratch is sized from these once, in fa_create. */
+typedef struct {
+  uint32_t max_tris;       /* triangles of the largest registered mesh              */
+  uint32_t max_verts;      /* vertices of the largest registered mesh               */
+  uint32_t max_charts;     /* charts per frame (paper: "user-defined maximal number
+                              of charts", data structures table); at most 1<<22     */
+  uint32_t max_width;      /* largest viewport, pixels (<= 16384)                   */
+  uint32_t max_height;
+  uint32_t max_atlas_log2; /* largest atlas side omega = 2^log2 (<= 14)             */
+  uint32_t min_box;        /* smallest packed box side in texels (paper: 2)        */
+  uint32_t gutter;         /* texels added on every side of a packed box (0)       */
+  int32_t device;          /* CUDA device ordinal                                   */
+} fa_config;
+
+typedef struct fa_ctx fa_ctx;
+typedef struct fa_mesh fa_mesh;
+
+/* Per-chart arrays (structure of arrays, caller-owned device memory, each with
+ * room for fa_config.max_charts entries). */
+typedef struct {
+  uint32_t* root;  /* smallest triangle id of the chart; charts numbered by root   */
+  float* bbox;     /* [C][4] xmin, ymin, xmax, ymax of the conservative NDC box    */
+  uint32_t* fa;    /* [C] footprint width in 1/256 texel after rotation (fa <= fb) */
+  uint32_t* fb;    /* [C] footprint height in 1/256 texel                          */
+  uint8_t* rot;    /* [C] 1 if the box was rotated by 90 degrees to stand tall     */
+  uint32_t* count; /* [1] number of charts C of the frame                          */
+} fa_charts;
+
+/* Placement of one chart in the chosen candidate's virtual Omega x Omega grid; the
+ * real atlas rectangle is alpha * [x, x + w) x alpha * [y, y + h), alpha = omega /
+ * Omega, and the chart's content starts gutter texels inside it. */
+typedef struct {
+  int32_t x, y, w, h;
+} fa_placement;
+
+typedef struct {
+  uint32_t k;      /* chosen scale numerator: scale = k / n_scales                 */
+  uint32_t omega;  /* virtual side Omega = omega + m of the chosen candidate       */
+  uint32_t height; /* stacked height H <= Omega                                    */
+  int32_t status;  /* fa_status of the packing                                     */
+  uint32_t count;  /* number of boxes packed                                       */
+} fa_pack_result;
+
+typedef struct {
+  float view_proj[16];  /* row major, clip = M . [p, 1]                            */
+  uint32_t width;       /* viewport, pixels                                        */
+  uint32_t height;
+  float ratio;          /* texel-to-pixel ratio r (linear, per axis; 0 < r <= 64) */
+  uint32_t atlas_log2;  /* omega = 2^atlas_log2                                    */
+  uint32_t chart_mode;  /* fa_chart_mode                                           */
+  uint32_t n_scales;    /* candidate scales k / n, k = 1..n; n in {1,2,4,...,64}   */
+  uint32_t select_mode; /* fa_select_mode                                          */
+} fa_frame_params;
+
+/* All outputs of fa_atlas_frame (caller-owned device memory). */
+typedef struct {
+  uint32_t* vt;           /* [ceil(T/32)] visible-triangle bits                     */
+  int32_t* tri_chart;     /* [T] chart of each triangle, -1 if not visible          */
+  int32_t* vert_chart;    /* [V] chart of each vertex (vertex mode), -1 if none; may
+                             be NULL                                                */
+  fa_charts charts;       /* per-chart arrays                                       */
+  uint32_t* order;        /* [max_charts] packing order; may be NULL                */
+  fa_placement* place;    /* [max_charts] placements, chart order                   */
+  fa_pack_result* result; /* [1]                                                    */
+  float* uv;              /* [T][3][2] atlas texel coordinates per visible corner;
+                             NaN where w <= 0; untouched for invisible triangles; may
+                             be NULL                                                */
+  float* affine;          /* [max_charts][6] (a11, a12, b1, a21, a22, b2):
+                             uv = A . ndc + b, i.e. uv * w = A . (x, y) + b * w;
+                             may be NULL                                            */
+} fa_frame_out;
+
+/* Library version (major * 10000 + minor * 100 + patch). */
+uint32_t fa_version(void);
+
+/* Human readable name of a status code (static storage). */
+const char* fa_status_string(fa_status s);
+
+/* Create a context on cfg->device and allocate its scratch for the maxima in cfg
+ * (once; the paper likewise allocates its scratch "at the start of program
+ * execution", Sec. 4.1).  *out is set to NULL on failure.
+ * Errors: FA_E_INVALID_ARG (NULL pointers, zero or too large maxima),
+ * FA_E_OUT_OF_MEMORY, FA_E_CUDA. */
+fa_status fa_create(fa_ctx** out, const fa_config* cfg);
+
+/* Free the context and its scratch.  Waits for the device.  NULL is ignored. */
+void fa_destroy(fa_ctx* ctx);
+
+/* Register a triangle mesh: d_pos float[V][3] positions, d_idx uint32[T][3]
+ * CCW index triples (both caller-owned, kept by pointer: positions may be
+ * rewritten between frames, the topology may not).  Builds the triangle
+ * adjacency that Alg. 1 walks (the half-edge twins of the data-structures
+ * table) once on the device: two triangles are adjacent when they share an
+ * undirected edge {a, b}, a != b, of the index buffer; an edge with three or more
+ * triangles (non-manifold) joins all of them.  This call allocates the mesh's own
+ * device buffers and synchronizes `stream`; it is set-up, not per-frame work.
+ * Errors: FA_E_INVALID_ARG (T > max_tris, V > max_verts, an index >= V is
+ * reported as FA_E_INVALID_ARG after the synchronizing check), FA_E_OUT_OF_MEMORY,
+ * FA_E_CUDA. */
+fa_status fa_mesh_register(fa_ctx* ctx, const float* d_pos, uint32_t V, const uint32_t* d_idx,
+                           uint32_t T, fa_mesh** out, fa_stream_t stream);
+
+/* Free a mesh's device buffers (waits for the device).  NULL is ignored. */
+void fa_mesh_release(fa_mesh* mesh);
+
+/* Visible triangles (Sec. 5.1; App. A "Detecting Visible Triangles"): a depth
+ * pre-pass over the width x height viewport, then a marking pass in which a
+ * triangle is visible iff one of its samples passes the "less than or equal"
+ * depth test.  Samples are pixel centres; coverage uses the top-left rule on
+ * vertices snapped to 1/256 pixel after clipping against the near plane and a
+ * guard band |x|, |y| <= 64 w; back faces and zero-area triangles are culled.
+ * d_vt: uint32[ceil(T/32)], bit t%32 of word t/32 (fully overwritten).
+ * Errors: FA_E_INVALID_ARG (viewport above the context maximum, NULL pointers). */
+fa_status fa_visibility(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16],
+                        uint32_t width, uint32_t height, uint32_t* d_vt, fa_stream_t stream);
+
+/* Charts (Sec. 5.1; App. A "GPU Union Find", Alg. 1): connected components of
+ * the visible triangles under shared edges (FA_CHARTS_EDGE) or shared vertices
+ * (FA_CHARTS_VERTEX).  A chart's root is its smallest triangle id, and charts are
+ * numbered by ascending root.  Writes d_tri_chart int32[T] (-1 = invisible),
+ * charts->root and charts->count; d_vert_chart int32[V] (may be NULL) gets each
+ * vertex's chart in vertex mode and -1 otherwise.  More than max_charts charts
+ * sets FA_E_CAPACITY in the device status word (outputs then undefined).
+ * Errors: FA_E_INVALID_ARG. */
+fa_status fa_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* d_vt, uint32_t mode,
+                      int32_t* d_tri_chart, int32_t* d_vert_chart, const fa_charts* charts,
+                      fa_stream_t stream);
+
+/* Chart boxes and footprints (Sec. 5.2, Sec. 4.1): each visible triangle is
+ * clipped against the near plane when it crosses it, each remaining vertex is
+ * clamped to [-w, w] and divided (Blinn's estimator), and the chart box is the
+ * min / max over its triangles (a vertex with w <= 0 left after the near clip
+ * makes the box [-1,1]^2).  The box's viewport size is scaled by `ratio`,
+ * quantized up to 1/256 texel, and rotated to stand tall (fa <= fb, rot = 1 when
+ * the width exceeded the height).  Reads charts->count; writes bbox, fa, fb, rot.
+ * Errors: FA_E_INVALID_ARG. */
+fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16],
+                          uint32_t width, uint32_t height, float ratio,
+                          const int32_t* d_tri_chart, const fa_charts* charts, fa_stream_t stream);
+
+/* Packing (Sec. 4.1-4.3).  Inputs: d_count[0] boxes with footprints d_fa, d_fb in
+ * 1/256 texel (the box index is the tie-break of the order, so pass boxes by
+ * ascending root for the paper's order).  Order: integer height ceil(fb/256)
+ * (clamped to [1, 8192]) descending, index ascending.  Candidates k = 1..n_scales
+ * (n_scales a power of two <= 64): box w = max(min_box, ceil(k fa / (256 n))) +
+ * 2 gutter (same for h from fb); the exclusive prefix sum P of the widths gives
+ * row = P >> atlas_log2 and offset P & (omega - 1); m = the largest overflow past
+ * omega, Omega = omega + m; rows with row % 3 == 0 run left to right, the others
+ * right to left mirrored in Omega; rows are then pushed up against the frontline.
+ * A candidate fits iff its height H <= Omega.  The selected candidate is written
+ * to *d_res and its placements (chart order) to d_place; d_order (may be NULL)
+ * receives the packing order.  No fitting candidate: d_res->status =
+ * FA_E_PACK_FAILED.  A candidate with Omega above the frontline capacity
+ * min(8 omega, 40960) sets FA_E_CAPACITY.
+ * Errors: FA_E_INVALID_ARG (atlas_log2 out of range, n_scales not a power of two
+ * in [1, 64], select_mode unknown, NULL pointers). */
+fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const uint32_t* d_count,
+                  uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* d_order,
+                  fa_placement* d_place, fa_pack_result* d_res, fa_stream_t stream);
+
+/* Parameterization (Sec. 3; App. A "Shading and Rasterization"): every visible
+ * corner with w > 0 maps to alpha * ((x + gutter, y + gutter) + s * local) in atlas
+ * texels, alpha = omega / Omega, s = ratio * k / n_scales, local = the corner's
+ * viewport position relative to the chart box, rotated by +90 degrees for rotated
+ * charts (local = (py, Wpx - px)).  Computed from the fp32 clip coordinates with
+ * compensated fp32 arithmetic; within 1e-4 texel (plus half an fp32 ulp of the
+ * result above 2048) of the exact value.  d_uv float[T][3][2] (NaN for w <= 0,
+ * untouched for invisible triangles), d_affine float[C][6] (may be NULL).
+ * Skipped when d_res->status != FA_OK.  Errors: FA_E_INVALID_ARG. */
+fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
+                uint32_t height, float ratio, const int32_t* d_tri_chart, const fa_charts* charts,
+                const fa_placement* d_place, const fa_pack_result* d_res, uint32_t atlas_log2,
+                uint32_t n_scales, float* d_uv, float* d_affine, fa_stream_t stream);
+
+/* The whole per-frame path: fa_visibility, fa_chartify, fa_parameterize,
+ * fa_pack and fa_uv in one stream-ordered launch sequence (device status word
+ * cleared first).  Errors: FA_E_INVALID_ARG (as for the steps). */
+fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* params,
+                         const fa_frame_out* out, fa_stream_t stream);
+
+/* Synchronize `stream`, read the context's sticky device status word into *out
+ * and clear it.  Returns FA_E_CUDA if the stream reported a CUDA error. */
+fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out);
+
+/* Number of kernels the library launched on this context since creation (a
+ * host-side counter; used to report launches per frame). */
+uint64_t fa_launch_count(const fa_ctx* ctx);
+
+/* Per-kernel tracing (the paper times its stages per frame, App. B "Timing
+ * Methodology"; here every kernel of a public call gets a slot).  When enabled,
+ * each public call records a CUDA event on `stream` before each of its kernels
+ * and one after the last, so slot i spans kernel i (and any launch gap before
+ * kernel i + 1).  Recording works inside CUDA-graph capture: a replay then
+ * re-records the same events.  fa_profile_enable(ctx, 1) creates the events (call
+ * it outside any capture); 0 destroys them.  Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_profile_enable(fa_ctx* ctx, int enable);
+
+/* Wait for the last traced call to finish and return up to max_n slot durations
+ * in milliseconds (ms[i]) with the kernel names (names[i], static strings); *n_out
+ * receives the number of slots of that call (0 when tracing is off).
+ * Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_profile_read(fa_ctx* ctx, int max_n, float* ms, const char** names, int* n_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FASTATLAS_H_ */

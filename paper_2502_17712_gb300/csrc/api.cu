@@ -1,0 +1,380 @@
+// C ABI of libfastatlas: argument checks, context / mesh lifetime and the
+// stream-ordered launch sequences.  All compute happens in the kernels of the
+// other translation units.
+#include <cstdlib>
+#include <cstring>
+
+#include "fa_internal.cuh"
+
+using namespace fa;
+
+namespace {
+
+bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
+
+Mat4 to_mat(const float* m) {
+  Mat4 M;
+  std::memcpy(M.m, m, sizeof(M.m));
+  return M;
+}
+
+template <class T>
+fa_status alloc(T** p, size_t n) {
+  *p = nullptr;
+  if (n == 0) n = 1;
+  if (cudaMalloc((void**)p, n * sizeof(T)) != cudaSuccess) {
+    cudaGetLastError();
+    return FA_E_OUT_OF_MEMORY;
+  }
+  return FA_OK;
+}
+
+fa_status check_view(const fa_ctx* ctx, const float* M, uint32_t W, uint32_t H) {
+  if (!M || W == 0 || H == 0 || W > ctx->cfg.max_width || H > ctx->cfg.max_height) return FA_E_INVALID_ARG;
+  return FA_OK;
+}
+
+fa_status check_charts(const fa_charts* ch) {
+  if (!ch || !ch->root || !ch->bbox || !ch->fa || !ch->fb || !ch->rot || !ch->count) return FA_E_INVALID_ARG;
+  return FA_OK;
+}
+
+fa_status check_pack(const fa_ctx* ctx, uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode) {
+  if (atlas_log2 < 1 || atlas_log2 > ctx->cfg.max_atlas_log2) return FA_E_INVALID_ARG;
+  if (!is_pow2(n_scales) || n_scales > (uint32_t)kMaxScales) return FA_E_INVALID_ARG;
+  if (select_mode > FA_SELECT_LARGEST_K) return FA_E_INVALID_ARG;
+  return FA_OK;
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+uint32_t fa_version(void) { return 10000u; }
+
+const char* fa_status_string(fa_status s) {
+  switch (s) {
+    case FA_OK: return "FA_OK";
+    case FA_E_INVALID_ARG: return "FA_E_INVALID_ARG";
+    case FA_E_OUT_OF_MEMORY: return "FA_E_OUT_OF_MEMORY";
+    case FA_E_CAPACITY: return "FA_E_CAPACITY";
+    case FA_E_PACK_FAILED: return "FA_E_PACK_FAILED";
+    case FA_E_TIMEOUT: return "FA_E_TIMEOUT";
+    case FA_E_CUDA: return "FA_E_CUDA";
+  }
+  return "FA_E_UNKNOWN";
+}
+
+void fa_destroy(fa_ctx* ctx) {
+  if (!ctx) return;
+  DeviceGuard g(ctx->device);
+  cudaDeviceSynchronize();
+  if (ctx->prof_on)
+    for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->label, ctx->cid, ctx->blockcnt,
+                  ctx->box_enc, ctx->box_full, ctx->ord_counts, ctx->ord_rank, ctx->ord_binstart,
+                  ctx->order, ctx->cand_P, ctx->cand_wh, ctx->cand_xy, ctx->cand_rows, ctx->cand,
+                  ctx->res, ctx->place};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  std::free(ctx);
+}
+
+fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
+  if (!out) return FA_E_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg) return FA_E_INVALID_ARG;
+  const fa_config& c = *cfg;
+  if (c.max_tris == 0 || c.max_verts == 0 || c.max_charts == 0 || c.max_width == 0 || c.max_height == 0)
+    return FA_E_INVALID_ARG;
+  if (c.max_width > 16384 || c.max_height > 16384 || c.max_atlas_log2 < 1 || c.max_atlas_log2 > 14)
+    return FA_E_INVALID_ARG;
+  if (c.max_charts > (1u << 22) || (uint64_t)c.max_tris + c.max_verts > 0x7FFFFFFFull) return FA_E_INVALID_ARG;
+  if (c.min_box < 1 || c.min_box > 4096 || c.gutter > 4096) return FA_E_INVALID_ARG;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess) {
+    cudaGetLastError();
+    return FA_E_CUDA;
+  }
+  if (c.device < 0 || c.device >= ndev) return FA_E_INVALID_ARG;
+  DeviceGuard g(c.device);
+  fa_ctx* ctx = (fa_ctx*)std::calloc(1, sizeof(fa_ctx));
+  if (!ctx) return FA_E_OUT_OF_MEMORY;
+  ctx->cfg = c;
+  ctx->device = c.device;
+  fa_status st = FA_OK;
+  const uint64_t T = c.max_tris, V = c.max_verts, C = c.max_charts;
+  ctx->queue_cap = (uint32_t)(T < (1u << 20) ? T + 1024 : (1u << 20));
+  ctx->max_order_tiles = (uint32_t)((C + kOrderTile - 1) / kOrderTile);
+  const uint64_t nblocks = (T + 1023) / 1024 + 1;
+#define FA_ALLOC(ptr, n) \
+  if (st == FA_OK) st = alloc(&ptr, (size_t)(n));
+  FA_ALLOC(ctx->ctr, 1);
+  FA_ALLOC(ctx->zbuf, (uint64_t)c.max_width * c.max_height);
+  FA_ALLOC(ctx->bigbits, (T + 31) / 32);
+  FA_ALLOC(ctx->queue, ctx->queue_cap);
+  FA_ALLOC(ctx->label, T + V);
+  FA_ALLOC(ctx->cid, T);
+  FA_ALLOC(ctx->blockcnt, nblocks + 1);
+  FA_ALLOC(ctx->box_enc, 4 * C);
+  FA_ALLOC(ctx->box_full, C);
+  FA_ALLOC(ctx->ord_counts, (uint64_t)kMaxH * ctx->max_order_tiles);
+  FA_ALLOC(ctx->ord_rank, C);
+  FA_ALLOC(ctx->ord_binstart, kMaxH);
+  FA_ALLOC(ctx->order, C);
+  FA_ALLOC(ctx->cand_P, (uint64_t)kMaxScales * C);
+  FA_ALLOC(ctx->cand_wh, (uint64_t)kMaxScales * C);
+  FA_ALLOC(ctx->cand_xy, (uint64_t)kMaxScales * C);
+  FA_ALLOC(ctx->cand_rows, (uint64_t)kMaxScales * C);
+  FA_ALLOC(ctx->cand, kMaxScales);
+  FA_ALLOC(ctx->res, 1);
+  FA_ALLOC(ctx->place, C);
+#undef FA_ALLOC
+  if (st == FA_OK && cudaMemset(ctx->ctr, 0, sizeof(DevCounters)) != cudaSuccess) st = FA_E_CUDA;
+  if (st == FA_OK && cudaDeviceSynchronize() != cudaSuccess) st = FA_E_CUDA;
+  if (st != FA_OK) {
+    fa_destroy(ctx);
+    return st;
+  }
+  *out = ctx;
+  return FA_OK;
+}
+
+fa_status fa_mesh_register(fa_ctx* ctx, const float* d_pos, uint32_t V, const uint32_t* d_idx, uint32_t T,
+                           fa_mesh** out, fa_stream_t stream) {
+  if (!out) return FA_E_INVALID_ARG;
+  *out = nullptr;
+  if (!ctx || !d_pos || !d_idx || V == 0 || T == 0) return FA_E_INVALID_ARG;
+  if (T > ctx->cfg.max_tris || V > ctx->cfg.max_verts) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  fa_mesh* m = (fa_mesh*)std::calloc(1, sizeof(fa_mesh));
+  if (!m) return FA_E_OUT_OF_MEMORY;
+  m->ctx = ctx;
+  m->pos = d_pos;
+  m->idx = d_idx;
+  m->V = V;
+  m->T = T;
+  fa_status st = build_adjacency(ctx, m, (cudaStream_t)stream);
+  if (st != FA_OK) {
+    std::free(m);
+    return st;
+  }
+  *out = m;
+  return FA_OK;
+}
+
+void fa_mesh_release(fa_mesh* m) {
+  if (!m) return;
+  DeviceGuard g(m->ctx->device);
+  cudaDeviceSynchronize();
+  if (m->adj) cudaFree(m->adj);
+  if (m->nm_off) cudaFree(m->nm_off);
+  if (m->nm_list) cudaFree(m->nm_list);
+  std::free(m);
+}
+
+fa_status fa_visibility(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
+                        uint32_t height, uint32_t* d_vt, fa_stream_t stream) {
+  if (!ctx || !mesh || !d_vt || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  fa_status st = check_view(ctx, view_proj, width, height);
+  if (st != FA_OK) return st;
+  DeviceGuard g(ctx->device);
+  trace_begin(ctx);
+  st = launch_visibility(ctx, mesh, to_mat(view_proj), width, height, d_vt, (cudaStream_t)stream);
+  trace_end(ctx, (cudaStream_t)stream);
+  return st;
+}
+
+fa_status fa_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* d_vt, uint32_t mode,
+                      int32_t* d_tri_chart, int32_t* d_vert_chart, const fa_charts* charts,
+                      fa_stream_t stream) {
+  if (!ctx || !mesh || !d_vt || !d_tri_chart || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  if (mode > FA_CHARTS_VERTEX) return FA_E_INVALID_ARG;
+  if (!charts || !charts->root || !charts->count) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  trace_begin(ctx);
+  fa_status st = launch_chartify(ctx, mesh, d_vt, mode, d_tri_chart, d_vert_chart, charts, (cudaStream_t)stream);
+  trace_end(ctx, (cudaStream_t)stream);
+  return st;
+}
+
+// The box and UV kernels walk the VT words; the standalone calls derive them from
+// tri_chart so that they need no extra argument.
+namespace {
+__global__ void k_vt_from_chart(const int32_t* tri_chart, uint32_t T, uint32_t* vt) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (T + 31) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
+       w += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t t = (w << 5) + lane;
+    const bool v = t < T && tri_chart[t] >= 0;
+    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, v);
+    if (lane == 0) vt[w] = bits;
+  }
+}
+}  // namespace
+
+fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
+                          uint32_t height, float ratio, const int32_t* d_tri_chart, const fa_charts* charts,
+                          fa_stream_t stream) {
+  if (!ctx || !mesh || !d_tri_chart || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  fa_status st = check_view(ctx, view_proj, width, height);
+  if (st == FA_OK) st = check_charts(charts);
+  if (st != FA_OK) return st;
+  if (!(ratio > 0.0f && ratio <= 64.0f)) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* vt = ctx->bigbits;  // reuse: the raster's queue bits are dead after visibility
+  trace_begin(ctx);
+  mark(ctx, "k_vt_from_chart", s);
+  k_vt_from_chart<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s>>>(d_tri_chart,
+                                                                                              mesh->T, vt);
+  st = launch_parameterize(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, vt, charts, true, s);
+  trace_end(ctx, s);
+  return st;
+}
+
+fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const uint32_t* d_count,
+                  uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* d_order,
+                  fa_placement* d_place, fa_pack_result* d_res, fa_stream_t stream) {
+  if (!ctx || !d_fa || !d_fb || !d_count || !d_place || !d_res) return FA_E_INVALID_ARG;
+  fa_status st = check_pack(ctx, atlas_log2, n_scales, select_mode);
+  if (st != FA_OK) return st;
+  DeviceGuard g(ctx->device);
+  trace_begin(ctx);
+  st = launch_pack(ctx, d_fa, d_fb, d_count, atlas_log2, n_scales, select_mode, d_order, d_place, d_res,
+                   (cudaStream_t)stream);
+  trace_end(ctx, (cudaStream_t)stream);
+  return st;
+}
+
+fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width, uint32_t height,
+                float ratio, const int32_t* d_tri_chart, const fa_charts* charts, const fa_placement* d_place,
+                const fa_pack_result* d_res, uint32_t atlas_log2, uint32_t n_scales, float* d_uv,
+                float* d_affine, fa_stream_t stream) {
+  if (!ctx || !mesh || !d_tri_chart || !d_place || !d_res || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  if (!d_uv && !d_affine) return FA_E_INVALID_ARG;
+  fa_status st = check_view(ctx, view_proj, width, height);
+  if (st == FA_OK) st = check_charts(charts);
+  if (st == FA_OK) st = check_pack(ctx, atlas_log2, n_scales, 0);
+  if (st != FA_OK) return st;
+  if (!(ratio > 0.0f && ratio <= 64.0f)) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  uint32_t* vt = ctx->bigbits;
+  trace_begin(ctx);
+  mark(ctx, "k_vt_from_chart", s);
+  k_vt_from_chart<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s>>>(d_tri_chart,
+                                                                                              mesh->T, vt);
+  st = launch_uv(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, vt, charts, d_place, d_res,
+                 atlas_log2, n_scales, d_uv, d_affine, s);
+  trace_end(ctx, s);
+  return st;
+}
+
+namespace {
+__global__ void k_reset_status(DevCounters* ctr) { ctr->status = 0; }
+}  // namespace
+
+fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const fa_frame_out* o,
+                         fa_stream_t stream) {
+  if (!ctx || !mesh || !p || !o || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  if (!o->vt || !o->tri_chart || !o->place || !o->result) return FA_E_INVALID_ARG;
+  fa_status st = check_view(ctx, p->view_proj, p->width, p->height);
+  if (st == FA_OK) st = check_charts(&o->charts);
+  if (st == FA_OK) st = check_pack(ctx, p->atlas_log2, p->n_scales, p->select_mode);
+  if (st != FA_OK) return st;
+  if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  const Mat4 M = to_mat(p->view_proj);
+  trace_begin(ctx);
+  mark(ctx, "k_reset_status", s);
+  k_reset_status<<<1, 1, 0, s>>>(ctx->ctr);
+  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, s)) != FA_OK) return st;
+  if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
+    return st;
+  // k_number of chartify already reset the chart-box accumulators
+  if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, o->vt, &o->charts,
+                                false, s)) != FA_OK)
+    return st;
+  if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
+                        p->select_mode, o->order, o->place, o->result, s)) != FA_OK)
+    return st;
+  if (o->uv || o->affine) {
+    if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, o->vt, &o->charts, o->place,
+                        o->result, p->atlas_log2, p->n_scales, o->uv, o->affine, s)) != FA_OK)
+      return st;
+  }
+  trace_end(ctx, s);
+  return FA_OK;
+}
+
+fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {
+  if (!ctx || !out) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  cudaStream_t s = (cudaStream_t)stream;
+  int32_t v = 0;
+  if (cudaMemcpyAsync(&v, &ctx->ctr->status, sizeof(v), cudaMemcpyDeviceToHost, s) != cudaSuccess)
+    return FA_E_CUDA;
+  if (cudaStreamSynchronize(s) != cudaSuccess) return FA_E_CUDA;
+  if (v != 0) {
+    if (cudaMemsetAsync(&ctx->ctr->status, 0, sizeof(int32_t), s) != cudaSuccess) return FA_E_CUDA;
+    if (cudaStreamSynchronize(s) != cudaSuccess) return FA_E_CUDA;
+  }
+  *out = v;
+  return FA_OK;
+}
+
+uint64_t fa_launch_count(const fa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fa_status fa_profile_enable(fa_ctx* ctx, int enable) {
+  if (!ctx) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  if (enable && !ctx->prof_on) {
+    for (int i = 0; i <= kMaxProf; ++i) {
+      if (cudaEventCreate(&ctx->prof_ev[i]) != cudaSuccess) {
+        for (int j = 0; j < i; ++j) cudaEventDestroy(ctx->prof_ev[j]);
+        return FA_E_CUDA;
+      }
+    }
+    ctx->prof_on = 1;
+    ctx->prof_n = 0;
+  } else if (!enable && ctx->prof_on) {
+    cudaDeviceSynchronize();
+    for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
+    ctx->prof_on = 0;
+    ctx->prof_n = 0;
+  }
+  return FA_OK;
+}
+
+fa_status fa_profile_read(fa_ctx* ctx, int max_n, float* ms, const char** names, int* n_out) {
+  if (!ctx || !n_out || max_n < 0 || (max_n > 0 && (!ms || !names))) return FA_E_INVALID_ARG;
+  *n_out = 0;
+  if (!ctx->prof_on || ctx->prof_n == 0) return FA_OK;
+  DeviceGuard g(ctx->device);
+  if (cudaEventSynchronize(ctx->prof_ev[ctx->prof_n]) != cudaSuccess) return FA_E_CUDA;
+  const int n = ctx->prof_n < max_n ? ctx->prof_n : max_n;
+  for (int i = 0; i < n; ++i) {
+    float t = 0.0f;
+    if (cudaEventElapsedTime(&t, ctx->prof_ev[i], ctx->prof_ev[i + 1]) != cudaSuccess) return FA_E_CUDA;
+    ms[i] = t;
+    names[i] = ctx->prof_name[i];
+  }
+  *n_out = ctx->prof_n;
+  return FA_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,307 @@
+// Charts: connected components of the visible triangles (Sec. 5.1) by union-find
+// with pointer hooking in the style of ECL-CC (App. A "GPU Union Find", Alg. 1):
+// initialise each visible triangle to the smallest visible neighbour, hook roots
+// with atomicCAS so the larger root always points to the smaller one, then flatten.
+// The root of a component is therefore its smallest triangle id.  Charts are
+// numbered by ascending root with a block-count scan.
+//
+// Edge mode joins triangles across shared edges (the adjacency built at mesh
+// registration, plus the incidence lists of non-manifold edges).  Vertex mode
+// (the vertex merge of App. A) joins each visible triangle with its three vertices:
+// vertices are extra nodes T + v, so every component's smallest node is a triangle.
+//
+// Visible triangles are found from the VT words: a warp owns 32 consecutive
+// triangles and skips the whole word when it is zero.
+#include "fa_internal.cuh"
+
+namespace fa {
+namespace {
+
+constexpr int kBlock = 256;
+constexpr int kPerBlock = 1024;  // triangles per counting block (4 per thread)
+
+// Representative with path halving (labels only decrease; parents are smaller).
+__device__ __forceinline__ int32_t find_rep(volatile int32_t* label, int32_t x) {
+  int32_t cur = label[x];
+  if (cur != x) {
+    int32_t prev = x, next;
+    while (cur > (next = label[cur])) {
+      label[prev] = next;
+      prev = cur;
+      cur = next;
+    }
+  }
+  return cur;
+}
+
+// Hook the components of a and b: the larger root is CASed onto the smaller.
+__device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevCounters* ctr) {
+  volatile int32_t* vl = label;
+  int32_t ra = find_rep(vl, a), rb = find_rep(vl, b);
+  uint32_t guard = 0;
+  while (ra != rb) {
+    if (++guard > kLoopCap) {
+      set_status(ctr, FA_E_TIMEOUT);
+      return;
+    }
+    int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+    int32_t old = atomicCAS(label + hi, hi, lo);
+    if (old == hi) return;
+    // hi stopped being a root; retry from the current representatives
+    ra = find_rep(vl, old);
+    rb = find_rep(vl, lo);
+  }
+}
+
+struct UfArgs {
+  const uint32_t* vt;
+  const uint32_t* idx;
+  const int32_t* adj;
+  uint32_t T, V;
+  int32_t* label;
+  DevCounters* ctr;
+};
+
+// Edge mode init: label[t] = min(t, visible edge neighbours)  (Alg. 1, first loop).
+// Vertex mode init: label[t] = t for visible t; vertex nodes are set by k_uf_init_v.
+__global__ void __launch_bounds__(kBlock) k_uf_init(UfArgs a, int vertex_mode) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (a.T + 31) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
+       w += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t word = __ldg(a.vt + w);
+    if (word == 0) continue;
+    const uint32_t t = (w << 5) + lane;
+    if (!((word >> lane) & 1u)) continue;
+    int32_t lab = (int32_t)t;
+    if (!vertex_mode) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
+        if (n >= 0 && n < lab && vt_bit(a.vt, (uint32_t)n)) lab = n;
+      }
+    }
+    a.label[t] = lab;
+  }
+}
+
+__global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
+    label[T + v] = (int32_t)(T + v);
+}
+
+// Hooking (Alg. 1, second loop): each undirected edge once, from its lower end.
+__global__ void __launch_bounds__(kBlock) k_uf_hook(UfArgs a, int vertex_mode) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (a.T + 31) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
+       w += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t word = __ldg(a.vt + w);
+    if (word == 0) continue;
+    const uint32_t t = (w << 5) + lane;
+    if (!((word >> lane) & 1u)) continue;
+    if (vertex_mode) {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        uint32_t v = __ldg(a.idx + 3 * (size_t)t + j);
+        unite(a.label, (int32_t)t, (int32_t)(a.T + v), a.ctr);
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
+        if (n > (int32_t)t && vt_bit(a.vt, (uint32_t)n)) unite(a.label, (int32_t)t, n, a.ctr);
+      }
+    }
+  }
+}
+
+// Non-manifold edges: join consecutive visible triangles of each incidence list.
+__global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* nm_list, uint32_t n_nm) {
+  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nm; e += gridDim.x * blockDim.x) {
+    int32_t prev = -1;
+    for (uint32_t i = nm_off[e]; i < nm_off[e + 1]; ++i) {
+      uint32_t t = nm_list[i];
+      if (!vt_bit(a.vt, t)) continue;
+      if (prev >= 0 && prev != (int32_t)t) unite(a.label, prev, (int32_t)t, a.ctr);
+      prev = (int32_t)t;
+    }
+  }
+}
+
+// Flatten visible triangles to their root and count roots per block of
+// kPerBlock triangles.
+__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt) {
+  __shared__ uint32_t cnt;
+  if (threadIdx.x == 0) cnt = 0;
+  __syncthreads();
+  const uint32_t base = blockIdx.x * kPerBlock;
+  uint32_t mine = 0;
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t t = base + k * kBlock + threadIdx.x;
+    if (t >= a.T || !vt_bit(a.vt, t)) continue;
+    int32_t r = find_rep(a.label, (int32_t)t);
+    a.label[t] = r;
+    mine += (r == (int32_t)t);
+  }
+  mine = __reduce_add_sync(0xFFFFFFFFu, mine);
+  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&cnt, mine);
+  __syncthreads();
+  if (threadIdx.x == 0) blockcnt[blockIdx.x] = cnt;
+}
+
+// Exclusive scan of the per-block root counts (one block); writes the chart count.
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blockcnt, uint32_t nblocks,
+                                                      uint32_t* count_out, uint32_t max_charts,
+                                                      DevCounters* ctr) {
+  __shared__ uint32_t warp_tot[32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (uint32_t base = 0; base < nblocks; base += 1024) {
+    const uint32_t i = base + threadIdx.x;
+    uint32_t v = i < nblocks ? blockcnt[i] : 0;
+    uint32_t x = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if ((threadIdx.x & 31) >= (unsigned)o) x += y;
+    }
+    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      uint32_t t = warp_tot[threadIdx.x];
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+        if (threadIdx.x >= (unsigned)o) t += y;
+      }
+      warp_tot[threadIdx.x] = t;
+    }
+    __syncthreads();
+    const uint32_t wprefix = (threadIdx.x >= 32) ? warp_tot[(threadIdx.x >> 5) - 1] : 0;
+    if (i < nblocks) blockcnt[i] = carry + wprefix + x - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry += wprefix + x;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    blockcnt[nblocks] = carry;
+    ctr->chart_count = carry;
+    *count_out = carry;
+    if (carry > max_charts) set_status(ctr, FA_E_CAPACITY);
+  }
+}
+
+// Number the roots in triangle order (same blocking as k_uf_flatten); record the
+// chart's root and reset its box accumulators.
+__global__ void __launch_bounds__(kBlock) k_number(UfArgs a, const uint32_t* blockcnt, int32_t* cid,
+                                                   uint32_t* roots, uint32_t* box_enc,
+                                                   uint32_t* box_full, uint32_t max_charts) {
+  __shared__ uint32_t warp_tot[kBlock / 32];
+  __shared__ uint32_t carry;
+  if (threadIdx.x == 0) carry = blockcnt[blockIdx.x];
+  __syncthreads();
+  const uint32_t base = blockIdx.x * kPerBlock;
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t t = base + k * kBlock + threadIdx.x;
+    bool root = false;
+    if (t < a.T && vt_bit(a.vt, t)) root = (__ldcg(a.label + t) == (int32_t)t);
+    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, root);
+    const uint32_t lane = threadIdx.x & 31;
+    if (lane == 0) warp_tot[threadIdx.x >> 5] = __popc(ball);
+    __syncthreads();
+    uint32_t pre = carry;
+    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) pre += warp_tot[w];
+    pre += __popc(ball & ((1u << lane) - 1u));
+    if (root && pre < max_charts) {
+      cid[t] = (int32_t)pre;
+      roots[pre] = t;
+      box_enc[4 * pre + 0] = 0xFFFFFFFFu;  // min x (ordered encoding)
+      box_enc[4 * pre + 1] = 0xFFFFFFFFu;  // min y
+      box_enc[4 * pre + 2] = 0u;           // max x
+      box_enc[4 * pre + 3] = 0u;           // max y
+      box_full[pre] = 0u;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kBlock / 32; ++w) tot += warp_tot[w];
+      carry += tot;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* cid, int32_t* tri_chart) {
+  if (__ldcg(&a.ctr->status) != 0) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (a.T + 31) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
+       w += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t word = __ldg(a.vt + w);
+    const uint32_t t = (w << 5) + lane;
+    if (t >= a.T) continue;
+    int32_t out = -1;
+    if ((word >> lane) & 1u) out = __ldcg(cid + __ldcg(a.label + t));
+    tri_chart[t] = out;
+  }
+}
+
+__global__ void k_vert_chart(UfArgs a, const int32_t* cid, int32_t* vert_chart, int vertex_mode) {
+  if (__ldcg(&a.ctr->status) != 0) return;
+  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
+    int32_t out = -1;
+    if (vertex_mode) {
+      int32_t r = find_rep(a.label, (int32_t)(a.T + v));
+      if (r < (int32_t)a.T) out = __ldcg(cid + r);
+    }
+    vert_chart[v] = out;
+  }
+}
+
+}  // namespace
+
+fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
+                          int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch, cudaStream_t s) {
+  UfArgs a;
+  a.vt = vt;
+  a.idx = mesh->idx;
+  a.adj = mesh->adj;
+  a.T = mesh->T;
+  a.V = mesh->V;
+  a.label = ctx->label;
+  a.ctr = ctx->ctr;
+  const int vm = mode == FA_CHARTS_VERTEX;
+  const unsigned gw = grid_for((uint64_t)((mesh->T + 31) / 32) * 32, kBlock, 152 * 16);
+  if (vm) {
+    mark(ctx, "k_uf_init_v", s);
+    k_uf_init_v<<<grid_for(mesh->V, 256, 152 * 8), 256, 0, s>>>(ctx->label, mesh->T, mesh->V);
+  }
+  mark(ctx, "k_uf_init", s);
+  k_uf_init<<<gw, kBlock, 0, s>>>(a, vm);
+  mark(ctx, "k_uf_hook", s);
+  k_uf_hook<<<gw, kBlock, 0, s>>>(a, vm);
+  if (!vm && mesh->n_nm) {
+    mark(ctx, "k_uf_hook_nm", s);
+    k_uf_hook_nm<<<grid_for(mesh->n_nm, 256), 256, 0, s>>>(a, mesh->nm_off, mesh->nm_list, mesh->n_nm);
+  }
+  const uint32_t nb = (mesh->T + kPerBlock - 1) / kPerBlock;
+  mark(ctx, "k_uf_flatten", s);
+  k_uf_flatten<<<nb ? nb : 1, kBlock, 0, s>>>(a, ctx->blockcnt);
+  mark(ctx, "k_scan_blocks", s);
+  k_scan_blocks<<<1, 1024, 0, s>>>(ctx->blockcnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts, ctx->ctr);
+  mark(ctx, "k_number", s);
+  k_number<<<nb ? nb : 1, kBlock, 0, s>>>(a, ctx->blockcnt, ctx->cid, ch->root, ctx->box_enc,
+                                          ctx->box_full, ctx->cfg.max_charts);
+  mark(ctx, "k_tri_chart", s);
+  k_tri_chart<<<gw, kBlock, 0, s>>>(a, ctx->cid, tri_chart);
+  if (vert_chart) {
+    mark(ctx, "k_vert_chart", s);
+    k_vert_chart<<<grid_for(mesh->V, 256, 152 * 8), 256, 0, s>>>(a, ctx->cid, vert_chart, vm);
+  }
+  FA_CUDA_TRY(cudaGetLastError());
+  return FA_OK;
+}
+
+}  // namespace fa

@@ -1,0 +1,201 @@
+// Internal declarations shared by the CUDA translation units of libfastatlas.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/fastatlas.h"
+
+namespace fa {
+
+// ----------------------------------------------------------------- constants
+
+constexpr float kGuard = 64.0f;     // guard band |x|,|y| <= kGuard * w
+constexpr int kSub = 256;           // sub-pixel steps per pixel (1/256 px snapping)
+constexpr uint32_t kMaxH = 8192;    // height buckets of the box order (Sec. 4.1)
+constexpr int kMaxScales = 64;      // candidate scales (Sec. 4.2)
+constexpr uint32_t kFrontCap = 40960;  // frontline entries per candidate (smem)
+constexpr int kBigTile = 16;        // tile side of the large-triangle raster
+constexpr int kSmallMaxPix = 16;    // in-thread raster when the pixel box has <= this
+constexpr int kOrderTile = 1024;    // boxes per tile of the stable order
+constexpr uint32_t kLoopCap = 1u << 24;  // device iteration cap (FA_E_TIMEOUT)
+
+// ----------------------------------------------------------------- device state
+
+// Small counters that live in device memory (one struct per context).
+struct DevCounters {
+  int32_t status;          // sticky fa_status of the context
+  uint32_t pad0;
+  unsigned long long big;  // big-triangle queue: entries << 40 | tiles
+  uint32_t pack_done;      // candidate CTAs finished (last one selects)
+  uint32_t order_tiles;    // tiles of the current order pass
+  uint32_t chart_count;    // scratch copy of the frame's chart count
+  uint32_t n_groups[kMaxScales];
+};
+
+// One queued (large) sub-triangle of the raster: snapped vertices, depths and its
+// clamped pixel box; tiles [tile0, tile0 + ntiles) of the queue belong to it.
+struct BigTri {
+  int32_t X[3], Y[3];
+  float zn[3];
+  int32_t px0, py0, px1, py1;
+  uint32_t tri;
+  uint32_t tile0;
+  uint32_t pad;
+};
+static_assert(sizeof(BigTri) == 64, "BigTri is one 64-byte record");
+
+struct PackCand {
+  uint32_t ok;      // 1 = fits
+  uint32_t omega;   // Omega
+  uint32_t height;  // H
+  int32_t status;   // FA_OK / FA_E_CAPACITY
+};
+
+}  // namespace fa
+
+constexpr int kMaxProf = 64;
+
+struct fa_ctx {
+  fa_config cfg;
+  int device;
+  uint64_t launches;
+  // per-kernel event trace of the last public call (fa_profile_enable)
+  int prof_on;
+  int prof_n;
+  cudaEvent_t prof_ev[kMaxProf + 1];
+  const char* prof_name[kMaxProf];
+  // scratch
+  fa::DevCounters* ctr;
+  uint32_t* zbuf;        // [max_w * max_h]
+  uint32_t* bigbits;     // [ceil(max_tris/32)]
+  fa::BigTri* queue;     // [queue_cap]
+  uint32_t queue_cap;
+  int32_t* label;        // [max_tris + max_verts]
+  int32_t* cid;          // [max_tris] chart id of root triangles
+  uint32_t* blockcnt;    // [n_blocks + 1]
+  uint32_t* box_enc;     // [max_charts * 4] ordered-int chart boxes
+  uint32_t* box_full;    // [max_charts]
+  uint32_t* ord_counts;  // [kMaxH * max_order_tiles]
+  uint32_t* ord_rank;    // [max_charts]
+  uint32_t* ord_binstart;  // [kMaxH]
+  uint32_t* order;       // [max_charts] (used when the caller passes none)
+  uint32_t max_order_tiles;
+  unsigned long long* cand_P;  // [kMaxScales * max_charts]
+  uint2* cand_wh;        // [kMaxScales * max_charts]
+  uint2* cand_xy;        // [kMaxScales * max_charts]
+  uint32_t* cand_rows;   // [kMaxScales * max_charts] first box of each row group
+  fa::PackCand* cand;    // [kMaxScales]
+  fa_pack_result* res;   // internal result when the caller passes none
+  fa_placement* place;   // internal placements
+};
+
+struct fa_mesh {
+  fa_ctx* ctx;
+  const float* pos;      // caller-owned [V][3]
+  const uint32_t* idx;   // caller-owned [T][3]
+  uint32_t V, T;
+  int32_t* adj;          // [T][3]: neighbour across edge j (v_j, v_j+1), -1 boundary,
+                         // -2 - e for non-manifold edge e
+  uint32_t n_nm;         // non-manifold edges
+  uint32_t* nm_off;      // [n_nm + 1]
+  uint32_t* nm_list;     // incident triangles of the non-manifold edges
+};
+
+namespace fa {
+
+// ----------------------------------------------------------------- helpers
+
+struct Mat4 {
+  float m[16];
+};
+
+#define FA_CUDA_TRY(expr)                         \
+  do {                                            \
+    cudaError_t e_ = (expr);                      \
+    if (e_ != cudaSuccess) return FA_E_CUDA;      \
+  } while (0)
+
+// Pinned fp32 evaluation of clip = M . [p, 1]: ((m0 x + m1 y) + m2 z) + m3 per row,
+// one rounding per operation (no contraction).
+__device__ __forceinline__ float4 transform(const Mat4& M, float x, float y, float z) {
+  float r[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    float acc = __fmul_rn(M.m[4 * i + 0], x);
+    acc = __fadd_rn(acc, __fmul_rn(M.m[4 * i + 1], y));
+    acc = __fadd_rn(acc, __fmul_rn(M.m[4 * i + 2], z));
+    acc = __fadd_rn(acc, M.m[4 * i + 3]);
+    r[i] = acc;
+  }
+  return make_float4(r[0], r[1], r[2], r[3]);
+}
+
+__device__ __forceinline__ float4 load_clip(const Mat4& M, const float* __restrict__ pos, uint32_t v) {
+  const float* p = pos + 3 * (size_t)v;
+  return transform(M, __ldg(p), __ldg(p + 1), __ldg(p + 2));
+}
+
+// Order-preserving map float -> uint32 (with -0 folded onto +0).
+__device__ __forceinline__ uint32_t ordered(float f) {
+  uint32_t u = __float_as_uint(f);
+  if (u == 0x80000000u) u = 0u;
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+__device__ __forceinline__ float unordered(uint32_t k) {
+  uint32_t u = (k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k;
+  return __uint_as_float(u);
+}
+
+__device__ __forceinline__ void set_status(DevCounters* c, int32_t s) {
+  atomicCAS(&c->status, 0, s);
+}
+
+__device__ __forceinline__ bool vt_bit(const uint32_t* vt, uint32_t t) {
+  return (__ldg(vt + (t >> 5)) >> (t & 31)) & 1u;
+}
+
+inline unsigned grid_for(uint64_t n, unsigned block, unsigned cap = 152u * 16u) {
+  uint64_t g = (n + block - 1) / block;
+  if (g < 1) g = 1;
+  if (g > cap) g = cap;
+  return (unsigned)g;
+}
+
+// Called right before every kernel launch: counts the launch and, when tracing is
+// on, records the event that opens this kernel's slot.
+inline void mark(fa_ctx* ctx, const char* name, cudaStream_t s) {
+  ctx->launches++;
+  if (ctx->prof_on && ctx->prof_n < kMaxProf) {
+    cudaEventRecord(ctx->prof_ev[ctx->prof_n], s);
+    ctx->prof_name[ctx->prof_n] = name;
+    ctx->prof_n++;
+  }
+}
+// Start / close the trace of one public call.
+inline void trace_begin(fa_ctx* ctx) { ctx->prof_n = 0; }
+inline void trace_end(fa_ctx* ctx, cudaStream_t s) {
+  if (ctx->prof_on && ctx->prof_n > 0) cudaEventRecord(ctx->prof_ev[ctx->prof_n], s);
+}
+
+// ----------------------------------------------------------------- launchers
+// Each returns FA_OK or FA_E_CUDA (launch error) and bumps ctx->launches.
+
+fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
+                            uint32_t H, uint32_t* vt, cudaStream_t s);
+fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
+                          int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
+                          cudaStream_t s);
+fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
+                              uint32_t H, float ratio, const int32_t* tri_chart,
+                              const uint32_t* vt, const fa_charts* ch, bool reset_boxes, cudaStream_t s);
+fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
+                      uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
+                      uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s);
+fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
+                    float ratio, const int32_t* tri_chart, const uint32_t* vt, const fa_charts* ch,
+                    const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
+                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s);
+fa_status build_adjacency(fa_ctx* ctx, fa_mesh* mesh, cudaStream_t s);
+
+}  // namespace fa

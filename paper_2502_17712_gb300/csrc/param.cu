@@ -1,0 +1,369 @@
+// Chart boxes, footprints and UVs.
+//
+// k_bbox (Sec. 5.2): per visible triangle, clip against the near plane when it
+//   crosses it, clamp each vertex to [-w, w] and divide (Blinn's estimator), then
+//   a warp-segmented min / max per chart (__match_any_sync + __reduce_*_sync) and one
+//   atomic per chart and warp on order-preserving integer encodings (exact and
+//   order independent).
+// k_footprint (Sec. 5.2, Sec. 4.1): viewport size of the box, scaled by the
+//   texel-to-pixel ratio, quantized up to 1/256 texel, rotated to stand tall.
+// k_uv (Sec. 3, App. A): projection of each visible corner into its chart's atlas
+//   box in compensated fp32 ("double-float": Knuth TwoSum, FMA TwoProd), rounded
+//   once at the end.
+#include "fa_internal.cuh"
+
+namespace fa {
+namespace {
+
+struct CV {
+  float x, y, z, w;
+};
+
+__device__ __forceinline__ CV lerp_in_out(const CV& a, const CV& b, float da, float db) {
+  float t = __fdiv_rn(da, __fsub_rn(da, db));
+  CV r;
+  r.x = __fadd_rn(a.x, __fmul_rn(t, __fsub_rn(b.x, a.x)));
+  r.y = __fadd_rn(a.y, __fmul_rn(t, __fsub_rn(b.y, a.y)));
+  r.z = __fadd_rn(a.z, __fmul_rn(t, __fsub_rn(b.z, a.z)));
+  r.w = __fadd_rn(a.w, __fmul_rn(t, __fsub_rn(b.w, a.w)));
+  return r;
+}
+
+struct Box {
+  float xmin, ymin, xmax, ymax;
+  bool full;
+};
+
+__device__ __forceinline__ void box_add(Box& b, const CV& c) {
+  if (!(c.w > 0.0f)) {
+    b.full = true;
+    return;
+  }
+  float x = c.x, y = c.y;
+  const float nw = -c.w;
+  if (x < nw) x = nw;
+  if (x > c.w) x = c.w;
+  if (y < nw) y = nw;
+  if (y > c.w) y = c.w;
+  float nx = __fdiv_rn(x, c.w), ny = __fdiv_rn(y, c.w);
+  if (nx == 0.0f) nx = 0.0f;
+  if (ny == 0.0f) ny = 0.0f;
+  b.xmin = fminf(b.xmin, nx);
+  b.ymin = fminf(b.ymin, ny);
+  b.xmax = fmaxf(b.xmax, nx);
+  b.ymax = fmaxf(b.ymax, ny);
+}
+
+struct BoxArgs {
+  Mat4 M;
+  const float* pos;
+  const uint32_t* idx;
+  const uint32_t* vt;
+  const int32_t* tri_chart;
+  uint32_t T;
+  uint32_t* box_enc;
+  uint32_t* box_full;
+  uint32_t max_charts;
+  DevCounters* ctr;
+};
+
+__global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
+  if (__ldcg(&a.ctr->status) != 0) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (a.T + 31) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
+       w += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t word = __ldg(a.vt + w);
+    if (word == 0) continue;
+    const uint32_t t = (w << 5) + lane;
+    int32_t c = -1;
+    Box b{__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0xff800000),
+          __int_as_float(0xff800000), false};
+    if ((word >> lane) & 1u) {
+      c = __ldcg(a.tri_chart + t);
+      if ((uint32_t)c >= a.max_charts) c = -1;  // not a chart of this context: ignored
+    }
+    if (c >= 0) {
+      const uint32_t* f = a.idx + 3 * (size_t)t;
+      float4 p0 = load_clip(a.M, a.pos, __ldg(f)), p1 = load_clip(a.M, a.pos, __ldg(f + 1)),
+             p2 = load_clip(a.M, a.pos, __ldg(f + 2));
+      CV v[3] = {{p0.x, p0.y, p0.z, p0.w}, {p1.x, p1.y, p1.z, p1.w}, {p2.x, p2.y, p2.z, p2.w}};
+      float d[3] = {__fadd_rn(p0.z, p0.w), __fadd_rn(p1.z, p1.w), __fadd_rn(p2.z, p2.w)};
+      const bool all_in = d[0] >= 0.0f && d[1] >= 0.0f && d[2] >= 0.0f;
+      if (all_in) {
+        box_add(b, v[0]);
+        box_add(b, v[1]);
+        box_add(b, v[2]);
+      } else {
+        // Sutherland-Hodgman against the near plane only (3 -> 3 or 4 vertices)
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+          const int nx = (i + 1) % 3;
+          const bool ic = d[i] >= 0.0f, in_ = d[nx] >= 0.0f;
+          if (ic) box_add(b, v[i]);
+          if (ic != in_) box_add(b, ic ? lerp_in_out(v[i], v[nx], d[i], d[nx]) : lerp_in_out(v[nx], v[i], d[nx], d[i]));
+        }
+      }
+    }
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, c);
+    const uint32_t e0 = __reduce_min_sync(peers, ordered(b.xmin));
+    const uint32_t e1 = __reduce_min_sync(peers, ordered(b.ymin));
+    const uint32_t e2 = __reduce_max_sync(peers, ordered(b.xmax));
+    const uint32_t e3 = __reduce_max_sync(peers, ordered(b.ymax));
+    const uint32_t fl = __reduce_or_sync(peers, b.full ? 1u : 0u);
+    if (c >= 0 && (__ffs(peers) - 1) == (int)lane) {
+      uint32_t* be = a.box_enc + 4 * (size_t)c;
+      atomicMin(be + 0, e0);
+      atomicMin(be + 1, e1);
+      atomicMax(be + 2, e2);
+      atomicMax(be + 3, e3);
+      if (fl) atomicOr(a.box_full + c, 1u);
+    }
+  }
+}
+
+__global__ void k_box_reset(const uint32_t* count, uint32_t max_charts, uint32_t* box_enc, uint32_t* box_full) {
+  const uint32_t C = min(__ldcg(count), max_charts);
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    reinterpret_cast<uint4*>(box_enc)[c] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+    box_full[c] = 0u;
+  }
+}
+
+__global__ void k_footprint(const uint32_t* count, uint32_t max_charts, const uint32_t* box_enc,
+                            const uint32_t* box_full, float hx, float hy, float s256, float* bbox,
+                            uint32_t* fa_, uint32_t* fb, uint8_t* rot, DevCounters* ctr) {
+  if (__ldcg(&ctr->status) != 0) return;
+  const uint32_t C = min(__ldcg(count), max_charts);
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    float x0, y0, x1, y1;
+    if (__ldcg(box_full + c)) {
+      x0 = y0 = -1.0f;
+      x1 = y1 = 1.0f;
+    } else {
+      x0 = unordered(__ldcg(box_enc + 4 * c + 0));
+      y0 = unordered(__ldcg(box_enc + 4 * c + 1));
+      x1 = unordered(__ldcg(box_enc + 4 * c + 2));
+      y1 = unordered(__ldcg(box_enc + 4 * c + 3));
+    }
+    reinterpret_cast<float4*>(bbox)[c] = make_float4(x0, y0, x1, y1);
+    const float wpx = __fmul_rn(__fsub_rn(x1, x0), hx);
+    const float hpx = __fmul_rn(__fsub_rn(y1, y0), hy);
+    const uint32_t fw = __float2uint_rz(ceilf(__fmul_rn(s256, wpx)));
+    const uint32_t fh = __float2uint_rz(ceilf(__fmul_rn(s256, hpx)));
+    const bool r = fw > fh;
+    rot[c] = r ? 1 : 0;
+    fa_[c] = r ? fh : fw;
+    fb[c] = r ? fw : fh;
+  }
+}
+
+// ------------------------------------------------------------ compensated fp32
+
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  const float err = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  return DF{s, err};
+}
+__device__ __forceinline__ DF quick_two_sum(float a, float b) {  // |a| >= |b| or a == 0
+  const float s = __fadd_rn(a, b);
+  return DF{s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  DF s = two_sum(a.hi, b.hi);
+  DF t = two_sum(a.lo, b.lo);
+  s.lo = __fadd_rn(s.lo, t.hi);
+  s = quick_two_sum(s.hi, s.lo);
+  s.lo = __fadd_rn(s.lo, t.lo);
+  return quick_two_sum(s.hi, s.lo);
+}
+__device__ __forceinline__ DF df_neg(DF a) { return DF{-a.hi, -a.lo}; }
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  const float e = __fmaf_rn(a.hi, b.hi, -p);
+  const float lo = __fmaf_rn(a.hi, b.lo, __fmaf_rn(a.lo, b.hi, e));
+  return quick_two_sum(p, lo);
+}
+__device__ __forceinline__ DF df_mul_f(DF a, float b) {
+  const float p = __fmul_rn(a.hi, b);
+  const float e = __fmaf_rn(a.hi, b, -p);
+  return quick_two_sum(p, __fmaf_rn(a.lo, b, e));
+}
+// a / b for fp32 a, b: the remainder a - q b is exact for the rounded quotient q.
+__device__ __forceinline__ DF df_div(float a, float b) {
+  const float q = __fdiv_rn(a, b);
+  const float r = __fmaf_rn(-q, b, a);
+  return quick_two_sum(q, __fdiv_rn(r, b));
+}
+
+struct UvArgs {
+  Mat4 M;
+  const float* pos;
+  const uint32_t* idx;
+  const uint32_t* vt;
+  const int32_t* tri_chart;
+  uint32_t T;
+  float hx, hy;
+  float ratio;
+  uint32_t atlas_log2;
+  uint32_t n_scales;
+  uint32_t gutter;
+  const uint32_t* count;
+  uint32_t max_charts;
+  const float* bbox;
+  const uint8_t* rot;
+  const fa_placement* place;
+  const fa_pack_result* res;
+  float* uv;
+  float* affine;
+  DevCounters* ctr;
+};
+
+__global__ void __launch_bounds__(256) k_uv(UvArgs a) {
+  if (__ldcg(&a.ctr->status) != 0 || __ldcg(&a.res->status) != FA_OK) return;
+  const uint32_t k = __ldcg(&a.res->k);
+  const float om = (float)(1u << a.atlas_log2), Om = (float)__ldcg(&a.res->omega);
+  const DF alpha = df_div(om, Om);
+  DF g = quick_two_sum(__fmul_rn(a.ratio, (float)k), __fmaf_rn(a.ratio, (float)k, -__fmul_rn(a.ratio, (float)k)));
+  const float inv_n = 1.0f / (float)a.n_scales;  // power of two: exact
+  g.hi = __fmul_rn(g.hi, inv_n);
+  g.lo = __fmul_rn(g.lo, inv_n);
+  const float gut = (float)a.gutter;
+
+  // per-chart affine (uv = A . ndc + b)
+  if (a.affine) {
+    const uint32_t C = min(__ldcg(a.count), a.max_charts);
+    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+      const float4 bb = reinterpret_cast<const float4*>(a.bbox)[c];
+      const fa_placement pl = a.place[c];
+      const DF X = two_sum((float)pl.x, gut), Y = two_sum((float)pl.y, gut);
+      const DF agx = df_mul(df_mul_f(alpha, a.hx), g), agy = df_mul(df_mul_f(alpha, a.hy), g);
+      const DF gx = df_mul_f(g, a.hx), gy = df_mul_f(g, a.hy);
+      float* o = a.affine + 6 * (size_t)c;
+      if (__ldg(a.rot + c)) {
+        o[0] = 0.0f;
+        o[1] = agy.hi;
+        o[2] = df_mul(alpha, df_add(X, df_neg(df_mul_f(gy, bb.y)))).hi;
+        o[3] = -agx.hi;
+        o[4] = 0.0f;
+        o[5] = df_mul(alpha, df_add(Y, df_mul_f(gx, bb.z))).hi;
+      } else {
+        o[0] = agx.hi;
+        o[1] = 0.0f;
+        o[2] = df_mul(alpha, df_add(X, df_neg(df_mul_f(gx, bb.x)))).hi;
+        o[3] = 0.0f;
+        o[4] = agy.hi;
+        o[5] = df_mul(alpha, df_add(Y, df_neg(df_mul_f(gy, bb.y)))).hi;
+      }
+    }
+  }
+  if (!a.uv) return;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t nwords = (a.T + 31) >> 5;
+  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
+       w += (gridDim.x * blockDim.x) >> 5) {
+    const uint32_t word = __ldg(a.vt + w);
+    const uint32_t t = (w << 5) + lane;
+    if (!((word >> lane) & 1u)) continue;
+    const int32_t c = __ldcg(a.tri_chart + t);
+    if (c < 0 || (uint32_t)c >= min(__ldcg(a.count), a.max_charts)) continue;
+    const float4 bb = reinterpret_cast<const float4*>(a.bbox)[c];
+    const fa_placement pl = a.place[c];
+    const bool r = __ldg(a.rot + c) != 0;
+    const DF X = two_sum((float)pl.x, gut), Y = two_sum((float)pl.y, gut);
+    const DF wpx = df_mul_f(two_sum(bb.z, -bb.x), a.hx);
+    const uint32_t* f = a.idx + 3 * (size_t)t;
+    float2* o = reinterpret_cast<float2*>(a.uv + 6 * (size_t)t);
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      const float4 cc = load_clip(a.M, a.pos, __ldg(f + j));
+      if (!(cc.w > 0.0f)) {
+        o[j] = make_float2(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
+        continue;
+      }
+      const DF nx = df_div(cc.x, cc.w), ny = df_div(cc.y, cc.w);
+      const DF px = df_mul_f(df_add(nx, DF{-bb.x, 0.0f}), a.hx);
+      const DF py = df_mul_f(df_add(ny, DF{-bb.y, 0.0f}), a.hy);
+      DF lu, lv;
+      if (r) {
+        lu = df_mul(py, g);
+        lv = df_mul(df_add(wpx, df_neg(px)), g);
+      } else {
+        lu = df_mul(px, g);
+        lv = df_mul(py, g);
+      }
+      const DF u = df_mul(df_add(X, lu), alpha), v = df_mul(df_add(Y, lv), alpha);
+      o[j] = make_float2(__fadd_rn(u.hi, u.lo), __fadd_rn(v.hi, v.lo));
+    }
+  }
+}
+
+}  // namespace
+
+fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
+                              float ratio, const int32_t* tri_chart, const uint32_t* vt,
+                              const fa_charts* ch, bool reset_boxes, cudaStream_t s) {
+  if (reset_boxes) {
+    mark(ctx, "k_box_reset", s);
+    k_box_reset<<<grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s>>>(ch->count, ctx->cfg.max_charts,
+                                                                            ctx->box_enc, ctx->box_full);
+  }
+  BoxArgs a;
+  a.M = M;
+  a.pos = mesh->pos;
+  a.idx = mesh->idx;
+  a.vt = vt;
+  a.tri_chart = tri_chart;
+  a.T = mesh->T;
+  a.box_enc = ctx->box_enc;
+  a.box_full = ctx->box_full;
+  a.max_charts = ctx->cfg.max_charts;
+  a.ctr = ctx->ctr;
+  mark(ctx, "k_bbox", s);
+  k_bbox<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s>>>(a);
+  mark(ctx, "k_footprint", s);
+  k_footprint<<<grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s>>>(
+      ch->count, ctx->cfg.max_charts, ctx->box_enc, ctx->box_full, 0.5f * (float)W, 0.5f * (float)H,
+      256.0f * ratio, ch->bbox, ch->fa, ch->fb, ch->rot, ctx->ctr);
+  FA_CUDA_TRY(cudaGetLastError());
+  return FA_OK;
+}
+
+fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H, float ratio,
+                    const int32_t* tri_chart, const uint32_t* vt, const fa_charts* ch,
+                    const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
+                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s) {
+  UvArgs a;
+  a.M = M;
+  a.pos = mesh->pos;
+  a.idx = mesh->idx;
+  a.vt = vt;
+  a.tri_chart = tri_chart;
+  a.T = mesh->T;
+  a.hx = 0.5f * (float)W;
+  a.hy = 0.5f * (float)H;
+  a.ratio = ratio;
+  a.atlas_log2 = atlas_log2;
+  a.n_scales = n_scales;
+  a.gutter = ctx->cfg.gutter;
+  a.count = ch->count;
+  a.max_charts = ctx->cfg.max_charts;
+  a.bbox = ch->bbox;
+  a.rot = ch->rot;
+  a.place = place;
+  a.res = res;
+  a.uv = uv;
+  a.affine = affine;
+  a.ctr = ctx->ctr;
+  mark(ctx, "k_uv", s);
+  k_uv<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s>>>(a);
+  FA_CUDA_TRY(cudaGetLastError());
+  return FA_OK;
+}
+
+}  // namespace fa

@@ -1,0 +1,340 @@
+"""Thin Python binding of libfastatlas (include/fastatlas.h).
+
+Functions named ``fa_*`` mirror the C ABI one to one and only marshal arguments:
+torch CUDA tensors are passed as raw device pointers and
+``torch.cuda.current_stream().cuda_stream`` as the stream.  Every step of the
+atlasing path runs in the library's CUDA kernels; there is no CPU fallback, and
+loading fails loudly when the library has not been built.
+
+The small classes at the bottom (``Context``, ``Mesh``, ``FrameBuffers``) own the
+torch tensors the calls write into, so that they stay alive while kernels run.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libfastatlas.so")
+
+FA_OK = 0
+FA_E_INVALID_ARG = 1
+FA_E_OUT_OF_MEMORY = 2
+FA_E_CAPACITY = 3
+FA_E_PACK_FAILED = 4
+FA_E_TIMEOUT = 5
+FA_E_CUDA = 6
+FA_CHARTS_EDGE = 0
+FA_CHARTS_VERTEX = 1
+FA_SELECT_EFFECTIVE = 0
+FA_SELECT_LARGEST_K = 1
+
+EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
+           "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
+           "fa_atlas_frame", "fa_last_device_status", "fa_launch_count", "fa_profile_enable",
+           "fa_profile_read"]
+
+
+class fa_config(ctypes.Structure):
+    _fields_ = [("max_tris", ctypes.c_uint32), ("max_verts", ctypes.c_uint32),
+                ("max_charts", ctypes.c_uint32), ("max_width", ctypes.c_uint32),
+                ("max_height", ctypes.c_uint32), ("max_atlas_log2", ctypes.c_uint32),
+                ("min_box", ctypes.c_uint32), ("gutter", ctypes.c_uint32), ("device", ctypes.c_int32)]
+
+
+class fa_charts(ctypes.Structure):
+    _fields_ = [("root", ctypes.c_void_p), ("bbox", ctypes.c_void_p), ("fa", ctypes.c_void_p),
+                ("fb", ctypes.c_void_p), ("rot", ctypes.c_void_p), ("count", ctypes.c_void_p)]
+
+
+class fa_placement(ctypes.Structure):
+    _fields_ = [("x", ctypes.c_int32), ("y", ctypes.c_int32), ("w", ctypes.c_int32), ("h", ctypes.c_int32)]
+
+
+class fa_pack_result(ctypes.Structure):
+    _fields_ = [("k", ctypes.c_uint32), ("omega", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("status", ctypes.c_int32), ("count", ctypes.c_uint32)]
+
+
+class fa_frame_params(ctypes.Structure):
+    _fields_ = [("view_proj", ctypes.c_float * 16), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
+                ("ratio", ctypes.c_float), ("atlas_log2", ctypes.c_uint32), ("chart_mode", ctypes.c_uint32),
+                ("n_scales", ctypes.c_uint32), ("select_mode", ctypes.c_uint32)]
+
+
+class fa_frame_out(ctypes.Structure):
+    _fields_ = [("vt", ctypes.c_void_p), ("tri_chart", ctypes.c_void_p), ("vert_chart", ctypes.c_void_p),
+                ("charts", fa_charts), ("order", ctypes.c_void_p), ("place", ctypes.c_void_p),
+                ("result", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("affine", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libfastatlas.so (raises if it is missing: there is no fallback)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"libfastatlas is not built ({path} missing); run "
+                           "python -m paper_2502_17712_gb300.build")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    u32 = ctypes.c_uint32
+    f32 = ctypes.c_float
+    st = ctypes.c_int
+    lib.fa_version.restype = u32
+    lib.fa_status_string.argtypes = [st]
+    lib.fa_status_string.restype = ctypes.c_char_p
+    lib.fa_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(fa_config)]
+    lib.fa_create.restype = st
+    lib.fa_destroy.argtypes = [P]
+    lib.fa_destroy.restype = None
+    lib.fa_mesh_register.argtypes = [P, P, u32, P, u32, ctypes.POINTER(P), P]
+    lib.fa_mesh_register.restype = st
+    lib.fa_mesh_release.argtypes = [P]
+    lib.fa_mesh_release.restype = None
+    lib.fa_visibility.argtypes = [P, P, P, u32, u32, P, P]
+    lib.fa_visibility.restype = st
+    lib.fa_chartify.argtypes = [P, P, P, u32, P, P, ctypes.POINTER(fa_charts), P]
+    lib.fa_chartify.restype = st
+    lib.fa_parameterize.argtypes = [P, P, P, u32, u32, f32, P, ctypes.POINTER(fa_charts), P]
+    lib.fa_parameterize.restype = st
+    lib.fa_pack.argtypes = [P, P, P, P, u32, u32, u32, P, P, P, P]
+    lib.fa_pack.restype = st
+    lib.fa_uv.argtypes = [P, P, P, u32, u32, f32, P, ctypes.POINTER(fa_charts), P, P, u32, u32, P, P, P]
+    lib.fa_uv.restype = st
+    lib.fa_atlas_frame.argtypes = [P, P, ctypes.POINTER(fa_frame_params), ctypes.POINTER(fa_frame_out), P]
+    lib.fa_atlas_frame.restype = st
+    lib.fa_last_device_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int32)]
+    lib.fa_last_device_status.restype = st
+    lib.fa_launch_count.argtypes = [P]
+    lib.fa_launch_count.restype = ctypes.c_uint64
+    lib.fa_profile_enable.argtypes = [P, ctypes.c_int]
+    lib.fa_profile_enable.restype = st
+    lib.fa_profile_read.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
+                                    ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]
+    lib.fa_profile_read.restype = st
+    _lib = lib
+    return lib
+
+
+class FastAtlasError(RuntimeError):
+    def __init__(self, status: int, where: str):
+        self.status = status
+        name = load().fa_status_string(status).decode() if _lib is not None else str(status)
+        super().__init__(f"{where}: {name}")
+
+
+def _check(status: int, where: str):
+    if status != FA_OK:
+        raise FastAtlasError(status, where)
+
+
+def _ptr(t) -> int | None:
+    if t is None:
+        return None
+    assert t.is_cuda and t.is_contiguous(), "device tensors must be contiguous CUDA tensors"
+    return t.data_ptr()
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _mat(M):
+    return (ctypes.c_float * 16)(*np.ascontiguousarray(M, np.float32).ravel().tolist())
+
+
+# ------------------------------------------------------------------ C ABI mirrors
+
+def fa_version() -> int:
+    return load().fa_version()
+
+
+def fa_create(cfg: fa_config) -> int:
+    h = ctypes.c_void_p()
+    _check(load().fa_create(ctypes.byref(h), ctypes.byref(cfg)), "fa_create")
+    return h.value
+
+
+def fa_destroy(ctx: int):
+    load().fa_destroy(ctx)
+
+
+def fa_mesh_register(ctx, pos, idx, stream=None) -> int:
+    m = ctypes.c_void_p()
+    _check(load().fa_mesh_register(ctx, _ptr(pos), pos.shape[0], _ptr(idx), idx.shape[0], ctypes.byref(m),
+                                   _stream(stream)), "fa_mesh_register")
+    return m.value
+
+
+def fa_mesh_release(mesh: int):
+    load().fa_mesh_release(mesh)
+
+
+def fa_visibility(ctx, mesh, M, width, height, vt, stream=None):
+    _check(load().fa_visibility(ctx, mesh, _mat(M), width, height, _ptr(vt), _stream(stream)), "fa_visibility")
+
+
+def fa_chartify(ctx, mesh, vt, mode, tri_chart, vert_chart, charts: fa_charts, stream=None):
+    _check(load().fa_chartify(ctx, mesh, _ptr(vt), mode, _ptr(tri_chart), _ptr(vert_chart),
+                              ctypes.byref(charts), _stream(stream)), "fa_chartify")
+
+
+def fa_parameterize(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_charts, stream=None):
+    _check(load().fa_parameterize(ctx, mesh, _mat(M), width, height, float(ratio), _ptr(tri_chart),
+                                  ctypes.byref(charts), _stream(stream)), "fa_parameterize")
+
+
+def fa_pack(ctx, fa, fb, count, atlas_log2, n_scales, select_mode, order, place, res, stream=None):
+    _check(load().fa_pack(ctx, _ptr(fa), _ptr(fb), _ptr(count), atlas_log2, n_scales, select_mode, _ptr(order),
+                          _ptr(place), _ptr(res), _stream(stream)), "fa_pack")
+
+
+def fa_uv(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_charts, place, res, atlas_log2, n_scales,
+          uv, affine, stream=None):
+    _check(load().fa_uv(ctx, mesh, _mat(M), width, height, float(ratio), _ptr(tri_chart), ctypes.byref(charts),
+                        _ptr(place), _ptr(res), atlas_log2, n_scales, _ptr(uv), _ptr(affine), _stream(stream)),
+           "fa_uv")
+
+
+def fa_atlas_frame(ctx, mesh, params: fa_frame_params, out: fa_frame_out, stream=None):
+    _check(load().fa_atlas_frame(ctx, mesh, ctypes.byref(params), ctypes.byref(out), _stream(stream)),
+           "fa_atlas_frame")
+
+
+def fa_last_device_status(ctx, stream=None) -> int:
+    v = ctypes.c_int32()
+    _check(load().fa_last_device_status(ctx, _stream(stream), ctypes.byref(v)), "fa_last_device_status")
+    return v.value
+
+
+def fa_launch_count(ctx) -> int:
+    return load().fa_launch_count(ctx)
+
+
+def fa_profile_enable(ctx, enable: bool):
+    _check(load().fa_profile_enable(ctx, 1 if enable else 0), "fa_profile_enable")
+
+
+def fa_profile_read(ctx, max_n: int = 64):
+    """[(kernel name, ms)] of the last traced call (waits for it to finish)."""
+    ms = (ctypes.c_float * max_n)()
+    names = (ctypes.c_char_p * max_n)()
+    n = ctypes.c_int()
+    _check(load().fa_profile_read(ctx, max_n, ms, names, ctypes.byref(n)), "fa_profile_read")
+    return [(names[i].decode(), float(ms[i])) for i in range(min(n.value, max_n))]
+
+
+# ------------------------------------------------------------------ owners of device buffers
+
+class Context:
+    """An fa_ctx plus its configuration."""
+
+    def __init__(self, max_tris, max_verts, max_charts=1 << 16, max_width=1920, max_height=1080,
+                 max_atlas_log2=12, min_box=2, gutter=0, device=0):
+        self.cfg = fa_config(max_tris, max_verts, max_charts, max_width, max_height, max_atlas_log2,
+                             min_box, gutter, device)
+        self.handle = fa_create(self.cfg)
+
+    def close(self):
+        if self.handle:
+            fa_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def device_status(self, stream=None) -> int:
+        return fa_last_device_status(self.handle, stream)
+
+    @property
+    def launches(self) -> int:
+        return fa_launch_count(self.handle)
+
+
+class Mesh:
+    """A registered mesh; keeps its position / index tensors alive."""
+
+    def __init__(self, ctx: Context, pos, idx, stream=None):
+        import torch
+        self.ctx = ctx
+        self.pos = pos if torch.is_tensor(pos) else torch.as_tensor(np.ascontiguousarray(pos, np.float32)).cuda()
+        idx_np = idx if torch.is_tensor(idx) else np.ascontiguousarray(idx, np.uint32).view(np.int32)
+        self.idx = idx_np if torch.is_tensor(idx_np) else torch.as_tensor(idx_np).cuda()
+        self.T = int(self.idx.shape[0])
+        self.V = int(self.pos.shape[0])
+        self.handle = fa_mesh_register(ctx.handle, self.pos, self.idx, stream)
+
+    def close(self):
+        if self.handle:
+            fa_mesh_release(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+@dataclass
+class FrameBuffers:
+    """Device outputs of one frame (torch tensors) and their C views."""
+    vt: object
+    tri_chart: object
+    vert_chart: object
+    root: object
+    bbox: object
+    fa: object
+    fb: object
+    rot: object
+    count: object
+    order: object
+    place: object
+    result: object
+    uv: object
+    affine: object
+
+    @staticmethod
+    def allocate(T, V, max_charts, uv=True, vert_chart=False, device="cuda"):
+        import torch
+        i32, u8, f32 = torch.int32, torch.uint8, torch.float32
+        z = lambda *s, dt=i32: torch.zeros(*s, dtype=dt, device=device)
+        return FrameBuffers(
+            vt=z((T + 31) // 32), tri_chart=z(T), vert_chart=z(V) if vert_chart else None,
+            root=z(max_charts), bbox=z(max_charts, 4, dt=f32), fa=z(max_charts), fb=z(max_charts),
+            rot=z(max_charts, dt=u8), count=z(1), order=z(max_charts), place=z(max_charts, 4),
+            result=z(5), uv=torch.full((T, 3, 2), float("nan"), dtype=f32, device=device) if uv else None,
+            affine=z(max_charts, 6, dt=f32))
+
+    def charts(self) -> fa_charts:
+        return fa_charts(_ptr(self.root), _ptr(self.bbox), _ptr(self.fa), _ptr(self.fb), _ptr(self.rot),
+                         _ptr(self.count))
+
+    def c_out(self) -> fa_frame_out:
+        return fa_frame_out(_ptr(self.vt), _ptr(self.tri_chart), _ptr(self.vert_chart), self.charts(),
+                            _ptr(self.order), _ptr(self.place), _ptr(self.result), _ptr(self.uv),
+                            _ptr(self.affine))
+
+
+def frame_params(M, width, height, ratio, atlas_log2, chart_mode=FA_CHARTS_EDGE, n_scales=64,
+                 select_mode=FA_SELECT_EFFECTIVE) -> fa_frame_params:
+    return fa_frame_params(_mat(M), width, height, float(ratio), atlas_log2, chart_mode, n_scales, select_mode)
+
+
+def atlas_frame(ctx: Context, mesh: Mesh, bufs: FrameBuffers, M, width, height, ratio, atlas_log2,
+                chart_mode=FA_CHARTS_EDGE, n_scales=64, select_mode=FA_SELECT_EFFECTIVE, stream=None):
+    """Enqueue the whole per-frame path (fa_atlas_frame); results land in ``bufs``."""
+    p = frame_params(M, width, height, ratio, atlas_log2, chart_mode, n_scales, select_mode)
+    fa_atlas_frame(ctx.handle, mesh.handle, p, bufs.c_out(), stream)

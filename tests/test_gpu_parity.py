@@ -1,0 +1,285 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI.
+
+Bit-exact: VT bits, chart ids, roots, chart count, NDC boxes (fp32 bits),
+footprints, rotations, the packing order, placements and the chosen candidate.
+UVs: |GPU - fp64 oracle| <= 1e-4 texel + half an fp32 ulp of the value (the
+half ulp is the unavoidable final rounding; below 2048 texels it is <= 6.1e-5).
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_17712_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+UV_TOL = 1e-4
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2502_17712_gb300 import build, fastatlas
+    build.build()
+    fastatlas.load()
+    return fastatlas
+
+
+def run_gpu(F, ctx, mesh, M, W, H, ratio, log2, mode=0, n_scales=64, select_mode=0, bufs=None):
+    import torch
+    if bufs is None:
+        bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts, vert_chart=True)
+    F.atlas_frame(ctx, mesh, bufs, M, W, H, ratio, log2, mode, n_scales, select_mode)
+    torch.cuda.synchronize()
+    st = ctx.device_status()
+    return bufs, st
+
+
+def to_np(t):
+    return t.cpu().numpy()
+
+
+def compare_frame(sc, M, W, H, ratio, log2, bufs, status, mode=0, n_scales=64, select_mode=0, vt=None):
+    fr = O.atlas_frame(M, sc.pos, sc.idx, W, H, ratio, log2, mode=mode, n_scales=n_scales,
+                       select_mode=select_mode, vt=vt)
+    assert status == 0
+    T = sc.T
+    gvt = to_np(bufs.vt).view(np.uint32)
+    if vt is None:
+        assert (gvt == fr.vt).all(), f"VT differs in {int((gvt != fr.vt).sum())} words"
+    C = int(to_np(bufs.count)[0])
+    assert C == fr.charts.C
+    assert (to_np(bufs.tri_chart) == fr.charts.tri_chart).all()
+    assert (to_np(bufs.root)[:C].view(np.uint32) == fr.charts.roots).all()
+    if mode == 1:
+        assert (to_np(bufs.vert_chart) == fr.charts.vert_chart).all()
+    gb = to_np(bufs.bbox)[:C]
+    assert (gb.view(np.uint32) == fr.fp.bbox.view(np.uint32)).all()
+    assert (to_np(bufs.fa)[:C].view(np.uint32) == fr.fp.fa).all()
+    assert (to_np(bufs.fb)[:C].view(np.uint32) == fr.fp.fb).all()
+    assert (to_np(bufs.rot)[:C] == fr.fp.rot).all()
+    assert (to_np(bufs.order)[:C].view(np.uint32) == fr.order).all()
+    res = to_np(bufs.result).view(np.uint32)
+    assert int(res[3]) == fr.pk.status
+    if fr.pk.status == 0:
+        assert (int(res[0]), int(res[1]), int(res[2])) == (fr.pk.k, fr.pk.omega, fr.pk.height)
+        assert (to_np(bufs.place)[:C] == fr.pk.place).all()
+        u = to_np(bufs.uv).astype(np.float64)
+        vis = fr.charts.tri_chart >= 0
+        ou = fr.uv[vis]
+        gu = u[vis]
+        nan = np.isnan(ou)
+        assert (np.isnan(gu) == nan).all()
+        tol = UV_TOL + 0.5 * np.spacing(np.abs(ou[~nan]).astype(np.float32)).astype(np.float64)
+        err = np.abs(gu[~nan] - ou[~nan])
+        assert (err <= tol).all(), f"max UV error {err.max():.3g}"
+        ga = to_np(bufs.affine)[:C].astype(np.float64)
+        assert np.allclose(ga, fr.affine, rtol=1e-6, atol=2e-4)
+    return fr
+
+
+@pytest.fixture(scope="module")
+def small_ctx(F):
+    return F.Context(max_tris=1 << 16, max_verts=1 << 16, max_charts=1 << 15, max_width=1920,
+                     max_height=1080, max_atlas_log2=12)
+
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+@pytest.mark.parametrize("mode", [0, 1])
+def test_heightfield_frame(F, small_ctx, seed, mode):
+    sc, M, p = S.heightfield_frame(seed)
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, small_ctx, mesh, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], mode)
+    compare_frame(sc, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], bufs, st, mode)
+
+
+@pytest.mark.parametrize("ratio,log2,n_scales,sel", [(0.5, 9, 64, 0), (2.0, 10, 32, 0), (1.0, 8, 16, 1),
+                                                     (4.0, 9, 64, 0)])
+def test_heightfield_variants(F, small_ctx, ratio, log2, n_scales, sel):
+    sc = S.grid_scene(5)
+    W, H = 1280, 720
+    M = S.hemisphere_camera(5, W, H, radius=2.2)
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, small_ctx, mesh, M, W, H, ratio, log2, 0, n_scales, sel)
+    compare_frame(sc, M, W, H, ratio, log2, bufs, st, 0, n_scales, sel)
+
+
+def test_big_triangles_full_hd(F, small_ctx):
+    # ~500-pixel triangles exercise the queued tile rasterizer
+    for seed in (7, 8):
+        sc = S.grid_scene(seed)
+        M = S.spline_cameras(seed, 5, 1920, 1080)[seed % 5]
+        mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+        bufs, st = run_gpu(F, small_ctx, mesh, M, 1920, 1080, 1.0, 11)
+        compare_frame(sc, M, 1920, 1080, 1.0, 11, bufs, st)
+
+
+def test_near_plane_and_guard_band_clipping(F, small_ctx):
+    # camera inside a field of instanced patches, close to the surface
+    sc = S.instanced_grid_scene(3, 6, n=24)
+    W, H = 640, 360
+    for i, eye in enumerate([(0.1, 0.2, 0.12), (-0.5, 0.3, 0.06), (1.0, -1.0, 0.3)]):
+        M = S.view_proj(eye, (eye[0] + 1.0, eye[1] + 0.4, -0.2), (0, 0, 1), W, H, near=0.05)
+        mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+        bufs, st = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, 10)
+        compare_frame(sc, M, W, H, 1.0, 10, bufs, st)
+
+
+def test_nothing_visible(F, small_ctx):
+    sc = S.grid_scene(1)
+    M = S.view_proj((0, 0, 3), (0, 0, 6), (0, 1, 0), 320, 240)  # looking away
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, small_ctx, mesh, M, 320, 240, 1.0, 10)
+    fr = compare_frame(sc, M, 320, 240, 1.0, 10, bufs, st)
+    assert fr.charts.C == 0 and int(to_np(bufs.count)[0]) == 0
+
+
+def test_non_manifold_and_degenerate_mesh(F, small_ctx):
+    # a fan of four triangles on one edge, degenerate triangles, an isolated one
+    pos = np.array([[-0.5, -0.5, 0.0], [0.5, -0.5, 0.0], [0.0, 0.5, 0.0], [0.0, -0.9, 0.1],
+                    [0.3, 0.6, -0.1], [-0.6, 0.2, 0.05], [0.6, 0.1, 0.2], [-0.8, -0.8, 0.0],
+                    [-0.7, -0.8, 0.0], [-0.75, -0.7, 0.0]], np.float32)
+    idx = np.array([[0, 1, 2], [1, 0, 3], [0, 1, 4], [0, 1, 6], [0, 0, 5], [2, 2, 2], [7, 8, 9],
+                    [1, 2, 6]], np.uint32)
+    M = np.eye(4, dtype=np.float32)
+    mesh = F.Mesh(small_ctx, pos, idx)
+    for mode in (0, 1):
+        # visibility from the GPU; also force a VT that keeps the fan visible
+        bufs, st = run_gpu(F, small_ctx, mesh, M, 64, 64, 1.0, 8, mode)
+        compare_frame(S.Scene(pos, idx), M, 64, 64, 1.0, 8, bufs, st, mode)
+
+
+def test_standalone_calls_equal_frame(F, small_ctx):
+    import torch
+    sc, M, p = S.heightfield_frame(4)
+    W, H, r, L = p["width"], p["height"], p["ratio"], p["atlas_log2"]
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    ref, st = run_gpu(F, small_ctx, mesh, M, W, H, r, L)
+    b = F.FrameBuffers.allocate(mesh.T, mesh.V, small_ctx.cfg.max_charts)
+    h = small_ctx.handle
+    F.fa_visibility(h, mesh.handle, M, W, H, b.vt)
+    ch = b.charts()
+    F.fa_chartify(h, mesh.handle, b.vt, 0, b.tri_chart, None, ch)
+    F.fa_parameterize(h, mesh.handle, M, W, H, r, b.tri_chart, ch)
+    F.fa_pack(h, b.fa, b.fb, b.count, L, 64, 0, b.order, b.place, b.result)
+    F.fa_uv(h, mesh.handle, M, W, H, r, b.tri_chart, ch, b.place, b.result, L, 64, b.uv, b.affine)
+    torch.cuda.synchronize()
+    assert small_ctx.device_status() == 0
+    for name in ("vt", "tri_chart", "count", "bbox", "fa", "fb", "rot", "place", "result", "affine"):
+        assert torch.equal(getattr(ref, name), getattr(b, name)), name
+    assert torch.equal(torch.nan_to_num(ref.uv, 7.0), torch.nan_to_num(b.uv, 7.0))
+
+
+def test_deterministic_repeat(F, small_ctx):
+    import torch
+    sc, M, p = S.heightfield_frame(6)
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    a, _ = run_gpu(F, small_ctx, mesh, M, p["width"], p["height"], 1.0, 10)
+    b, _ = run_gpu(F, small_ctx, mesh, M, p["width"], p["height"], 1.0, 10)
+    for name in ("vt", "tri_chart", "bbox", "place", "result"):
+        assert torch.equal(getattr(a, name), getattr(b, name))
+    assert torch.equal(torch.nan_to_num(a.uv, 7.0), torch.nan_to_num(b.uv, 7.0))
+
+
+# ------------------------------------------------------------------ packing alone
+
+
+@pytest.mark.parametrize("n,log2,seed", [(1, 4, 0), (3, 5, 1), (1000, 10, 2), (1023, 9, 3), (1025, 11, 4),
+                                         (12000, 11, 5), (40000, 12, 6)])
+def test_pack_matches_oracle(F, n, log2, seed):
+    import torch
+    ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1 << 16, max_width=64, max_height=64,
+                    max_atlas_log2=12)
+    fa, fb = S.lognormal_boxes(seed, n, mean_texels=6 if n > 5000 else 12)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    order = torch.zeros(1 << 16, dtype=torch.int32, device="cuda")
+    place = torch.zeros(1 << 16, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    for sel in (0, 1):
+        F.fa_pack(ctx.handle, d_fa, d_fb, cnt, log2, 64, sel, order, place, res)
+        torch.cuda.synchronize()
+        pk = O.pack(fa, fb, log2, select_mode=sel)
+        r = to_np(res).view(np.uint32)
+        assert int(r[3]) == pk.status
+        assert (to_np(order)[:n].view(np.uint32) == O.order(fb)).all()
+        if pk.status == 0:
+            assert (int(r[0]), int(r[1]), int(r[2])) == (pk.k, pk.omega, pk.height)
+            assert (to_np(place)[:n] == pk.place).all()
+    ctx.close()
+
+
+def test_pack_failure_and_capacity(F):
+    import torch
+    ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1024, max_width=64, max_height=64,
+                    max_atlas_log2=12)
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    place = torch.zeros(1024, 4, dtype=torch.int32, device="cuda")
+    # a single box far taller than the atlas: no candidate fits
+    fa = torch.tensor([256 * 100], dtype=torch.int32, device="cuda")
+    fb = torch.tensor([256 * 100000], dtype=torch.int32, device="cuda")
+    cnt = torch.tensor([1], dtype=torch.int32, device="cuda")
+    F.fa_pack(ctx.handle, fa, fb, cnt, 6, 64, 0, None, place, res)
+    torch.cuda.synchronize()
+    assert int(res[3]) == F.FA_E_PACK_FAILED
+    # a box wider than 8 omega overflows the frontline capacity
+    fa = torch.tensor([256 * 1000], dtype=torch.int32, device="cuda")
+    fb = torch.tensor([256 * 1000], dtype=torch.int32, device="cuda")
+    F.fa_pack(ctx.handle, fa, fb, cnt, 6, 64, 0, None, place, res)
+    torch.cuda.synchronize()
+    assert int(res[3]) == F.FA_E_CAPACITY
+    # more boxes than max_charts
+    cnt = torch.tensor([5000], dtype=torch.int32, device="cuda")
+    F.fa_pack(ctx.handle, fa, fb, cnt, 6, 64, 0, None, place, res)
+    torch.cuda.synchronize()
+    assert int(res[3]) == F.FA_E_CAPACITY
+    # host-side argument errors
+    with pytest.raises(F.FastAtlasError):
+        F.fa_pack(ctx.handle, fa, fb, cnt, 13, 64, 0, None, place, res)  # above max_atlas_log2
+    with pytest.raises(F.FastAtlasError):
+        F.fa_pack(ctx.handle, fa, fb, cnt, 6, 48, 0, None, place, res)  # not a power of two
+    ctx.close()
+
+
+def test_chart_capacity_error(F):
+    sc, M, p = S.heightfield_frame(2)
+    ctx = F.Context(max_tris=1 << 14, max_verts=1 << 13, max_charts=4, max_width=480, max_height=270,
+                    max_atlas_log2=10)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    # vertex-disjoint checkerboard-like visibility through many charts: use edge mode on
+    # a frame whose edge charts exceed 4 by forcing a sparse VT
+    import torch
+    b = F.FrameBuffers.allocate(mesh.T, mesh.V, 4)
+    vis = np.zeros(sc.T, bool)
+    vis[::2] = True
+    b.vt.copy_(torch.as_tensor(O.bool_to_vt(vis).view(np.int32)))
+    F.fa_chartify(ctx.handle, mesh.handle, b.vt, 0, b.tri_chart, None, b.charts())
+    torch.cuda.synchronize()
+    assert ctx.device_status() == F.FA_E_CAPACITY
+    assert int(b.count[0]) == sc.T // 2
+    assert ctx.device_status() == 0  # read-and-clear
+
+
+# ------------------------------------------------------------------ the 4.1M-triangle frame
+
+
+@pytest.fixture(scope="module")
+def sphere_frame():
+    return S.icosphere_frame(1)
+
+
+@pytest.mark.parametrize("mode", [0, 1])
+def test_icosphere_frame_full_size(F, sphere_frame, mode):
+    """200 icospheres (4,096,000 triangles), 1920x1080, 2048^2 atlas: the whole frame
+    at full size, every output compared (the oracle takes ~10 s here)."""
+    sc, M, p = sphere_frame
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 17, max_width=1920, max_height=1080,
+                    max_atlas_log2=11)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, ctx, mesh, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], mode)
+    compare_frame(sc, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], bufs, st, mode)
+    mesh.close()
+    ctx.close()
