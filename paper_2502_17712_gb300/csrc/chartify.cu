@@ -34,6 +34,15 @@ __device__ __forceinline__ int32_t find_rep(volatile int32_t* label, int32_t x) 
   return cur;
 }
 
+// Root without writing: used once hooking is over.  (Path halving here would race
+// with the final store of another thread: a halving write can replace a label that
+// was just set to the root by a non-root ancestor.)
+__device__ __forceinline__ int32_t find_root(const volatile int32_t* label, int32_t x) {
+  int32_t cur = x, next;
+  while ((next = label[cur]) != cur) cur = next;
+  return cur;
+}
+
 // Hook the components of a and b: the larger root is CASed onto the smaller.
 __device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevCounters* ctr) {
   volatile int32_t* vl = label;
@@ -140,7 +149,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* block
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
     const uint32_t t = base + k * kBlock + threadIdx.x;
     if (t >= a.T || !vt_bit(a.vt, t)) continue;
-    int32_t r = find_rep(a.label, (int32_t)t);
+    int32_t r = find_root(a.label, (int32_t)t);
     a.label[t] = r;
     mine += (r == (int32_t)t);
   }
@@ -253,7 +262,7 @@ __global__ void k_vert_chart(UfArgs a, const int32_t* cid, int32_t* vert_chart, 
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
     int32_t out = -1;
     if (vertex_mode) {
-      int32_t r = find_rep(a.label, (int32_t)(a.T + v));
+      int32_t r = find_root(a.label, (int32_t)(a.T + v));
       if (r < (int32_t)a.T) out = __ldcg(cid + r);
     }
     vert_chart[v] = out;

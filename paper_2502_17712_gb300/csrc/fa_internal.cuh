@@ -162,12 +162,20 @@ inline unsigned grid_for(uint64_t n, unsigned block, unsigned cap = 152u * 16u) 
   return (unsigned)g;
 }
 
+// Event record that stays a real (timeable) record when the stream is being
+// captured into a CUDA graph.
+inline void record_event(cudaEvent_t e, cudaStream_t s) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(s, &cs);
+  if (cs == cudaStreamCaptureStatusActive) cudaEventRecordWithFlags(e, s, cudaEventRecordExternal);
+  else cudaEventRecord(e, s);
+}
 // Called right before every kernel launch: counts the launch and, when tracing is
 // on, records the event that opens this kernel's slot.
 inline void mark(fa_ctx* ctx, const char* name, cudaStream_t s) {
   ctx->launches++;
   if (ctx->prof_on && ctx->prof_n < kMaxProf) {
-    cudaEventRecord(ctx->prof_ev[ctx->prof_n], s);
+    record_event(ctx->prof_ev[ctx->prof_n], s);
     ctx->prof_name[ctx->prof_n] = name;
     ctx->prof_n++;
   }
@@ -175,7 +183,7 @@ inline void mark(fa_ctx* ctx, const char* name, cudaStream_t s) {
 // Start / close the trace of one public call.
 inline void trace_begin(fa_ctx* ctx) { ctx->prof_n = 0; }
 inline void trace_end(fa_ctx* ctx, cudaStream_t s) {
-  if (ctx->prof_on && ctx->prof_n > 0) cudaEventRecord(ctx->prof_ev[ctx->prof_n], s);
+  if (ctx->prof_on && ctx->prof_n > 0) record_event(ctx->prof_ev[ctx->prof_n], s);
 }
 
 // ----------------------------------------------------------------- launchers
