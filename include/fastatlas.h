@@ -220,6 +220,35 @@ fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const
                   uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* d_order,
                   fa_placement* d_place, fa_pack_result* d_res, fa_stream_t stream);
 
+/* Packing without any allocation.  The paper has no counterpart: this is a
+ * service for callers that may not allocate device memory where they pack, such as
+ * code running in a host application's per-frame callback or plugin slot whose
+ * device memory is owned and budgeted by the host, or a real-time loop that must
+ * not pay cudaMalloc's implicit device synchronization.  It computes exactly what
+ * fa_pack computes (same order, candidates, selection and placements) for n boxes
+ * d_fa, d_fb (n given on the host), with min_box and gutter passed directly, and
+ * needs no context.
+ * Scratch: one file-scope device array of about 7.2 MiB inside the library, sized
+ * for at most 4096 boxes; every GPU that loads the library holds it until the
+ * process exits.  The call never runs cudaMalloc, cudaFree or any allocating
+ * library routine.
+ * The first call on a device looks up the array's device address (with that device
+ * current) and raises the pack kernel's shared-memory limit; make that first call
+ * before any stream capture.  Later calls only launch kernels on `stream`, on the
+ * current device.
+ * All calls share the one array, and each call leaves its contents behind (the
+ * call clears what must start at zero itself); calls whose kernels overlap on the
+ * GPU (different streams, or different host threads) race on it and must be
+ * serialized by the caller.
+ * Errors: FA_E_CAPACITY (n > 4096), FA_E_INVALID_ARG (NULL pointers, atlas_log2
+ * outside [1, 14], n_scales not a power of two in [1, 64], unknown select_mode,
+ * min_box outside [1, 4096], gutter > 4096), FA_E_CUDA (set-up or launch failed);
+ * device-side results and errors land in d_res as for fa_pack. */
+fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb, uint32_t n, uint32_t atlas_log2,
+                          uint32_t n_scales, uint32_t select_mode, uint32_t min_box, uint32_t gutter,
+                          uint32_t* d_order, fa_placement* d_place, fa_pack_result* d_res,
+                          fa_stream_t stream);
+
 /* Parameterization (Sec. 3; App. A "Shading and Rasterization"): every visible
  * corner with w > 0 maps to alpha * ((x + gutter, y + gutter) + s * local) in atlas
  * texels, alpha = omega / Omega, s = ratio * k / n_scales, local = the corner's

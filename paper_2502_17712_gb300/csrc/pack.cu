@@ -484,3 +484,139 @@ fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, cons
 }
 
 }  // namespace fa
+
+// ------------------------------------------------------------------ allocation-free packing
+//
+// fa_pack_noalloc runs the same order and pack kernels as fa_pack, but its scratch
+// is one file-scope device array instead of context memory, so the call itself never
+// allocates.  It exists for callers that are not allowed to allocate device memory
+// at the point where they pack: code running inside a host application's frame
+// callback or plugin slot whose device memory is owned and budgeted by the host,
+// and real-time loops that must not hit cudaMalloc's implicit device
+// synchronization.  The array (about 7.2 MiB, for up to 4096 boxes) stays resident
+// on every GPU that loads the library, until the process exits.
+
+#include <mutex>
+
+namespace fa {
+namespace {
+
+constexpr uint32_t kNoAllocMaxBoxes = 4096;
+constexpr uint32_t kNoAllocTiles = kNoAllocMaxBoxes / kOrderTile;
+
+constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
+constexpr size_t kOffCtr = 0;
+constexpr size_t kOffCount = align256(kOffCtr + sizeof(DevCounters));
+constexpr size_t kOffCand = align256(kOffCount + sizeof(uint32_t));
+constexpr size_t kOffCounts = align256(kOffCand + sizeof(PackCand) * kMaxScales);
+constexpr size_t kOffRank = align256(kOffCounts + sizeof(uint32_t) * kMaxH * kNoAllocTiles);
+constexpr size_t kOffBinstart = align256(kOffRank + sizeof(uint32_t) * kNoAllocMaxBoxes);
+constexpr size_t kOffOrder = align256(kOffBinstart + sizeof(uint32_t) * kMaxH);
+constexpr size_t kOffP = align256(kOffOrder + sizeof(uint32_t) * kNoAllocMaxBoxes);
+constexpr size_t kOffWH = align256(kOffP + sizeof(unsigned long long) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kOffXY = align256(kOffWH + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kOffRows = align256(kOffXY + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kNoAllocBytes = align256(kOffRows + sizeof(uint32_t) * kMaxScales * kNoAllocMaxBoxes);
+
+// The scratch of fa_pack_noalloc.  Host code must not use this name as a device
+// address: it is a host-side shadow there; the device address comes from
+// cudaGetSymbolAddress in noalloc_scratch() below.
+static __device__ __align__(256) unsigned char g_pack_scratch[kNoAllocBytes];
+
+constexpr int kNoAllocMaxDevices = 64;
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
+
+// Once per device, with that device current: the array's device address, and the
+// pack kernel's shared-memory limit.
+fa_status noalloc_scratch(int dev, unsigned char** out) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return FA_E_INVALID_ARG;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_pack_scratch) != cudaSuccess) {
+      cudaGetLastError();
+      return FA_E_CUDA;
+    }
+    if (cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)((size_t)kFrontCap * 4 + (size_t)kStage * 16)) != cudaSuccess) {
+      cudaGetLastError();
+      return FA_E_CUDA;
+    }
+    g_noalloc_ptr[dev] = (unsigned char*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return FA_OK;
+}
+
+// Clears what the kernels expect at zero (status word, finished-candidate counter)
+// and stores the box count where the kernels read it.
+__global__ void k_noalloc_reset(DevCounters* ctr, uint32_t* count, uint32_t n) {
+  ctr->status = 0;
+  ctr->pack_done = 0;
+  *count = n;
+}
+
+}  // namespace
+}  // namespace fa
+
+extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb, uint32_t n,
+                                     uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
+                                     uint32_t min_box, uint32_t gutter, uint32_t* d_order,
+                                     fa_placement* d_place, fa_pack_result* d_res, fa_stream_t stream) {
+  using namespace fa;
+  if (!d_fa || !d_fb || !d_place || !d_res) return FA_E_INVALID_ARG;
+  if (atlas_log2 < 1 || atlas_log2 > 14) return FA_E_INVALID_ARG;
+  if (n_scales == 0 || (n_scales & (n_scales - 1)) || n_scales > (uint32_t)kMaxScales) return FA_E_INVALID_ARG;
+  if (select_mode > FA_SELECT_LARGEST_K) return FA_E_INVALID_ARG;
+  if (min_box < 1 || min_box > 4096 || gutter > 4096) return FA_E_INVALID_ARG;
+  if (n > kNoAllocMaxBoxes) return FA_E_CAPACITY;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) {
+    cudaGetLastError();
+    return FA_E_CUDA;
+  }
+  unsigned char* base = nullptr;
+  fa_status st = noalloc_scratch(dev, &base);
+  if (st != FA_OK) return st;
+  cudaStream_t s = (cudaStream_t)stream;
+  DevCounters* ctr = (DevCounters*)(base + kOffCtr);
+  uint32_t* count = (uint32_t*)(base + kOffCount);
+  uint32_t* counts = (uint32_t*)(base + kOffCounts);
+  uint32_t* rank = (uint32_t*)(base + kOffRank);
+  uint32_t* binstart = (uint32_t*)(base + kOffBinstart);
+  uint32_t* ord = d_order ? d_order : (uint32_t*)(base + kOffOrder);
+  k_noalloc_reset<<<1, 1, 0, s>>>(ctr, count, n);
+  k_order_tile<<<kNoAllocTiles, kOrderTile, 0, s>>>(d_fb, count, kNoAllocMaxBoxes, counts, rank, ctr);
+  k_order_scan<<<1, 1024, 0, s>>>(count, kNoAllocMaxBoxes, counts, binstart, ctr);
+  k_order_scatter<<<kNoAllocTiles, kOrderTile, 0, s>>>(d_fb, count, kNoAllocMaxBoxes, counts, rank, binstart,
+                                                       ord, ctr);
+  PackArgs a;
+  a.fa = d_fa;
+  a.fb = d_fb;
+  a.count = count;
+  a.order = ord;
+  a.max_charts = kNoAllocMaxBoxes;
+  a.atlas_log2 = atlas_log2;
+  a.n_scales = n_scales;
+  uint32_t sh = 8;
+  while ((1u << (sh - 8)) < n_scales) ++sh;
+  a.shift = sh;
+  a.min_box = min_box;
+  a.gutter = gutter;
+  a.select_mode = select_mode;
+  const uint32_t om = 1u << atlas_log2;
+  a.front_cap = (8u * om < kFrontCap) ? 8u * om : kFrontCap;
+  a.P = (unsigned long long*)(base + kOffP);
+  a.wh = (uint2*)(base + kOffWH);
+  a.xy = (uint2*)(base + kOffXY);
+  a.rows = (uint32_t*)(base + kOffRows);
+  a.cand = (PackCand*)(base + kOffCand);
+  a.ctr = ctr;
+  a.place = d_place;
+  a.res = d_res;
+  const size_t smem = (size_t)a.front_cap * 4 + (size_t)kStage * 16;
+  k_pack<<<n_scales, kPackThreads, smem, s>>>(a);
+  if (cudaGetLastError() != cudaSuccess) return FA_E_CUDA;
+  return FA_OK;
+}

@@ -35,7 +35,7 @@ FA_SELECT_LARGEST_K = 1
 EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
            "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
            "fa_atlas_frame", "fa_last_device_status", "fa_launch_count", "fa_profile_enable",
-           "fa_profile_read"]
+           "fa_profile_read", "fa_pack_noalloc"]
 
 
 class fa_config(ctypes.Structure):
@@ -119,6 +119,8 @@ def load(path: str = LIB_PATH):
     lib.fa_profile_read.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
                                     ctypes.POINTER(ctypes.c_char_p), ctypes.POINTER(ctypes.c_int)]
     lib.fa_profile_read.restype = st
+    lib.fa_pack_noalloc.argtypes = [P, P, u32, u32, u32, u32, u32, u32, P, P, P, P]
+    lib.fa_pack_noalloc.restype = st
     _lib = lib
     return lib
 
@@ -196,6 +198,14 @@ def fa_parameterize(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_ch
 def fa_pack(ctx, fa, fb, count, atlas_log2, n_scales, select_mode, order, place, res, stream=None):
     _check(load().fa_pack(ctx, _ptr(fa), _ptr(fb), _ptr(count), atlas_log2, n_scales, select_mode, _ptr(order),
                           _ptr(place), _ptr(res), _stream(stream)), "fa_pack")
+
+
+def fa_pack_noalloc(fa, fb, n, atlas_log2, n_scales, select_mode, min_box, gutter, order, place, res,
+                    stream=None):
+    """fa_pack without a context or any allocation (scratch is a static device array
+    inside the library, at most 4096 boxes); for callers that may not allocate."""
+    _check(load().fa_pack_noalloc(_ptr(fa), _ptr(fb), n, atlas_log2, n_scales, select_mode, min_box, gutter,
+                                  _ptr(order), _ptr(place), _ptr(res), _stream(stream)), "fa_pack_noalloc")
 
 
 def fa_uv(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_charts, place, res, atlas_log2, n_scales,
