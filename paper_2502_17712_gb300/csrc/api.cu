@@ -82,10 +82,10 @@ void fa_destroy(fa_ctx* ctx) {
   cudaDeviceSynchronize();
   if (ctx->prof_on)
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
-  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->label, ctx->cid, ctx->blockcnt,
-                  ctx->box_enc, ctx->box_full, ctx->ord_counts, ctx->ord_rank, ctx->ord_binstart,
-                  ctx->order, ctx->cand_P, ctx->cand_wh, ctx->cand_xy, ctx->cand_rows, ctx->cand,
-                  ctx->res, ctx->place};
+  const PackScratch& p = ctx->pack;
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->label, ctx->cid, ctx->blockcnt,
+                  ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
+                  p.order, p.tile_tot, p.rec, p.m, p.xy, p.cand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::free(ctx);
@@ -116,7 +116,9 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   fa_status st = FA_OK;
   const uint64_t T = c.max_tris, V = c.max_verts, C = c.max_charts;
   ctx->queue_cap = (uint32_t)(T < (1u << 20) ? T + 1024 : (1u << 20));
-  ctx->max_order_tiles = (uint32_t)((C + kOrderTile - 1) / kOrderTile);
+  PackScratch& pk = ctx->pack;
+  pk.max_boxes = (uint32_t)C;
+  pk.max_tiles = (uint32_t)((C + kOrderTile - 1) / kOrderTile);
   const uint64_t nblocks = (T + 1023) / 1024 + 1;
 #define FA_ALLOC(ptr, n) \
   if (st == FA_OK) st = alloc(&ptr, (size_t)(n));
@@ -124,24 +126,28 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->zbuf, (uint64_t)c.max_width * c.max_height);
   FA_ALLOC(ctx->bigbits, (T + 31) / 32);
   FA_ALLOC(ctx->queue, ctx->queue_cap);
+  ctx->tile_cap = 4u * ctx->queue_cap;
+  FA_ALLOC(ctx->tile_owner, ctx->tile_cap);
   FA_ALLOC(ctx->label, T + V);
   FA_ALLOC(ctx->cid, T);
   FA_ALLOC(ctx->blockcnt, nblocks + 1);
   FA_ALLOC(ctx->box_enc, 4 * C);
   FA_ALLOC(ctx->box_full, C);
-  FA_ALLOC(ctx->ord_counts, (uint64_t)kMaxH * ctx->max_order_tiles);
-  FA_ALLOC(ctx->ord_rank, C);
-  FA_ALLOC(ctx->ord_binstart, kMaxH);
-  FA_ALLOC(ctx->order, C);
-  FA_ALLOC(ctx->cand_P, (uint64_t)kMaxScales * C);
-  FA_ALLOC(ctx->cand_wh, (uint64_t)kMaxScales * C);
-  FA_ALLOC(ctx->cand_xy, (uint64_t)kMaxScales * C);
-  FA_ALLOC(ctx->cand_rows, (uint64_t)kMaxScales * C);
-  FA_ALLOC(ctx->cand, kMaxScales);
-  FA_ALLOC(ctx->res, 1);
-  FA_ALLOC(ctx->place, C);
+  FA_ALLOC(pk.ord_counts, (uint64_t)kMaxH * pk.max_tiles);
+  FA_ALLOC(pk.ord_rank, C);
+  FA_ALLOC(pk.ord_total, kMaxH);
+  FA_ALLOC(pk.ord_binstart, kMaxH);
+  FA_ALLOC(pk.order, C);
+  FA_ALLOC(pk.tile_tot, (uint64_t)kMaxScales * pk.max_tiles);
+  FA_ALLOC(pk.rec, (uint64_t)kMaxScales * C);
+  FA_ALLOC(pk.m, kMaxScales);
+  FA_ALLOC(pk.xy, (uint64_t)kMaxScales * C);
+  FA_ALLOC(pk.cand, kMaxScales);
 #undef FA_ALLOC
+  pk.ctr = ctx->ctr;
+  pk.count = nullptr;
   if (st == FA_OK && cudaMemset(ctx->ctr, 0, sizeof(DevCounters)) != cudaSuccess) st = FA_E_CUDA;
+  if (st == FA_OK && cudaMemset(pk.ord_total, 0, kMaxH * sizeof(uint32_t)) != cudaSuccess) st = FA_E_CUDA;
   if (st == FA_OK && cudaDeviceSynchronize() != cudaSuccess) st = FA_E_CUDA;
   if (st != FA_OK) {
     fa_destroy(ctx);

@@ -71,26 +71,67 @@ struct UfArgs {
   DevCounters* ctr;
 };
 
-// Edge mode init: label[t] = min(t, visible edge neighbours)  (Alg. 1, first loop).
-// Vertex mode init: label[t] = t for visible t; vertex nodes are set by k_uf_init_v.
-__global__ void __launch_bounds__(kBlock) k_uf_init(UfArgs a, int vertex_mode) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
-       w += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t word = __ldg(a.vt + w);
-    if (word == 0) continue;
-    const uint32_t t = (w << 5) + lane;
-    if (!((word >> lane) & 1u)) continue;
-    int32_t lab = (int32_t)t;
-    if (!vertex_mode) {
+// Union of the edges inside one tile of kTile consecutive triangles, in shared
+// memory, then label[t] = the tile-local root (its smallest triangle).  Replaces the
+// global init: afterwards every visible triangle points to a root, and only edges that
+// leave the tile remain for the global hooking.
+constexpr int kTile = 1024;
+
+__device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
+  int32_t cur = lab[x];
+  if (cur != x) {
+    int32_t prev = x, next;
+    while (cur > (next = lab[cur])) {
+      lab[prev] = next;
+      prev = cur;
+      cur = next;
+    }
+  }
+  return cur;
+}
+
+__global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
+  __shared__ int32_t lab[kTile];
+  __shared__ uint32_t vis[kTile / 32];
+  __shared__ uint32_t any;
+  const uint32_t base = blockIdx.x * kTile;
+  if (threadIdx.x == 0) any = 0;
+  __syncthreads();
+  if (threadIdx.x < kTile / 32) {
+    const uint32_t w = (base >> 5) + threadIdx.x;
+    const uint32_t v = w < ((a.T + 31) >> 5) ? __ldg(a.vt + w) : 0u;
+    vis[threadIdx.x] = v;
+    if (v) atomicOr(&any, 1u);
+  }
+  for (uint32_t i = threadIdx.x; i < kTile; i += kBlock) lab[i] = (int32_t)i;
+  __syncthreads();
+  if (!any) return;
+  volatile int32_t* vl = lab;
+  for (uint32_t i = threadIdx.x; i < kTile; i += kBlock) {
+    if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
+    const uint32_t t = base + i;
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
-        if (n >= 0 && n < lab && vt_bit(a.vt, (uint32_t)n)) lab = n;
+    for (int j = 0; j < 3; ++j) {
+      const int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
+      if (n <= (int32_t)t || (uint32_t)n >= base + kTile) continue;
+      const uint32_t ni = (uint32_t)n - base;
+      if (!((vis[ni >> 5] >> (ni & 31)) & 1u)) continue;
+      int32_t ra = lfind(vl, (int32_t)i), rb = lfind(vl, (int32_t)ni);
+      while (ra != rb) {
+        const int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
+        const int32_t old = atomicCAS(lab + hi, hi, lo);
+        if (old == hi) break;
+        ra = lfind(vl, old);
+        rb = lfind(vl, lo);
       }
     }
-    a.label[t] = lab;
+  }
+  __syncthreads();
+  for (uint32_t i = threadIdx.x; i < kTile; i += kBlock) {
+    if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
+    int32_t r = (int32_t)i, nx;
+    while ((nx = vl[r]) != r) r = nx;
+    a.label[base + i] = (int32_t)base + r;
   }
 }
 
@@ -119,7 +160,9 @@ __global__ void __launch_bounds__(kBlock) k_uf_hook(UfArgs a, int vertex_mode) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
-        if (n > (int32_t)t && vt_bit(a.vt, (uint32_t)n)) unite(a.label, (int32_t)t, n, a.ctr);
+        // edges inside a tile were joined by k_uf_local
+        if (n > (int32_t)t && ((uint32_t)n / kTile) != (t / kTile) && vt_bit(a.vt, (uint32_t)n))
+          unite(a.label, (int32_t)t, n, a.ctr);
       }
     }
   }
@@ -287,8 +330,8 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
     mark(ctx, "k_uf_init_v", s);
     k_uf_init_v<<<grid_for(mesh->V, 256, 152 * 8), 256, 0, s>>>(ctx->label, mesh->T, mesh->V);
   }
-  mark(ctx, "k_uf_init", s);
-  k_uf_init<<<gw, kBlock, 0, s>>>(a, vm);
+  mark(ctx, "k_uf_local", s);
+  k_uf_local<<<(mesh->T + kTile - 1) / kTile, kBlock, 0, s>>>(a);
   mark(ctx, "k_uf_hook", s);
   k_uf_hook<<<gw, kBlock, 0, s>>>(a, vm);
   if (!vm && mesh->n_nm) {

@@ -52,6 +52,32 @@ struct PackCand {
   int32_t status;   // FA_OK / FA_E_CAPACITY
 };
 
+// One scaled box of one candidate: exclusive prefix P of the widths, w, h.
+struct BoxRec {
+  unsigned long long P;
+  uint32_t w, h;
+};
+static_assert(sizeof(BoxRec) == 16, "BoxRec is one 16-byte record");
+
+// Scratch of the order + pack kernels (context memory, or the static array of
+// fa_pack_noalloc).
+struct PackScratch {
+  DevCounters* ctr;
+  const uint32_t* count;        // device box count
+  uint32_t max_boxes;
+  uint32_t max_tiles;           // ceil(max_boxes / 1024)
+  uint32_t* ord_counts;         // [max_tiles][kMaxH]
+  uint32_t* ord_rank;           // [max_boxes]
+  uint32_t* ord_total;          // [kMaxH], zero between calls
+  uint32_t* ord_binstart;       // [kMaxH]
+  uint32_t* order;              // [max_boxes] when the caller passes none
+  unsigned long long* tile_tot; // [kMaxScales][max_tiles]
+  BoxRec* rec;                  // [kMaxScales][max_boxes]
+  uint32_t* m;                  // [kMaxScales] largest overflow
+  uint2* xy;                    // [kMaxScales][max_boxes]
+  PackCand* cand;               // [kMaxScales]
+};
+
 }  // namespace fa
 
 constexpr int kMaxProf = 64;
@@ -71,23 +97,15 @@ struct fa_ctx {
   uint32_t* bigbits;     // [ceil(max_tris/32)]
   fa::BigTri* queue;     // [queue_cap]
   uint32_t queue_cap;
+  uint32_t* tile_owner;  // [tile_cap] queue record of each 16x16 tile
+  uint32_t tile_cap;
   int32_t* label;        // [max_tris + max_verts]
   int32_t* cid;          // [max_tris] chart id of root triangles
   uint32_t* blockcnt;    // [n_blocks + 1]
   uint32_t* box_enc;     // [max_charts * 4] ordered-int chart boxes
   uint32_t* box_full;    // [max_charts]
-  uint32_t* ord_counts;  // [kMaxH * max_order_tiles]
-  uint32_t* ord_rank;    // [max_charts]
-  uint32_t* ord_binstart;  // [kMaxH]
-  uint32_t* order;       // [max_charts] (used when the caller passes none)
-  uint32_t max_order_tiles;
-  unsigned long long* cand_P;  // [kMaxScales * max_charts]
-  uint2* cand_wh;        // [kMaxScales * max_charts]
-  uint2* cand_xy;        // [kMaxScales * max_charts]
-  uint32_t* cand_rows;   // [kMaxScales * max_charts] first box of each row group
-  fa::PackCand* cand;    // [kMaxScales]
-  fa_pack_result* res;   // internal result when the caller passes none
-  fa_placement* place;   // internal placements
+  fa::PackScratch pack;  // order + pack scratch (count filled per call)
+  int pack_smem_set;
 };
 
 struct fa_mesh {
@@ -205,5 +223,10 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
                     uint32_t n_scales, float* uv, float* affine, cudaStream_t s);
 fa_status build_adjacency(fa_ctx* ctx, fa_mesh* mesh, cudaStream_t s);
+fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
+                              uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
+                              uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
+                              cudaStream_t s);
+fa_status pack_set_smem_limit();
 
 }  // namespace fa

@@ -3,28 +3,32 @@
 // Order: stable counting sort of the boxes by integer height
 //   h0 = clamp(ceil(fb / 256), 1, 8192), tallest first, ties by box index (the
 //   boxes arrive numbered by ascending root, so this is the paper's
-//   (height, lowest triangle id) order).  Three kernels: per 1024-box tile a
-//   bitonic sort of (bin, index) keys gives stable in-tile ranks and a per-bin
-//   count row; one block scans the counts over tiles and bins; a scatter writes the
-//   order.  This replaces the paper's cuckoo-hash bucketing with the same result
-//   contract (deterministic, identical for identical frames).
+//   (height, lowest triangle id) order).  k_order_tile bitonic-sorts the
+//   (bin, index) keys of each 1024-box tile, giving stable in-tile ranks, a per-bin
+//   count row per tile and global bin totals; k_order_binscan scans the totals;
+//   k_order_scatter adds, for each box, the counts of its bin in earlier tiles.
+//   This replaces the paper's cuckoo-hash bucketing with the same result contract
+//   (deterministic, identical for identical frames).
 //
-// Pack: one CTA per candidate scale k / n (Sec. 4.2).  Phase 1 computes the scaled
-//   integer boxes, the exclusive prefix sum P of the widths (block scan, 64-bit),
-//   rows P >> log2(omega), in-row offsets and the largest overflow m (Sec. 4.3);
-//   Omega = omega + m.  Phase 2 pushes the rows up against a frontline kept in
-//   shared memory: a row's texels are processed in parallel, each thread finding
-//   its box by binary search over the row's staged offsets, a shared-memory
-//   atomicMax giving each box its resting height, then the frontline is
-//   overwritten with the box tops.  The last CTA to finish selects the candidate
-//   and writes the placements.
+// Pack: candidates k / n, k = 1..n (Sec. 4.2).  The per-box work is spread over
+//   (tile, candidate) CTAs: k_pack_boxes computes the scaled integer boxes and
+//   tile-local exclusive prefix sums of the widths; k_pack_fix adds the tile's
+//   offset (a block reduction over the preceding tile totals), giving P, and
+//   reduces the largest overflow m past omega (Sec. 4.3).  Then one CTA per
+//   candidate (k_pack_push) pushes the rows up against a frontline in shared
+//   memory: boxes are staged 1024 at a time with cp.async (double buffered), the
+//   rows inside a chunk are found by a block scan, and each row segment is processed
+//   box-parallel (a warp per box for rows of at most 32 boxes, a thread per box
+//   otherwise): resting height = max of the frontline under the box, then the
+//   frontline takes the box top.  Segments of one row never overlap in x, so a row
+//   may span two chunks.  The last CTA to finish selects the candidate and writes
+//   the placements.
 #include "fa_internal.cuh"
 
 namespace fa {
 namespace {
 
-constexpr int kPackThreads = 1024;
-constexpr int kStage = 2048;  // boxes staged per row chunk
+constexpr int kThreads = 1024;
 
 __device__ __forceinline__ uint32_t height_bin(uint32_t fb) {
   uint32_t h = (uint32_t)(((uint64_t)fb + 255u) >> 8);
@@ -32,150 +36,7 @@ __device__ __forceinline__ uint32_t height_bin(uint32_t fb) {
   return kMaxH - h;  // ascending bin = descending height
 }
 
-// ------------------------------------------------------------------ order
-
-__global__ void __launch_bounds__(kOrderTile) k_order_tile(const uint32_t* __restrict__ fb,
-                                                           const uint32_t* count, uint32_t max_charts,
-                                                           uint32_t* counts, uint32_t* rank,
-                                                           DevCounters* ctr) {
-  __shared__ uint32_t key[kOrderTile];
-  __shared__ uint32_t cnt[kMaxH];
-  __shared__ uint16_t first[kMaxH];
-  if (__ldcg(&ctr->status) != 0) return;
-  const uint32_t C = __ldcg(count);
-  if (C > max_charts) return;
-  const uint32_t ntiles = (C + kOrderTile - 1) / kOrderTile;
-  if (blockIdx.x >= ntiles) return;
-  const uint32_t tid = threadIdx.x;
-  const uint32_t i = blockIdx.x * kOrderTile + tid;
-  key[tid] = i < C ? (height_bin(__ldg(fb + i)) << 10) | tid : 0xFFFFFFFFu;
-  for (uint32_t b = tid; b < kMaxH; b += kOrderTile) cnt[b] = 0;
-  __syncthreads();
-  // bitonic sort, ascending
-  for (uint32_t size = 2; size <= kOrderTile; size <<= 1) {
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      const uint32_t j = tid ^ stride;
-      if (j > tid) {
-        const uint32_t a = key[tid], b = key[j];
-        const bool up = (tid & size) == 0;
-        if ((a > b) == up) {
-          key[tid] = b;
-          key[j] = a;
-        }
-      }
-      __syncthreads();
-    }
-  }
-  const uint32_t k = key[tid];
-  const bool valid = k != 0xFFFFFFFFu;
-  const uint32_t bin = k >> 10;
-  if (valid && (tid == 0 || (key[tid - 1] >> 10) != bin)) first[bin] = (uint16_t)tid;
-  __syncthreads();
-  if (valid) {
-    const uint32_t r = tid - first[bin];
-    rank[blockIdx.x * kOrderTile + (k & 1023u)] = r;
-    if (tid == kOrderTile - 1 || (key[tid + 1] >> 10) != bin) cnt[bin] = r + 1;
-  }
-  __syncthreads();
-  uint32_t* row = counts + (size_t)blockIdx.x * kMaxH;
-  for (uint32_t b = tid; b < kMaxH; b += kOrderTile) row[b] = cnt[b];
-}
-
-// counts[t][b] -> exclusive prefix over tiles; binstart[b] = exclusive prefix over bins.
-__global__ void __launch_bounds__(1024) k_order_scan(const uint32_t* count, uint32_t max_charts,
-                                                     uint32_t* counts, uint32_t* binstart,
-                                                     DevCounters* ctr) {
-  __shared__ uint32_t wt[32];
-  if (__ldcg(&ctr->status) != 0) return;
-  const uint32_t C = __ldcg(count);
-  if (C > max_charts) return;
-  const uint32_t ntiles = (C + kOrderTile - 1) / kOrderTile;
-  constexpr uint32_t kPer = kMaxH / 1024;
-  uint32_t tot[kPer];
-  uint32_t sum = 0;
-#pragma unroll
-  for (uint32_t j = 0; j < kPer; ++j) {
-    const uint32_t b = threadIdx.x * kPer + j;
-    uint32_t run = 0;
-    for (uint32_t t = 0; t < ntiles; ++t) {
-      uint32_t* p = counts + (size_t)t * kMaxH + b;
-      const uint32_t c = *p;
-      *p = run;
-      run += c;
-    }
-    tot[j] = run;
-    sum += run;
-  }
-  // block exclusive scan of the per-thread sums
-  uint32_t x = sum;
-  const uint32_t lane = threadIdx.x & 31;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= (unsigned)o) x += y;
-  }
-  if (lane == 31) wt[threadIdx.x >> 5] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint32_t v = wt[threadIdx.x];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, v, o);
-      if (threadIdx.x >= (unsigned)o) v += y;
-    }
-    wt[threadIdx.x] = v;
-  }
-  __syncthreads();
-  uint32_t run = (threadIdx.x >= 32 ? wt[(threadIdx.x >> 5) - 1] : 0) + x - sum;
-#pragma unroll
-  for (uint32_t j = 0; j < kPer; ++j) {
-    binstart[threadIdx.x * kPer + j] = run;
-    run += tot[j];
-  }
-}
-
-__global__ void __launch_bounds__(kOrderTile) k_order_scatter(const uint32_t* __restrict__ fb,
-                                                              const uint32_t* count, uint32_t max_charts,
-                                                              const uint32_t* counts, const uint32_t* rank,
-                                                              const uint32_t* binstart, uint32_t* order,
-                                                              DevCounters* ctr) {
-  if (__ldcg(&ctr->status) != 0) return;
-  const uint32_t C = __ldcg(count);
-  if (C > max_charts) return;
-  const uint32_t i = blockIdx.x * kOrderTile + threadIdx.x;
-  if (i >= C) return;
-  const uint32_t bin = height_bin(__ldg(fb + i));
-  const uint32_t pos = __ldcg(binstart + bin) + __ldcg(counts + (size_t)blockIdx.x * kMaxH + bin) + __ldcg(rank + i);
-  if (pos < C) order[pos] = i;
-}
-
-// ------------------------------------------------------------------ pack
-
-struct PackArgs {
-  const uint32_t* fa;
-  const uint32_t* fb;
-  const uint32_t* count;
-  const uint32_t* order;
-  uint32_t max_charts;
-  uint32_t atlas_log2;
-  uint32_t n_scales;
-  uint32_t shift;  // log2(256 * n_scales)
-  uint32_t min_box;
-  uint32_t gutter;
-  uint32_t select_mode;
-  uint32_t front_cap;
-  unsigned long long* P;  // [n_scales][max_charts]
-  uint2* wh;
-  uint2* xy;
-  uint32_t* rows;
-  PackCand* cand;
-  DevCounters* ctr;
-  fa_placement* place;
-  fa_pack_result* res;
-};
-
-// Block-wide inclusive scan (1024 threads) of a 64-bit value; returns the
-// inclusive prefix and writes the block total to *total.
+// Block-wide inclusive scan (1024 threads); writes the block total to *total.
 template <typename T>
 __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T* total) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -203,284 +64,438 @@ __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T* total) {
   return r;
 }
 
-__global__ void __launch_bounds__(kPackThreads) k_pack(PackArgs a) {
-  extern __shared__ uint32_t smem[];
-  uint32_t* F = smem;                      // [front_cap]
-  uint32_t* s_xr = F + a.front_cap;        // [kStage]
-  uint32_t* s_w = s_xr + kStage;
-  uint32_t* s_h = s_w + kStage;
-  uint32_t* s_y = s_h + kStage;
-  __shared__ unsigned long long ws64[32];
-  __shared__ uint32_t ws32[32];
-  __shared__ uint32_t s_flag;
-  __shared__ uint32_t s_last;
+template <typename T>
+__device__ __forceinline__ T block_max(T v, T* warp_vals) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    T y = __shfl_xor_sync(0xFFFFFFFFu, v, o);
+    v = v > y ? v : y;
+  }
+  if ((threadIdx.x & 31) == 0) warp_vals[threadIdx.x >> 5] = v;
+  __syncthreads();
+  T r = warp_vals[0];
+  for (int w = 1; w < (int)(blockDim.x >> 5); ++w) r = r > warp_vals[w] ? r : warp_vals[w];
+  __syncthreads();
+  return r;
+}
 
-  const uint32_t k = blockIdx.x + 1;
+// ------------------------------------------------------------------ order
+
+__global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const uint32_t* __restrict__ fb) {
+  __shared__ uint32_t key[kOrderTile];
+  __shared__ uint16_t first[kMaxH];
+  if (__ldcg(&p.ctr->status) != 0) return;
+  const uint32_t C = __ldcg(p.count);
+  if (C > p.max_boxes) return;
+  const uint32_t ntiles = (C + kOrderTile - 1) / kOrderTile;
+  if (blockIdx.x >= ntiles) return;
   const uint32_t tid = threadIdx.x;
-  const int32_t st0 = __ldcg(&a.ctr->status);
-  if (st0 != 0) {
-    if (blockIdx.x == 0 && tid == 0) {
-      a.res->k = 0;
-      a.res->omega = 0;
-      a.res->height = 0;
-      a.res->status = st0;
-      a.res->count = 0;
+  const uint32_t i = blockIdx.x * kOrderTile + tid;
+  key[tid] = i < C ? (height_bin(__ldg(fb + i)) << 10) | tid : 0xFFFFFFFFu;
+  uint32_t* row = p.ord_counts + (size_t)blockIdx.x * kMaxH;
+  for (uint32_t b = tid; b < kMaxH; b += kOrderTile) row[b] = 0;
+  __syncthreads();
+  for (uint32_t size = 2; size <= kOrderTile; size <<= 1) {  // bitonic sort, ascending
+    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+      const uint32_t j = tid ^ stride;
+      if (j > tid) {
+        const uint32_t a = key[tid], b = key[j];
+        if ((a > b) == ((tid & size) == 0)) {
+          key[tid] = b;
+          key[j] = a;
+        }
+      }
+      __syncthreads();
     }
+  }
+  const uint32_t k = key[tid];
+  const bool valid = k != 0xFFFFFFFFu;
+  const uint32_t bin = k >> 10;
+  if (valid && (tid == 0 || (key[tid - 1] >> 10) != bin)) first[bin] = (uint16_t)tid;
+  __syncthreads();
+  if (valid) {
+    const uint32_t r = tid - first[bin];
+    p.ord_rank[blockIdx.x * kOrderTile + (k & 1023u)] = r;
+    if (tid == kOrderTile - 1 || (key[tid + 1] >> 10) != bin) {
+      row[bin] = r + 1;
+      atomicAdd(p.ord_total + bin, r + 1);
+    }
+  }
+}
+
+// binstart = exclusive scan of the bin totals; the totals are cleared for the next call.
+__global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
+  __shared__ uint32_t wt[32];
+  if (__ldcg(&p.ctr->status) != 0) return;
+  constexpr uint32_t kPer = kMaxH / 1024;
+  uint4* t4 = reinterpret_cast<uint4*>(p.ord_total) + threadIdx.x * (kPer / 4);
+  uint32_t v[kPer];
+#pragma unroll
+  for (uint32_t j = 0; j < kPer / 4; ++j) {
+    const uint4 q = __ldcg(t4 + j);
+    v[4 * j] = q.x;
+    v[4 * j + 1] = q.y;
+    v[4 * j + 2] = q.z;
+    v[4 * j + 3] = q.w;
+    t4[j] = make_uint4(0, 0, 0, 0);
+  }
+  uint32_t sum = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kPer; ++j) sum += v[j];
+  uint32_t tot;
+  const uint32_t incl = block_scan_incl<uint32_t>(sum, wt, &tot);
+  uint32_t run = incl - sum;
+  uint4* b4 = reinterpret_cast<uint4*>(p.ord_binstart) + threadIdx.x * (kPer / 4);
+#pragma unroll
+  for (uint32_t j = 0; j < kPer / 4; ++j) {
+    uint4 q;
+    q.x = run; run += v[4 * j];
+    q.y = run; run += v[4 * j + 1];
+    q.z = run; run += v[4 * j + 2];
+    q.w = run; run += v[4 * j + 3];
+    b4[j] = q;
+  }
+}
+
+__global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, const uint32_t* __restrict__ fb,
+                                                              uint32_t* order) {
+  if (__ldcg(&p.ctr->status) != 0) return;
+  const uint32_t C = __ldcg(p.count);
+  if (C > p.max_boxes) return;
+  const uint32_t i = blockIdx.x * kOrderTile + threadIdx.x;
+  if (i >= C) return;
+  const uint32_t bin = height_bin(__ldg(fb + i));
+  uint32_t pos = __ldcg(p.ord_binstart + bin) + __ldcg(p.ord_rank + i);
+  uint32_t t = 0;
+  for (; t + 4 <= blockIdx.x; t += 4) {
+    const uint32_t* c = p.ord_counts + (size_t)t * kMaxH + bin;
+    pos += __ldcg(c) + __ldcg(c + kMaxH) + __ldcg(c + 2 * kMaxH) + __ldcg(c + 3 * kMaxH);
+  }
+  for (; t < blockIdx.x; ++t) pos += __ldcg(p.ord_counts + (size_t)t * kMaxH + bin);
+  if (pos < C) order[pos] = i;
+}
+
+// ------------------------------------------------------------------ pack
+
+struct PackArgs {
+  const uint32_t* fa;
+  const uint32_t* fb;
+  const uint32_t* order;
+  uint32_t atlas_log2;
+  uint32_t shift;  // log2(256 * n_scales)
+  uint32_t min_box;
+  uint32_t gutter;
+  uint32_t select_mode;
+  uint32_t front_cap;
+  fa_placement* place;
+  fa_pack_result* res;
+};
+
+// Scaled boxes and tile-local exclusive prefix of the widths.  Persistent grid over
+// (tile, candidate) work items.
+__global__ void __launch_bounds__(kThreads) k_pack_boxes(PackScratch p, PackArgs a, uint32_t n_scales) {
+  __shared__ unsigned long long ws[32];
+  if (__ldcg(&p.ctr->status) != 0) return;
+  const uint32_t C = __ldcg(p.count);
+  if (C > p.max_boxes) return;
+  if (blockIdx.x == 0 && threadIdx.x < n_scales) p.m[threadIdx.x] = 0;
+  const uint32_t ntiles = (C + kThreads - 1) / kThreads;
+  const unsigned long long d = (1ull << a.shift) - 1ull;
+  for (uint32_t item = blockIdx.x; item < ntiles * n_scales; item += gridDim.x) {
+    const uint32_t kidx = item / ntiles, tile = item % ntiles, k = kidx + 1;
+    const uint32_t i = tile * kThreads + threadIdx.x;
+    uint32_t w = 0, h = 0;
+    if (i < C) {
+      const uint32_t b = __ldg(a.order + i);
+      const uint32_t sw = (uint32_t)(((unsigned long long)k * __ldg(a.fa + b) + d) >> a.shift);
+      const uint32_t sh = (uint32_t)(((unsigned long long)k * __ldg(a.fb + b) + d) >> a.shift);
+      w = (sw > a.min_box ? sw : a.min_box) + 2u * a.gutter;
+      h = (sh > a.min_box ? sh : a.min_box) + 2u * a.gutter;
+    }
+    unsigned long long tot;
+    const unsigned long long incl = block_scan_incl<unsigned long long>(w, ws, &tot);
+    BoxRec* rec = p.rec + (size_t)kidx * p.max_boxes;
+    if (i < C) rec[i] = BoxRec{incl - w, w, h};
+    if (threadIdx.x == 0) p.tile_tot[(size_t)kidx * p.max_tiles + tile] = tot;
+  }
+}
+
+// Global prefix P (tile offset + local) and the largest overflow past omega.
+__global__ void __launch_bounds__(kThreads) k_pack_fix(PackScratch p, PackArgs a, uint32_t n_scales) {
+  __shared__ unsigned long long ws[32];
+  __shared__ uint32_t wm[32];
+  if (__ldcg(&p.ctr->status) != 0) return;
+  const uint32_t C = __ldcg(p.count);
+  if (C > p.max_boxes) return;
+  const uint32_t ntiles = (C + kThreads - 1) / kThreads;
+  const uint32_t om = 1u << a.atlas_log2;
+  for (uint32_t item = blockIdx.x; item < ntiles * n_scales; item += gridDim.x) {
+    const uint32_t kidx = item / ntiles, tile = item % ntiles;
+    const unsigned long long* tt = p.tile_tot + (size_t)kidx * p.max_tiles;
+    unsigned long long off = 0;
+    for (uint32_t t = threadIdx.x; t < tile; t += kThreads) off += __ldcg(tt + t);
+    unsigned long long total;
+    block_scan_incl<unsigned long long>(off, ws, &total);
+    const uint32_t i = tile * kThreads + threadIdx.x;
+    uint32_t m = 0;
+    if (i < C) {
+      BoxRec* r = p.rec + (size_t)kidx * p.max_boxes + i;
+      BoxRec v = *r;
+      v.P += total;
+      r->P = v.P;
+      const uint32_t xr = (uint32_t)(v.P & (om - 1));
+      if (xr + v.w > om) m = xr + v.w - om;
+    }
+    m = block_max<uint32_t>(m, wm);
+    if (threadIdx.x == 0 && m) atomicMax(p.m + kidx, m);
+  }
+}
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Row push of one candidate per CTA, then the last CTA selects.
+__global__ void __launch_bounds__(kThreads) k_pack_push(PackScratch p, PackArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                        // [2][kThreads]
+  uint32_t* s_y = reinterpret_cast<uint32_t*>(buf + 2 * kThreads);        // [kThreads]
+  uint32_t* s_seg = s_y + kThreads;                                         // [kThreads + 1]
+  uint32_t* F = s_seg + kThreads + 4;                                       // [front_cap]
+  __shared__ uint32_t ws32[32];
+  __shared__ uint32_t s_flag, s_nseg, s_last, s_best;
+  __shared__ int32_t s_status;
+
+  const uint32_t kidx = blockIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int32_t st0 = __ldcg(&p.ctr->status);
+  if (st0 != 0) {
+    if (kidx == 0 && tid == 0) *a.res = fa_pack_result{0, 0, 0, st0, 0};
     return;
   }
-  const uint32_t C = __ldcg(a.count);
+  const uint32_t C = __ldcg(p.count);
   const uint32_t om = 1u << a.atlas_log2;
-  unsigned long long* P = a.P + (size_t)blockIdx.x * a.max_charts;
-  uint2* wh = a.wh + (size_t)blockIdx.x * a.max_charts;
-  uint2* xy = a.xy + (size_t)blockIdx.x * a.max_charts;
-  uint32_t* rows = a.rows + (size_t)blockIdx.x * a.max_charts;
   int32_t status = FA_OK;
   uint32_t Om = om, H = 0, ok = 0;
-  if (C > a.max_charts) {
+  if (C > p.max_boxes) {
     status = FA_E_CAPACITY;
   } else {
-    // ---- phase 1: scaled boxes, prefix sum, rows, overflow
-    unsigned long long carry = 0;
-    uint32_t gcarry = 0;
-    unsigned long long prev_row = ~0ull;
-    uint32_t m = 0;
-    const uint32_t g2 = 2u * a.gutter;
-    for (uint32_t base = 0; base < C; base += kPackThreads) {
-      const uint32_t i = base + tid;
-      uint32_t w = 0, h = 0;
-      if (i < C) {
-        const uint32_t b = __ldg(a.order + i);
-        const unsigned long long d = (1ull << a.shift) - 1ull;
-        uint32_t sw = (uint32_t)(((unsigned long long)k * __ldg(a.fa + b) + d) >> a.shift);
-        uint32_t sh = (uint32_t)(((unsigned long long)k * __ldg(a.fb + b) + d) >> a.shift);
-        w = (sw > a.min_box ? sw : a.min_box) + g2;
-        h = (sh > a.min_box ? sh : a.min_box) + g2;
-      }
-      unsigned long long tot;
-      const unsigned long long incl = block_scan_incl<unsigned long long>(w, ws64, &tot);
-      const unsigned long long Pi = carry + incl - w;
-      const unsigned long long row = Pi >> a.atlas_log2;
-      // row of the previous box (across the chunk boundary via prev_row)
-      unsigned long long rprev = __shfl_up_sync(0xFFFFFFFFu, row, 1);
-      if ((tid & 31) == 0) rprev = 0;  // fixed below
-      __shared__ unsigned long long s_lastrow[32];
-      if ((tid & 31) == 31) s_lastrow[tid >> 5] = row;
-      __syncthreads();
-      if ((tid & 31) == 0) rprev = (tid == 0) ? prev_row : s_lastrow[(tid >> 5) - 1];
-      const uint32_t start = (i < C && row != rprev) ? 1u : 0u;
-      uint32_t gtot;
-      const uint32_t gincl = block_scan_incl<uint32_t>(start, ws32, &gtot);
-      if (i < C) {
-        const uint32_t xr = (uint32_t)(Pi & (om - 1));
-        if (xr + w > om) m = max(m, xr + w - om);
-        P[i] = Pi;
-        wh[i] = make_uint2(w, h);
-        if (start) rows[gcarry + gincl - 1] = i;
-      }
-      carry += tot;
-      gcarry += gtot;
-      __syncthreads();
-      const uint32_t last = min(C - base, (uint32_t)kPackThreads) - 1;
-      if (tid == last) s_lastrow[0] = row;
-      __syncthreads();
-      prev_row = s_lastrow[0];
-      __syncthreads();
-    }
-    // ---- overflow -> Omega
-    m = __reduce_max_sync(0xFFFFFFFFu, m);
-    if ((tid & 31) == 0) ws32[tid >> 5] = m;
-    __syncthreads();
-    if (tid < 32) {
-      uint32_t v = __reduce_max_sync(0xFFFFFFFFu, ws32[tid]);
-      if (tid == 0) ws32[0] = v;
-    }
-    __syncthreads();
-    m = ws32[0];
-    __syncthreads();
-    Om = om + m;
-    const uint32_t G = gcarry;
+    Om = om + __ldcg(p.m + kidx);
     if (Om > a.front_cap) {
       status = FA_E_CAPACITY;
     } else {
-      // ---- phase 2: push rows up against the frontline
-      for (uint32_t x = tid; x < Om; x += kPackThreads) F[x] = 0;
+      const BoxRec* rec = p.rec + (size_t)kidx * p.max_boxes;
+      uint2* xy = p.xy + (size_t)kidx * p.max_boxes;
+      for (uint32_t x = tid; x < Om; x += kThreads) F[x] = 0;
       if (tid == 0) s_flag = 0;
       uint32_t Hloc = 0;
+      const uint32_t nchunks = (C + kThreads - 1) / kThreads;
+      if (nchunks) {
+        if (tid < C) cp_async16(buf + tid, rec + tid);
+        cp_async_commit();
+      }
       __syncthreads();
-      for (uint32_t g = 0; g < G && !s_flag; ++g) {
-        const uint32_t s0 = __ldcg(rows + g);
-        const uint32_t e0 = (g + 1 < G) ? __ldcg(rows + g + 1) : C;
-        const unsigned long long q = __ldcg(P + s0) >> a.atlas_log2;
-        const unsigned long long qbase = q << a.atlas_log2;
-        const bool l2r = (q % 3ull) == 0ull;
-        for (uint32_t cs = s0; cs < e0; cs += kStage) {
-          const uint32_t n = min(e0 - cs, (uint32_t)kStage);
-          for (uint32_t j = tid; j < n; j += kPackThreads) {
-            const uint2 v = __ldcg(wh + cs + j);
-            s_xr[j] = (uint32_t)(__ldcg(P + cs + j) - qbase);
-            s_w[j] = v.x;
-            s_h[j] = v.y;
-            s_y[j] = 0;
-          }
-          __syncthreads();
-          const uint32_t o0 = s_xr[0];
-          const uint32_t L = s_xr[n - 1] + s_w[n - 1] - o0;
-          // pass A: resting height of each box = max frontline under it
-          for (uint32_t u = tid; u < L; u += kPackThreads) {
-            const uint32_t o = o0 + u;
-            uint32_t lo = 0, hi = n;  // last j with s_xr[j] <= o
-            while (hi - lo > 1) {
-              const uint32_t mid = (lo + hi) >> 1;
-              if (s_xr[mid] <= o) lo = mid;
-              else hi = mid;
-            }
-            const uint32_t x = l2r ? o : Om - 1 - o;
-            atomicMax(s_y + lo, F[x]);
-          }
-          __syncthreads();
-          // pass B: frontline := top of the box; record the placement
-          for (uint32_t u = tid; u < L; u += kPackThreads) {
-            const uint32_t o = o0 + u;
-            uint32_t lo = 0, hi = n;
-            while (hi - lo > 1) {
-              const uint32_t mid = (lo + hi) >> 1;
-              if (s_xr[mid] <= o) lo = mid;
-              else hi = mid;
-            }
-            const uint32_t x = l2r ? o : Om - 1 - o;
-            F[x] = s_y[lo] + s_h[lo];
-          }
-          for (uint32_t j = tid; j < n; j += kPackThreads) {
-            const uint32_t y = s_y[j], top = y + s_h[j];
-            const uint32_t x = l2r ? s_xr[j] : Om - s_xr[j] - s_w[j];
-            xy[cs + j] = make_uint2(x, y);
-            Hloc = max(Hloc, top);
-            if (top > Om) s_flag = 1;
-          }
-          __syncthreads();
+      for (uint32_t c = 0; c < nchunks; ++c) {
+        const uint32_t base = c * kThreads;
+        const uint32_t n = min(C - base, (uint32_t)kThreads);
+        BoxRec* cur = buf + (c & 1) * kThreads;
+        if (c + 1 < nchunks) {
+          const uint32_t nb = base + kThreads + tid;
+          if (nb < C) cp_async16(buf + ((c + 1) & 1) * kThreads + tid, rec + nb);
         }
+        cp_async_commit();
+        cp_async_wait1();
+        __syncthreads();
+        // row segments inside the chunk
+        uint32_t flag = 0;
+        if (tid < n) {
+          const unsigned long long q = cur[tid].P >> a.atlas_log2;
+          flag = (tid == 0 || (cur[tid - 1].P >> a.atlas_log2) != q) ? 1u : 0u;
+        }
+        uint32_t nseg;
+        const uint32_t si = block_scan_incl<uint32_t>(flag, ws32, &nseg);
+        if (flag) s_seg[si - 1] = tid;
+        if (tid == 0) {
+          s_seg[nseg] = n;
+          s_nseg = nseg;
+        }
+        __syncthreads();
+        for (uint32_t sgi = 0; sgi < s_nseg; ++sgi) {
+          const uint32_t j0 = s_seg[sgi], j1 = s_seg[sgi + 1], nbx = j1 - j0;
+          const bool l2r = ((cur[j0].P >> a.atlas_log2) % 3ull) == 0ull;
+          if (nbx <= 32) {
+            if (wid < nbx) {
+              const BoxRec r = cur[j0 + wid];
+              const uint32_t xr = (uint32_t)(r.P & (om - 1));
+              const uint32_t x = l2r ? xr : Om - xr - r.w;
+              uint32_t mx = 0;
+              for (uint32_t u = lane; u < r.w; u += 32) mx = max(mx, F[x + u]);
+              mx = __reduce_max_sync(0xFFFFFFFFu, mx);
+              if (lane == 0) s_y[j0 + wid] = mx;
+            }
+          } else {
+            for (uint32_t j = j0 + tid; j < j1; j += kThreads) {
+              const BoxRec r = cur[j];
+              const uint32_t xr = (uint32_t)(r.P & (om - 1));
+              const uint32_t x = l2r ? xr : Om - xr - r.w;
+              uint32_t mx = 0;
+              for (uint32_t u = 0; u < r.w; ++u) mx = max(mx, F[x + u]);
+              s_y[j] = mx;
+            }
+          }
+          __syncthreads();
+          if (nbx <= 32) {
+            if (wid < nbx) {
+              const uint32_t j = j0 + wid;
+              const BoxRec r = cur[j];
+              const uint32_t xr = (uint32_t)(r.P & (om - 1));
+              const uint32_t x = l2r ? xr : Om - xr - r.w;
+              const uint32_t y = s_y[j], top = y + r.h;
+              for (uint32_t u = lane; u < r.w; u += 32) F[x + u] = top;
+              if (lane == 0) {
+                xy[base + j] = make_uint2(x, y);
+                Hloc = max(Hloc, top);
+                if (top > Om) s_flag = 1;
+              }
+            }
+          } else {
+            for (uint32_t j = j0 + tid; j < j1; j += kThreads) {
+              const BoxRec r = cur[j];
+              const uint32_t xr = (uint32_t)(r.P & (om - 1));
+              const uint32_t x = l2r ? xr : Om - xr - r.w;
+              const uint32_t y = s_y[j], top = y + r.h;
+              for (uint32_t u = 0; u < r.w; ++u) F[x + u] = top;
+              xy[base + j] = make_uint2(x, y);
+              Hloc = max(Hloc, top);
+              if (top > Om) s_flag = 1;
+            }
+          }
+          __syncthreads();
+          if (s_flag) break;
+        }
+        if (s_flag) break;
+        __syncthreads();  // the buffer of this chunk is refilled two chunks later
       }
-      Hloc = __reduce_max_sync(0xFFFFFFFFu, Hloc);
-      if ((tid & 31) == 0) ws32[tid >> 5] = Hloc;
-      __syncthreads();
-      if (tid < 32) {
-        uint32_t v = __reduce_max_sync(0xFFFFFFFFu, ws32[tid]);
-        if (tid == 0) ws32[0] = v;
-      }
-      __syncthreads();
-      H = ws32[0];
+      cp_async_wait0();
+      H = block_max<uint32_t>(Hloc, ws32);
       ok = (!s_flag && H <= Om) ? 1u : 0u;
     }
   }
-  // ---- publish this candidate; the last CTA selects
+  // publish this candidate; the last CTA selects
   if (tid == 0) {
-    a.cand[blockIdx.x] = PackCand{ok, Om, H, status};
+    p.cand[kidx] = PackCand{ok, Om, H, status};
     __threadfence();
-    const uint32_t done = atomicAdd(&a.ctr->pack_done, 1u);
+    const uint32_t done = atomicAdd(&p.ctr->pack_done, 1u);
     s_last = (done == gridDim.x - 1) ? 1u : 0u;
   }
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  __shared__ uint32_t s_best;
-  __shared__ int32_t s_status;
   if (tid == 0) {
-    uint32_t best = 0;
+    uint32_t best = 0, bestOm = 0;
     int32_t pst = FA_OK;
-    uint32_t bestOm = 0;
     for (uint32_t kk = 1; kk <= gridDim.x; ++kk) {
-      const uint4 cv = __ldcg(reinterpret_cast<const uint4*>(a.cand) + (kk - 1));
-      const PackCand c{cv.x, cv.y, cv.z, (int32_t)cv.w};
-      if (c.status != FA_OK) pst = c.status;
-      if (!c.ok) continue;
+      const uint4 cv = __ldcg(reinterpret_cast<const uint4*>(p.cand) + (kk - 1));
+      if ((int32_t)cv.w != FA_OK) pst = (int32_t)cv.w;
+      if (!cv.x) continue;
       if (best == 0 || a.select_mode == FA_SELECT_LARGEST_K ||
-          (unsigned long long)kk * bestOm >= (unsigned long long)best * c.omega) {
+          (unsigned long long)kk * bestOm >= (unsigned long long)best * cv.y) {
         best = kk;
-        bestOm = c.omega;
+        bestOm = cv.y;
       }
     }
     if (pst == FA_OK && best == 0) pst = FA_E_PACK_FAILED;
-    s_best = pst == FA_OK ? best : 0;
-    s_status = pst;
-    fa_pack_result r;
-    r.count = C;
-    r.status = pst;
+    fa_pack_result r{0, 0, 0, pst, C};
     if (pst == FA_OK) {
-      const uint4 cv = __ldcg(reinterpret_cast<const uint4*>(a.cand) + (best - 1));
-      const PackCand c{cv.x, cv.y, cv.z, (int32_t)cv.w};
+      const uint4 cv = __ldcg(reinterpret_cast<const uint4*>(p.cand) + (best - 1));
       r.k = best;
-      r.omega = c.omega;
-      r.height = c.height;
-    } else {
-      r.k = 0;
-      r.omega = 0;
-      r.height = 0;
+      r.omega = cv.y;
+      r.height = cv.z;
     }
     *a.res = r;
-    a.ctr->pack_done = 0;
+    s_best = pst == FA_OK ? best : 0;
+    s_status = pst;
+    p.ctr->pack_done = 0;
   }
   __syncthreads();
   if (s_status != FA_OK) return;
   const uint32_t kb = s_best - 1;
-  const uint2* bxy = a.xy + (size_t)kb * a.max_charts;
-  const uint2* bwh = a.wh + (size_t)kb * a.max_charts;
-  for (uint32_t i = tid; i < C; i += kPackThreads) {
+  const uint2* bxy = p.xy + (size_t)kb * p.max_boxes;
+  const BoxRec* brec = p.rec + (size_t)kb * p.max_boxes;
+  for (uint32_t i = tid; i < C; i += kThreads) {
     const uint32_t b = __ldcg(a.order + i);
-    const uint2 p = __ldcg(bxy + i), s = __ldcg(bwh + i);
-    a.place[b] = fa_placement{(int32_t)p.x, (int32_t)p.y, (int32_t)s.x, (int32_t)s.y};
+    const uint2 q = __ldcg(bxy + i);
+    const BoxRec r = brec[i];
+    a.place[b] = fa_placement{(int32_t)q.x, (int32_t)q.y, (int32_t)r.w, (int32_t)r.h};
   }
+}
+
+size_t push_smem_bytes(uint32_t front_cap) {
+  return (size_t)2 * kThreads * sizeof(BoxRec) + (size_t)(2 * kThreads + 4) * 4 + (size_t)front_cap * 4;
 }
 
 }  // namespace
 
-fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
-                      uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* order,
-                      fa_placement* place, fa_pack_result* res, cudaStream_t s) {
-  const uint32_t maxc = ctx->cfg.max_charts;
-  const uint32_t ntiles = (maxc + kOrderTile - 1) / kOrderTile;
-  uint32_t* ord = order ? order : ctx->order;
-  mark(ctx, "k_order_tile", s);
-  k_order_tile<<<ntiles, kOrderTile, 0, s>>>(fb, count, maxc, ctx->ord_counts, ctx->ord_rank, ctx->ctr);
-  mark(ctx, "k_order_scan", s);
-  k_order_scan<<<1, 1024, 0, s>>>(count, maxc, ctx->ord_counts, ctx->ord_binstart, ctx->ctr);
-  mark(ctx, "k_order_scatter", s);
-  k_order_scatter<<<ntiles, kOrderTile, 0, s>>>(fb, count, maxc, ctx->ord_counts, ctx->ord_rank,
-                                                ctx->ord_binstart, ord, ctx->ctr);
+fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
+                              uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
+                              uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
+                              cudaStream_t s) {
+  uint32_t* ord = order ? order : p.order;
+  if (ctx) mark(ctx, "k_order_tile", s);
+  k_order_tile<<<p.max_tiles, kOrderTile, 0, s>>>(p, fb);
+  if (ctx) mark(ctx, "k_order_binscan", s);
+  k_order_binscan<<<1, 1024, 0, s>>>(p);
+  if (ctx) mark(ctx, "k_order_scatter", s);
+  k_order_scatter<<<p.max_tiles, kOrderTile, 0, s>>>(p, fb, ord);
   PackArgs a;
   a.fa = fa_;
   a.fb = fb;
-  a.count = count;
   a.order = ord;
-  a.max_charts = maxc;
   a.atlas_log2 = atlas_log2;
-  a.n_scales = n_scales;
   uint32_t sh = 8;
   while ((1u << (sh - 8)) < n_scales) ++sh;
   a.shift = sh;
-  a.min_box = ctx->cfg.min_box;
-  a.gutter = ctx->cfg.gutter;
+  a.min_box = min_box;
+  a.gutter = gutter;
   a.select_mode = select_mode;
   const uint32_t om = 1u << atlas_log2;
   a.front_cap = (8u * om < kFrontCap) ? 8u * om : kFrontCap;
-  a.P = ctx->cand_P;
-  a.wh = ctx->cand_wh;
-  a.xy = ctx->cand_xy;
-  a.rows = ctx->cand_rows;
-  a.cand = ctx->cand;
-  a.ctr = ctx->ctr;
   a.place = place;
   a.res = res;
-  const size_t smem = (size_t)a.front_cap * 4 + (size_t)kStage * 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    FA_CUDA_TRY(cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     (int)((size_t)kFrontCap * 4 + (size_t)kStage * 16)));
-    attr_set = true;
-  }
-  mark(ctx, "k_pack", s);
-  k_pack<<<n_scales, kPackThreads, smem, s>>>(a);
+  const uint32_t items = p.max_tiles * n_scales;
+  const unsigned g2 = items < 152u * 2u ? items : 152u * 2u;
+  if (ctx) mark(ctx, "k_pack_boxes", s);
+  k_pack_boxes<<<g2, kThreads, 0, s>>>(p, a, n_scales);
+  if (ctx) mark(ctx, "k_pack_fix", s);
+  k_pack_fix<<<g2, kThreads, 0, s>>>(p, a, n_scales);
+  if (ctx) mark(ctx, "k_pack_push", s);
+  k_pack_push<<<n_scales, kThreads, push_smem_bytes(a.front_cap), s>>>(p, a);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
+}
+
+fa_status pack_set_smem_limit() {
+  FA_CUDA_TRY(cudaFuncSetAttribute(k_pack_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)push_smem_bytes(kFrontCap)));
+  return FA_OK;
+}
+
+fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
+                      uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* order,
+                      fa_placement* place, fa_pack_result* res, cudaStream_t s) {
+  if (!ctx->pack_smem_set) {
+    fa_status st = pack_set_smem_limit();
+    if (st != FA_OK) return st;
+    ctx->pack_smem_set = 1;
+  }
+  PackScratch p = ctx->pack;
+  p.count = count;
+  return launch_pack_kernels(ctx, p, fa_, fb, atlas_log2, n_scales, select_mode, ctx->cfg.min_box,
+                             ctx->cfg.gutter, order, place, res, s);
 }
 
 }  // namespace fa
@@ -508,15 +523,16 @@ constexpr size_t align256(size_t x) { return (x + 255) & ~size_t(255); }
 constexpr size_t kOffCtr = 0;
 constexpr size_t kOffCount = align256(kOffCtr + sizeof(DevCounters));
 constexpr size_t kOffCand = align256(kOffCount + sizeof(uint32_t));
-constexpr size_t kOffCounts = align256(kOffCand + sizeof(PackCand) * kMaxScales);
+constexpr size_t kOffM = align256(kOffCand + sizeof(PackCand) * kMaxScales);
+constexpr size_t kOffCounts = align256(kOffM + sizeof(uint32_t) * kMaxScales);
 constexpr size_t kOffRank = align256(kOffCounts + sizeof(uint32_t) * kMaxH * kNoAllocTiles);
-constexpr size_t kOffBinstart = align256(kOffRank + sizeof(uint32_t) * kNoAllocMaxBoxes);
+constexpr size_t kOffTotal = align256(kOffRank + sizeof(uint32_t) * kNoAllocMaxBoxes);
+constexpr size_t kOffBinstart = align256(kOffTotal + sizeof(uint32_t) * kMaxH);
 constexpr size_t kOffOrder = align256(kOffBinstart + sizeof(uint32_t) * kMaxH);
-constexpr size_t kOffP = align256(kOffOrder + sizeof(uint32_t) * kNoAllocMaxBoxes);
-constexpr size_t kOffWH = align256(kOffP + sizeof(unsigned long long) * kMaxScales * kNoAllocMaxBoxes);
-constexpr size_t kOffXY = align256(kOffWH + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
-constexpr size_t kOffRows = align256(kOffXY + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
-constexpr size_t kNoAllocBytes = align256(kOffRows + sizeof(uint32_t) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kOffTileTot = align256(kOffOrder + sizeof(uint32_t) * kNoAllocMaxBoxes);
+constexpr size_t kOffRec = align256(kOffTileTot + sizeof(unsigned long long) * kMaxScales * kNoAllocTiles);
+constexpr size_t kOffXY = align256(kOffRec + sizeof(BoxRec) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kNoAllocBytes = align256(kOffXY + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
 
 // The scratch of fa_pack_noalloc.  Host code must not use this name as a device
 // address: it is a host-side shadow there; the device address comes from
@@ -528,7 +544,7 @@ std::mutex g_noalloc_mutex;
 unsigned char* g_noalloc_ptr[kNoAllocMaxDevices] = {};
 
 // Once per device, with that device current: the array's device address, and the
-// pack kernel's shared-memory limit.
+// push kernel's shared-memory limit.
 fa_status noalloc_scratch(int dev, unsigned char** out) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return FA_E_INVALID_ARG;
   std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -538,8 +554,7 @@ fa_status noalloc_scratch(int dev, unsigned char** out) {
       cudaGetLastError();
       return FA_E_CUDA;
     }
-    if (cudaFuncSetAttribute(k_pack, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)((size_t)kFrontCap * 4 + (size_t)kStage * 16)) != cudaSuccess) {
+    if (pack_set_smem_limit() != FA_OK) {
       cudaGetLastError();
       return FA_E_CUDA;
     }
@@ -549,12 +564,15 @@ fa_status noalloc_scratch(int dev, unsigned char** out) {
   return FA_OK;
 }
 
-// Clears what the kernels expect at zero (status word, finished-candidate counter)
-// and stores the box count where the kernels read it.
-__global__ void k_noalloc_reset(DevCounters* ctr, uint32_t* count, uint32_t n) {
-  ctr->status = 0;
-  ctr->pack_done = 0;
-  *count = n;
+// Clears what the kernels expect at zero (status word, finished-candidate counter,
+// bin totals) and stores the box count where the kernels read it.
+__global__ void k_noalloc_reset(DevCounters* ctr, uint32_t* count, uint32_t* total, uint32_t n) {
+  if (threadIdx.x == 0) {
+    ctr->status = 0;
+    ctr->pack_done = 0;
+    *count = n;
+  }
+  for (uint32_t b = threadIdx.x; b < kMaxH; b += blockDim.x) total[b] = 0;
 }
 
 }  // namespace
@@ -580,43 +598,22 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   fa_status st = noalloc_scratch(dev, &base);
   if (st != FA_OK) return st;
   cudaStream_t s = (cudaStream_t)stream;
-  DevCounters* ctr = (DevCounters*)(base + kOffCtr);
-  uint32_t* count = (uint32_t*)(base + kOffCount);
-  uint32_t* counts = (uint32_t*)(base + kOffCounts);
-  uint32_t* rank = (uint32_t*)(base + kOffRank);
-  uint32_t* binstart = (uint32_t*)(base + kOffBinstart);
-  uint32_t* ord = d_order ? d_order : (uint32_t*)(base + kOffOrder);
-  k_noalloc_reset<<<1, 1, 0, s>>>(ctr, count, n);
-  k_order_tile<<<kNoAllocTiles, kOrderTile, 0, s>>>(d_fb, count, kNoAllocMaxBoxes, counts, rank, ctr);
-  k_order_scan<<<1, 1024, 0, s>>>(count, kNoAllocMaxBoxes, counts, binstart, ctr);
-  k_order_scatter<<<kNoAllocTiles, kOrderTile, 0, s>>>(d_fb, count, kNoAllocMaxBoxes, counts, rank, binstart,
-                                                       ord, ctr);
-  PackArgs a;
-  a.fa = d_fa;
-  a.fb = d_fb;
-  a.count = count;
-  a.order = ord;
-  a.max_charts = kNoAllocMaxBoxes;
-  a.atlas_log2 = atlas_log2;
-  a.n_scales = n_scales;
-  uint32_t sh = 8;
-  while ((1u << (sh - 8)) < n_scales) ++sh;
-  a.shift = sh;
-  a.min_box = min_box;
-  a.gutter = gutter;
-  a.select_mode = select_mode;
-  const uint32_t om = 1u << atlas_log2;
-  a.front_cap = (8u * om < kFrontCap) ? 8u * om : kFrontCap;
-  a.P = (unsigned long long*)(base + kOffP);
-  a.wh = (uint2*)(base + kOffWH);
-  a.xy = (uint2*)(base + kOffXY);
-  a.rows = (uint32_t*)(base + kOffRows);
-  a.cand = (PackCand*)(base + kOffCand);
-  a.ctr = ctr;
-  a.place = d_place;
-  a.res = d_res;
-  const size_t smem = (size_t)a.front_cap * 4 + (size_t)kStage * 16;
-  k_pack<<<n_scales, kPackThreads, smem, s>>>(a);
-  if (cudaGetLastError() != cudaSuccess) return FA_E_CUDA;
-  return FA_OK;
+  PackScratch p;
+  p.ctr = (DevCounters*)(base + kOffCtr);
+  p.count = (uint32_t*)(base + kOffCount);
+  p.max_boxes = kNoAllocMaxBoxes;
+  p.max_tiles = kNoAllocTiles;
+  p.ord_counts = (uint32_t*)(base + kOffCounts);
+  p.ord_rank = (uint32_t*)(base + kOffRank);
+  p.ord_total = (uint32_t*)(base + kOffTotal);
+  p.ord_binstart = (uint32_t*)(base + kOffBinstart);
+  p.order = (uint32_t*)(base + kOffOrder);
+  p.tile_tot = (unsigned long long*)(base + kOffTileTot);
+  p.rec = (BoxRec*)(base + kOffRec);
+  p.m = (uint32_t*)(base + kOffM);
+  p.xy = (uint2*)(base + kOffXY);
+  p.cand = (PackCand*)(base + kOffCand);
+  k_noalloc_reset<<<1, 256, 0, s>>>(p.ctr, (uint32_t*)p.count, p.ord_total, n);
+  return launch_pack_kernels(nullptr, p, d_fa, d_fb, atlas_log2, n_scales, select_mode, min_box, gutter, d_order,
+                             d_place, d_res, s);
 }

@@ -154,6 +154,8 @@ struct RasterArgs {
   uint32_t* bigbits;
   BigTri* queue;
   uint32_t queue_cap;
+  uint32_t* tile_owner;  // queue record of each reserved tile
+  uint32_t tile_cap;
   DevCounters* ctr;
   uint32_t* vt;
 };
@@ -179,7 +181,7 @@ __device__ bool raster_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n)
       unsigned long long old =
           atomicAdd(&A.ctr->big, ((unsigned long long)nq << 40) | (unsigned long long)tiles);
       uint64_t e0 = old >> 40, tile = old & ((1ull << 40) - 1);
-      if (e0 + nq <= A.queue_cap) {
+      if (e0 + nq <= A.queue_cap && tile + tiles <= A.tile_cap) {
         int q = 0;
         for (int i = 1; i + 1 < n; ++i) {
           Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
@@ -193,20 +195,23 @@ __device__ bool raster_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n)
           bt.tile0 = (uint32_t)tile;
           bt.pad = 0;
           A.queue[e0 + q] = bt;
-          int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
-          tile += (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
+          const int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
+          const uint64_t nt = (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
+          for (uint64_t j = 0; j < nt; ++j) A.tile_owner[tile + j] = (uint32_t)(e0 + q);
+          tile += nt;
           ++q;
         }
         return true;
       }
-      // queue full: entries reserved inside the capacity become empty records and
-      // the triangle is rasterized here instead
+      // queue or tile table full: reserved records become empty, reserved tiles get
+      // no owner, and the triangle is rasterized here instead
       for (uint64_t e = e0; e < e0 + nq && e < A.queue_cap; ++e) {
         BigTri bt = {};
         bt.px0 = 1; bt.px1 = 0; bt.py0 = 1; bt.py1 = 0;
         bt.tile0 = (uint32_t)tile;
         A.queue[e] = bt;
       }
+      for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
     }
   }
   for (int i = 1; i + 1 < n; ++i) {
@@ -321,14 +326,10 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
   const uint64_t n_ent = (st >> 40) < A.queue_cap ? (st >> 40) : A.queue_cap;
   const uint64_t n_tiles = st & ((1ull << 40) - 1);
   if (n_ent == 0) return;
-  for (uint64_t g = warp; g < n_tiles; g += nwarps) {
-    // last entry with tile0 <= g
-    uint64_t lo = 0, hi = n_ent;  // invariant: tile0[lo] <= g, answer in [lo, hi)
-    while (hi - lo > 1) {
-      uint64_t mid = (lo + hi) >> 1;
-      if (__ldg(&A.queue[mid].tile0) <= g) lo = mid;
-      else hi = mid;
-    }
+  const uint64_t n_used = n_tiles < A.tile_cap ? n_tiles : A.tile_cap;
+  for (uint64_t g = warp; g < n_used; g += nwarps) {
+    const uint32_t lo = __ldg(A.tile_owner + g);
+    if (lo >= n_ent) continue;
     const BigTri& q = A.queue[lo];
     const int px0 = q.px0, py0 = q.py0, px1 = q.px1, py1 = q.py1;
     if (px1 < px0 || py1 < py0) continue;
@@ -370,6 +371,8 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.bigbits = ctx->bigbits;
   A.queue = ctx->queue;
   A.queue_cap = ctx->queue_cap;
+  A.tile_owner = ctx->tile_owner;
+  A.tile_cap = ctx->tile_cap;
   A.ctr = ctx->ctr;
   A.vt = vt;
   const uint32_t npix = W * H;
