@@ -28,6 +28,7 @@ struct DevCounters {
   uint32_t pad0;
   unsigned long long big;  // big-triangle queue: entries << 40 | tiles
   uint32_t pack_done;      // candidate CTAs finished (last one selects)
+  uint32_t ncand;          // small sub-triangles recorded by the depth pre-pass
   uint32_t order_tiles;    // tiles of the current order pass
   uint32_t chart_count;    // scratch copy of the frame's chart count
   uint32_t n_groups[kMaxScales];
@@ -99,6 +100,8 @@ struct fa_ctx {
   uint32_t queue_cap;
   uint32_t* tile_owner;  // [tile_cap] queue record of each 16x16 tile
   uint32_t tile_cap;
+  void* cand;            // [cand_cap] 48-byte records of small sub-triangles
+  uint32_t cand_cap;
   int32_t* label;        // [max_tris + max_verts]
   int32_t* cid;          // [max_tris] chart id of root triangles
   uint32_t* blockcnt;    // [n_blocks + 1]

@@ -143,6 +143,17 @@ __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, i
   return false;
 }
 
+// One small sub-triangle that passed the depth pre-pass set-up: its snapped
+// vertices, depths and clamped pixel box, kept so that the marking pass does not
+// redo the set-up.  48 bytes: {X0, Y0, X1, Y1}, {X2, Y2, px0 | py0 << 16,
+// px1 | py1 << 16}, {z0, z1, z2, triangle}.
+struct CandTri {
+  int4 a;
+  int4 b;
+  float4 c;
+};
+static_assert(sizeof(CandTri) == 48, "CandTri is 48 bytes");
+
 struct RasterArgs {
   Mat4 M;
   const float* pos;
@@ -151,83 +162,106 @@ struct RasterArgs {
   int W, H;
   float hx, hy;
   uint32_t* zbuf;
-  uint32_t* bigbits;
   BigTri* queue;
   uint32_t queue_cap;
   uint32_t* tile_owner;  // queue record of each reserved tile
   uint32_t tile_cap;
+  CandTri* cand;
+  uint32_t cand_cap;
   DevCounters* ctr;
   uint32_t* vt;
 };
 
-// Rasterize the fan (sv[0], sv[i], sv[i+1]) of one mesh triangle t.
-// PASS 0: depth pre-pass; returns whether the sub-triangles went to the big queue.
-// PASS 1: marking pass of a triangle not in the queue; returns visibility.
-template <int PASS>
-__device__ bool raster_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n) {
-  if (PASS == 0) {
-    int nq = 0;
-    uint64_t tiles = 0;
-    bool big = false;
-    for (int i = 1; i + 1 < n; ++i) {
-      Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
-      if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
-      int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
-      if (w * h > kSmallMaxPix) big = true;
-      ++nq;
-      tiles += (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
-    }
-    if (big) {
-      unsigned long long old =
-          atomicAdd(&A.ctr->big, ((unsigned long long)nq << 40) | (unsigned long long)tiles);
-      uint64_t e0 = old >> 40, tile = old & ((1ull << 40) - 1);
-      if (e0 + nq <= A.queue_cap && tile + tiles <= A.tile_cap) {
-        int q = 0;
-        for (int i = 1; i + 1 < n; ++i) {
-          Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
-          if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
-          BigTri bt;
-          bt.X[0] = (int32_t)sv[0].X; bt.X[1] = (int32_t)sv[i].X; bt.X[2] = (int32_t)sv[i + 1].X;
-          bt.Y[0] = (int32_t)sv[0].Y; bt.Y[1] = (int32_t)sv[i].Y; bt.Y[2] = (int32_t)sv[i + 1].Y;
-          bt.zn[0] = sv[0].zn; bt.zn[1] = sv[i].zn; bt.zn[2] = sv[i + 1].zn;
-          bt.px0 = s.px0; bt.py0 = s.py0; bt.px1 = s.px1; bt.py1 = s.py1;
-          bt.tri = t;
-          bt.tile0 = (uint32_t)tile;
-          bt.pad = 0;
-          A.queue[e0 + q] = bt;
-          const int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
-          const uint64_t nt = (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
-          for (uint64_t j = 0; j < nt; ++j) A.tile_owner[tile + j] = (uint32_t)(e0 + q);
-          tile += nt;
-          ++q;
-        }
-        return true;
-      }
-      // queue or tile table full: reserved records become empty, reserved tiles get
-      // no owner, and the triangle is rasterized here instead
-      for (uint64_t e = e0; e < e0 + nq && e < A.queue_cap; ++e) {
-        BigTri bt = {};
-        bt.px0 = 1; bt.px1 = 0; bt.py0 = 1; bt.py1 = 0;
-        bt.tile0 = (uint32_t)tile;
-        A.queue[e] = bt;
-      }
-      for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
-    }
+__device__ __forceinline__ CandTri make_cand(const SV& a, const SV& b, const SV& c, const Setup& s, uint32_t t) {
+  CandTri r;
+  r.a = make_int4((int)a.X, (int)a.Y, (int)b.X, (int)b.Y);
+  r.b = make_int4((int)c.X, (int)c.Y, s.px0 | (s.py0 << 16), s.px1 | (s.py1 << 16));
+  r.c = make_float4(a.zn, b.zn, c.zn, __uint_as_float(t));
+  return r;
+}
+
+__device__ __forceinline__ void store_cand(const RasterArgs& A, uint32_t slot, const CandTri& r) {
+  if (slot < A.cand_cap) {
+    float4* d = reinterpret_cast<float4*>(A.cand + slot);
+    d[0] = make_float4(__int_as_float(r.a.x), __int_as_float(r.a.y), __int_as_float(r.a.z), __int_as_float(r.a.w));
+    d[1] = make_float4(__int_as_float(r.b.x), __int_as_float(r.b.y), __int_as_float(r.b.z), __int_as_float(r.b.w));
+    d[2] = r.c;
+  } else {
+    set_status(A.ctr, FA_E_CAPACITY);
   }
+}
+
+// Depth pre-pass of the fan (sv[0], sv[i], sv[i+1]) of one mesh triangle t.  Large
+// sub-triangles go to the tile queue; small ones are rasterized here and, when
+// `out` is given and the fan has a single sub-triangle, returned for the candidate
+// list (otherwise appended one by one).  Returns the number of records in `out`.
+__device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, CandTri* out) {
+  int nq = 0;
+  uint64_t tiles = 0;
+  bool big = false;
+  for (int i = 1; i + 1 < n; ++i) {
+    Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
+    if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
+    int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
+    if (w * h > kSmallMaxPix) big = true;
+    ++nq;
+    tiles += (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
+  }
+  if (nq == 0) return 0;
+  if (big) {
+    unsigned long long old = atomicAdd(&A.ctr->big, ((unsigned long long)nq << 40) | (unsigned long long)tiles);
+    uint64_t e0 = old >> 40, tile = old & ((1ull << 40) - 1);
+    if (e0 + nq <= A.queue_cap && tile + tiles <= A.tile_cap) {
+      int q = 0;
+      for (int i = 1; i + 1 < n; ++i) {
+        Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
+        if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
+        BigTri bt;
+        bt.X[0] = (int32_t)sv[0].X; bt.X[1] = (int32_t)sv[i].X; bt.X[2] = (int32_t)sv[i + 1].X;
+        bt.Y[0] = (int32_t)sv[0].Y; bt.Y[1] = (int32_t)sv[i].Y; bt.Y[2] = (int32_t)sv[i + 1].Y;
+        bt.zn[0] = sv[0].zn; bt.zn[1] = sv[i].zn; bt.zn[2] = sv[i + 1].zn;
+        bt.px0 = s.px0; bt.py0 = s.py0; bt.px1 = s.px1; bt.py1 = s.py1;
+        bt.tri = t;
+        bt.tile0 = (uint32_t)tile;
+        bt.pad = 0;
+        A.queue[e0 + q] = bt;
+        const int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
+        const uint64_t nt = (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
+        for (uint64_t j = 0; j < nt; ++j) A.tile_owner[tile + j] = (uint32_t)(e0 + q);
+        tile += nt;
+        ++q;
+      }
+      return 0;
+    }
+    // queue or tile table full: the reserved records become empty, the reserved
+    // tiles get no owner, and the sub-triangles are handled here instead
+    for (uint64_t e = e0; e < e0 + nq && e < A.queue_cap; ++e) {
+      BigTri bt = {};
+      bt.px0 = 1; bt.px1 = 0; bt.py0 = 1; bt.py1 = 0;
+      bt.tile0 = (uint32_t)tile;
+      A.queue[e] = bt;
+    }
+    for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
+  }
+  int nout = 0;
   for (int i = 1; i + 1 < n; ++i) {
     Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
     if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
     float invA = __fdiv_rn(1.0f, __ll2float_rn(s.A));
-    if (raster_rect<PASS>(sv[0], sv[i], sv[i + 1], invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W))
-      return true;
+    raster_rect<0>(sv[0], sv[i], sv[i + 1], invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W);
+    const CandTri r = make_cand(sv[0], sv[i], sv[i + 1], s, t);
+    if (out && nq == 1) {
+      *out = r;
+      nout = 1;
+    } else {
+      store_cand(A, atomicAdd(&A.ctr->ncand, 1u), r);
+    }
   }
-  return false;
+  return nout;
 }
 
 // Triangles that cross the near plane or the guard band (rare): clip first.
-template <int PASS>
-__device__ __noinline__ bool raster_clipped(const RasterArgs& A, uint32_t t, float4 c0, float4 c1,
-                                            float4 c2) {
+__device__ __noinline__ void depth_clipped(const RasterArgs& A, uint32_t t, float4 c0, float4 c1, float4 c2) {
   CV poly[kMaxPoly];
   poly[0] = CV{c0.x, c0.y, c0.z, c0.w};
   poly[1] = CV{c1.x, c1.y, c1.z, c1.w};
@@ -235,83 +269,139 @@ __device__ __noinline__ bool raster_clipped(const RasterArgs& A, uint32_t t, flo
   int n = clip_polygon(poly, 3);
   if (n < 0) {
     set_status(A.ctr, FA_E_CAPACITY);
-    return false;
+    return;
   }
-  if (n < 3) return false;
+  if (n < 3) return;
   for (int i = 0; i < n; ++i)
-    if (!(poly[i].w > 0.0f)) return false;
+    if (!(poly[i].w > 0.0f)) return;
   SV sv[kMaxPoly];
   for (int i = 0; i < n; ++i) sv[i] = project(poly[i], A.hx, A.hy);
-  return raster_fan<PASS>(A, t, sv, n);
+  depth_fan(A, t, sv, n, nullptr);
 }
 
-// Returns: PASS 0 -> whether the triangle went to the big queue;
-//          PASS 1 -> whether an in-thread sample passed the depth test.
-template <int PASS>
-__device__ bool raster_triangle(const RasterArgs& A, uint32_t t) {
+// Conservative test on approximate screen positions (correctly rounded 1/w, then
+// the same screen mapping): true when the triangle surely covers no sample or is
+// surely back-facing.  m bounds, per axis, the distance between the approximate
+// position and the exact snapped vertex: 1/512 px of snapping plus
+// (|ndc| + 1) * (size / 2) * 2^-20 for the different rounding of x * (1/w) and x / w
+// followed by the same +1 and scale.  Both tests only drop triangles the exact path
+// would drop, so results are unchanged.
+__device__ __forceinline__ bool surely_empty(const RasterArgs& A, const float4& c0, const float4& c1, const float4& c2) {
+  const float r0 = __frcp_rn(c0.w), r1 = __frcp_rn(c1.w), r2 = __frcp_rn(c2.w);
+  const float nx0 = c0.x * r0, nx1 = c1.x * r1, nx2 = c2.x * r2;
+  const float ny0 = c0.y * r0, ny1 = c1.y * r1, ny2 = c2.y * r2;
+  const float x0 = (nx0 + 1.0f) * A.hx, x1 = (nx1 + 1.0f) * A.hx, x2 = (nx2 + 1.0f) * A.hx;
+  const float y0 = (ny0 + 1.0f) * A.hy, y1 = (ny1 + 1.0f) * A.hy, y2 = (ny2 + 1.0f) * A.hy;
+  const float ax = fmaxf(fabsf(nx0), fmaxf(fabsf(nx1), fabsf(nx2))) + 1.0f;
+  const float ay = fmaxf(fabsf(ny0), fmaxf(fabsf(ny1), fabsf(ny2))) + 1.0f;
+  const float mx = 0.001953125f + ax * A.hx * 9.5367431640625e-7f + 1e-6f;
+  const float my = 0.001953125f + ay * A.hy * 9.5367431640625e-7f + 1e-6f;
+  // pixel centres p + 0.5 inside the widened box, clamped to the viewport
+  const float lo_x = fminf(x0, fminf(x1, x2)) - mx, hi_x = fmaxf(x0, fmaxf(x1, x2)) + mx;
+  const float lo_y = fminf(y0, fminf(y1, y2)) - my, hi_y = fmaxf(y0, fmaxf(y1, y2)) + my;
+  const float px0 = fmaxf(ceilf(lo_x - 0.5f), 0.0f), px1 = fminf(floorf(hi_x - 0.5f), (float)(A.W - 1));
+  const float py0 = fmaxf(ceilf(lo_y - 0.5f), 0.0f), py1 = fminf(floorf(hi_y - 0.5f), (float)(A.H - 1));
+  if (px0 > px1 || py0 > py1) return true;
+  // signed doubled area in px^2 against its error bound
+  const float e1x = x1 - x0, e1y = y1 - y0, e2x = x2 - x0, e2y = y2 - y0;
+  const float p1 = e1x * e2y, p2 = e1y * e2x;
+  const float area = p1 - p2;
+  const float m = fmaxf(mx, my);
+  const float bound = 2.0f * m * (fabsf(e1x) + fabsf(e1y) + fabsf(e2x) + fabsf(e2y)) + 24.0f * m * m +
+                      2.384185791015625e-7f * (fabsf(p1) + fabsf(p2)) + 1e-6f;
+  return area < -bound;
+}
+
+// Depth pre-pass for one mesh triangle; a single small sub-triangle is returned in
+// *out (1) for the warp to append, everything else is handled here (0).
+__device__ int depth_triangle(const RasterArgs& A, uint32_t t, CandTri* out) {
   const uint32_t* f = A.idx + 3 * (size_t)t;
   const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
-  float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
+  const float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
   // trivial reject: all vertices outside one side plane, or all behind the near plane
   // (no sample can be covered then: see the design notes on exactness)
   if ((c0.x > c0.w && c1.x > c1.w && c2.x > c2.w) || (c0.x < -c0.w && c1.x < -c1.w && c2.x < -c2.w) ||
       (c0.y > c0.w && c1.y > c1.w && c2.y > c2.w) || (c0.y < -c0.w && c1.y < -c1.w && c2.y < -c2.w) ||
       (__fadd_rn(c0.z, c0.w) < 0.0f && __fadd_rn(c1.z, c1.w) < 0.0f && __fadd_rn(c2.z, c2.w) < 0.0f))
-    return false;
+    return 0;
   const CV v0{c0.x, c0.y, c0.z, c0.w}, v1{c1.x, c1.y, c1.z, c1.w}, v2{c2.x, c2.y, c2.z, c2.w};
   bool outside = false;
 #pragma unroll
   for (int pl = 0; pl < 5; ++pl)
-    outside |= !(plane_dist(v0, pl) >= 0.0f) || !(plane_dist(v1, pl) >= 0.0f) ||
-               !(plane_dist(v2, pl) >= 0.0f);
-  if (outside) return raster_clipped<PASS>(A, t, c0, c1, c2);
-  if (!(v0.w > 0.0f) || !(v1.w > 0.0f) || !(v2.w > 0.0f)) return false;
+    outside |= !(plane_dist(v0, pl) >= 0.0f) || !(plane_dist(v1, pl) >= 0.0f) || !(plane_dist(v2, pl) >= 0.0f);
+  if (outside) {
+    depth_clipped(A, t, c0, c1, c2);
+    return 0;
+  }
+  if (!(v0.w > 0.0f) || !(v1.w > 0.0f) || !(v2.w > 0.0f)) return 0;
+  if (surely_empty(A, c0, c1, c2)) return 0;
   SV sv[3] = {project(v0, A.hx, A.hy), project(v1, A.hx, A.hy), project(v2, A.hx, A.hy)};
-  return raster_fan<PASS>(A, t, sv, 3);
+  return depth_fan(A, t, sv, 3, out);
 }
 
-__global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, DevCounters* ctr, int reset_status) {
+__global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __restrict__ vt, uint32_t nwords,
+                        DevCounters* ctr) {
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctr->big = 0ull;
-    if (reset_status) ctr->status = 0;
+    ctr->ncand = 0u;
   }
   uint4* z4 = reinterpret_cast<uint4*>(zbuf);
   const uint4 ff = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-  uint32_t n4 = n / 4;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += gridDim.x * blockDim.x) z4[i] = ff;
-  for (uint32_t i = n4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x)
-    zbuf[i] = 0xFFFFFFFFu;
+  const uint32_t n4 = n / 4;
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) z4[i] = ff;
+  for (uint32_t i = n4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) zbuf[i] = 0xFFFFFFFFu;
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride) vt[i] = 0u;
 }
 
-// Small-triangle pass: warp w handles triangles [32 w', 32 w' + 32) for w' = w,
-// w + nwarps, ...  PASS 0 writes the big-queue bits, PASS 1 the VT words.
-template <int PASS>
-__global__ void __launch_bounds__(256) k_raster(RasterArgs A) {
+// Depth pre-pass: one thread per triangle; warps append their single-sub-triangle
+// candidates with one atomic each.
+__global__ void __launch_bounds__(256) k_raster_depth(RasterArgs A) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t nwords = (A.T + 31) >> 5;
-  if (PASS == 1 && __ldcg(&A.ctr->status) != 0) {
-    for (uint32_t w = warp; w < nwords; w += nwarps)
-      if (lane == 0) A.vt[w] = 0u;
-    return;
-  }
-  for (uint32_t w = warp; w < nwords; w += nwarps) {
+  const uint32_t nchunks = (A.T + 31) >> 5;
+  for (uint32_t w = warp; w < nchunks; w += nwarps) {
     const uint32_t t = (w << 5) + lane;
-    bool flag = false;
-    if (t < A.T) {
-      if (PASS == 0) {
-        flag = raster_triangle<0>(A, t);
-      } else {
-        const bool big = (__ldg(A.bigbits + w) >> lane) & 1u;
-        if (!big) flag = raster_triangle<1>(A, t);
-      }
+    CandTri r;
+    int has = 0;
+    if (t < A.T) has = depth_triangle(A, t, &r);
+    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, has != 0);
+    if (ball == 0) continue;
+    uint32_t base = 0;
+    if (lane == 0) base = atomicAdd(&A.ctr->ncand, (uint32_t)__popc(ball));
+    base = __shfl_sync(0xFFFFFFFFu, base, 0);
+    if (has) store_cand(A, base + __popc(ball & ((1u << lane) - 1u)), r);
+  }
+}
+
+// Marking pass over the candidate list: a record is visible when one of its samples
+// has key <= the depth buffer; visible bits are OR-ed per VT word and warp.
+__global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
+  if (__ldcg(&A.ctr->status) != 0) return;
+  const uint32_t n = min(__ldcg(&A.ctr->ncand), A.cand_cap);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const uint32_t i = base + threadIdx.x;
+    bool vis = false;
+    uint32_t t = 0xFFFFFFFFu;
+    if (i < n) {
+      const float4* s = reinterpret_cast<const float4*>(A.cand + i);
+      const float4 fa = __ldcs(s), fb = __ldcs(s + 1), fc = __ldcs(s + 2);
+      const SV a{__float_as_int(fa.x), __float_as_int(fa.y), fc.x};
+      const SV b{__float_as_int(fa.z), __float_as_int(fa.w), fc.y};
+      const SV c{__float_as_int(fb.x), __float_as_int(fb.y), fc.z};
+      const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
+      t = __float_as_uint(fc.w);
+      const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
+      const float invA = __fdiv_rn(1.0f, __ll2float_rn(Ar));
+      vis = raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
+                           (int)(b1 >> 16), A.zbuf, A.W);
     }
-    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, flag);
-    if (lane == 0) {
-      if (PASS == 0) A.bigbits[w] = bits;
-      else A.vt[w] = bits;
-    }
+    const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, word);
+    const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << (t & 31)) : 0u);
+    if (vis && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicOr(A.vt + word, bits);
   }
 }
 
@@ -368,25 +458,26 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.hx = 0.5f * (float)W;
   A.hy = 0.5f * (float)H;
   A.zbuf = ctx->zbuf;
-  A.bigbits = ctx->bigbits;
   A.queue = ctx->queue;
   A.queue_cap = ctx->queue_cap;
   A.tile_owner = ctx->tile_owner;
   A.tile_cap = ctx->tile_cap;
+  A.cand = reinterpret_cast<CandTri*>(ctx->cand);
+  A.cand_cap = ctx->cand_cap;
   A.ctr = ctx->ctr;
   A.vt = vt;
   const uint32_t npix = W * H;
-  mark(ctx, "k_clear", s);
-  k_clear<<<grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s>>>(ctx->zbuf, npix, ctx->ctr, 0);
   const uint32_t nwords = (mesh->T + 31) / 32;
+  mark(ctx, "k_clear", s);
+  k_clear<<<grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s>>>(ctx->zbuf, npix, vt, nwords, ctx->ctr);
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_depth", s);
-  k_raster<0><<<g, 256, 0, s>>>(A);
+  k_raster_depth<<<g, 256, 0, s>>>(A);
   mark(ctx, "k_raster_depth_big", s);
   k_raster_big<0><<<gb, 256, 0, s>>>(A);
   mark(ctx, "k_raster_mark", s);
-  k_raster<1><<<g, 256, 0, s>>>(A);
+  k_raster_mark<<<152 * 8, 256, 0, s>>>(A);
   mark(ctx, "k_raster_mark_big", s);
   k_raster_big<1><<<gb, 256, 0, s>>>(A);
   FA_CUDA_TRY(cudaGetLastError());
