@@ -260,18 +260,45 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Row push of one candidate per CTA, then the last CTA selects.
-__global__ void __launch_bounds__(kThreads) k_pack_push(PackScratch p, PackArgs a) {
+constexpr int kPushThreads = 256;
+constexpr int kChunk = 1024;  // boxes staged per chunk
+constexpr int kPerThread = kChunk / kPushThreads;
+
+// Block (kPushThreads) exclusive scan of small counts; returns the exclusive prefix.
+__device__ __forceinline__ uint32_t push_scan(uint32_t v, uint32_t* ws, uint32_t* total) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+    if (lane >= (unsigned)o) x += y;
+  }
+  if (lane == 31) ws[wid] = x;
+  __syncthreads();
+  uint32_t pre = 0, tot = 0;
+#pragma unroll
+  for (int w = 0; w < kPushThreads / 32; ++w) {
+    const uint32_t t = ws[w];
+    pre += (w < (int)wid) ? t : 0u;
+    tot += t;
+  }
+  *total = tot;
+  __syncthreads();
+  return pre + x - v;
+}
+
+__global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                        // [2][kThreads]
-  uint32_t* s_y = reinterpret_cast<uint32_t*>(buf + 2 * kThreads);        // [kThreads]
-  uint32_t* s_seg = s_y + kThreads;                                         // [kThreads + 1]
-  uint32_t* F = s_seg + kThreads + 4;                                       // [front_cap]
+  BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                  // [2][kChunk]
+  uint32_t* s_y = reinterpret_cast<uint32_t*>(buf + 2 * kChunk);     // [kChunk]
+  uint32_t* s_seg = s_y + kChunk;                                      // [kChunk + 1]
+  uint32_t* F = s_seg + kChunk + 4;                                    // [front_cap]
   __shared__ uint32_t ws32[32];
   __shared__ uint32_t s_flag, s_nseg, s_last, s_best;
   __shared__ int32_t s_status;
 
   const uint32_t kidx = blockIdx.x;
-  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const uint32_t tid = threadIdx.x;
   const int32_t st0 = __ldcg(&p.ctr->status);
   if (st0 != 0) {
     if (kidx == 0 && tid == 0) *a.res = fa_pack_result{0, 0, 0, st0, 0};
@@ -290,35 +317,49 @@ __global__ void __launch_bounds__(kThreads) k_pack_push(PackScratch p, PackArgs 
     } else {
       const BoxRec* rec = p.rec + (size_t)kidx * p.max_boxes;
       uint2* xy = p.xy + (size_t)kidx * p.max_boxes;
-      for (uint32_t x = tid; x < Om; x += kThreads) F[x] = 0;
+      for (uint32_t x = tid; x < Om; x += kPushThreads) F[x] = 0;
       if (tid == 0) s_flag = 0;
       uint32_t Hloc = 0;
-      const uint32_t nchunks = (C + kThreads - 1) / kThreads;
+      const uint32_t nchunks = (C + kChunk - 1) / kChunk;
       if (nchunks) {
-        if (tid < C) cp_async16(buf + tid, rec + tid);
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e) {
+          const uint32_t j = tid + e * kPushThreads;
+          if (j < C) cp_async16(buf + j, rec + j);
+        }
         cp_async_commit();
       }
       __syncthreads();
       for (uint32_t c = 0; c < nchunks; ++c) {
-        const uint32_t base = c * kThreads;
-        const uint32_t n = min(C - base, (uint32_t)kThreads);
-        BoxRec* cur = buf + (c & 1) * kThreads;
+        const uint32_t base = c * kChunk;
+        const uint32_t n = min(C - base, (uint32_t)kChunk);
+        BoxRec* cur = buf + (c & 1) * kChunk;
         if (c + 1 < nchunks) {
-          const uint32_t nb = base + kThreads + tid;
-          if (nb < C) cp_async16(buf + ((c + 1) & 1) * kThreads + tid, rec + nb);
+          BoxRec* nxt = buf + ((c + 1) & 1) * kChunk;
+#pragma unroll
+          for (int e = 0; e < kPerThread; ++e) {
+            const uint32_t j = tid + e * kPushThreads;
+            if (base + kChunk + j < C) cp_async16(nxt + j, rec + base + kChunk + j);
+          }
         }
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
-        // row segments inside the chunk
-        uint32_t flag = 0;
-        if (tid < n) {
-          const unsigned long long q = cur[tid].P >> a.atlas_log2;
-          flag = (tid == 0 || (cur[tid - 1].P >> a.atlas_log2) != q) ? 1u : 0u;
+        // row segments inside the chunk: thread tid owns boxes 4 tid .. 4 tid + 3
+        uint32_t flags = 0, cnt = 0;
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e) {
+          const uint32_t j = tid * kPerThread + e;
+          if (j < n && (j == 0 || (cur[j - 1].P >> a.atlas_log2) != (cur[j].P >> a.atlas_log2))) {
+            flags |= 1u << e;
+            ++cnt;
+          }
         }
         uint32_t nseg;
-        const uint32_t si = block_scan_incl<uint32_t>(flag, ws32, &nseg);
-        if (flag) s_seg[si - 1] = tid;
+        uint32_t at = push_scan(cnt, ws32, &nseg);
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e)
+          if (flags & (1u << e)) s_seg[at++] = tid * kPerThread + e;
         if (tid == 0) {
           s_seg[nseg] = n;
           s_nseg = nseg;
@@ -327,61 +368,54 @@ __global__ void __launch_bounds__(kThreads) k_pack_push(PackScratch p, PackArgs 
         for (uint32_t sgi = 0; sgi < s_nseg; ++sgi) {
           const uint32_t j0 = s_seg[sgi], j1 = s_seg[sgi + 1], nbx = j1 - j0;
           const bool l2r = ((cur[j0].P >> a.atlas_log2) % 3ull) == 0ull;
-          if (nbx <= 32) {
-            if (wid < nbx) {
-              const BoxRec r = cur[j0 + wid];
+          // group of g threads per box: g = 32 for <= 8 boxes ... 1 for >= 256
+          uint32_t g = kPushThreads / nbx;
+          g = g >= 32 ? 32u : (g >= 16 ? 16u : (g >= 8 ? 8u : (g >= 4 ? 4u : (g >= 2 ? 2u : 1u))));
+          const uint32_t gid = tid / g, li = tid % g, per = kPushThreads / g;
+          for (uint32_t bb = 0; bb < nbx; bb += per) {
+            const uint32_t jj = bb + gid;
+            uint32_t mx = 0;
+            if (jj < nbx) {
+              const BoxRec r = cur[j0 + jj];
               const uint32_t xr = (uint32_t)(r.P & (om - 1));
               const uint32_t x = l2r ? xr : Om - xr - r.w;
-              uint32_t mx = 0;
-              for (uint32_t u = lane; u < r.w; u += 32) mx = max(mx, F[x + u]);
-              mx = __reduce_max_sync(0xFFFFFFFFu, mx);
-              if (lane == 0) s_y[j0 + wid] = mx;
+              for (uint32_t u = li; u < r.w; u += g) mx = max(mx, F[x + u]);
             }
-          } else {
-            for (uint32_t j = j0 + tid; j < j1; j += kThreads) {
-              const BoxRec r = cur[j];
-              const uint32_t xr = (uint32_t)(r.P & (om - 1));
-              const uint32_t x = l2r ? xr : Om - xr - r.w;
-              uint32_t mx = 0;
-              for (uint32_t u = 0; u < r.w; ++u) mx = max(mx, F[x + u]);
-              s_y[j] = mx;
-            }
+            for (uint32_t o = 1; o < g; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            if (jj < nbx && li == 0) s_y[j0 + jj] = mx;
           }
           __syncthreads();
-          if (nbx <= 32) {
-            if (wid < nbx) {
-              const uint32_t j = j0 + wid;
+          for (uint32_t bb = 0; bb < nbx; bb += per) {
+            const uint32_t jj = bb + gid;
+            if (jj < nbx) {
+              const uint32_t j = j0 + jj;
               const BoxRec r = cur[j];
               const uint32_t xr = (uint32_t)(r.P & (om - 1));
               const uint32_t x = l2r ? xr : Om - xr - r.w;
               const uint32_t y = s_y[j], top = y + r.h;
-              for (uint32_t u = lane; u < r.w; u += 32) F[x + u] = top;
-              if (lane == 0) {
+              for (uint32_t u = li; u < r.w; u += g) F[x + u] = top;
+              if (li == 0) {
                 xy[base + j] = make_uint2(x, y);
                 Hloc = max(Hloc, top);
                 if (top > Om) s_flag = 1;
               }
-            }
-          } else {
-            for (uint32_t j = j0 + tid; j < j1; j += kThreads) {
-              const BoxRec r = cur[j];
-              const uint32_t xr = (uint32_t)(r.P & (om - 1));
-              const uint32_t x = l2r ? xr : Om - xr - r.w;
-              const uint32_t y = s_y[j], top = y + r.h;
-              for (uint32_t u = 0; u < r.w; ++u) F[x + u] = top;
-              xy[base + j] = make_uint2(x, y);
-              Hloc = max(Hloc, top);
-              if (top > Om) s_flag = 1;
             }
           }
           __syncthreads();
           if (s_flag) break;
         }
         if (s_flag) break;
-        __syncthreads();  // the buffer of this chunk is refilled two chunks later
+        __syncthreads();  // this chunk's buffer is refilled two chunks later
       }
       cp_async_wait0();
-      H = block_max<uint32_t>(Hloc, ws32);
+      // block max of Hloc
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) Hloc = max(Hloc, __shfl_xor_sync(0xFFFFFFFFu, Hloc, o));
+      if ((tid & 31) == 0) ws32[tid >> 5] = Hloc;
+      __syncthreads();
+      H = 0;
+#pragma unroll
+      for (int w = 0; w < kPushThreads / 32; ++w) H = max(H, ws32[w]);
       ok = (!s_flag && H <= Om) ? 1u : 0u;
     }
   }
@@ -426,7 +460,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_push(PackScratch p, PackArgs 
   const uint32_t kb = s_best - 1;
   const uint2* bxy = p.xy + (size_t)kb * p.max_boxes;
   const BoxRec* brec = p.rec + (size_t)kb * p.max_boxes;
-  for (uint32_t i = tid; i < C; i += kThreads) {
+  for (uint32_t i = tid; i < C; i += kPushThreads) {
     const uint32_t b = __ldcg(a.order + i);
     const uint2 q = __ldcg(bxy + i);
     const BoxRec r = brec[i];
@@ -435,7 +469,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_push(PackScratch p, PackArgs 
 }
 
 size_t push_smem_bytes(uint32_t front_cap) {
-  return (size_t)2 * kThreads * sizeof(BoxRec) + (size_t)(2 * kThreads + 4) * 4 + (size_t)front_cap * 4;
+  return (size_t)2 * kChunk * sizeof(BoxRec) + (size_t)(2 * kChunk + 4) * 4 + (size_t)front_cap * 4;
 }
 
 }  // namespace
@@ -473,7 +507,7 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   if (ctx) mark(ctx, "k_pack_fix", s);
   k_pack_fix<<<g2, kThreads, 0, s>>>(p, a, n_scales);
   if (ctx) mark(ctx, "k_pack_push", s);
-  k_pack_push<<<n_scales, kThreads, push_smem_bytes(a.front_cap), s>>>(p, a);
+  k_pack_push<<<n_scales, kPushThreads, push_smem_bytes(a.front_cap), s>>>(p, a);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
