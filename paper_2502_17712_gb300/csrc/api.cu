@@ -83,7 +83,8 @@ void fa_destroy(fa_ctx* ctx) {
   if (ctx->prof_on)
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
-  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->label, ctx->cid, ctx->blockcnt,
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->clip,
+                  ctx->label, ctx->cid, ctx->blockcnt,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
                   p.order, p.tile_tot, p.rec, p.m, p.xy, p.cand};
   for (void* p : ptrs)
@@ -130,6 +131,8 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->tile_owner, ctx->tile_cap);
   ctx->cand_cap = (uint32_t)(T + 65536 < 0xFFFFFFFFull ? T + 65536 : 0xFFFFFFFFull);
   if (st == FA_OK) st = alloc((unsigned char**)&ctx->cand, (size_t)ctx->cand_cap * 48);
+  FA_ALLOC(ctx->surv, T);
+  FA_ALLOC(ctx->clip, T);
   FA_ALLOC(ctx->label, T + V);
   FA_ALLOC(ctx->cid, T);
   FA_ALLOC(ctx->blockcnt, nblocks + 1);

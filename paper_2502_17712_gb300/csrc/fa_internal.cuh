@@ -29,6 +29,8 @@ struct DevCounters {
   unsigned long long big;  // big-triangle queue: entries << 40 | tiles
   uint32_t pack_done;      // candidate CTAs finished (last one selects)
   uint32_t ncand;          // small sub-triangles recorded by the depth pre-pass
+  uint32_t nsurv;          // triangles that passed the raster front end
+  uint32_t nclip;          // triangles that need clipping
   uint32_t order_tiles;    // tiles of the current order pass
   uint32_t chart_count;    // scratch copy of the frame's chart count
   uint32_t n_groups[kMaxScales];
@@ -102,6 +104,8 @@ struct fa_ctx {
   uint32_t tile_cap;
   void* cand;            // [cand_cap] 48-byte records of small sub-triangles
   uint32_t cand_cap;
+  uint32_t* surv;        // [max_tris] raster survivors
+  uint32_t* clip;        // [max_tris] triangles to clip
   int32_t* label;        // [max_tris + max_verts]
   int32_t* cid;          // [max_tris] chart id of root triangles
   uint32_t* blockcnt;    // [n_blocks + 1]

@@ -260,38 +260,16 @@ __device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_g
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Row push of one candidate per CTA, then the last CTA selects.
-constexpr int kPushThreads = 256;
-constexpr int kChunk = 1024;  // boxes staged per chunk
-constexpr int kPerThread = kChunk / kPushThreads;
-
-// Block (kPushThreads) exclusive scan of small counts; returns the exclusive prefix.
-__device__ __forceinline__ uint32_t push_scan(uint32_t v, uint32_t* ws, uint32_t* total) {
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  uint32_t x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-    if (lane >= (unsigned)o) x += y;
-  }
-  if (lane == 31) ws[wid] = x;
-  __syncthreads();
-  uint32_t pre = 0, tot = 0;
-#pragma unroll
-  for (int w = 0; w < kPushThreads / 32; ++w) {
-    const uint32_t t = ws[w];
-    pre += (w < (int)wid) ? t : 0u;
-    tot += t;
-  }
-  *total = tot;
-  __syncthreads();
-  return pre + x - v;
-}
+constexpr int kPushThreads = 1024;
+constexpr int kChunk = 1024;  // boxes staged per chunk (one per thread)
 
 __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                  // [2][kChunk]
-  uint32_t* s_y = reinterpret_cast<uint32_t*>(buf + 2 * kChunk);     // [kChunk]
-  uint32_t* s_seg = s_y + kChunk;                                      // [kChunk + 1]
+  uint32_t* s_x = reinterpret_cast<uint32_t*>(buf + 2 * kChunk);     // [kChunk] box x
+  uint32_t* s_w = s_x + kChunk;                                        // [kChunk]
+  uint32_t* s_h = s_w + kChunk;                                        // [kChunk]
+  uint32_t* s_seg = s_h + kChunk;                                      // [kChunk + 1]
   uint32_t* F = s_seg + kChunk + 4;                                    // [front_cap]
   __shared__ uint32_t ws32[32];
   __shared__ uint32_t s_flag, s_nseg, s_last, s_best;
@@ -322,100 +300,68 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       uint32_t Hloc = 0;
       const uint32_t nchunks = (C + kChunk - 1) / kChunk;
       if (nchunks) {
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e) {
-          const uint32_t j = tid + e * kPushThreads;
-          if (j < C) cp_async16(buf + j, rec + j);
-        }
+        if (tid < C) cp_async16(buf + tid, rec + tid);
         cp_async_commit();
       }
-      __syncthreads();
       for (uint32_t c = 0; c < nchunks; ++c) {
         const uint32_t base = c * kChunk;
         const uint32_t n = min(C - base, (uint32_t)kChunk);
-        BoxRec* cur = buf + (c & 1) * kChunk;
-        if (c + 1 < nchunks) {
-          BoxRec* nxt = buf + ((c + 1) & 1) * kChunk;
-#pragma unroll
-          for (int e = 0; e < kPerThread; ++e) {
-            const uint32_t j = tid + e * kPushThreads;
-            if (base + kChunk + j < C) cp_async16(nxt + j, rec + base + kChunk + j);
-          }
-        }
+        const BoxRec* cur = buf + (c & 1) * kChunk;
+        if (c + 1 < nchunks && base + kChunk + tid < C)
+          cp_async16(buf + ((c + 1) & 1) * kChunk + tid, rec + base + kChunk + tid);
         cp_async_commit();
         cp_async_wait1();
         __syncthreads();
-        // row segments inside the chunk: thread tid owns boxes 4 tid .. 4 tid + 3
-        uint32_t flags = 0, cnt = 0;
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e) {
-          const uint32_t j = tid * kPerThread + e;
-          if (j < n && (j == 0 || (cur[j - 1].P >> a.atlas_log2) != (cur[j].P >> a.atlas_log2))) {
-            flags |= 1u << e;
-            ++cnt;
-          }
+        // per box: its x in the row's direction, w, h, and whether it starts a row
+        uint32_t flag = 0;
+        if (tid < n) {
+          const BoxRec r = cur[tid];
+          const unsigned long long q = r.P >> a.atlas_log2;
+          const uint32_t xr = (uint32_t)(r.P & (om - 1));
+          s_x[tid] = (q % 3ull == 0ull) ? xr : Om - xr - r.w;
+          s_w[tid] = r.w;
+          s_h[tid] = r.h;
+          flag = (tid == 0 || (cur[tid - 1].P >> a.atlas_log2) != q) ? 1u : 0u;
         }
         uint32_t nseg;
-        uint32_t at = push_scan(cnt, ws32, &nseg);
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e)
-          if (flags & (1u << e)) s_seg[at++] = tid * kPerThread + e;
+        const uint32_t si = block_scan_incl<uint32_t>(flag, ws32, &nseg);
+        if (flag) s_seg[si - 1] = tid;
         if (tid == 0) {
           s_seg[nseg] = n;
           s_nseg = nseg;
         }
         __syncthreads();
         for (uint32_t sgi = 0; sgi < s_nseg; ++sgi) {
-          const uint32_t j0 = s_seg[sgi], j1 = s_seg[sgi + 1], nbx = j1 - j0;
-          const bool l2r = ((cur[j0].P >> a.atlas_log2) % 3ull) == 0ull;
-          // group of g threads per box: g = 32 for <= 8 boxes ... 1 for >= 256
+          const uint32_t j0 = s_seg[sgi], nbx = s_seg[sgi + 1] - j0;
+          // a group of g threads per box, g = 32 for <= 32 boxes ... 1 for > 512 boxes;
+          // 1024 / g >= nbx, so every box has a group.  A box's group reads and then
+          // writes only that box's texels, which no other box of the row touches.
           uint32_t g = kPushThreads / nbx;
           g = g >= 32 ? 32u : (g >= 16 ? 16u : (g >= 8 ? 8u : (g >= 4 ? 4u : (g >= 2 ? 2u : 1u))));
-          const uint32_t gid = tid / g, li = tid % g, per = kPushThreads / g;
-          for (uint32_t bb = 0; bb < nbx; bb += per) {
-            const uint32_t jj = bb + gid;
-            uint32_t mx = 0;
-            if (jj < nbx) {
-              const BoxRec r = cur[j0 + jj];
-              const uint32_t xr = (uint32_t)(r.P & (om - 1));
-              const uint32_t x = l2r ? xr : Om - xr - r.w;
-              for (uint32_t u = li; u < r.w; u += g) mx = max(mx, F[x + u]);
-            }
-            for (uint32_t o = 1; o < g; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-            if (jj < nbx && li == 0) s_y[j0 + jj] = mx;
+          const uint32_t jj = tid / g, li = tid % g;
+          uint32_t mx = 0, x = 0, w = 0;
+          if (jj < nbx) {
+            x = s_x[j0 + jj];
+            w = s_w[j0 + jj];
+            for (uint32_t u = li; u < w; u += g) mx = max(mx, F[x + u]);
           }
-          __syncthreads();
-          for (uint32_t bb = 0; bb < nbx; bb += per) {
-            const uint32_t jj = bb + gid;
-            if (jj < nbx) {
-              const uint32_t j = j0 + jj;
-              const BoxRec r = cur[j];
-              const uint32_t xr = (uint32_t)(r.P & (om - 1));
-              const uint32_t x = l2r ? xr : Om - xr - r.w;
-              const uint32_t y = s_y[j], top = y + r.h;
-              for (uint32_t u = li; u < r.w; u += g) F[x + u] = top;
-              if (li == 0) {
-                xy[base + j] = make_uint2(x, y);
-                Hloc = max(Hloc, top);
-                if (top > Om) s_flag = 1;
-              }
+          for (uint32_t o = 1; o < g; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+          if (jj < nbx) {
+            const uint32_t top = mx + s_h[j0 + jj];
+            for (uint32_t u = li; u < w; u += g) F[x + u] = top;
+            if (li == 0) {
+              xy[base + j0 + jj] = make_uint2(x, mx);
+              Hloc = max(Hloc, top);
+              if (top > Om) s_flag = 1;
             }
           }
           __syncthreads();
           if (s_flag) break;
         }
         if (s_flag) break;
-        __syncthreads();  // this chunk's buffer is refilled two chunks later
       }
       cp_async_wait0();
-      // block max of Hloc
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) Hloc = max(Hloc, __shfl_xor_sync(0xFFFFFFFFu, Hloc, o));
-      if ((tid & 31) == 0) ws32[tid >> 5] = Hloc;
-      __syncthreads();
-      H = 0;
-#pragma unroll
-      for (int w = 0; w < kPushThreads / 32; ++w) H = max(H, ws32[w]);
+      H = block_max<uint32_t>(Hloc, ws32);
       ok = (!s_flag && H <= Om) ? 1u : 0u;
     }
   }
@@ -469,7 +415,7 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
 }
 
 size_t push_smem_bytes(uint32_t front_cap) {
-  return (size_t)2 * kChunk * sizeof(BoxRec) + (size_t)(2 * kChunk + 4) * 4 + (size_t)front_cap * 4;
+  return (size_t)2 * kChunk * sizeof(BoxRec) + (size_t)(4 * kChunk + 4) * 4 + (size_t)front_cap * 4;
 }
 
 }  // namespace

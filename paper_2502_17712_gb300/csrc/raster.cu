@@ -168,6 +168,8 @@ struct RasterArgs {
   uint32_t tile_cap;
   CandTri* cand;
   uint32_t cand_cap;
+  uint32_t* surv;  // [T] triangles that need the exact set-up
+  uint32_t* clip;  // [T] triangles that need clipping
   DevCounters* ctr;
   uint32_t* vt;
 };
@@ -312,9 +314,10 @@ __device__ __forceinline__ bool surely_empty(const RasterArgs& A, const float4& 
   return area < -bound;
 }
 
-// Depth pre-pass for one mesh triangle; a single small sub-triangle is returned in
-// *out (1) for the warp to append, everything else is handled here (0).
-__device__ int depth_triangle(const RasterArgs& A, uint32_t t, CandTri* out) {
+// Front end of the depth pre-pass for one mesh triangle: transform, trivial reject,
+// route to the clipped list, conservative reject.  Returns 1 when the triangle needs
+// the exact set-up (unclipped), 2 when it must be clipped first, 0 when dropped.
+__device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t) {
   const uint32_t* f = A.idx + 3 * (size_t)t;
   const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
   const float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
@@ -329,12 +332,18 @@ __device__ int depth_triangle(const RasterArgs& A, uint32_t t, CandTri* out) {
 #pragma unroll
   for (int pl = 0; pl < 5; ++pl)
     outside |= !(plane_dist(v0, pl) >= 0.0f) || !(plane_dist(v1, pl) >= 0.0f) || !(plane_dist(v2, pl) >= 0.0f);
-  if (outside) {
-    depth_clipped(A, t, c0, c1, c2);
-    return 0;
-  }
+  if (outside) return 2;
   if (!(v0.w > 0.0f) || !(v1.w > 0.0f) || !(v2.w > 0.0f)) return 0;
   if (surely_empty(A, c0, c1, c2)) return 0;
+  return 1;
+}
+
+// Exact set-up and depth raster of an unclipped triangle.
+__device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, CandTri* out) {
+  const uint32_t* f = A.idx + 3 * (size_t)t;
+  const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
+  const float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
+  const CV v0{c0.x, c0.y, c0.z, c0.w}, v1{c1.x, c1.y, c1.z, c1.w}, v2{c2.x, c2.y, c2.z, c2.w};
   SV sv[3] = {project(v0, A.hx, A.hy), project(v1, A.hx, A.hy), project(v2, A.hx, A.hy)};
   return depth_fan(A, t, sv, 3, out);
 }
@@ -344,6 +353,8 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     ctr->big = 0ull;
     ctr->ncand = 0u;
+    ctr->nsurv = 0u;
+    ctr->nclip = 0u;
   }
   uint4* z4 = reinterpret_cast<uint4*>(zbuf);
   const uint4 ff = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
@@ -354,24 +365,61 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride) vt[i] = 0u;
 }
 
-// Depth pre-pass: one thread per triangle; warps append their single-sub-triangle
-// candidates with one atomic each.
-__global__ void __launch_bounds__(256) k_raster_depth(RasterArgs A) {
+// Depth pre-pass, front end: one thread per triangle; survivors go to a compact list
+// (warp-aggregated appends) so that the exact set-up runs on full warps.
+__global__ void __launch_bounds__(256) k_raster_front(RasterArgs A) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
   const uint32_t nchunks = (A.T + 31) >> 5;
   for (uint32_t w = warp; w < nchunks; w += nwarps) {
     const uint32_t t = (w << 5) + lane;
+    const int r = t < A.T ? front_triangle(A, t) : 0;
+    const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, r == 1), b2 = __ballot_sync(0xFFFFFFFFu, r == 2);
+    if (b1) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&A.ctr->nsurv, (uint32_t)__popc(b1));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (r == 1) A.surv[base + __popc(b1 & ((1u << lane) - 1u))] = t;
+    }
+    if (b2) {
+      uint32_t base = 0;
+      if (lane == 0) base = atomicAdd(&A.ctr->nclip, (uint32_t)__popc(b2));
+      base = __shfl_sync(0xFFFFFFFFu, base, 0);
+      if (r == 2) A.clip[base + __popc(b2 & ((1u << lane) - 1u))] = t;
+    }
+  }
+}
+
+// Depth pre-pass, exact part: survivors of the front end; single small sub-triangles
+// are appended to the candidate list by warp.
+__global__ void __launch_bounds__(256) k_raster_exact(RasterArgs A) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t n = __ldcg(&A.ctr->nsurv);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const uint32_t i = base + lane;
     CandTri r;
     int has = 0;
-    if (t < A.T) has = depth_triangle(A, t, &r);
+    if (i < n) has = exact_triangle(A, __ldcg(A.surv + i), &r);
     const uint32_t ball = __ballot_sync(0xFFFFFFFFu, has != 0);
     if (ball == 0) continue;
-    uint32_t base = 0;
-    if (lane == 0) base = atomicAdd(&A.ctr->ncand, (uint32_t)__popc(ball));
-    base = __shfl_sync(0xFFFFFFFFu, base, 0);
-    if (has) store_cand(A, base + __popc(ball & ((1u << lane) - 1u)), r);
+    uint32_t slot = 0;
+    if (lane == 0) slot = atomicAdd(&A.ctr->ncand, (uint32_t)__popc(ball));
+    slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
+    if (has) store_cand(A, slot + __popc(ball & ((1u << lane) - 1u)), r);
+  }
+}
+
+// Depth pre-pass of the (rare) triangles that need clipping.
+__global__ void __launch_bounds__(256) k_raster_clip(RasterArgs A) {
+  const uint32_t n = __ldcg(&A.ctr->nclip);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint32_t t = __ldcg(A.clip + i);
+    const uint32_t* f = A.idx + 3 * (size_t)t;
+    const float4 c0 = load_clip(A.M, A.pos, __ldg(f)), c1 = load_clip(A.M, A.pos, __ldg(f + 1)),
+                 c2 = load_clip(A.M, A.pos, __ldg(f + 2));
+    depth_clipped(A, t, c0, c1, c2);
   }
 }
 
@@ -464,6 +512,8 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.tile_cap = ctx->tile_cap;
   A.cand = reinterpret_cast<CandTri*>(ctx->cand);
   A.cand_cap = ctx->cand_cap;
+  A.surv = ctx->surv;
+  A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;
   const uint32_t npix = W * H;
@@ -472,8 +522,12 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   k_clear<<<grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s>>>(ctx->zbuf, npix, vt, nwords, ctx->ctr);
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
-  mark(ctx, "k_raster_depth", s);
-  k_raster_depth<<<g, 256, 0, s>>>(A);
+  mark(ctx, "k_raster_front", s);
+  k_raster_front<<<g, 256, 0, s>>>(A);
+  mark(ctx, "k_raster_exact", s);
+  k_raster_exact<<<152 * 8, 256, 0, s>>>(A);
+  mark(ctx, "k_raster_clip", s);
+  k_raster_clip<<<152 * 2, 256, 0, s>>>(A);
   mark(ctx, "k_raster_depth_big", s);
   k_raster_big<0><<<gb, 256, 0, s>>>(A);
   mark(ctx, "k_raster_mark", s);
