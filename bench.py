@@ -119,19 +119,20 @@ class Clocks:
 def algorithmic_bytes(kernel, T, V, W, H, T_vis, C):
     vt = (T + 31) // 32 * 4
     table = {
-        # read indices + positions once, read-modify-write the depth buffer, write the queue bits
-        "k_raster_depth": 12 * T + 12 * V + 4 * W * H + vt,
-        # read indices + positions once, read the depth buffer, write the VT words
-        "k_raster_mark": 12 * T + 12 * V + 4 * W * H + 2 * vt,
-        "k_clear": 4 * W * H,
-        "k_uf_init": vt + 12 * T_vis + 4 * T_vis,
+        # read indices + positions once; write the survivors (id + clip coordinates)
+        "k_raster_front": 12 * T + 12 * V,
+        "k_clear": 4 * W * H + vt,
+        "k_uf_local": vt + 12 * T_vis + 4 * T_vis,
         "k_uf_hook": vt + 12 * T_vis + 8 * T_vis,
         "k_uf_flatten": vt + 8 * T_vis,
         "k_tri_chart": vt + 4 * T + 8 * T_vis,
         "k_bbox": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis,
         "k_uv": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis + 24 * T_vis,
         "k_number": vt + 4 * T_vis,
-        "k_pack": 64 * 8 * C,
+        # per candidate: read the box record (16 B) and write the placement (8 B)
+        "k_pack_push": 64 * 24 * C,
+        "k_pack_boxes": 64 * (16 * C) + 12 * C,
+        "k_pack_fix": 64 * 32 * C,
     }
     return table.get(kernel)
 

@@ -93,30 +93,47 @@ __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
 __global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
   __shared__ int32_t lab[kTile];
   __shared__ uint32_t vis[kTile / 32];
-  __shared__ uint32_t any;
   const uint32_t base = blockIdx.x * kTile;
-  if (threadIdx.x == 0) any = 0;
-  __syncthreads();
+  uint32_t v = 0;
   if (threadIdx.x < kTile / 32) {
     const uint32_t w = (base >> 5) + threadIdx.x;
-    const uint32_t v = w < ((a.T + 31) >> 5) ? __ldg(a.vt + w) : 0u;
+    v = w < ((a.T + 31) >> 5) ? __ldg(a.vt + w) : 0u;
     vis[threadIdx.x] = v;
-    if (v) atomicOr(&any, 1u);
   }
-  for (uint32_t i = threadIdx.x; i < kTile; i += kBlock) lab[i] = (int32_t)i;
-  __syncthreads();
-  if (!any) return;
+  if (!__syncthreads_or(v != 0u)) return;  // no visible triangle in this tile
   volatile int32_t* vl = lab;
-  for (uint32_t i = threadIdx.x; i < kTile; i += kBlock) {
-    if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
-    const uint32_t t = base + i;
+  // start from the smallest visible neighbour inside the tile (Alg. 1, first loop)
+  int32_t nb[kTile / kBlock][3];
+#pragma unroll
+  for (int k = 0; k < kTile / kBlock; ++k) {
+    const uint32_t i = threadIdx.x + k * kBlock;
+    int32_t l = (int32_t)i;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) nb[k][j] = -1;
+    if ((vis[i >> 5] >> (i & 31)) & 1u) {
+      const uint32_t t = base + i;
+#pragma unroll
+      for (int j = 0; j < 3; ++j) {
+        const int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
+        if (n < (int32_t)base || (uint32_t)n >= base + kTile) continue;
+        const uint32_t ni = (uint32_t)n - base;
+        if (!((vis[ni >> 5] >> (ni & 31)) & 1u)) continue;
+        nb[k][j] = (int32_t)ni;
+        if ((int32_t)ni < l) l = (int32_t)ni;
+      }
+    }
+    lab[i] = l;
+  }
+  __syncthreads();
+  // hook every in-tile edge once, from its lower end
+#pragma unroll
+  for (int k = 0; k < kTile / kBlock; ++k) {
+    const int32_t i = (int32_t)(threadIdx.x + k * kBlock);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
-      if (n <= (int32_t)t || (uint32_t)n >= base + kTile) continue;
-      const uint32_t ni = (uint32_t)n - base;
-      if (!((vis[ni >> 5] >> (ni & 31)) & 1u)) continue;
-      int32_t ra = lfind(vl, (int32_t)i), rb = lfind(vl, (int32_t)ni);
+      const int32_t ni = nb[k][j];
+      if (ni <= i) continue;
+      int32_t ra = lfind(vl, i), rb = lfind(vl, ni);
       while (ra != rb) {
         const int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
         const int32_t old = atomicCAS(lab + hi, hi, lo);

@@ -105,6 +105,7 @@ struct fa_ctx {
   void* cand;            // [cand_cap] 48-byte records of small sub-triangles
   uint32_t cand_cap;
   uint32_t* surv;        // [max_tris] raster survivors
+  void* surv_clip;       // [max_tris][3] float4 clip coordinates of the survivors
   uint32_t* clip;        // [max_tris] triangles to clip
   int32_t* label;        // [max_tris + max_verts]
   int32_t* cid;          // [max_tris] chart id of root triangles

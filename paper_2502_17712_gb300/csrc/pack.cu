@@ -336,9 +336,11 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
           // a group of g threads per box, g = 32 for <= 32 boxes ... 1 for > 512 boxes;
           // 1024 / g >= nbx, so every box has a group.  A box's group reads and then
           // writes only that box's texels, which no other box of the row touches.
-          uint32_t g = kPushThreads / nbx;
-          g = g >= 32 ? 32u : (g >= 16 ? 16u : (g >= 8 ? 8u : (g >= 4 ? 4u : (g >= 2 ? 2u : 1u))));
-          const uint32_t jj = tid / g, li = tid % g;
+          // g = 2^lg = largest power of two <= 1024 / nbx, at most 32
+          const int lgb = nbx > 1 ? 32 - __clz(nbx - 1) : 0;  // ceil(log2(nbx))
+          const int lg = min(max(10 - lgb, 0), 5);
+          const uint32_t g = 1u << lg;
+          const uint32_t jj = tid >> lg, li = tid & (g - 1u);
           uint32_t mx = 0, x = 0, w = 0;
           if (jj < nbx) {
             x = s_x[j0 + jj];

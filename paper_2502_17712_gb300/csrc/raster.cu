@@ -169,6 +169,7 @@ struct RasterArgs {
   CandTri* cand;
   uint32_t cand_cap;
   uint32_t* surv;  // [T] triangles that need the exact set-up
+  float4* surv_clip;  // [T][3] their clip coordinates
   uint32_t* clip;  // [T] triangles that need clipping
   DevCounters* ctr;
   uint32_t* vt;
@@ -316,8 +317,9 @@ __device__ __forceinline__ bool surely_empty(const RasterArgs& A, const float4& 
 
 // Front end of the depth pre-pass for one mesh triangle: transform, trivial reject,
 // route to the clipped list, conservative reject.  Returns 1 when the triangle needs
-// the exact set-up (unclipped), 2 when it must be clipped first, 0 when dropped.
-__device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t) {
+// the exact set-up (unclipped; its clip coordinates are left in c[3]), 2 when it must
+// be clipped first, 0 when dropped.
+__device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t, float4* c) {
   const uint32_t* f = A.idx + 3 * (size_t)t;
   const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
   const float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
@@ -335,14 +337,15 @@ __device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t) {
   if (outside) return 2;
   if (!(v0.w > 0.0f) || !(v1.w > 0.0f) || !(v2.w > 0.0f)) return 0;
   if (surely_empty(A, c0, c1, c2)) return 0;
+  c[0] = c0;
+  c[1] = c1;
+  c[2] = c2;
   return 1;
 }
 
-// Exact set-up and depth raster of an unclipped triangle.
-__device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, CandTri* out) {
-  const uint32_t* f = A.idx + 3 * (size_t)t;
-  const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
-  const float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
+// Exact set-up and depth raster of an unclipped triangle from its clip coordinates.
+__device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, const float4& c0, const float4& c1,
+                                              const float4& c2, CandTri* out) {
   const CV v0{c0.x, c0.y, c0.z, c0.w}, v1{c1.x, c1.y, c1.z, c1.w}, v2{c2.x, c2.y, c2.z, c2.w};
   SV sv[3] = {project(v0, A.hx, A.hy), project(v1, A.hx, A.hy), project(v2, A.hx, A.hy)};
   return depth_fan(A, t, sv, 3, out);
@@ -374,13 +377,21 @@ __global__ void __launch_bounds__(256) k_raster_front(RasterArgs A) {
   const uint32_t nchunks = (A.T + 31) >> 5;
   for (uint32_t w = warp; w < nchunks; w += nwarps) {
     const uint32_t t = (w << 5) + lane;
-    const int r = t < A.T ? front_triangle(A, t) : 0;
+    float4 c[3];
+    const int r = t < A.T ? front_triangle(A, t, c) : 0;
     const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, r == 1), b2 = __ballot_sync(0xFFFFFFFFu, r == 2);
     if (b1) {
       uint32_t base = 0;
       if (lane == 0) base = atomicAdd(&A.ctr->nsurv, (uint32_t)__popc(b1));
       base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (r == 1) A.surv[base + __popc(b1 & ((1u << lane) - 1u))] = t;
+      if (r == 1) {
+        const uint32_t slot = base + __popc(b1 & ((1u << lane) - 1u));
+        A.surv[slot] = t;
+        float4* sc = A.surv_clip + 3 * (size_t)slot;
+        sc[0] = c[0];
+        sc[1] = c[1];
+        sc[2] = c[2];
+      }
     }
     if (b2) {
       uint32_t base = 0;
@@ -393,7 +404,7 @@ __global__ void __launch_bounds__(256) k_raster_front(RasterArgs A) {
 
 // Depth pre-pass, exact part: survivors of the front end; single small sub-triangles
 // are appended to the candidate list by warp.
-__global__ void __launch_bounds__(256) k_raster_exact(RasterArgs A) {
+__global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t n = __ldcg(&A.ctr->nsurv);
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -401,7 +412,10 @@ __global__ void __launch_bounds__(256) k_raster_exact(RasterArgs A) {
     const uint32_t i = base + lane;
     CandTri r;
     int has = 0;
-    if (i < n) has = exact_triangle(A, __ldcg(A.surv + i), &r);
+    if (i < n) {
+      const float4* sc = A.surv_clip + 3 * (size_t)i;
+      has = exact_triangle(A, __ldcg(A.surv + i), __ldcs(sc), __ldcs(sc + 1), __ldcs(sc + 2), &r);
+    }
     const uint32_t ball = __ballot_sync(0xFFFFFFFFu, has != 0);
     if (ball == 0) continue;
     uint32_t slot = 0;
@@ -513,6 +527,7 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.cand = reinterpret_cast<CandTri*>(ctx->cand);
   A.cand_cap = ctx->cand_cap;
   A.surv = ctx->surv;
+  A.surv_clip = reinterpret_cast<float4*>(ctx->surv_clip);
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;
