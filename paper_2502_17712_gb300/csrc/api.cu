@@ -8,6 +8,16 @@
 
 using namespace fa;
 
+namespace fa {
+bool pdl_enabled() {
+  static const bool on = [] {
+    const char* e = std::getenv("FA_PDL");
+    return !(e && e[0] == '0');
+  }();
+  return on;
+}
+}  // namespace fa
+
 namespace {
 
 bool is_pow2(uint32_t x) { return x && !(x & (x - 1)); }
@@ -203,7 +213,7 @@ fa_status fa_visibility(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[
   if (st != FA_OK) return st;
   DeviceGuard g(ctx->device);
   trace_begin(ctx);
-  st = launch_visibility(ctx, mesh, to_mat(view_proj), width, height, d_vt, (cudaStream_t)stream);
+  st = launch_visibility(ctx, mesh, to_mat(view_proj), width, height, d_vt, false, (cudaStream_t)stream);
   trace_end(ctx, (cudaStream_t)stream);
   return st;
 }
@@ -225,6 +235,7 @@ fa_status fa_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* d_vt, ui
 // tri_chart so that they need no extra argument.
 namespace {
 __global__ void k_vt_from_chart(const int32_t* tri_chart, uint32_t T, uint32_t* vt) {
+  pdl_wait();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwords = (T + 31) >> 5;
   for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
@@ -250,7 +261,7 @@ fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_pro
   uint32_t* vt = ctx->bigbits;  // reuse: the raster's queue bits are dead after visibility
   trace_begin(ctx);
   mark(ctx, "k_vt_from_chart", s);
-  k_vt_from_chart<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s>>>(d_tri_chart,
+  launch_k(k_vt_from_chart, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s, d_tri_chart,
                                                                                               mesh->T, vt);
   st = launch_parameterize(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, vt, charts, true, s);
   trace_end(ctx, s);
@@ -287,7 +298,7 @@ fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uin
   uint32_t* vt = ctx->bigbits;
   trace_begin(ctx);
   mark(ctx, "k_vt_from_chart", s);
-  k_vt_from_chart<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s>>>(d_tri_chart,
+  launch_k(k_vt_from_chart, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s, d_tri_chart,
                                                                                               mesh->T, vt);
   st = launch_uv(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, vt, charts, d_place, d_res,
                  atlas_log2, n_scales, d_uv, d_affine, s);
@@ -295,9 +306,7 @@ fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uin
   return st;
 }
 
-namespace {
-__global__ void k_reset_status(DevCounters* ctr) { ctr->status = 0; }
-}  // namespace
+
 
 fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const fa_frame_out* o,
                          fa_stream_t stream) {
@@ -312,9 +321,8 @@ fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params
   cudaStream_t s = (cudaStream_t)stream;
   const Mat4 M = to_mat(p->view_proj);
   trace_begin(ctx);
-  mark(ctx, "k_reset_status", s);
-  k_reset_status<<<1, 1, 0, s>>>(ctx->ctr);
-  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, s)) != FA_OK) return st;
+  // k_clear (first kernel of the visibility step) also clears the status word
+  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s)) != FA_OK) return st;
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators

@@ -91,6 +91,7 @@ __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
 }
 
 __global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
+  pdl_wait();
   __shared__ int32_t lab[kTile];
   __shared__ uint32_t vis[kTile / 32];
   const uint32_t base = blockIdx.x * kTile;
@@ -153,12 +154,14 @@ __global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
 }
 
 __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
+  pdl_wait();
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
     label[T + v] = (int32_t)(T + v);
 }
 
 // Hooking (Alg. 1, second loop): each undirected edge once, from its lower end.
 __global__ void __launch_bounds__(kBlock) k_uf_hook(UfArgs a, int vertex_mode) {
+  pdl_wait();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwords = (a.T + 31) >> 5;
   for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
@@ -187,6 +190,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_hook(UfArgs a, int vertex_mode) {
 
 // Non-manifold edges: join consecutive visible triangles of each incidence list.
 __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* nm_list, uint32_t n_nm) {
+  pdl_wait();
   for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nm; e += gridDim.x * blockDim.x) {
     int32_t prev = -1;
     for (uint32_t i = nm_off[e]; i < nm_off[e + 1]; ++i) {
@@ -201,6 +205,7 @@ __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* n
 // Flatten visible triangles to their root and count roots per block of
 // kPerBlock triangles.
 __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt) {
+  pdl_wait();
   __shared__ uint32_t cnt;
   if (threadIdx.x == 0) cnt = 0;
   __syncthreads();
@@ -223,6 +228,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* block
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blockcnt, uint32_t nblocks,
                                                       uint32_t* count_out, uint32_t max_charts,
                                                       DevCounters* ctr) {
+  pdl_wait();
   __shared__ uint32_t warp_tot[32];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = 0;
@@ -267,6 +273,7 @@ __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blockcnt, uint32
 __global__ void __launch_bounds__(kBlock) k_number(UfArgs a, const uint32_t* blockcnt, int32_t* cid,
                                                    uint32_t* roots, uint32_t* box_enc,
                                                    uint32_t* box_full, uint32_t max_charts) {
+  pdl_wait();
   __shared__ uint32_t warp_tot[kBlock / 32];
   __shared__ uint32_t carry;
   if (threadIdx.x == 0) carry = blockcnt[blockIdx.x];
@@ -303,6 +310,7 @@ __global__ void __launch_bounds__(kBlock) k_number(UfArgs a, const uint32_t* blo
 }
 
 __global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* cid, int32_t* tri_chart) {
+  pdl_wait();
   if (__ldcg(&a.ctr->status) != 0) return;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwords = (a.T + 31) >> 5;
@@ -318,6 +326,7 @@ __global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* c
 }
 
 __global__ void k_vert_chart(UfArgs a, const int32_t* cid, int32_t* vert_chart, int vertex_mode) {
+  pdl_wait();
   if (__ldcg(&a.ctr->status) != 0) return;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
     int32_t out = -1;
@@ -345,29 +354,29 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   const unsigned gw = grid_for((uint64_t)((mesh->T + 31) / 32) * 32, kBlock, 152 * 16);
   if (vm) {
     mark(ctx, "k_uf_init_v", s);
-    k_uf_init_v<<<grid_for(mesh->V, 256, 152 * 8), 256, 0, s>>>(ctx->label, mesh->T, mesh->V);
+    launch_k(k_uf_init_v, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, ctx->label, mesh->T, mesh->V);
   }
   mark(ctx, "k_uf_local", s);
-  k_uf_local<<<(mesh->T + kTile - 1) / kTile, kBlock, 0, s>>>(a);
+  launch_k(k_uf_local, (mesh->T + kTile - 1) / kTile, kBlock, 0, s, a);
   mark(ctx, "k_uf_hook", s);
-  k_uf_hook<<<gw, kBlock, 0, s>>>(a, vm);
+  launch_k(k_uf_hook, gw, kBlock, 0, s, a, vm);
   if (!vm && mesh->n_nm) {
     mark(ctx, "k_uf_hook_nm", s);
-    k_uf_hook_nm<<<grid_for(mesh->n_nm, 256), 256, 0, s>>>(a, mesh->nm_off, mesh->nm_list, mesh->n_nm);
+    launch_k(k_uf_hook_nm, grid_for(mesh->n_nm, 256), 256, 0, s, a, mesh->nm_off, mesh->nm_list, mesh->n_nm);
   }
   const uint32_t nb = (mesh->T + kPerBlock - 1) / kPerBlock;
   mark(ctx, "k_uf_flatten", s);
-  k_uf_flatten<<<nb ? nb : 1, kBlock, 0, s>>>(a, ctx->blockcnt);
+  launch_k(k_uf_flatten, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt);
   mark(ctx, "k_scan_blocks", s);
-  k_scan_blocks<<<1, 1024, 0, s>>>(ctx->blockcnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts, ctx->ctr);
+  launch_k(k_scan_blocks, 1, 1024, 0, s, ctx->blockcnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts, ctx->ctr);
   mark(ctx, "k_number", s);
-  k_number<<<nb ? nb : 1, kBlock, 0, s>>>(a, ctx->blockcnt, ctx->cid, ch->root, ctx->box_enc,
+  launch_k(k_number, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->cid, ch->root, ctx->box_enc,
                                           ctx->box_full, ctx->cfg.max_charts);
   mark(ctx, "k_tri_chart", s);
-  k_tri_chart<<<gw, kBlock, 0, s>>>(a, ctx->cid, tri_chart);
+  launch_k(k_tri_chart, gw, kBlock, 0, s, a, ctx->cid, tri_chart);
   if (vert_chart) {
     mark(ctx, "k_vert_chart", s);
-    k_vert_chart<<<grid_for(mesh->V, 256, 152 * 8), 256, 0, s>>>(a, ctx->cid, vert_chart, vm);
+    launch_k(k_vert_chart, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, a, ctx->cid, vert_chart, vm);
   }
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;

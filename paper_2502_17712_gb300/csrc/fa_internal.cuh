@@ -212,11 +212,35 @@ inline void trace_end(fa_ctx* ctx, cudaStream_t s) {
   if (ctx->prof_on && ctx->prof_n > 0) record_event(ctx->prof_ev[ctx->prof_n], s);
 }
 
+// Programmatic dependent launch: every per-frame kernel is launched with
+// programmatic stream serialization, so its blocks may be scheduled while the
+// previous kernel drains; each kernel's first statement waits until the previous
+// grid has completed and its writes are visible (a no-op without the attribute).
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+bool pdl_enabled();  // FA_PDL=0 in the environment turns it off
+
+template <typename... KArgs, typename... Args>
+inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                     Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = pdl_enabled() ? 1 : 0;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+
 // ----------------------------------------------------------------- launchers
 // Each returns FA_OK or FA_E_CUDA (launch error) and bumps ctx->launches.
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
-                            uint32_t H, uint32_t* vt, cudaStream_t s);
+                            uint32_t H, uint32_t* vt, bool reset_status, cudaStream_t s);
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
                           cudaStream_t s);

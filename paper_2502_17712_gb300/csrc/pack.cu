@@ -82,6 +82,7 @@ __device__ __forceinline__ T block_max(T v, T* warp_vals) {
 // ------------------------------------------------------------------ order
 
 __global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const uint32_t* __restrict__ fb) {
+  pdl_wait();
   __shared__ uint32_t key[kOrderTile];
   __shared__ uint16_t first[kMaxH];
   if (__ldcg(&p.ctr->status) != 0) return;
@@ -125,6 +126,7 @@ __global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const 
 
 // binstart = exclusive scan of the bin totals; the totals are cleared for the next call.
 __global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
+  pdl_wait();
   __shared__ uint32_t wt[32];
   if (__ldcg(&p.ctr->status) != 0) return;
   constexpr uint32_t kPer = kMaxH / 1024;
@@ -159,6 +161,7 @@ __global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
 
 __global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, const uint32_t* __restrict__ fb,
                                                               uint32_t* order) {
+  pdl_wait();
   if (__ldcg(&p.ctr->status) != 0) return;
   const uint32_t C = __ldcg(p.count);
   if (C > p.max_boxes) return;
@@ -194,6 +197,7 @@ struct PackArgs {
 // Scaled boxes and tile-local exclusive prefix of the widths.  Persistent grid over
 // (tile, candidate) work items.
 __global__ void __launch_bounds__(kThreads) k_pack_boxes(PackScratch p, PackArgs a, uint32_t n_scales) {
+  pdl_wait();
   __shared__ unsigned long long ws[32];
   if (__ldcg(&p.ctr->status) != 0) return;
   const uint32_t C = __ldcg(p.count);
@@ -222,6 +226,7 @@ __global__ void __launch_bounds__(kThreads) k_pack_boxes(PackScratch p, PackArgs
 
 // Global prefix P (tile offset + local) and the largest overflow past omega.
 __global__ void __launch_bounds__(kThreads) k_pack_fix(PackScratch p, PackArgs a, uint32_t n_scales) {
+  pdl_wait();
   __shared__ unsigned long long ws[32];
   __shared__ uint32_t wm[32];
   if (__ldcg(&p.ctr->status) != 0) return;
@@ -264,6 +269,7 @@ constexpr int kPushThreads = 1024;
 constexpr int kChunk = 1024;  // boxes staged per chunk (one per thread)
 
 __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
+  pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                  // [2][kChunk]
   uint32_t* s_x = reinterpret_cast<uint32_t*>(buf + 2 * kChunk);     // [kChunk] box x
@@ -272,8 +278,7 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
   uint32_t* s_seg = s_h + kChunk;                                      // [kChunk + 1]
   uint32_t* F = s_seg + kChunk + 4;                                    // [front_cap]
   __shared__ uint32_t ws32[32];
-  __shared__ uint32_t s_flag, s_nseg, s_last, s_best;
-  __shared__ int32_t s_status;
+  __shared__ uint32_t s_flag, s_nseg, s_last;
 
   const uint32_t kidx = blockIdx.x;
   const uint32_t tid = threadIdx.x;
@@ -399,20 +404,22 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       r.height = cv.z;
     }
     *a.res = r;
-    s_best = pst == FA_OK ? best : 0;
-    s_status = pst;
     p.ctr->pack_done = 0;
   }
-  __syncthreads();
-  if (s_status != FA_OK) return;
-  const uint32_t kb = s_best - 1;
+}
+
+// Placements of the selected candidate, in chart order (all CTAs).
+__global__ void __launch_bounds__(256) k_pack_place(PackScratch p, PackArgs a) {
+  pdl_wait();
+  if (__ldcg(&a.res->status) != FA_OK) return;
+  const uint32_t C = __ldcg(&a.res->count), kb = __ldcg(&a.res->k) - 1;
   const uint2* bxy = p.xy + (size_t)kb * p.max_boxes;
   const BoxRec* brec = p.rec + (size_t)kb * p.max_boxes;
-  for (uint32_t i = tid; i < C; i += kPushThreads) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
     const uint32_t b = __ldcg(a.order + i);
     const uint2 q = __ldcg(bxy + i);
-    const BoxRec r = brec[i];
-    a.place[b] = fa_placement{(int32_t)q.x, (int32_t)q.y, (int32_t)r.w, (int32_t)r.h};
+    const uint2 wh = __ldcg(reinterpret_cast<const uint2*>(brec + i) + 1);
+    a.place[b] = fa_placement{(int32_t)q.x, (int32_t)q.y, (int32_t)wh.x, (int32_t)wh.y};
   }
 }
 
@@ -428,11 +435,11 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
                               cudaStream_t s) {
   uint32_t* ord = order ? order : p.order;
   if (ctx) mark(ctx, "k_order_tile", s);
-  k_order_tile<<<p.max_tiles, kOrderTile, 0, s>>>(p, fb);
+  launch_k(k_order_tile, p.max_tiles, kOrderTile, 0, s, p, fb);
   if (ctx) mark(ctx, "k_order_binscan", s);
-  k_order_binscan<<<1, 1024, 0, s>>>(p);
+  launch_k(k_order_binscan, 1, 1024, 0, s, p);
   if (ctx) mark(ctx, "k_order_scatter", s);
-  k_order_scatter<<<p.max_tiles, kOrderTile, 0, s>>>(p, fb, ord);
+  launch_k(k_order_scatter, p.max_tiles, kOrderTile, 0, s, p, fb, ord);
   PackArgs a;
   a.fa = fa_;
   a.fb = fb;
@@ -451,11 +458,13 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   const uint32_t items = p.max_tiles * n_scales;
   const unsigned g2 = items < 152u * 2u ? items : 152u * 2u;
   if (ctx) mark(ctx, "k_pack_boxes", s);
-  k_pack_boxes<<<g2, kThreads, 0, s>>>(p, a, n_scales);
+  launch_k(k_pack_boxes, g2, kThreads, 0, s, p, a, n_scales);
   if (ctx) mark(ctx, "k_pack_fix", s);
-  k_pack_fix<<<g2, kThreads, 0, s>>>(p, a, n_scales);
+  launch_k(k_pack_fix, g2, kThreads, 0, s, p, a, n_scales);
   if (ctx) mark(ctx, "k_pack_push", s);
-  k_pack_push<<<n_scales, kPushThreads, push_smem_bytes(a.front_cap), s>>>(p, a);
+  launch_k(k_pack_push, n_scales, kPushThreads, push_smem_bytes(a.front_cap), s, p, a);
+  if (ctx) mark(ctx, "k_pack_place", s);
+  launch_k(k_pack_place, 152 * 2, 256, 0, s, p, a);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
@@ -549,6 +558,7 @@ fa_status noalloc_scratch(int dev, unsigned char** out) {
 // Clears what the kernels expect at zero (status word, finished-candidate counter,
 // bin totals) and stores the box count where the kernels read it.
 __global__ void k_noalloc_reset(DevCounters* ctr, uint32_t* count, uint32_t* total, uint32_t n) {
+  pdl_wait();
   if (threadIdx.x == 0) {
     ctr->status = 0;
     ctr->pack_done = 0;
@@ -595,7 +605,7 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   p.m = (uint32_t*)(base + kOffM);
   p.xy = (uint2*)(base + kOffXY);
   p.cand = (PackCand*)(base + kOffCand);
-  k_noalloc_reset<<<1, 256, 0, s>>>(p.ctr, (uint32_t*)p.count, p.ord_total, n);
+  launch_k(k_noalloc_reset, 1, 256, 0, s, p.ctr, (uint32_t*)p.count, p.ord_total, n);
   return launch_pack_kernels(nullptr, p, d_fa, d_fb, atlas_log2, n_scales, select_mode, min_box, gutter, d_order,
                              d_place, d_res, s);
 }

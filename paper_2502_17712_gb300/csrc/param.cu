@@ -68,6 +68,7 @@ struct BoxArgs {
 };
 
 __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
+  pdl_wait();
   if (__ldcg(&a.ctr->status) != 0) return;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwords = (a.T + 31) >> 5;
@@ -123,6 +124,7 @@ __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
 }
 
 __global__ void k_box_reset(const uint32_t* count, uint32_t max_charts, uint32_t* box_enc, uint32_t* box_full) {
+  pdl_wait();
   const uint32_t C = min(__ldcg(count), max_charts);
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
     reinterpret_cast<uint4*>(box_enc)[c] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
@@ -133,6 +135,7 @@ __global__ void k_box_reset(const uint32_t* count, uint32_t max_charts, uint32_t
 __global__ void k_footprint(const uint32_t* count, uint32_t max_charts, const uint32_t* box_enc,
                             const uint32_t* box_full, float hx, float hy, float s256, float* bbox,
                             uint32_t* fa_, uint32_t* fb, uint8_t* rot, DevCounters* ctr) {
+  pdl_wait();
   if (__ldcg(&ctr->status) != 0) return;
   const uint32_t C = min(__ldcg(count), max_charts);
   for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
@@ -225,6 +228,7 @@ struct UvArgs {
 };
 
 __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
+  pdl_wait();
   if (__ldcg(&a.ctr->status) != 0 || __ldcg(&a.res->status) != FA_OK) return;
   const uint32_t k = __ldcg(&a.res->k);
   const float om = (float)(1u << a.atlas_log2), Om = (float)__ldcg(&a.res->omega);
@@ -310,7 +314,7 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
                               const fa_charts* ch, bool reset_boxes, cudaStream_t s) {
   if (reset_boxes) {
     mark(ctx, "k_box_reset", s);
-    k_box_reset<<<grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s>>>(ch->count, ctx->cfg.max_charts,
+    launch_k(k_box_reset, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts,
                                                                             ctx->box_enc, ctx->box_full);
   }
   BoxArgs a;
@@ -325,10 +329,9 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
   a.max_charts = ctx->cfg.max_charts;
   a.ctr = ctx->ctr;
   mark(ctx, "k_bbox", s);
-  k_bbox<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s>>>(a);
+  launch_k(k_bbox, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
   mark(ctx, "k_footprint", s);
-  k_footprint<<<grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s>>>(
-      ch->count, ctx->cfg.max_charts, ctx->box_enc, ctx->box_full, 0.5f * (float)W, 0.5f * (float)H,
+  launch_k(k_footprint, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts, ctx->box_enc, ctx->box_full, 0.5f * (float)W, 0.5f * (float)H,
       256.0f * ratio, ch->bbox, ch->fa, ch->fb, ch->rot, ctx->ctr);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
@@ -361,7 +364,7 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
   a.affine = affine;
   a.ctr = ctx->ctr;
   mark(ctx, "k_uv", s);
-  k_uv<<<grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s>>>(a);
+  launch_k(k_uv, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }

@@ -352,8 +352,10 @@ __device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, c
 }
 
 __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __restrict__ vt, uint32_t nwords,
-                        DevCounters* ctr) {
+                        DevCounters* ctr, int reset_status) {
+  pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (reset_status) ctr->status = 0;
     ctr->big = 0ull;
     ctr->ncand = 0u;
     ctr->nsurv = 0u;
@@ -371,6 +373,7 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
 // Depth pre-pass, front end: one thread per triangle; survivors go to a compact list
 // (warp-aggregated appends) so that the exact set-up runs on full warps.
 __global__ void __launch_bounds__(256) k_raster_front(RasterArgs A) {
+  pdl_wait();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -405,6 +408,7 @@ __global__ void __launch_bounds__(256) k_raster_front(RasterArgs A) {
 // Depth pre-pass, exact part: survivors of the front end; single small sub-triangles
 // are appended to the candidate list by warp.
 __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
+  pdl_wait();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t n = __ldcg(&A.ctr->nsurv);
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -423,12 +427,9 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
     slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
     if (has) store_cand(A, slot + __popc(ball & ((1u << lane) - 1u)), r);
   }
-}
-
-// Depth pre-pass of the (rare) triangles that need clipping.
-__global__ void __launch_bounds__(256) k_raster_clip(RasterArgs A) {
-  const uint32_t n = __ldcg(&A.ctr->nclip);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  // then the (rare) triangles that need clipping
+  const uint32_t nc = __ldcg(&A.ctr->nclip);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) {
     const uint32_t t = __ldcg(A.clip + i);
     const uint32_t* f = A.idx + 3 * (size_t)t;
     const float4 c0 = load_clip(A.M, A.pos, __ldg(f)), c1 = load_clip(A.M, A.pos, __ldg(f + 1)),
@@ -440,6 +441,7 @@ __global__ void __launch_bounds__(256) k_raster_clip(RasterArgs A) {
 // Marking pass over the candidate list: a record is visible when one of its samples
 // has key <= the depth buffer; visible bits are OR-ed per VT word and warp.
 __global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
+  pdl_wait();
   if (__ldcg(&A.ctr->status) != 0) return;
   const uint32_t n = min(__ldcg(&A.ctr->ncand), A.cand_cap);
   const uint32_t stride = gridDim.x * blockDim.x;
@@ -470,6 +472,7 @@ __global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
 // Large sub-triangles: one warp per 16x16 tile of a queued record.
 template <int PASS>
 __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
+  pdl_wait();
   if (PASS == 1 && __ldcg(&A.ctr->status) != 0) return;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -509,7 +512,7 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
 }  // namespace
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
-                            uint32_t* vt, cudaStream_t s) {
+                            uint32_t* vt, bool reset_status, cudaStream_t s) {
   RasterArgs A;
   A.M = M;
   A.pos = mesh->pos;
@@ -534,21 +537,20 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   const uint32_t npix = W * H;
   const uint32_t nwords = (mesh->T + 31) / 32;
   mark(ctx, "k_clear", s);
-  k_clear<<<grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s>>>(ctx->zbuf, npix, vt, nwords, ctx->ctr);
+  launch_k(k_clear, grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s, ctx->zbuf, npix, vt, nwords, ctx->ctr,
+           reset_status ? 1 : 0);
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_front", s);
-  k_raster_front<<<g, 256, 0, s>>>(A);
+  launch_k(k_raster_front, g, 256, 0, s, A);
   mark(ctx, "k_raster_exact", s);
-  k_raster_exact<<<152 * 8, 256, 0, s>>>(A);
-  mark(ctx, "k_raster_clip", s);
-  k_raster_clip<<<152 * 2, 256, 0, s>>>(A);
+  launch_k(k_raster_exact, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_depth_big", s);
-  k_raster_big<0><<<gb, 256, 0, s>>>(A);
+  launch_k(k_raster_big<0>, gb, 256, 0, s, A);
   mark(ctx, "k_raster_mark", s);
-  k_raster_mark<<<152 * 8, 256, 0, s>>>(A);
+  launch_k(k_raster_mark, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_mark_big", s);
-  k_raster_big<1><<<gb, 256, 0, s>>>(A);
+  launch_k(k_raster_big<1>, gb, 256, 0, s, A);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
