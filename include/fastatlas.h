@@ -213,7 +213,7 @@ fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_pro
  * to *d_res and its placements (chart order) to d_place; d_order (may be NULL)
  * receives the packing order.  No fitting candidate: d_res->status =
  * FA_E_PACK_FAILED.  A candidate with Omega above the frontline capacity
- * min(8 omega, 40960) sets FA_E_CAPACITY.
+ * min(8 omega, 32768) sets FA_E_CAPACITY.
  * Errors: FA_E_INVALID_ARG (atlas_log2 out of range, n_scales not a power of two
  * in [1, 64], select_mode unknown, NULL pointers). */
 fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const uint32_t* d_count,

@@ -14,7 +14,7 @@ constexpr float kGuard = 64.0f;     // guard band |x|,|y| <= kGuard * w
 constexpr int kSub = 256;           // sub-pixel steps per pixel (1/256 px snapping)
 constexpr uint32_t kMaxH = 8192;    // height buckets of the box order (Sec. 4.1)
 constexpr int kMaxScales = 64;      // candidate scales (Sec. 4.2)
-constexpr uint32_t kFrontCap = 40960;  // frontline entries per candidate (smem)
+constexpr uint32_t kFrontCap = 32768;  // frontline entries per candidate (smem)
 constexpr int kBigTile = 16;        // tile side of the large-triangle raster
 constexpr int kSmallMaxPix = 16;    // in-thread raster when the pixel box has <= this
 constexpr int kOrderTile = 1024;    // boxes per tile of the stable order

@@ -261,18 +261,21 @@ __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
   asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 // Row push of one candidate per CTA, then the last CTA selects.
 constexpr int kPushThreads = 1024;
 constexpr int kChunk = 1024;  // boxes staged per chunk (one per thread)
+constexpr int kStages = 4;    // chunk buffers in the prefetch ring
+__device__ __forceinline__ void cp_async_wait_stages() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 1) : "memory");
+}
 
 __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                  // [2][kChunk]
-  uint32_t* s_x = reinterpret_cast<uint32_t*>(buf + 2 * kChunk);     // [kChunk] box x
+  BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                     // [kStages][kChunk]
+  uint32_t* s_x = reinterpret_cast<uint32_t*>(buf + kStages * kChunk);  // [kChunk] box x
   uint32_t* s_w = s_x + kChunk;                                        // [kChunk]
   uint32_t* s_h = s_w + kChunk;                                        // [kChunk]
   uint32_t* s_seg = s_h + kChunk;                                      // [kChunk + 1]
@@ -304,18 +307,21 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       if (tid == 0) s_flag = 0;
       uint32_t Hloc = 0;
       const uint32_t nchunks = (C + kChunk - 1) / kChunk;
-      if (nchunks) {
-        if (tid < C) cp_async16(buf + tid, rec + tid);
+      // ring of kStages chunk buffers with kStages - 1 chunks in flight ahead
+#pragma unroll
+      for (uint32_t c = 0; c + 1 < (uint32_t)kStages; ++c) {
+        if (c < nchunks && c * kChunk + tid < C) cp_async16(buf + c * kChunk + tid, rec + c * kChunk + tid);
         cp_async_commit();
       }
       for (uint32_t c = 0; c < nchunks; ++c) {
         const uint32_t base = c * kChunk;
         const uint32_t n = min(C - base, (uint32_t)kChunk);
-        const BoxRec* cur = buf + (c & 1) * kChunk;
-        if (c + 1 < nchunks && base + kChunk + tid < C)
-          cp_async16(buf + ((c + 1) & 1) * kChunk + tid, rec + base + kChunk + tid);
+        const BoxRec* cur = buf + (c % kStages) * kChunk;
+        const uint32_t nc = c + kStages - 1;
+        if (nc < nchunks && nc * kChunk + tid < C)
+          cp_async16(buf + (nc % kStages) * kChunk + tid, rec + nc * kChunk + tid);
         cp_async_commit();
-        cp_async_wait1();
+        cp_async_wait_stages();
         __syncthreads();
         // per box: its x in the row's direction, w, h, and whether it starts a row
         uint32_t flag = 0;
@@ -424,7 +430,7 @@ __global__ void __launch_bounds__(256) k_pack_place(PackScratch p, PackArgs a) {
 }
 
 size_t push_smem_bytes(uint32_t front_cap) {
-  return (size_t)2 * kChunk * sizeof(BoxRec) + (size_t)(4 * kChunk + 4) * 4 + (size_t)front_cap * 4;
+  return (size_t)kStages * kChunk * sizeof(BoxRec) + (size_t)(4 * kChunk + 4) * 4 + (size_t)front_cap * 4;
 }
 
 }  // namespace

@@ -81,10 +81,6 @@ __device__ __forceinline__ SV project(const CV& c, float hx, float hy) {
   return s;
 }
 
-__device__ __forceinline__ bool top_left(int64_t ax, int64_t ay, int64_t bx, int64_t by) {
-  int64_t dx = bx - ax, dy = by - ay;
-  return dy < 0 || (dy == 0 && dx < 0);
-}
 
 // Setup of one sub-triangle: area, 1/A, clamped pixel box.
 struct Setup {
@@ -107,38 +103,71 @@ __device__ __forceinline__ Setup setup(const SV& a, const SV& b, const SV& c, in
   return s;
 }
 
-// Visit covered samples of a sub-triangle over pixel rect [px0..px1] x [py0..py1].
-// PASS 0: atomicMin the depth key.  PASS 1: return true on the first sample whose
-// key <= zbuf.
+// Edge functions of a sub-triangle at the sample of pixel (px, py) and their steps
+// per pixel in x and y (exact int64; E is affine in the sample position).
+struct Edges {
+  int64_t e[3];   // E0 (edge b->c), E1 (c->a), E2 (a->b) at the sample
+  int64_t dx[3];  // change per +1 pixel in x
+  int64_t dy[3];  // change per +1 pixel in y
+  bool tl[3];
+};
+
+__device__ __forceinline__ Edges edges_at(const SV& a, const SV& b, const SV& c, int px, int py) {
+  Edges E;
+  const int64_t sx = (int64_t)px * 256 + 128, sy = (int64_t)py * 256 + 128;
+  const SV* v0[3] = {&b, &c, &a};
+  const SV* v1[3] = {&c, &a, &b};
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    const int64_t ex = v1[i]->X - v0[i]->X, ey = v1[i]->Y - v0[i]->Y;
+    E.e[i] = ex * (sy - v0[i]->Y) - ey * (sx - v0[i]->X);
+    E.dx[i] = -ey * 256;
+    E.dy[i] = ex * 256;
+    E.tl[i] = ey < 0 || (ey == 0 && ex < 0);
+  }
+  return E;
+}
+
+// Test and shade one sample with edge values e: covered (top-left rule) and a depth
+// in [-1, 1].  PASS 0: atomicMin the depth key; PASS 1: return key <= zbuf.
+template <int PASS>
+__device__ __forceinline__ bool sample(const Edges& E, const int64_t* e, const SV& a, const SV& b, const SV& c,
+                                       float invA, uint32_t* __restrict__ z) {
+  const bool in = (e[0] > 0 || (e[0] == 0 && E.tl[0])) && (e[1] > 0 || (e[1] == 0 && E.tl[1])) &&
+                  (e[2] > 0 || (e[2] == 0 && E.tl[2]));
+  if (!in) return false;
+  float s = __fmul_rn(__ll2float_rn(e[0]), a.zn);
+  s = __fadd_rn(s, __fmul_rn(__ll2float_rn(e[1]), b.zn));
+  s = __fadd_rn(s, __fmul_rn(__ll2float_rn(e[2]), c.zn));
+  const float d = __fmul_rn(s, invA);
+  if (!(d >= -1.0f && d <= 1.0f)) return false;
+  const uint32_t key = ordered(d);
+  if (PASS == 0) {
+    if (key < *z) atomicMin(z, key);
+    return false;
+  }
+  return key <= __ldcg(z);
+}
+
+// Visit the samples of a sub-triangle over pixel rect [px0..px1] x [py0..py1],
+// stepping the edge functions.  PASS 1 returns true at the first visible sample.
 template <int PASS>
 __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, int px0, int py0,
                             int px1, int py1, uint32_t* __restrict__ zbuf, int W) {
-  const bool tl0 = top_left(b.X, b.Y, c.X, c.Y);
-  const bool tl1 = top_left(c.X, c.Y, a.X, a.Y);
-  const bool tl2 = top_left(a.X, a.Y, b.X, b.Y);
+  const Edges E = edges_at(a, b, c, px0, py0);
+  int64_t er[3] = {E.e[0], E.e[1], E.e[2]};
   for (int py = py0; py <= py1; ++py) {
-    const int64_t sy = (int64_t)py * 256 + 128;
+    int64_t e[3] = {er[0], er[1], er[2]};
+    uint32_t* zrow = zbuf + (size_t)py * W;
     for (int px = px0; px <= px1; ++px) {
-      const int64_t sx = (int64_t)px * 256 + 128;
-      int64_t e0 = (c.X - b.X) * (sy - b.Y) - (c.Y - b.Y) * (sx - b.X);
-      int64_t e1 = (a.X - c.X) * (sy - c.Y) - (a.Y - c.Y) * (sx - c.X);
-      int64_t e2 = (b.X - a.X) * (sy - a.Y) - (b.Y - a.Y) * (sx - a.X);
-      bool in = (e0 > 0 || (e0 == 0 && tl0)) && (e1 > 0 || (e1 == 0 && tl1)) &&
-                (e2 > 0 || (e2 == 0 && tl2));
-      if (!in) continue;
-      float s = __fmul_rn(__ll2float_rn(e0), a.zn);
-      s = __fadd_rn(s, __fmul_rn(__ll2float_rn(e1), b.zn));
-      s = __fadd_rn(s, __fmul_rn(__ll2float_rn(e2), c.zn));
-      float d = __fmul_rn(s, invA);
-      if (!(d >= -1.0f && d <= 1.0f)) continue;
-      uint32_t key = ordered(d);
-      uint32_t* z = zbuf + (size_t)py * W + px;
-      if (PASS == 0) {
-        if (key < *z) atomicMin(z, key);
-      } else {
-        if (key <= __ldcg(z)) return true;
-      }
+      if (sample<PASS>(E, e, a, b, c, invA, zrow + px) && PASS == 1) return true;
+      e[0] += E.dx[0];
+      e[1] += E.dx[1];
+      e[2] += E.dx[2];
     }
+    er[0] += E.dy[0];
+    er[1] += E.dy[1];
+    er[2] += E.dy[2];
   }
   return false;
 }
@@ -497,11 +526,15 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
     const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
     const float invA = __fdiv_rn(1.0f, __ll2float_rn(Ar));
     bool vis = false;
+    const int px = bx + (int)(lane % kBigTile), py_first = by + (int)(lane / kBigTile);
+    const Edges E = edges_at(a, b, c, px, py_first);
+    int64_t e[3] = {E.e[0], E.e[1], E.e[2]};
 #pragma unroll 1
-    for (int j = lane; j < kBigTile * kBigTile; j += 32) {
-      const int px = bx + (j % kBigTile), py = by + (j / kBigTile);
-      if (px > px1 || py > py1) continue;
-      vis |= raster_rect<PASS>(a, b, c, invA, px, py, px, py, A.zbuf, A.W);
+    for (int py = py_first; py < by + kBigTile; py += 32 / kBigTile) {
+      if (px <= px1 && py <= py1) vis |= sample<PASS>(E, e, a, b, c, invA, A.zbuf + (size_t)py * A.W + px);
+      e[0] += E.dy[0] * (32 / kBigTile);
+      e[1] += E.dy[1] * (32 / kBigTile);
+      e[2] += E.dy[2] * (32 / kBigTile);
     }
     if (PASS == 1) {
       if (__any_sync(0xFFFFFFFFu, vis) && lane == 0) atomicOr(A.vt + (q.tri >> 5), 1u << (q.tri & 31));
