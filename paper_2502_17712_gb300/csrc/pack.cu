@@ -16,13 +16,13 @@
 //   offset (a block reduction over the preceding tile totals), giving P, and
 //   reduces the largest overflow m past omega (Sec. 4.3).  Then one CTA per
 //   candidate (k_pack_push) pushes the rows up against a frontline in shared
-//   memory: boxes are staged 1024 at a time with cp.async (double buffered), the
+//   memory: boxes are read 4096 at a time into shared-memory x / w / h arrays, the
 //   rows inside a chunk are found by a block scan, and each row segment is processed
-//   box-parallel (a warp per box for rows of at most 32 boxes, a thread per box
-//   otherwise): resting height = max of the frontline under the box, then the
-//   frontline takes the box top.  Segments of one row never overlap in x, so a row
-//   may span two chunks.  The last CTA to finish selects the candidate and writes
-//   the placements.
+//   box-parallel (a group of 32 .. 1 threads per box, by the row's box count):
+//   resting height = max of the frontline under the box, then the frontline takes
+//   the box top, one barrier per segment.  Segments of one row never overlap in x,
+//   so a row may span two chunks.  The last CTA to finish selects the candidate;
+//   k_pack_place writes the placements with all CTAs.
 #include "fa_internal.cuh"
 
 namespace fa {
@@ -256,30 +256,19 @@ __global__ void __launch_bounds__(kThreads) k_pack_fix(PackScratch p, PackArgs a
   }
 }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  const uint32_t s = (uint32_t)__cvta_generic_to_shared(smem);
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
 // Row push of one candidate per CTA, then the last CTA selects.
 constexpr int kPushThreads = 1024;
-constexpr int kChunk = 1024;  // boxes staged per chunk (one per thread)
-constexpr int kStages = 4;    // chunk buffers in the prefetch ring
-__device__ __forceinline__ void cp_async_wait_stages() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(kStages - 1) : "memory");
-}
+constexpr int kChunk = 4096;                        // boxes per chunk
+constexpr int kPerThread = kChunk / kPushThreads;   // consecutive boxes per thread
 
 __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
   pdl_wait();
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  BoxRec* buf = reinterpret_cast<BoxRec*>(smem_raw);                     // [kStages][kChunk]
-  uint32_t* s_x = reinterpret_cast<uint32_t*>(buf + kStages * kChunk);  // [kChunk] box x
-  uint32_t* s_w = s_x + kChunk;                                        // [kChunk]
-  uint32_t* s_h = s_w + kChunk;                                        // [kChunk]
-  uint32_t* s_seg = s_h + kChunk;                                      // [kChunk + 1]
-  uint32_t* F = s_seg + kChunk + 4;                                    // [front_cap]
+  uint32_t* s_x = reinterpret_cast<uint32_t*>(smem_raw);  // [kChunk] box x in its row's direction
+  uint32_t* s_w = s_x + kChunk;                            // [kChunk]
+  uint32_t* s_h = s_w + kChunk;                            // [kChunk]
+  uint32_t* s_seg = s_h + kChunk;                          // [kChunk + 1] first box of each segment
+  uint32_t* F = s_seg + kChunk + 4;                        // [front_cap]
   __shared__ uint32_t ws32[32];
   __shared__ uint32_t s_flag, s_nseg, s_last;
 
@@ -307,36 +296,39 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       if (tid == 0) s_flag = 0;
       uint32_t Hloc = 0;
       const uint32_t nchunks = (C + kChunk - 1) / kChunk;
-      // ring of kStages chunk buffers with kStages - 1 chunks in flight ahead
-#pragma unroll
-      for (uint32_t c = 0; c + 1 < (uint32_t)kStages; ++c) {
-        if (c < nchunks && c * kChunk + tid < C) cp_async16(buf + c * kChunk + tid, rec + c * kChunk + tid);
-        cp_async_commit();
-      }
       for (uint32_t c = 0; c < nchunks; ++c) {
         const uint32_t base = c * kChunk;
         const uint32_t n = min(C - base, (uint32_t)kChunk);
-        const BoxRec* cur = buf + (c % kStages) * kChunk;
-        const uint32_t nc = c + kStages - 1;
-        if (nc < nchunks && nc * kChunk + tid < C)
-          cp_async16(buf + (nc % kStages) * kChunk + tid, rec + nc * kChunk + tid);
-        cp_async_commit();
-        cp_async_wait_stages();
-        __syncthreads();
-        // per box: its x in the row's direction, w, h, and whether it starts a row
-        uint32_t flag = 0;
-        if (tid < n) {
-          const BoxRec r = cur[tid];
-          const unsigned long long q = r.P >> a.atlas_log2;
-          const uint32_t xr = (uint32_t)(r.P & (om - 1));
-          s_x[tid] = (q % 3ull == 0ull) ? xr : Om - xr - r.w;
-          s_w[tid] = r.w;
-          s_h[tid] = r.h;
-          flag = (tid == 0 || (cur[tid - 1].P >> a.atlas_log2) != q) ? 1u : 0u;
+        // thread tid owns boxes kPerThread * tid .. + kPerThread - 1 of the chunk
+        BoxRec r[kPerThread];
+        unsigned long long qprev = ~0ull;
+        const uint32_t j0t = tid * kPerThread;
+        if (j0t > 0 && j0t - 1 < n) qprev = __ldcg(&rec[base + j0t - 1].P) >> a.atlas_log2;
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e)
+          if (j0t + e < n) r[e] = rec[base + j0t + e];
+        uint32_t flags = 0, cnt = 0;
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e) {
+          const uint32_t j = j0t + e;
+          if (j < n) {
+            const unsigned long long q = r[e].P >> a.atlas_log2;
+            const uint32_t xr = (uint32_t)(r[e].P & (om - 1));
+            s_x[j] = (q % 3ull == 0ull) ? xr : Om - xr - r[e].w;
+            s_w[j] = r[e].w;
+            s_h[j] = r[e].h;
+            if (j == 0 || q != qprev) {
+              flags |= 1u << e;
+              ++cnt;
+            }
+            qprev = q;
+          }
         }
         uint32_t nseg;
-        const uint32_t si = block_scan_incl<uint32_t>(flag, ws32, &nseg);
-        if (flag) s_seg[si - 1] = tid;
+        uint32_t at = block_scan_incl<uint32_t>(cnt, ws32, &nseg) - cnt;
+#pragma unroll
+        for (int e = 0; e < kPerThread; ++e)
+          if (flags & (1u << e)) s_seg[at++] = j0t + e;
         if (tid == 0) {
           s_seg[nseg] = n;
           s_nseg = nseg;
@@ -344,28 +336,41 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
         __syncthreads();
         for (uint32_t sgi = 0; sgi < s_nseg; ++sgi) {
           const uint32_t j0 = s_seg[sgi], nbx = s_seg[sgi + 1] - j0;
-          // a group of g threads per box, g = 32 for <= 32 boxes ... 1 for > 512 boxes;
-          // 1024 / g >= nbx, so every box has a group.  A box's group reads and then
-          // writes only that box's texels, which no other box of the row touches.
-          // g = 2^lg = largest power of two <= 1024 / nbx, at most 32
-          const int lgb = nbx > 1 ? 32 - __clz(nbx - 1) : 0;  // ceil(log2(nbx))
-          const int lg = min(max(10 - lgb, 0), 5);
-          const uint32_t g = 1u << lg;
-          const uint32_t jj = tid >> lg, li = tid & (g - 1u);
-          uint32_t mx = 0, x = 0, w = 0;
-          if (jj < nbx) {
-            x = s_x[j0 + jj];
-            w = s_w[j0 + jj];
-            for (uint32_t u = li; u < w; u += g) mx = max(mx, F[x + u]);
-          }
-          for (uint32_t o = 1; o < g; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
-          if (jj < nbx) {
-            const uint32_t top = mx + s_h[j0 + jj];
-            for (uint32_t u = li; u < w; u += g) F[x + u] = top;
-            if (li == 0) {
-              xy[base + j0 + jj] = make_uint2(x, mx);
+          if (nbx > (uint32_t)kPushThreads) {
+            // a thread per box, several boxes per thread
+            for (uint32_t jj = tid; jj < nbx; jj += kPushThreads) {
+              const uint32_t j = j0 + jj, x = s_x[j], w = s_w[j];
+              uint32_t mx = 0;
+              for (uint32_t u = 0; u < w; ++u) mx = max(mx, F[x + u]);
+              const uint32_t top = mx + s_h[j];
+              for (uint32_t u = 0; u < w; ++u) F[x + u] = top;
+              xy[base + j] = make_uint2(x, mx);
               Hloc = max(Hloc, top);
               if (top > Om) s_flag = 1;
+            }
+          } else {
+            // a group of g threads per box, g = 32 for <= 32 boxes ... 1 for > 512:
+            // 1024 / g >= nbx, so every box has a group.  A box's group reads and then
+            // writes only that box's texels, which no other box of the row touches.
+            const int lgb = nbx > 1 ? 32 - __clz(nbx - 1) : 0;  // ceil(log2(nbx))
+            const int lg = min(max(10 - lgb, 0), 5);
+            const uint32_t g = 1u << lg;
+            const uint32_t jj = tid >> lg, li = tid & (g - 1u);
+            uint32_t mx = 0, x = 0, w = 0;
+            if (jj < nbx) {
+              x = s_x[j0 + jj];
+              w = s_w[j0 + jj];
+              for (uint32_t u = li; u < w; u += g) mx = max(mx, F[x + u]);
+            }
+            for (uint32_t o = 1; o < g; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
+            if (jj < nbx) {
+              const uint32_t top = mx + s_h[j0 + jj];
+              for (uint32_t u = li; u < w; u += g) F[x + u] = top;
+              if (li == 0) {
+                xy[base + j0 + jj] = make_uint2(x, mx);
+                Hloc = max(Hloc, top);
+                if (top > Om) s_flag = 1;
+              }
             }
           }
           __syncthreads();
@@ -373,7 +378,6 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
         }
         if (s_flag) break;
       }
-      cp_async_wait0();
       H = block_max<uint32_t>(Hloc, ws32);
       ok = (!s_flag && H <= Om) ? 1u : 0u;
     }
@@ -430,7 +434,7 @@ __global__ void __launch_bounds__(256) k_pack_place(PackScratch p, PackArgs a) {
 }
 
 size_t push_smem_bytes(uint32_t front_cap) {
-  return (size_t)kStages * kChunk * sizeof(BoxRec) + (size_t)(4 * kChunk + 4) * 4 + (size_t)front_cap * 4;
+  return (size_t)(4 * kChunk + 4) * 4 + (size_t)front_cap * 4;
 }
 
 }  // namespace

@@ -143,7 +143,7 @@ __device__ __forceinline__ bool sample(const Edges& E, const int64_t* e, const S
   if (!(d >= -1.0f && d <= 1.0f)) return false;
   const uint32_t key = ordered(d);
   if (PASS == 0) {
-    if (key < *z) atomicMin(z, key);
+    atomicMin(z, key);  // result unused: a fire-and-forget reduction
     return false;
   }
   return key <= __ldcg(z);
@@ -156,11 +156,13 @@ __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, i
                             int px1, int py1, uint32_t* __restrict__ zbuf, int W) {
   const Edges E = edges_at(a, b, c, px0, py0);
   int64_t er[3] = {E.e[0], E.e[1], E.e[2]};
+  bool vis = false;  // PASS 1: no early exit, so the depth loads can overlap
   for (int py = py0; py <= py1; ++py) {
     int64_t e[3] = {er[0], er[1], er[2]};
     uint32_t* zrow = zbuf + (size_t)py * W;
+#pragma unroll 2
     for (int px = px0; px <= px1; ++px) {
-      if (sample<PASS>(E, e, a, b, c, invA, zrow + px) && PASS == 1) return true;
+      vis |= sample<PASS>(E, e, a, b, c, invA, zrow + px);
       e[0] += E.dx[0];
       e[1] += E.dx[1];
       e[2] += E.dx[2];
@@ -169,7 +171,7 @@ __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, i
     er[1] += E.dy[1];
     er[2] += E.dy[2];
   }
-  return false;
+  return vis;
 }
 
 // One small sub-triangle that passed the depth pre-pass set-up: its snapped
