@@ -203,25 +203,31 @@ __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* n
 }
 
 // Flatten visible triangles to their root and count roots per block of
-// kPerBlock triangles.
+// kPerBlock triangles: warp w of the block owns VT words w, w + 8, w + 16, w + 24.
 __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt) {
   pdl_wait();
-  __shared__ uint32_t cnt;
-  if (threadIdx.x == 0) cnt = 0;
-  __syncthreads();
-  const uint32_t base = blockIdx.x * kPerBlock;
+  __shared__ uint32_t cnt[kBlock / 32];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t nwords = (a.T + 31) >> 5;
   uint32_t mine = 0;
+#pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t t = base + k * kBlock + threadIdx.x;
-    if (t >= a.T || !vt_bit(a.vt, t)) continue;
-    int32_t r = find_root(a.label, (int32_t)t);
+    const uint32_t w = blockIdx.x * (kPerBlock / 32) + k * (kBlock / 32) + wid;
+    const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
+    if (!((word >> lane) & 1u)) continue;
+    const uint32_t t = (w << 5) + lane;
+    const int32_t r = find_root(a.label, (int32_t)t);
     a.label[t] = r;
     mine += (r == (int32_t)t);
   }
   mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-  if ((threadIdx.x & 31) == 0 && mine) atomicAdd(&cnt, mine);
+  if (lane == 0) cnt[wid] = mine;
   __syncthreads();
-  if (threadIdx.x == 0) blockcnt[blockIdx.x] = cnt;
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int i = 0; i < kBlock / 32; ++i) s += cnt[i];
+    blockcnt[blockIdx.x] = s;
+  }
 }
 
 // Exclusive scan of the per-block root counts (one block); writes the chart count.
@@ -274,38 +280,37 @@ __global__ void __launch_bounds__(kBlock) k_number(UfArgs a, const uint32_t* blo
                                                    uint32_t* roots, uint32_t* box_enc,
                                                    uint32_t* box_full, uint32_t max_charts) {
   pdl_wait();
-  __shared__ uint32_t warp_tot[kBlock / 32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = blockcnt[blockIdx.x];
-  __syncthreads();
-  const uint32_t base = blockIdx.x * kPerBlock;
+  __shared__ uint32_t wcount[kPerBlock / 32];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const uint32_t nwords = (a.T + 31) >> 5;
+  // roots of each of the block's 32 words (word order = triangle order)
+  uint32_t rbits[kPerBlock / kBlock];
+#pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t t = base + k * kBlock + threadIdx.x;
+    const uint32_t wl = k * (kBlock / 32) + wid;
+    const uint32_t w = blockIdx.x * (kPerBlock / 32) + wl;
+    const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
     bool root = false;
-    if (t < a.T && vt_bit(a.vt, t)) root = (__ldcg(a.label + t) == (int32_t)t);
-    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, root);
-    const uint32_t lane = threadIdx.x & 31;
-    if (lane == 0) warp_tot[threadIdx.x >> 5] = __popc(ball);
-    __syncthreads();
-    uint32_t pre = carry;
-    for (uint32_t w = 0; w < (threadIdx.x >> 5); ++w) pre += warp_tot[w];
-    pre += __popc(ball & ((1u << lane) - 1u));
-    if (root && pre < max_charts) {
+    if ((word >> lane) & 1u) root = __ldcg(a.label + (w << 5) + lane) == (int32_t)((w << 5) + lane);
+    rbits[k] = __ballot_sync(0xFFFFFFFFu, root);
+    if (lane == 0) wcount[wl] = __popc(rbits[k]);
+  }
+  __syncthreads();
+  const uint32_t base = __ldcg(blockcnt + blockIdx.x);
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t wl = k * (kBlock / 32) + wid;
+    if (!((rbits[k] >> lane) & 1u)) continue;
+    uint32_t pre = base;
+    for (uint32_t i = 0; i < wl; ++i) pre += wcount[i];
+    pre += __popc(rbits[k] & ((1u << lane) - 1u));
+    const uint32_t t = ((blockIdx.x * (kPerBlock / 32) + wl) << 5) + lane;
+    if (pre < max_charts) {
       cid[t] = (int32_t)pre;
       roots[pre] = t;
-      box_enc[4 * pre + 0] = 0xFFFFFFFFu;  // min x (ordered encoding)
-      box_enc[4 * pre + 1] = 0xFFFFFFFFu;  // min y
-      box_enc[4 * pre + 2] = 0u;           // max x
-      box_enc[4 * pre + 3] = 0u;           // max y
+      reinterpret_cast<uint4*>(box_enc)[pre] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
       box_full[pre] = 0u;
     }
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      uint32_t tot = 0;
-      for (int w = 0; w < kBlock / 32; ++w) tot += warp_tot[w];
-      carry += tot;
-    }
-    __syncthreads();
   }
 }
 

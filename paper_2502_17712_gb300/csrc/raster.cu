@@ -374,12 +374,47 @@ __device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t, f
   return 1;
 }
 
-// Exact set-up and depth raster of an unclipped triangle from its clip coordinates.
+// Exact set-up and depth raster of an unclipped triangle from its clip coordinates,
+// all in registers (the fan of an unclipped triangle is the triangle itself).
+// Returns 1 with the candidate record in *out for a small triangle.
 __device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, const float4& c0, const float4& c1,
                                               const float4& c2, CandTri* out) {
-  const CV v0{c0.x, c0.y, c0.z, c0.w}, v1{c1.x, c1.y, c1.z, c1.w}, v2{c2.x, c2.y, c2.z, c2.w};
-  SV sv[3] = {project(v0, A.hx, A.hy), project(v1, A.hx, A.hy), project(v2, A.hx, A.hy)};
-  return depth_fan(A, t, sv, 3, out);
+  const SV a = project(CV{c0.x, c0.y, c0.z, c0.w}, A.hx, A.hy);
+  const SV b = project(CV{c1.x, c1.y, c1.z, c1.w}, A.hx, A.hy);
+  const SV c = project(CV{c2.x, c2.y, c2.z, c2.w}, A.hx, A.hy);
+  const Setup s = setup(a, b, c, A.W, A.H);
+  if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) return 0;
+  const int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
+  if (w * h > kSmallMaxPix) {
+    const uint64_t tiles = (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
+    const unsigned long long old = atomicAdd(&A.ctr->big, (1ull << 40) | (unsigned long long)tiles);
+    const uint64_t e0 = old >> 40, tile = old & ((1ull << 40) - 1);
+    if (e0 < A.queue_cap && tile + tiles <= A.tile_cap) {
+      BigTri bt;
+      bt.X[0] = (int32_t)a.X; bt.X[1] = (int32_t)b.X; bt.X[2] = (int32_t)c.X;
+      bt.Y[0] = (int32_t)a.Y; bt.Y[1] = (int32_t)b.Y; bt.Y[2] = (int32_t)c.Y;
+      bt.zn[0] = a.zn; bt.zn[1] = b.zn; bt.zn[2] = c.zn;
+      bt.px0 = s.px0; bt.py0 = s.py0; bt.px1 = s.px1; bt.py1 = s.py1;
+      bt.tri = t;
+      bt.tile0 = (uint32_t)tile;
+      bt.pad = 0;
+      A.queue[e0] = bt;
+      for (uint64_t j = 0; j < tiles; ++j) A.tile_owner[tile + j] = (uint32_t)e0;
+      return 0;
+    }
+    // queue or tile table full: empty record, no owners, rasterized here
+    if (e0 < A.queue_cap) {
+      BigTri bt = {};
+      bt.px0 = 1; bt.px1 = 0; bt.py0 = 1; bt.py1 = 0;
+      bt.tile0 = (uint32_t)tile;
+      A.queue[e0] = bt;
+    }
+    for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
+  }
+  const float invA = __fdiv_rn(1.0f, __ll2float_rn(s.A));
+  raster_rect<0>(a, b, c, invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W);
+  *out = make_cand(a, b, c, s, t);
+  return 1;
 }
 
 __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __restrict__ vt, uint32_t nwords,
