@@ -162,6 +162,28 @@ __device__ __forceinline__ float4 load_clip(const Mat4& M, const float* __restri
   return transform(M, __ldg(p), __ldg(p + 1), __ldg(p + 2));
 }
 
+// int64 -> fp32 with round-to-nearest-even, on the integer and fp32 pipes (the
+// hardware 64-bit conversion runs on the fp64 units, which this GPU has few of).
+// Exact: the same value as a correctly rounded conversion.
+__device__ __forceinline__ float ll2float_rn(long long v) {
+  if (v >= -2147483648ll && v <= 2147483647ll) return __int2float_rn((int)v);
+  const bool neg = v < 0;
+  unsigned long long u = neg ? 0ull - (unsigned long long)v : (unsigned long long)v;
+  const int lz = __clzll(u);
+  int shift = 40 - lz;  // bits dropped so that 24 remain (u >= 2^31, so shift > 0)
+  unsigned long long mant = u >> shift;
+  const unsigned long long rem = u & ((1ull << shift) - 1ull), half = 1ull << (shift - 1);
+  if (rem > half || (rem == half && (mant & 1ull))) ++mant;
+  if (mant == (1ull << 24)) {
+    mant >>= 1;
+    ++shift;
+  }
+  const float m = __uint2float_rn((unsigned)mant);              // exact: mant < 2^24
+  const float scale = __uint_as_float((unsigned)(127 + shift) << 23);  // 2^shift
+  const float r = m * scale;                                     // exact power-of-two scaling
+  return neg ? -r : r;
+}
+
 // Order-preserving map float -> uint32 (with -0 folded onto +0).
 __device__ __forceinline__ uint32_t ordered(float f) {
   uint32_t u = __float_as_uint(f);

@@ -296,17 +296,29 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       if (tid == 0) s_flag = 0;
       uint32_t Hloc = 0;
       const uint32_t nchunks = (C + kChunk - 1) / kChunk;
+      // thread tid owns boxes kPerThread * tid .. + kPerThread - 1 of each chunk; the
+      // next chunk's records are loaded into registers while this one is pushed
+      const uint32_t j0t = tid * kPerThread;
+      BoxRec nxt[kPerThread];
+      unsigned long long nprev = 0;
+#pragma unroll
+      for (int e = 0; e < kPerThread; ++e)
+        if (j0t + e < C) nxt[e] = rec[j0t + e];
+      if (j0t > 0 && j0t - 1 < C) nprev = __ldcg(&rec[j0t - 1].P);
       for (uint32_t c = 0; c < nchunks; ++c) {
         const uint32_t base = c * kChunk;
         const uint32_t n = min(C - base, (uint32_t)kChunk);
-        // thread tid owns boxes kPerThread * tid .. + kPerThread - 1 of the chunk
         BoxRec r[kPerThread];
-        unsigned long long qprev = ~0ull;
-        const uint32_t j0t = tid * kPerThread;
-        if (j0t > 0 && j0t - 1 < n) qprev = __ldcg(&rec[base + j0t - 1].P) >> a.atlas_log2;
 #pragma unroll
-        for (int e = 0; e < kPerThread; ++e)
-          if (j0t + e < n) r[e] = rec[base + j0t + e];
+        for (int e = 0; e < kPerThread; ++e) r[e] = nxt[e];
+        unsigned long long qprev = (j0t > 0) ? (nprev >> a.atlas_log2) : ~0ull;
+        if (c + 1 < nchunks) {
+          const uint32_t nb = base + kChunk;
+#pragma unroll
+          for (int e = 0; e < kPerThread; ++e)
+            if (nb + j0t + e < C) nxt[e] = rec[nb + j0t + e];
+          if (j0t > 0 && nb + j0t - 1 < C) nprev = __ldcg(&rec[nb + j0t - 1].P);
+        }
         uint32_t flags = 0, cnt = 0;
 #pragma unroll
         for (int e = 0; e < kPerThread; ++e) {

@@ -75,8 +75,10 @@ __device__ __forceinline__ SV project(const CV& c, float hx, float hy) {
   float xs = __fmul_rn(__fadd_rn(nx, 1.0f), hx);
   float ys = __fmul_rn(__fadd_rn(ny, 1.0f), hy);
   SV s;
-  s.X = __float2ll_rn(__fmul_rn(xs, 256.0f));
-  s.Y = __float2ll_rn(__fmul_rn(ys, 256.0f));
+  // |xs * 256| < 2^28 inside the guard band |x|, |y| <= 64 w, so the rounded value
+  // fits an int32 (and the 32-bit conversion avoids the fp64 units)
+  s.X = __float2int_rn(__fmul_rn(xs, 256.0f));
+  s.Y = __float2int_rn(__fmul_rn(ys, 256.0f));
   s.zn = zn;
   return s;
 }
@@ -136,9 +138,9 @@ __device__ __forceinline__ bool sample(const Edges& E, const int64_t* e, const S
   const bool in = (e[0] > 0 || (e[0] == 0 && E.tl[0])) && (e[1] > 0 || (e[1] == 0 && E.tl[1])) &&
                   (e[2] > 0 || (e[2] == 0 && E.tl[2]));
   if (!in) return false;
-  float s = __fmul_rn(__ll2float_rn(e[0]), a.zn);
-  s = __fadd_rn(s, __fmul_rn(__ll2float_rn(e[1]), b.zn));
-  s = __fadd_rn(s, __fmul_rn(__ll2float_rn(e[2]), c.zn));
+  float s = __fmul_rn(ll2float_rn(e[0]), a.zn);
+  s = __fadd_rn(s, __fmul_rn(ll2float_rn(e[1]), b.zn));
+  s = __fadd_rn(s, __fmul_rn(ll2float_rn(e[2]), c.zn));
   const float d = __fmul_rn(s, invA);
   if (!(d >= -1.0f && d <= 1.0f)) return false;
   const uint32_t key = ordered(d);
@@ -281,7 +283,7 @@ __device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, C
   for (int i = 1; i + 1 < n; ++i) {
     Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
     if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
-    float invA = __fdiv_rn(1.0f, __ll2float_rn(s.A));
+    float invA = __fdiv_rn(1.0f, ll2float_rn(s.A));
     raster_rect<0>(sv[0], sv[i], sv[i + 1], invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W);
     const CandTri r = make_cand(sv[0], sv[i], sv[i + 1], s, t);
     if (out && nq == 1) {
@@ -411,7 +413,7 @@ __device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, c
     }
     for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
   }
-  const float invA = __fdiv_rn(1.0f, __ll2float_rn(s.A));
+  const float invA = __fdiv_rn(1.0f, ll2float_rn(s.A));
   raster_rect<0>(a, b, c, invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W);
   *out = make_cand(a, b, c, s, t);
   return 1;
@@ -524,7 +526,7 @@ __global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
       const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
       t = __float_as_uint(fc.w);
       const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
-      const float invA = __fdiv_rn(1.0f, __ll2float_rn(Ar));
+      const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
       vis = raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
                            (int)(b1 >> 16), A.zbuf, A.W);
     }
@@ -561,7 +563,7 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
     const int bx = px0 + (int)(local % tx_n) * kBigTile, by = py0 + (int)(local / tx_n) * kBigTile;
     SV a{q.X[0], q.Y[0], q.zn[0]}, b{q.X[1], q.Y[1], q.zn[1]}, c{q.X[2], q.Y[2], q.zn[2]};
     const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
-    const float invA = __fdiv_rn(1.0f, __ll2float_rn(Ar));
+    const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
     bool vis = false;
     const int px = bx + (int)(lane % kBigTile), py_first = by + (int)(lane / kBigTile);
     const Edges E = edges_at(a, b, c, px, py_first);
