@@ -139,6 +139,7 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->queue, ctx->queue_cap);
   ctx->tile_cap = 4u * ctx->queue_cap;
   FA_ALLOC(ctx->tile_owner, ctx->tile_cap);
+  // survivor-indexed records [0, T) and clipped-path records [T, T + 65536)
   ctx->cand_cap = (uint32_t)(T + 65536 < 0xFFFFFFFFull ? T + 65536 : 0xFFFFFFFFull);
   if (st == FA_OK) st = alloc((unsigned char**)&ctx->cand, (size_t)ctx->cand_cap * 48);
   FA_ALLOC(ctx->surv, T);

@@ -187,6 +187,8 @@ struct CandTri {
 };
 static_assert(sizeof(CandTri) == 48, "CandTri is 48 bytes");
 
+constexpr int kFrontThreads = 512;
+
 struct RasterArgs {
   Mat4 M;
   const float* pos;
@@ -290,7 +292,7 @@ __device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, C
       *out = r;
       nout = 1;
     } else {
-      store_cand(A, atomicAdd(&A.ctr->ncand, 1u), r);
+      store_cand(A, A.T + atomicAdd(&A.ctr->ncand, 1u), r);
     }
   }
   return nout;
@@ -376,47 +378,21 @@ __device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t, f
   return 1;
 }
 
-// Exact set-up and depth raster of an unclipped triangle from its clip coordinates,
+// Snapped vertices and set-up of an unclipped triangle from its clip coordinates,
 // all in registers (the fan of an unclipped triangle is the triangle itself).
-// Returns 1 with the candidate record in *out for a small triangle.
-__device__ __forceinline__ int exact_triangle(const RasterArgs& A, uint32_t t, const float4& c0, const float4& c1,
-                                              const float4& c2, CandTri* out) {
-  const SV a = project(CV{c0.x, c0.y, c0.z, c0.w}, A.hx, A.hy);
-  const SV b = project(CV{c1.x, c1.y, c1.z, c1.w}, A.hx, A.hy);
-  const SV c = project(CV{c2.x, c2.y, c2.z, c2.w}, A.hx, A.hy);
-  const Setup s = setup(a, b, c, A.W, A.H);
-  if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) return 0;
-  const int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
-  if (w * h > kSmallMaxPix) {
-    const uint64_t tiles = (uint64_t)((w + kBigTile - 1) / kBigTile) * (uint64_t)((h + kBigTile - 1) / kBigTile);
-    const unsigned long long old = atomicAdd(&A.ctr->big, (1ull << 40) | (unsigned long long)tiles);
-    const uint64_t e0 = old >> 40, tile = old & ((1ull << 40) - 1);
-    if (e0 < A.queue_cap && tile + tiles <= A.tile_cap) {
-      BigTri bt;
-      bt.X[0] = (int32_t)a.X; bt.X[1] = (int32_t)b.X; bt.X[2] = (int32_t)c.X;
-      bt.Y[0] = (int32_t)a.Y; bt.Y[1] = (int32_t)b.Y; bt.Y[2] = (int32_t)c.Y;
-      bt.zn[0] = a.zn; bt.zn[1] = b.zn; bt.zn[2] = c.zn;
-      bt.px0 = s.px0; bt.py0 = s.py0; bt.px1 = s.px1; bt.py1 = s.py1;
-      bt.tri = t;
-      bt.tile0 = (uint32_t)tile;
-      bt.pad = 0;
-      A.queue[e0] = bt;
-      for (uint64_t j = 0; j < tiles; ++j) A.tile_owner[tile + j] = (uint32_t)e0;
-      return 0;
-    }
-    // queue or tile table full: empty record, no owners, rasterized here
-    if (e0 < A.queue_cap) {
-      BigTri bt = {};
-      bt.px0 = 1; bt.px1 = 0; bt.py0 = 1; bt.py1 = 0;
-      bt.tile0 = (uint32_t)tile;
-      A.queue[e0] = bt;
-    }
-    for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
-  }
-  const float invA = __fdiv_rn(1.0f, ll2float_rn(s.A));
-  raster_rect<0>(a, b, c, invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W);
-  *out = make_cand(a, b, c, s, t);
-  return 1;
+struct Exact {
+  SV a, b, c;
+  Setup s;
+};
+
+__device__ __forceinline__ Exact exact_setup(const RasterArgs& A, const float4& c0, const float4& c1,
+                                             const float4& c2) {
+  Exact E;
+  E.a = project(CV{c0.x, c0.y, c0.z, c0.w}, A.hx, A.hy);
+  E.b = project(CV{c1.x, c1.y, c1.z, c1.w}, A.hx, A.hy);
+  E.c = project(CV{c2.x, c2.y, c2.z, c2.w}, A.hx, A.hy);
+  E.s = setup(E.a, E.b, E.c, A.W, A.H);
+  return E;
 }
 
 __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __restrict__ vt, uint32_t nwords,
@@ -440,60 +416,126 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
 
 // Depth pre-pass, front end: one thread per triangle; survivors go to a compact list
 // (warp-aggregated appends) so that the exact set-up runs on full warps.
-__global__ void __launch_bounds__(256) k_raster_front(RasterArgs A) {
+__global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
   pdl_wait();
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const uint32_t nwarps = (gridDim.x * blockDim.x) >> 5;
-  const uint32_t nchunks = (A.T + 31) >> 5;
-  for (uint32_t w = warp; w < nchunks; w += nwarps) {
-    const uint32_t t = (w << 5) + lane;
+  __shared__ uint32_t s_cnt[2][kFrontThreads / 32];
+  __shared__ uint32_t s_base[2];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  // one block iteration covers kFrontThreads consecutive triangles; the block's
+  // survivors and clipped triangles are appended with one atomic each
+  for (uint32_t base = blockIdx.x * kFrontThreads; base < A.T; base += gridDim.x * kFrontThreads) {
+    const uint32_t t = base + threadIdx.x;
     float4 c[3];
     const int r = t < A.T ? front_triangle(A, t, c) : 0;
     const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, r == 1), b2 = __ballot_sync(0xFFFFFFFFu, r == 2);
-    if (b1) {
-      uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(&A.ctr->nsurv, (uint32_t)__popc(b1));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (r == 1) {
-        const uint32_t slot = base + __popc(b1 & ((1u << lane) - 1u));
-        A.surv[slot] = t;
-        float4* sc = A.surv_clip + 3 * (size_t)slot;
-        sc[0] = c[0];
-        sc[1] = c[1];
-        sc[2] = c[2];
-      }
+    if (lane == 0) {
+      s_cnt[0][wid] = __popc(b1);
+      s_cnt[1][wid] = __popc(b2);
     }
-    if (b2) {
-      uint32_t base = 0;
-      if (lane == 0) base = atomicAdd(&A.ctr->nclip, (uint32_t)__popc(b2));
-      base = __shfl_sync(0xFFFFFFFFu, base, 0);
-      if (r == 2) A.clip[base + __popc(b2 & ((1u << lane) - 1u))] = t;
+    __syncthreads();
+    if (threadIdx.x < 2) {
+      uint32_t tot = 0;
+      for (int w = 0; w < kFrontThreads / 32; ++w) tot += s_cnt[threadIdx.x][w];
+      s_base[threadIdx.x] = tot ? atomicAdd(threadIdx.x ? &A.ctr->nclip : &A.ctr->nsurv, tot) : 0u;
     }
+    __syncthreads();
+    uint32_t o1 = s_base[0], o2 = s_base[1];
+    for (uint32_t w = 0; w < wid; ++w) {
+      o1 += s_cnt[0][w];
+      o2 += s_cnt[1][w];
+    }
+    if (r == 1) {
+      const uint32_t slot = o1 + __popc(b1 & ((1u << lane) - 1u));
+      A.surv[slot] = t;
+      float4* sc = A.surv_clip + 3 * (size_t)slot;
+      sc[0] = c[0];
+      sc[1] = c[1];
+      sc[2] = c[2];
+    } else if (r == 2) {
+      A.clip[o2 + __popc(b2 & ((1u << lane) - 1u))] = t;
+    }
+    __syncthreads();  // s_cnt / s_base are rewritten by the next iteration
   }
 }
 
-// Depth pre-pass, exact part: survivors of the front end; single small sub-triangles
-// are appended to the candidate list by warp.
+// Depth pre-pass, exact part: survivors of the front end.  Survivor i writes its
+// candidate record (or an empty marker) at slot i, so no counter is needed; clipped
+// triangles append theirs after slot T.
 __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   pdl_wait();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t n = __ldcg(&A.ctr->nsurv);
   const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
-    const uint32_t i = base + lane;
-    CandTri r;
-    int has = 0;
+  for (uint32_t wbase = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n; wbase += stride) {
+    const uint32_t i = wbase + lane;
+    Exact E;
+    uint32_t t = 0, tiles = 0;
+    int kind = 0;  // 0 nothing, 1 small, 2 large
     if (i < n) {
       const float4* sc = A.surv_clip + 3 * (size_t)i;
-      has = exact_triangle(A, __ldcg(A.surv + i), __ldcs(sc), __ldcs(sc + 1), __ldcs(sc + 2), &r);
+      t = __ldcg(A.surv + i);
+      E = exact_setup(A, __ldcs(sc), __ldcs(sc + 1), __ldcs(sc + 2));
+      if (E.s.A > 0 && E.s.px1 >= E.s.px0 && E.s.py1 >= E.s.py0) {
+        const int w = E.s.px1 - E.s.px0 + 1, h = E.s.py1 - E.s.py0 + 1;
+        if (w * h > kSmallMaxPix) {
+          kind = 2;
+          tiles = (uint32_t)(((w + kBigTile - 1) / kBigTile) * ((h + kBigTile - 1) / kBigTile));
+        } else {
+          kind = 1;
+        }
+      }
     }
-    const uint32_t ball = __ballot_sync(0xFFFFFFFFu, has != 0);
-    if (ball == 0) continue;
-    uint32_t slot = 0;
-    if (lane == 0) slot = atomicAdd(&A.ctr->ncand, (uint32_t)__popc(ball));
-    slot = __shfl_sync(0xFFFFFFFFu, slot, 0);
-    if (has) store_cand(A, slot + __popc(ball & ((1u << lane) - 1u)), r);
+    // large triangles of the warp reserve queue records and tiles with one atomic
+    const uint32_t bigs = __ballot_sync(0xFFFFFFFFu, kind == 2);
+    if (bigs) {
+      uint32_t tpre = tiles;  // inclusive prefix of tiles over the warp
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, tpre, o);
+        if (lane >= (unsigned)o) tpre += y;
+      }
+      const uint32_t ttot = __shfl_sync(0xFFFFFFFFu, tpre, 31);
+      unsigned long long old = 0;
+      if (lane == 0)
+        old = atomicAdd(&A.ctr->big, ((unsigned long long)__popc(bigs) << 40) | (unsigned long long)ttot);
+      old = __shfl_sync(0xFFFFFFFFu, old, 0);
+      if (kind == 2) {
+        const uint64_t e = (old >> 40) + __popc(bigs & ((1u << lane) - 1u));
+        const uint64_t tile = (old & ((1ull << 40) - 1)) + (tpre - tiles);
+        if (e < A.queue_cap && tile + tiles <= A.tile_cap) {
+          BigTri bt;
+          bt.X[0] = (int32_t)E.a.X; bt.X[1] = (int32_t)E.b.X; bt.X[2] = (int32_t)E.c.X;
+          bt.Y[0] = (int32_t)E.a.Y; bt.Y[1] = (int32_t)E.b.Y; bt.Y[2] = (int32_t)E.c.Y;
+          bt.zn[0] = E.a.zn; bt.zn[1] = E.b.zn; bt.zn[2] = E.c.zn;
+          bt.px0 = E.s.px0; bt.py0 = E.s.py0; bt.px1 = E.s.px1; bt.py1 = E.s.py1;
+          bt.tri = t;
+          bt.tile0 = (uint32_t)tile;
+          bt.pad = 0;
+          A.queue[e] = bt;
+          for (uint32_t j = 0; j < tiles; ++j) A.tile_owner[tile + j] = (uint32_t)e;
+          kind = 0;
+        } else {
+          // queue or tile table full: empty record, no owners, rasterized here
+          if (e < A.queue_cap) {
+            BigTri bt = {};
+            bt.px0 = 1; bt.px1 = 0; bt.py0 = 1; bt.py1 = 0;
+            bt.tile0 = (uint32_t)tile;
+            A.queue[e] = bt;
+          }
+          for (uint64_t j = tile; j < tile + tiles && j < A.tile_cap; ++j) A.tile_owner[j] = 0xFFFFFFFFu;
+          kind = 1;
+        }
+      }
+    }
+    if (i < n) {
+      if (kind == 1) {
+        const float invA = __fdiv_rn(1.0f, ll2float_rn(E.s.A));
+        raster_rect<0>(E.a, E.b, E.c, invA, E.s.px0, E.s.py0, E.s.px1, E.s.py1, A.zbuf, A.W);
+        store_cand(A, i, make_cand(E.a, E.b, E.c, E.s, t));
+      } else {
+        reinterpret_cast<uint32_t*>(A.cand + i)[6] = 0xFFFFFFFFu;  // empty: px0 = py0 = 0xFFFF
+      }
+    }
   }
   // then the (rare) triangles that need clipping
   const uint32_t nc = __ldcg(&A.ctr->nclip);
@@ -511,24 +553,30 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
 __global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
   pdl_wait();
   if (__ldcg(&A.ctr->status) != 0) return;
-  const uint32_t n = min(__ldcg(&A.ctr->ncand), A.cand_cap);
+  const uint32_t ns = __ldcg(&A.ctr->nsurv);
+  const uint32_t nc = min(__ldcg(&A.ctr->ncand), A.cand_cap - A.T);
+  const uint32_t n = ns + nc;  // slots [0, ns) then [T, T + nc)
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const uint32_t i = base + threadIdx.x;
+    const uint32_t k = base + threadIdx.x;
     bool vis = false;
     uint32_t t = 0xFFFFFFFFu;
-    if (i < n) {
+    if (k < n) {
+      const uint32_t i = k < ns ? k : A.T + (k - ns);
       const float4* s = reinterpret_cast<const float4*>(A.cand + i);
-      const float4 fa = __ldcs(s), fb = __ldcs(s + 1), fc = __ldcs(s + 2);
-      const SV a{__float_as_int(fa.x), __float_as_int(fa.y), fc.x};
-      const SV b{__float_as_int(fa.z), __float_as_int(fa.w), fc.y};
-      const SV c{__float_as_int(fb.x), __float_as_int(fb.y), fc.z};
+      const float4 fb = __ldcs(s + 1);
       const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
-      t = __float_as_uint(fc.w);
-      const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
-      const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
-      vis = raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
-                           (int)(b1 >> 16), A.zbuf, A.W);
+      if (b0 != 0xFFFFFFFFu) {
+        const float4 fa = __ldcs(s), fc = __ldcs(s + 2);
+        const SV a{__float_as_int(fa.x), __float_as_int(fa.y), fc.x};
+        const SV b{__float_as_int(fa.z), __float_as_int(fa.w), fc.y};
+        const SV c{__float_as_int(fb.x), __float_as_int(fb.y), fc.z};
+        t = __float_as_uint(fc.w);
+        const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
+        const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
+        vis = raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
+                             (int)(b1 >> 16), A.zbuf, A.W);
+      }
     }
     const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, word);
@@ -614,7 +662,7 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_front", s);
-  launch_k(k_raster_front, g, 256, 0, s, A);
+  launch_k(k_raster_front, grid_for(mesh->T, kFrontThreads, 152 * 4), kFrontThreads, 0, s, A);
   mark(ctx, "k_raster_exact", s);
   launch_k(k_raster_exact, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_depth_big", s);
