@@ -93,7 +93,7 @@ void fa_destroy(fa_ctx* ctx) {
   if (ctx->prof_on)
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
-  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_clip, ctx->clip,
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
                   ctx->label, ctx->cid, ctx->blockcnt,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
                   p.order, p.tile_tot, p.rec, p.m, p.xy, p.cand};
@@ -139,11 +139,14 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->queue, ctx->queue_cap);
   ctx->tile_cap = 4u * ctx->queue_cap;
   FA_ALLOC(ctx->tile_owner, ctx->tile_cap);
-  // survivor-indexed records [0, T) and clipped-path records [T, T + 65536)
-  ctx->cand_cap = (uint32_t)(T + 65536 < 0xFFFFFFFFull ? T + 65536 : 0xFFFFFFFFull);
+  // survivor regions (one per raster front block, each rounded up to 512 slots) and
+  // then the clipped-path candidate records
+  ctx->surv_cap = (uint32_t)(T + 608ull * 512ull);
+  ctx->cand_cap = ctx->surv_cap + 65536u;
   if (st == FA_OK) st = alloc((unsigned char**)&ctx->cand, (size_t)ctx->cand_cap * 48);
-  FA_ALLOC(ctx->surv, T);
-  if (st == FA_OK) st = alloc((float4**)&ctx->surv_clip, (size_t)T * 3);
+  FA_ALLOC(ctx->surv, ctx->surv_cap);
+  FA_ALLOC(ctx->surv_count, 608);
+  if (st == FA_OK) st = alloc((float4**)&ctx->surv_clip, (size_t)ctx->surv_cap * 3);
   FA_ALLOC(ctx->clip, T);
   FA_ALLOC(ctx->label, T + V);
   FA_ALLOC(ctx->cid, T);

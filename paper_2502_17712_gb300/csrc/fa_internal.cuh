@@ -104,7 +104,9 @@ struct fa_ctx {
   uint32_t tile_cap;
   void* cand;            // [cand_cap] 48-byte records of small sub-triangles
   uint32_t cand_cap;
-  uint32_t* surv;        // [max_tris] raster survivors
+  uint32_t* surv;        // [surv_cap] raster survivors (per-block regions)
+  uint32_t* surv_count;  // [608] survivors of each raster front block
+  uint32_t surv_cap;
   void* surv_clip;       // [max_tris][3] float4 clip coordinates of the survivors
   uint32_t* clip;        // [max_tris] triangles to clip
   int32_t* label;        // [max_tris + max_verts]

@@ -188,6 +188,7 @@ struct CandTri {
 static_assert(sizeof(CandTri) == 48, "CandTri is 48 bytes");
 
 constexpr int kFrontThreads = 512;
+constexpr uint32_t kMaxFrontBlocks = 152 * 4;
 
 struct RasterArgs {
   Mat4 M;
@@ -203,7 +204,11 @@ struct RasterArgs {
   uint32_t tile_cap;
   CandTri* cand;
   uint32_t cand_cap;
-  uint32_t* surv;  // [T] triangles that need the exact set-up
+  uint32_t* surv;  // triangles that need the exact set-up, one region per front block
+  uint32_t* surv_count;  // [front_blocks] survivors per region
+  uint32_t surv_per_block;
+  uint32_t front_blocks;
+  uint32_t clip_base;  // first candidate slot of the clipped path
   float4* surv_clip;  // [T][3] their clip coordinates
   uint32_t* clip;  // [T] triangles that need clipping
   DevCounters* ctr;
@@ -292,7 +297,7 @@ __device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, C
       *out = r;
       nout = 1;
     } else {
-      store_cand(A, A.T + atomicAdd(&A.ctr->ncand, 1u), r);
+      store_cand(A, A.clip_base + atomicAdd(&A.ctr->ncand, 1u), r);
     }
   }
   return nout;
@@ -418,44 +423,91 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
 // (warp-aggregated appends) so that the exact set-up runs on full warps.
 __global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
   pdl_wait();
-  __shared__ uint32_t s_cnt[2][kFrontThreads / 32];
-  __shared__ uint32_t s_base[2];
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  // one block iteration covers kFrontThreads consecutive triangles; the block's
-  // survivors and clipped triangles are appended with one atomic each
+  __shared__ uint32_t s_count;
+  if (threadIdx.x == 0) s_count = 0;
+  __syncthreads();
+  const uint32_t lane = threadIdx.x & 31;
+  // block b owns survivor slots [b * surv_per_block, (b + 1) * surv_per_block): it sees
+  // at most that many triangles, so its region cannot overflow
+  const uint32_t region = blockIdx.x * A.surv_per_block;
   for (uint32_t base = blockIdx.x * kFrontThreads; base < A.T; base += gridDim.x * kFrontThreads) {
     const uint32_t t = base + threadIdx.x;
     float4 c[3];
     const int r = t < A.T ? front_triangle(A, t, c) : 0;
     const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, r == 1), b2 = __ballot_sync(0xFFFFFFFFu, r == 2);
-    if (lane == 0) {
-      s_cnt[0][wid] = __popc(b1);
-      s_cnt[1][wid] = __popc(b2);
+    if (b1) {
+      uint32_t o = 0;
+      if (lane == 0) o = atomicAdd(&s_count, (uint32_t)__popc(b1));
+      o = __shfl_sync(0xFFFFFFFFu, o, 0);
+      if (r == 1) {
+        const uint32_t slot = region + o + __popc(b1 & ((1u << lane) - 1u));
+        A.surv[slot] = t;
+        float4* sc = A.surv_clip + 3 * (size_t)slot;
+        sc[0] = c[0];
+        sc[1] = c[1];
+        sc[2] = c[2];
+      }
     }
-    __syncthreads();
-    if (threadIdx.x < 2) {
-      uint32_t tot = 0;
-      for (int w = 0; w < kFrontThreads / 32; ++w) tot += s_cnt[threadIdx.x][w];
-      s_base[threadIdx.x] = tot ? atomicAdd(threadIdx.x ? &A.ctr->nclip : &A.ctr->nsurv, tot) : 0u;
+    if (b2) {  // rare: one global counter
+      uint32_t o = 0;
+      if (lane == 0) o = atomicAdd(&A.ctr->nclip, (uint32_t)__popc(b2));
+      o = __shfl_sync(0xFFFFFFFFu, o, 0);
+      if (r == 2) A.clip[o + __popc(b2 & ((1u << lane) - 1u))] = t;
     }
-    __syncthreads();
-    uint32_t o1 = s_base[0], o2 = s_base[1];
-    for (uint32_t w = 0; w < wid; ++w) {
-      o1 += s_cnt[0][w];
-      o2 += s_cnt[1][w];
-    }
-    if (r == 1) {
-      const uint32_t slot = o1 + __popc(b1 & ((1u << lane) - 1u));
-      A.surv[slot] = t;
-      float4* sc = A.surv_clip + 3 * (size_t)slot;
-      sc[0] = c[0];
-      sc[1] = c[1];
-      sc[2] = c[2];
-    } else if (r == 2) {
-      A.clip[o2 + __popc(b2 & ((1u << lane) - 1u))] = t;
-    }
-    __syncthreads();  // s_cnt / s_base are rewritten by the next iteration
   }
+  __syncthreads();
+  if (threadIdx.x == 0) A.surv_count[blockIdx.x] = s_count;
+}
+
+// Exclusive prefix of the front blocks' survivor counts into shared memory
+// (front_blocks <= kMaxFrontBlocks); returns the total.  Called by every thread of a
+// block of exactly 256 threads.
+__device__ uint32_t surv_prefix(const RasterArgs& A, uint32_t* pre) {
+  constexpr uint32_t kPer = (kMaxFrontBlocks + 255) / 256;
+  __shared__ uint32_t s_warp[8];
+  const uint32_t nb = A.front_blocks, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t c[kPer], sum = 0;
+#pragma unroll
+  for (uint32_t j = 0; j < kPer; ++j) {
+    const uint32_t b = threadIdx.x * kPer + j;
+    c[j] = b < nb ? __ldcg(A.surv_count + b) : 0u;
+    sum += c[j];
+  }
+  uint32_t inc = sum;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, inc, o);
+    if (lane >= (uint32_t)o) inc += y;
+  }
+  if (lane == 31) s_warp[w] = inc;
+  __syncthreads();
+  uint32_t wpre = 0, tot = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < 8; ++k) {
+    const uint32_t x = s_warp[k];
+    wpre += k < w ? x : 0u;
+    tot += x;
+  }
+  uint32_t run = wpre + inc - sum;
+#pragma unroll
+  for (uint32_t j = 0; j < kPer; ++j) {
+    const uint32_t b = threadIdx.x * kPer + j;
+    if (b <= nb) pre[b] = run;
+    run += c[j];
+  }
+  __syncthreads();
+  return tot;
+}
+
+// Survivor slot of dense index v: block b with pre[b] <= v < pre[b + 1].
+__device__ __forceinline__ uint32_t surv_slot(const RasterArgs& A, const uint32_t* pre, uint32_t v) {
+  uint32_t lo = 0, hi = A.front_blocks;  // pre[lo] <= v < pre[hi]
+  while (hi - lo > 1) {
+    const uint32_t mid = (lo + hi) >> 1;
+    if (pre[mid] <= v) lo = mid;
+    else hi = mid;
+  }
+  return lo * A.surv_per_block + (v - pre[lo]);
 }
 
 // Depth pre-pass, exact part: survivors of the front end.  Survivor i writes its
@@ -463,15 +515,17 @@ __global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
 // triangles append theirs after slot T.
 __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   pdl_wait();
+  __shared__ uint32_t pre[kMaxFrontBlocks + 1];
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t n = __ldcg(&A.ctr->nsurv);
+  const uint32_t n = surv_prefix(A, pre);
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t wbase = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n; wbase += stride) {
-    const uint32_t i = wbase + lane;
+    const uint32_t v = wbase + lane;
+    const uint32_t i = v < n ? surv_slot(A, pre, v) : 0u;
     Exact E;
     uint32_t t = 0, tiles = 0;
     int kind = 0;  // 0 nothing, 1 small, 2 large
-    if (i < n) {
+    if (v < n) {
       const float4* sc = A.surv_clip + 3 * (size_t)i;
       t = __ldcg(A.surv + i);
       E = exact_setup(A, __ldcs(sc), __ldcs(sc + 1), __ldcs(sc + 2));
@@ -527,7 +581,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
         }
       }
     }
-    if (i < n) {
+    if (v < n) {
       if (kind == 1) {
         const float invA = __fdiv_rn(1.0f, ll2float_rn(E.s.A));
         raster_rect<0>(E.a, E.b, E.c, invA, E.s.px0, E.s.py0, E.s.px1, E.s.py1, A.zbuf, A.W);
@@ -552,17 +606,18 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
 // has key <= the depth buffer; visible bits are OR-ed per VT word and warp.
 __global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
   pdl_wait();
+  __shared__ uint32_t pre[kMaxFrontBlocks + 1];
   if (__ldcg(&A.ctr->status) != 0) return;
-  const uint32_t ns = __ldcg(&A.ctr->nsurv);
-  const uint32_t nc = min(__ldcg(&A.ctr->ncand), A.cand_cap - A.T);
-  const uint32_t n = ns + nc;  // slots [0, ns) then [T, T + nc)
+  const uint32_t ns = surv_prefix(A, pre);
+  const uint32_t nc = min(__ldcg(&A.ctr->ncand), A.cand_cap - A.clip_base);
+  const uint32_t n = ns + nc;  // survivor records, then the clipped-path records
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
     const uint32_t k = base + threadIdx.x;
     bool vis = false;
     uint32_t t = 0xFFFFFFFFu;
     if (k < n) {
-      const uint32_t i = k < ns ? k : A.T + (k - ns);
+      const uint32_t i = k < ns ? surv_slot(A, pre, k) : A.clip_base + (k - ns);
       const float4* s = reinterpret_cast<const float4*>(A.cand + i);
       const float4 fb = __ldcs(s + 1);
       const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
@@ -650,6 +705,13 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.cand = reinterpret_cast<CandTri*>(ctx->cand);
   A.cand_cap = ctx->cand_cap;
   A.surv = ctx->surv;
+  A.surv_count = ctx->surv_count;
+  A.front_blocks = grid_for(mesh->T, kFrontThreads, kMaxFrontBlocks);
+  {
+    const uint32_t iters = (mesh->T + A.front_blocks * kFrontThreads - 1) / (A.front_blocks * kFrontThreads);
+    A.surv_per_block = iters * kFrontThreads;
+  }
+  A.clip_base = A.front_blocks * A.surv_per_block;
   A.surv_clip = reinterpret_cast<float4*>(ctx->surv_clip);
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
@@ -662,7 +724,7 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_front", s);
-  launch_k(k_raster_front, grid_for(mesh->T, kFrontThreads, 152 * 4), kFrontThreads, 0, s, A);
+  launch_k(k_raster_front, A.front_blocks, kFrontThreads, 0, s, A);
   mark(ctx, "k_raster_exact", s);
   launch_k(k_raster_exact, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_depth_big", s);
