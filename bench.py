@@ -33,7 +33,7 @@ FLUSH_BYTES = 256 << 20
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=1000)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--ratio", type=float, default=1.0)
@@ -56,6 +56,25 @@ def dist_env():
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     return rank, world, local
+
+
+def max_over_ranks(x):
+    """Largest value of x over the ranks of the default process group (x itself
+    when there is none); the tensor lives on the GPU for NCCL, on the host otherwise."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_rate(world, steps, max_ms):
+    """Frames per second of the whole job: every rank atlases `steps` frames of its
+    own replica, and the job takes the slowest rank's time."""
+    return world * steps / (max_ms / 1e3)
 
 
 def peaks():
@@ -135,6 +154,38 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C):
         "k_pack_fix": 64 * 32 * C,
     }
     return table.get(kernel)
+
+
+def frame_algorithmic_bytes(T, V, W, H, T_vis, C, mode):
+    """Compulsory bytes of one whole frame: positions and indices read once, the
+    triangle adjacency read once in edge mode, the depth buffer written and read
+    once, the visibility bits, the per-triangle chart ids, the visible triangles'
+    UVs and the per-chart arrays (boxes, footprints, order, placements)."""
+    vt = (T + 31) // 32 * 4
+    b = 12 * V + 12 * T + 2 * 4 * W * H + vt + 4 * T + 24 * T_vis + C * (16 + 8 + 4 + 16)
+    if mode == 0:
+        b += 12 * T
+    return b
+
+
+def measured_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu capture, or None when the
+    kernel's source has changed since the counters were taken."""
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+            rec = json.load(f).get(kernel)
+        if rec is None:
+            return None
+        h = hashlib.sha256()
+        for name in (rec["source"], "fa_internal.cuh"):
+            with open(os.path.join(ROOT, "paper_2502_17712_gb300", "csrc", name), "rb") as f:
+                h.update(f.read())
+        if h.hexdigest()[:16] != rec["source_sha256_16"]:
+            return None
+        return rec["dram_bytes_per_launch"]
+    except Exception:
+        return None
 
 
 def run_reference(a):
@@ -253,10 +304,7 @@ def run_ours(a):
         dist.barrier()
     step_ms = [s.elapsed_time(e) for s, e in ev]
     total_ms = float(sum(step_ms))
-    if world > 1:
-        t = torch.tensor([total_ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = max_over_ranks(total_ms)
 
     # per-kernel trace (same frame, traced graph, same L2 flush between steps)
     F.fa_profile_enable(ctx.handle, True)
@@ -268,7 +316,8 @@ def run_ours(a):
         traced = tgraph.replay
     per_kernel = {}
     traced_ms = 0.0
-    for i in range(max(a.steps, 5)):
+    n_traced = min(max(a.steps, 5), 200)
+    for i in range(n_traced):
         flush.fill_(i)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -309,11 +358,8 @@ def run_ours(a):
             e1.record(stream)
             e1.synchronize()
             e_ms += e0.elapsed_time(e1)
-        if world > 1:
-            t = torch.tensor([e_ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e_ms = float(t.item())
-        e2e = {"value": world * a.steps / (e_ms / 1e3), "unit": "frames/s", "h2d_bytes_per_step": h2d,
+        e_ms = max_over_ranks(e_ms)
+        e2e = {"value": whole_job_rate(world, a.steps, e_ms), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
     if rank != 0:
@@ -331,19 +377,18 @@ def run_ours(a):
     if dom:
         avg_ms = tot[dom] / len(per_kernel[dom])
         ab = algorithmic_bytes(dom, sc.T, sc.V, W, H, T_vis, C)
-        traffic = None
-        try:
-            with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
-                traffic = json.load(f).get(dom)
-        except Exception:
-            pass
+        traffic = measured_traffic(dom)
         if ab is not None:
             ach = ab / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                     "frac": ach / peak, "peak_source": peak_kind, "traffic": traffic,
                     "algorithmic_bytes": ab, "avg_launch_ms": avg_ms,
                     "share": tot[dom] / frame_ms if frame_ms else None}
-    value = world * a.steps / (total_ms / 1e3)
+    value = whole_job_rate(world, a.steps, total_ms)
+    srt = sorted(step_ms)
+    fb = frame_algorithmic_bytes(sc.T, sc.V, W, H, T_vis, C, a.mode)
+    frame_roof = {"algorithmic_bytes": fb, "achieved": fb / (total_ms / a.steps * 1e-3) / 1e9, "peak": peak,
+                  "unit": "GB/s", "frac": fb / (total_ms / a.steps * 1e-3) / 1e9 / peak, "peak_source": peak_kind}
     line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world, "steps": a.steps,
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -353,8 +398,9 @@ def run_ours(a):
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": launches_per_frame * a.steps,
             "kernels_ms_per_frame": {k: tot[k] / len(per_kernel[k]) for k in sorted(tot, key=tot.get, reverse=True)},
-            "traced_ms_per_frame": traced_ms / max(a.steps, 5),
-            "roofline": roof, "e2e": e2e, "clocks": clk}
+            "traced_ms_per_frame": traced_ms / n_traced,
+            "ms_p50": srt[len(srt) // 2], "ms_p99": srt[min(len(srt) - 1, (99 * len(srt)) // 100)],
+            "roofline": roof, "frame_roofline": frame_roof, "e2e": e2e, "clocks": clk}
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, sc, M, p)
     print(json.dumps(line), flush=True)

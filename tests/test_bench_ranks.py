@@ -1,0 +1,76 @@
+"""Multi-rank host logic of bench.py on CPU (gloo, world size 2).
+
+Replicas share no data-path collective; the only exchange is the max of the timed
+region over ranks, and the whole-job rate is every rank's frames over that max.
+"""
+import io
+import os
+import socket
+import sys
+from contextlib import redirect_stdout
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _worker(rank, world, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(world), LOCAL_RANK=str(rank))
+    import bench
+    dist.init_process_group("gloo", init_method="env://", rank=rank, world_size=world)
+    try:
+        got = bench.max_over_ranks(10.0 * (rank + 1))
+        env = bench.dist_env()
+        # the reference arm runs on rank 0 alone: other ranks return without output
+        out = io.StringIO()
+        if rank != 0:
+            with redirect_stdout(out):
+                bench.run_reference(None)
+        dist.barrier()
+        q.put((rank, got, env, out.getvalue()))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_max_over_ranks_gloo_world2():
+    world, port = 2, _free_port()
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_worker, args=(r, world, port, q)) for r in range(world)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in range(world))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    assert [r[1] for r in res] == [20.0, 20.0]  # both ranks see the slowest rank's time
+    assert [r[2] for r in res] == [(0, 2, 0), (1, 2, 1)]
+    assert res[1][3] == ""
+
+
+def test_whole_job_rate_and_single_rank():
+    import bench
+    # 2 replicas x 100 frames, slowest rank 50 ms -> 4000 frames/s for the whole job
+    assert bench.whole_job_rate(2, 100, 50.0) == pytest.approx(4000.0)
+    assert bench.whole_job_rate(1, 100, 50.0) == pytest.approx(2000.0)
+    if not dist.is_initialized():
+        assert bench.max_over_ranks(3.5) == 3.5
+
+
+def test_frame_algorithmic_bytes():
+    import bench
+    T, V, W, H, Tv, C = 4096000, 2048400, 1920, 1080, 262158, 36112
+    edge = bench.frame_algorithmic_bytes(T, V, W, H, Tv, C, 0)
+    vert = bench.frame_algorithmic_bytes(T, V, W, H, Tv, C, 1)
+    assert edge - vert == 12 * T  # adjacency is read in edge mode only
+    assert 0.15e9 < edge < 0.21e9
