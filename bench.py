@@ -148,10 +148,10 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C):
         "k_bbox": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis,
         "k_uv": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis + 24 * T_vis,
         "k_number": vt + 4 * T_vis,
-        # per candidate: read the box record (16 B) and write the placement (8 B)
-        "k_pack_push": 64 * 24 * C,
-        "k_pack_boxes": 64 * (16 * C) + 12 * C,
-        "k_pack_fix": 64 * 32 * C,
+        # per candidate: read the push record (8 B) and write the resting position (8 B)
+        "k_pack_push": 64 * 16 * C,
+        # per candidate: read the sorted footprint (8 B) and write the push record (8 B)
+        "k_pack_scan": 64 * 16 * C,
     }
     return table.get(kernel)
 

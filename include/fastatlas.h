@@ -228,7 +228,7 @@ fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const
  * fa_pack computes (same order, candidates, selection and placements) for n boxes
  * d_fa, d_fb (n given on the host), with min_box and gutter passed directly, and
  * needs no context.
- * Scratch: one file-scope device array of about 7.2 MiB inside the library, sized
+ * Scratch: one file-scope device array of about 4.8 MiB inside the library, sized
  * for at most 4096 boxes; every GPU that loads the library holds it until the
  * process exits.  The call never runs cudaMalloc, cudaFree or any allocating
  * library routine.

@@ -96,7 +96,7 @@ void fa_destroy(fa_ctx* ctx) {
   void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
                   ctx->label, ctx->cid, ctx->blockcnt,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
-                  p.order, p.tile_tot, p.rec, p.m, p.xy, p.cand};
+                  p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::free(ctx);
@@ -130,6 +130,7 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   PackScratch& pk = ctx->pack;
   pk.max_boxes = (uint32_t)C;
   pk.max_tiles = (uint32_t)((C + kOrderTile - 1) / kOrderTile);
+  pk.max_chunks = (uint32_t)((C + kChunk - 1) / kChunk);
   const uint64_t nblocks = (T + 1023) / 1024 + 1;
 #define FA_ALLOC(ptr, n) \
   if (st == FA_OK) st = alloc(&ptr, (size_t)(n));
@@ -158,8 +159,10 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(pk.ord_total, kMaxH);
   FA_ALLOC(pk.ord_binstart, kMaxH);
   FA_ALLOC(pk.order, C);
-  FA_ALLOC(pk.tile_tot, (uint64_t)kMaxScales * pk.max_tiles);
-  FA_ALLOC(pk.rec, (uint64_t)kMaxScales * C);
+  FA_ALLOC(pk.fs, (uint64_t)pk.max_chunks * kChunk);
+  FA_ALLOC(pk.rec8, (uint64_t)kMaxScales * pk.max_chunks * kChunk);
+  FA_ALLOC(pk.segs, (uint64_t)kMaxScales * pk.max_chunks * kSegStride);
+  FA_ALLOC(pk.scan_state, (uint64_t)kMaxScales * pk.max_chunks);
   FA_ALLOC(pk.m, kMaxScales);
   FA_ALLOC(pk.xy, (uint64_t)kMaxScales * C);
   FA_ALLOC(pk.cand, kMaxScales);

@@ -34,6 +34,7 @@ struct DevCounters {
   uint32_t order_tiles;    // tiles of the current order pass
   uint32_t chart_count;    // scratch copy of the frame's chart count
   uint32_t n_groups[kMaxScales];
+  uint32_t pack_item;      // next (candidate, chunk) item of the width scan
 };
 
 // One queued (large) sub-triangle of the raster: snapped vertices, depths and its
@@ -55,12 +56,13 @@ struct PackCand {
   int32_t status;   // FA_OK / FA_E_CAPACITY
 };
 
-// One scaled box of one candidate: exclusive prefix P of the widths, w, h.
-struct BoxRec {
-  unsigned long long P;
-  uint32_t w, h;
-};
-static_assert(sizeof(BoxRec) == 16, "BoxRec is one 16-byte record");
+// Boxes per pack chunk: the unit of the width scan (one work item per candidate and
+// chunk) and of the push's shared-memory staging.
+constexpr uint32_t kChunk = 4096;
+// uint16 entries of one chunk's row-segment list: [0] = segment count s,
+// [1 .. s] = chunk-relative first box of each segment, [s + 1] = boxes in the chunk
+// (padded so that every list starts on a 16-byte boundary).
+constexpr uint32_t kSegStride = kChunk + 8;
 
 // Scratch of the order + pack kernels (context memory, or the static array of
 // fa_pack_noalloc).
@@ -74,8 +76,11 @@ struct PackScratch {
   uint32_t* ord_total;          // [kMaxH], zero between calls
   uint32_t* ord_binstart;       // [kMaxH]
   uint32_t* order;              // [max_boxes] when the caller passes none
-  unsigned long long* tile_tot; // [kMaxScales][max_tiles]
-  BoxRec* rec;                  // [kMaxScales][max_boxes]
+  uint32_t max_chunks;          // ceil(max_boxes / kChunk)
+  uint2* fs;                    // [max_chunks * kChunk] footprints (fa, fb) in box order
+  uint2* rec8;                  // [kMaxScales][max_chunks * kChunk] push records
+  uint16_t* segs;               // [kMaxScales][max_chunks][kSegStride] row segments per chunk
+  unsigned long long* scan_state;  // [kMaxScales][max_chunks] look-back state of the width scan
   uint32_t* m;                  // [kMaxScales] largest overflow
   uint2* xy;                    // [kMaxScales][max_boxes]
   PackCand* cand;               // [kMaxScales]

@@ -10,25 +10,20 @@
 //   This replaces the paper's cuckoo-hash bucketing with the same result contract
 //   (deterministic, identical for identical frames).
 //
-// Pack: candidates k / n, k = 1..n (Sec. 4.2).  The per-box work is spread over
-//   (tile, candidate) CTAs: k_pack_boxes computes the scaled integer boxes and
-//   tile-local exclusive prefix sums of the widths; k_pack_fix adds the tile's
-//   offset (a block reduction over the preceding tile totals), giving P, and
-//   reduces the largest overflow m past omega (Sec. 4.3).  Then one CTA per
-//   candidate (k_pack_push) pushes the rows up against a frontline in shared
-//   memory: boxes are read 4096 at a time into shared-memory x / w / h arrays, the
-//   rows inside a chunk are found by a block scan, and each row segment is processed
-//   box-parallel (a group of 32 .. 1 threads per box, by the row's box count):
-//   resting height = max of the frontline under the box, then the frontline takes
-//   the box top, one barrier per segment.  Segments of one row never overlap in x,
-//   so a row may span two chunks.  The last CTA to finish selects the candidate;
-//   k_pack_place writes the placements with all CTAs.
+// Pack: candidates k / n, k = 1..n (Sec. 4.2).  k_order_scatter also writes the
+//   footprints in box order.  k_pack_scan takes (candidate, 4096-box chunk) work
+//   items: scaled integer boxes, the exclusive prefix P of the widths (chunk-local
+//   scan plus a decoupled look-back over the preceding chunks), the largest
+//   overflow m past omega (Sec. 4.3), and per box a push-ready record (x inside the
+//   row, w, h, row direction) plus per chunk the list of row segments.  Then one CTA
+//   per candidate (k_pack_push) pushes the rows up against a frontline in shared
+//   memory, with the chunks staged by bulk asynchronous copies; segments of one
+//   row never overlap in x, so a row may span two chunks.  The last CTA to finish
+//   selects the candidate; k_pack_place writes the placements with all CTAs.
 #include "fa_internal.cuh"
 
 namespace fa {
 namespace {
-
-constexpr int kThreads = 1024;
 
 __device__ __forceinline__ uint32_t height_bin(uint32_t fb) {
   uint32_t h = (uint32_t)(((uint64_t)fb + 255u) >> 8);
@@ -36,7 +31,8 @@ __device__ __forceinline__ uint32_t height_bin(uint32_t fb) {
   return kMaxH - h;  // ascending bin = descending height
 }
 
-// Block-wide inclusive scan (1024 threads); writes the block total to *total.
+// Block-wide inclusive scan (any whole number of warps up to 1024 threads); writes
+// the block total to *total.
 template <typename T>
 __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T* total) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
@@ -48,8 +44,9 @@ __device__ __forceinline__ T block_scan_incl(T v, T* warp_sums, T* total) {
   }
   if (lane == 31) warp_sums[wid] = x;
   __syncthreads();
+  const uint32_t nw = blockDim.x >> 5;
   if (wid == 0) {
-    T s = warp_sums[lane];
+    T s = lane < nw ? warp_sums[lane] : (T)0;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
       T y = __shfl_up_sync(0xFFFFFFFFu, s, o);
@@ -141,6 +138,10 @@ __global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
     v[4 * j + 3] = q.w;
     t4[j] = make_uint4(0, 0, 0, 0);
   }
+  // the pack's look-back state, work counter and overflows start at zero
+  for (uint32_t i = threadIdx.x; i < kMaxScales * p.max_chunks; i += blockDim.x) p.scan_state[i] = 0ull;
+  if (threadIdx.x < kMaxScales) p.m[threadIdx.x] = 0u;
+  if (threadIdx.x == 0) p.ctr->pack_item = 0u;
   uint32_t sum = 0;
 #pragma unroll
   for (uint32_t j = 0; j < kPer; ++j) sum += v[j];
@@ -159,8 +160,8 @@ __global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
   }
 }
 
-__global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, const uint32_t* __restrict__ fb,
-                                                              uint32_t* order) {
+__global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, const uint32_t* __restrict__ fa,
+                                                              const uint32_t* __restrict__ fb, uint32_t* order) {
   pdl_wait();
   if (__ldcg(&p.ctr->status) != 0) return;
   const uint32_t C = __ldcg(p.count);
@@ -175,14 +176,15 @@ __global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, con
     pos += __ldcg(c) + __ldcg(c + kMaxH) + __ldcg(c + 2 * kMaxH) + __ldcg(c + 3 * kMaxH);
   }
   for (; t < blockIdx.x; ++t) pos += __ldcg(p.ord_counts + (size_t)t * kMaxH + bin);
-  if (pos < C) order[pos] = i;
+  if (pos < C) {
+    order[pos] = i;
+    p.fs[pos] = make_uint2(__ldg(fa + i), __ldg(fb + i));
+  }
 }
 
 // ------------------------------------------------------------------ pack
 
 struct PackArgs {
-  const uint32_t* fa;
-  const uint32_t* fb;
   const uint32_t* order;
   uint32_t atlas_log2;
   uint32_t shift;  // log2(256 * n_scales)
@@ -194,83 +196,226 @@ struct PackArgs {
   fa_pack_result* res;
 };
 
-// Scaled boxes and tile-local exclusive prefix of the widths.  Persistent grid over
-// (tile, candidate) work items.
-__global__ void __launch_bounds__(kThreads) k_pack_boxes(PackScratch p, PackArgs a, uint32_t n_scales) {
-  pdl_wait();
-  __shared__ unsigned long long ws[32];
-  if (__ldcg(&p.ctr->status) != 0) return;
-  const uint32_t C = __ldcg(p.count);
-  if (C > p.max_boxes) return;
-  if (blockIdx.x == 0 && threadIdx.x < n_scales) p.m[threadIdx.x] = 0;
-  const uint32_t ntiles = (C + kThreads - 1) / kThreads;
-  const unsigned long long d = (1ull << a.shift) - 1ull;
-  for (uint32_t item = blockIdx.x; item < ntiles * n_scales; item += gridDim.x) {
-    const uint32_t kidx = item / ntiles, tile = item % ntiles, k = kidx + 1;
-    const uint32_t i = tile * kThreads + threadIdx.x;
-    uint32_t w = 0, h = 0;
-    if (i < C) {
-      const uint32_t b = __ldg(a.order + i);
-      const uint32_t sw = (uint32_t)(((unsigned long long)k * __ldg(a.fa + b) + d) >> a.shift);
-      const uint32_t sh = (uint32_t)(((unsigned long long)k * __ldg(a.fb + b) + d) >> a.shift);
-      w = (sw > a.min_box ? sw : a.min_box) + 2u * a.gutter;
-      h = (sh > a.min_box ? sh : a.min_box) + 2u * a.gutter;
-    }
-    unsigned long long tot;
-    const unsigned long long incl = block_scan_incl<unsigned long long>(w, ws, &tot);
-    BoxRec* rec = p.rec + (size_t)kidx * p.max_boxes;
-    if (i < C) rec[i] = BoxRec{incl - w, w, h};
-    if (threadIdx.x == 0) p.tile_tot[(size_t)kidx * p.max_tiles + tile] = tot;
-  }
+// Width scan: one work item per (candidate, chunk of kChunk boxes), handed out in
+// increasing order by a counter, so the chunks before an item are always held by
+// running CTAs.  Each item computes the scaled boxes (Sec. 4.2), scans the widths,
+// and takes its chunk's offset P by a decoupled look-back over the preceding chunks'
+// published sums.  It then writes, per box, the push record
+//   x: xr = P mod omega (bits 0-15) | w (bits 16-31)
+//   y: h (bits 0-30) | row runs left to right (bit 31: row q = P / omega, q mod 3 == 0)
+// (w and h saturate; a candidate whose box exceeds 16 bits of width has Omega above
+// the frontline capacity and never reaches the push), the chunk's list of row
+// segments (first box of each row inside the chunk; the chunk's first box always
+// starts one), and folds the largest overflow past omega into m (Sec. 4.3).
+constexpr int kScanThreads = 512;
+constexpr int kScanPer = kChunk / kScanThreads;  // consecutive boxes per thread
+constexpr unsigned long long kStAgg = 1ull << 62;  // chunk sum published
+constexpr unsigned long long kStInc = 2ull << 62;  // inclusive prefix published
+constexpr unsigned long long kStVal = (1ull << 62) - 1ull;
+
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long* q) {
+  unsigned long long v;
+  asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(q) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long* q, unsigned long long v) {
+  asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(q), "l"(v) : "memory");
 }
 
-// Global prefix P (tile offset + local) and the largest overflow past omega.
-__global__ void __launch_bounds__(kThreads) k_pack_fix(PackScratch p, PackArgs a, uint32_t n_scales) {
+__global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackArgs a, uint32_t n_scales) {
   pdl_wait();
-  __shared__ unsigned long long ws[32];
-  __shared__ uint32_t wm[32];
+  __shared__ unsigned long long ws64[32];
+  __shared__ uint32_t ws32[32];
+  __shared__ uint32_t s_lastw[kScanThreads / 32];
+  __shared__ uint32_t s_item;
+  __shared__ unsigned long long s_prefix;
   if (__ldcg(&p.ctr->status) != 0) return;
   const uint32_t C = __ldcg(p.count);
-  if (C > p.max_boxes) return;
-  const uint32_t ntiles = (C + kThreads - 1) / kThreads;
+  if (C > p.max_boxes || C == 0) return;
+  const uint32_t nch = (C + kChunk - 1) / kChunk;
+  const uint32_t items = nch * n_scales;
   const uint32_t om = 1u << a.atlas_log2;
-  for (uint32_t item = blockIdx.x; item < ntiles * n_scales; item += gridDim.x) {
-    const uint32_t kidx = item / ntiles, tile = item % ntiles;
-    const unsigned long long* tt = p.tile_tot + (size_t)kidx * p.max_tiles;
-    unsigned long long off = 0;
-    for (uint32_t t = threadIdx.x; t < tile; t += kThreads) off += __ldcg(tt + t);
-    unsigned long long total;
-    block_scan_incl<unsigned long long>(off, ws, &total);
-    const uint32_t i = tile * kThreads + threadIdx.x;
-    uint32_t m = 0;
-    if (i < C) {
-      BoxRec* r = p.rec + (size_t)kidx * p.max_boxes + i;
-      BoxRec v = *r;
-      v.P += total;
-      r->P = v.P;
-      const uint32_t xr = (uint32_t)(v.P & (om - 1));
-      if (xr + v.w > om) m = xr + v.w - om;
+  const unsigned long long d = (1ull << a.shift) - 1ull;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const size_t rstride = (size_t)p.max_chunks * kChunk;
+  for (;;) {
+    if (tid == 0) s_item = atomicAdd(&p.ctr->pack_item, 1u);
+    __syncthreads();
+    const uint32_t item = s_item;
+    if (item >= items) break;
+    const uint32_t kidx = item / nch, c = item % nch;
+    const unsigned long long k = kidx + 1;
+    const uint32_t base = c * kChunk, n = min(C - base, kChunk);
+    const uint32_t j0 = tid * kScanPer;
+    // this thread's boxes (the footprint array is padded to whole chunks)
+    const uint4* f4 = reinterpret_cast<const uint4*>(p.fs + base + j0);
+    uint32_t w[kScanPer], h[kScanPer];
+    unsigned long long sum = 0;
+#pragma unroll
+    for (int q = 0; q < kScanPer / 2; ++q) {
+      const uint4 v = __ldcg(f4 + q);
+      const uint32_t fa2[2] = {v.x, v.z}, fb2[2] = {v.y, v.w};
+#pragma unroll
+      for (int e2 = 0; e2 < 2; ++e2) {
+        const int e = 2 * q + e2;
+        if (j0 + e < n) {
+          const uint32_t sw = (uint32_t)((k * fa2[e2] + d) >> a.shift);
+          const uint32_t sh = (uint32_t)((k * fb2[e2] + d) >> a.shift);
+          w[e] = (sw > a.min_box ? sw : a.min_box) + 2u * a.gutter;
+          h[e] = (sh > a.min_box ? sh : a.min_box) + 2u * a.gutter;
+        } else {
+          w[e] = 0;
+          h[e] = 0;
+        }
+        sum += w[e];
+      }
     }
-    m = block_max<uint32_t>(m, wm);
-    if (threadIdx.x == 0 && m) atomicMax(p.m + kidx, m);
+    if (lane == 31) s_lastw[wid] = w[kScanPer - 1];
+    unsigned long long tot;
+    const unsigned long long excl = block_scan_incl<unsigned long long>(sum, ws64, &tot) - sum;
+    // chunk offset by decoupled look-back (warp 0)
+    if (wid == 0) {
+      unsigned long long* st = p.scan_state + (size_t)kidx * p.max_chunks;
+      unsigned long long prefix = 0;
+      if (c == 0) {
+        if (lane == 0) st_relaxed_u64(st, kStInc | tot);
+      } else {
+        if (lane == 0) st_relaxed_u64(st + c, kStAgg | tot);
+        int jn = (int)c - 1;  // nearest chunk not yet folded in
+        uint32_t spins = 0;
+        for (;;) {
+          const int t = jn - (int)lane;
+          unsigned long long v = t >= 0 ? ld_relaxed_u64(st + t) : kStInc;
+          while (__any_sync(0xFFFFFFFFu, (v >> 62) == 0ull)) {
+            if (++spins > kLoopCap) {
+              if (lane == 0) set_status(p.ctr, FA_E_TIMEOUT);
+              v = kStInc;
+            } else if ((v >> 62) == 0ull) {
+              v = ld_relaxed_u64(st + t);
+            }
+          }
+          const uint32_t inc = __ballot_sync(0xFFFFFFFFu, (v >> 62) == 2ull);
+          const uint32_t upto = inc ? (uint32_t)(__ffs(inc) - 1) : 31u;
+          unsigned long long x = lane <= upto ? (v & kStVal) : 0ull;
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
+          prefix += x;
+          if (inc) break;
+          jn -= 32;
+        }
+        if (lane == 0) st_relaxed_u64(st + c, kStInc | ((prefix + tot) & kStVal));
+      }
+      if (lane == 0) s_prefix = prefix;
+    }
+    __syncthreads();
+    // previous box's width, for the row test of this thread's first box
+    uint32_t wprev = __shfl_up_sync(0xFFFFFFFFu, w[kScanPer - 1], 1);
+    if (lane == 0) wprev = wid ? s_lastw[wid - 1] : 0u;
+    unsigned long long P = s_prefix + excl;
+    uint32_t starts = 0, cnt = 0, mo = 0;
+    uint2 r8[kScanPer];
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e) {
+      r8[e] = make_uint2(0u, 0u);
+      if (j0 + e < n) {
+        const unsigned long long q = P >> a.atlas_log2;
+        const uint32_t xr = (uint32_t)(P & (om - 1u));
+        const uint32_t wp = e ? w[e - 1] : wprev;
+        if (j0 + e == 0 || ((P - wp) >> a.atlas_log2) != q) {
+          starts |= 1u << e;
+          ++cnt;
+        }
+        if (xr + w[e] > om) mo = max(mo, xr + w[e] - om);
+        const uint32_t ws = w[e] < 0xFFFFu ? w[e] : 0xFFFFu;
+        const uint32_t hs = h[e] < 0x7FFFFFFFu ? h[e] : 0x7FFFFFFFu;
+        r8[e] = make_uint2(xr | (ws << 16), hs | ((q % 3ull == 0ull) ? 0x80000000u : 0u));
+      }
+      P += w[e];
+    }
+    uint4* o4 = reinterpret_cast<uint4*>(p.rec8 + kidx * rstride + base + j0);
+#pragma unroll
+    for (int q = 0; q < kScanPer / 2; ++q) o4[q] = make_uint4(r8[2 * q].x, r8[2 * q].y, r8[2 * q + 1].x, r8[2 * q + 1].y);
+    uint32_t nseg;
+    uint32_t at = block_scan_incl<uint32_t>(cnt, ws32, &nseg) - cnt;
+    uint16_t* sg = p.segs + ((size_t)kidx * p.max_chunks + c) * kSegStride;
+#pragma unroll
+    for (int e = 0; e < kScanPer; ++e)
+      if (starts & (1u << e)) sg[1 + at++] = (uint16_t)(j0 + e);
+    if (tid == 0) {
+      sg[0] = (uint16_t)nseg;
+      sg[1 + nseg] = (uint16_t)n;
+    }
+    mo = block_max<uint32_t>(mo, ws32);
+    if (tid == 0 && mo) atomicMax(p.m + kidx, mo);
   }
 }
 
-// Row push of one candidate per CTA, then the last CTA selects.
+// Row push of one candidate per CTA, then the last CTA selects.  The chunks' push
+// records and segment lists are staged into shared memory by bulk asynchronous
+// copies, two chunks in flight; every row segment is processed box-parallel (a
+// group of 32 .. 1 threads per box, by the segment's box count): resting height =
+// max of the frontline under the box, then the frontline takes the box top, one
+// barrier per segment.  Segments of one row never overlap in x, so a row may span
+// two chunks.
 constexpr int kPushThreads = 1024;
-constexpr int kChunk = 4096;                        // boxes per chunk
-constexpr int kPerThread = kChunk / kPushThreads;   // consecutive boxes per thread
+constexpr uint32_t kStageBytes = kChunk * 8u + kSegStride * 2u;  // records + segment list
+static_assert(kStageBytes % 16u == 0u, "bulk copies move multiples of 16 bytes");
+constexpr unsigned long long kWaitNs = 1000000000ull;  // a second
+
+__device__ __forceinline__ uint32_t smem_addr(const void* q) { return (uint32_t)__cvta_generic_to_shared(q); }
+__device__ __forceinline__ unsigned long long global_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(unsigned long long* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(unsigned long long* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return ok != 0u;
+}
+// Waits at most kWaitNs for the phase of the given parity; false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = global_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_ns() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_addr(dst)),
+               "l"(src), "r"(bytes), "r"(smem_addr(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ bool better_cand(uint32_t k1, uint32_t o1, uint32_t k2, uint32_t o2, uint32_t mode) {
+  if (k1 == 0u) return false;
+  if (k2 == 0u) return true;
+  if (mode == FA_SELECT_LARGEST_K) return k1 > k2;
+  const unsigned long long l = (unsigned long long)k1 * o2, r = (unsigned long long)k2 * o1;
+  return l > r || (l == r && k1 > k2);  // larger effective scale, ties to the larger k
+}
 
 __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
   pdl_wait();
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint32_t* s_x = reinterpret_cast<uint32_t*>(smem_raw);  // [kChunk] box x in its row's direction
-  uint32_t* s_w = s_x + kChunk;                            // [kChunk]
-  uint32_t* s_h = s_w + kChunk;                            // [kChunk]
-  uint32_t* s_seg = s_h + kChunk;                          // [kChunk + 1] first box of each segment
-  uint32_t* F = s_seg + kChunk + 4;                        // [front_cap]
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint32_t* F = reinterpret_cast<uint32_t*>(smem_raw + 2 * kStageBytes);  // [front_cap]
+  __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ uint32_t ws32[32];
-  __shared__ uint32_t s_flag, s_nseg, s_last;
+  __shared__ uint32_t s_last;
 
   const uint32_t kidx = blockIdx.x;
   const uint32_t tid = threadIdx.x;
@@ -290,75 +435,59 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
     if (Om > a.front_cap) {
       status = FA_E_CAPACITY;
     } else {
-      const BoxRec* rec = p.rec + (size_t)kidx * p.max_boxes;
+      const uint2* rec = p.rec8 + (size_t)kidx * p.max_chunks * kChunk;
+      const uint16_t* sgg = p.segs + (size_t)kidx * p.max_chunks * kSegStride;
       uint2* xy = p.xy + (size_t)kidx * p.max_boxes;
-      for (uint32_t x = tid; x < Om; x += kPushThreads) F[x] = 0;
-      if (tid == 0) s_flag = 0;
-      uint32_t Hloc = 0;
       const uint32_t nchunks = (C + kChunk - 1) / kChunk;
-      // thread tid owns boxes kPerThread * tid .. + kPerThread - 1 of each chunk; the
-      // next chunk's records are loaded into registers while this one is pushed
-      const uint32_t j0t = tid * kPerThread;
-      BoxRec nxt[kPerThread];
-      unsigned long long nprev = 0;
-#pragma unroll
-      for (int e = 0; e < kPerThread; ++e)
-        if (j0t + e < C) nxt[e] = rec[j0t + e];
-      if (j0t > 0 && j0t - 1 < C) nprev = __ldcg(&rec[j0t - 1].P);
+      uint32_t issued = 0;  // chunks whose copies were issued (thread 0)
+      auto issue = [&](uint32_t c) {
+        unsigned char* dst = smem_raw + (c & 1u) * kStageBytes;
+        const uint32_t nb = min(C - c * kChunk, kChunk);
+        const uint32_t rbytes = ((nb + 1u) & ~1u) * 8u;  // whole 16-byte units (padded chunk)
+        mbar_expect_tx(&s_bar[c & 1u], rbytes + kSegStride * 2u);
+        bulk_g2s(dst, rec + (size_t)c * kChunk, rbytes, &s_bar[c & 1u]);
+        bulk_g2s(dst + kChunk * 8u, sgg + (size_t)c * kSegStride, kSegStride * 2u, &s_bar[c & 1u]);
+      };
+      for (uint32_t x = tid; x < Om; x += kPushThreads) F[x] = 0;
+      if (tid == 0) {
+        mbar_init(&s_bar[0], 1);
+        mbar_init(&s_bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        for (; issued < nchunks && issued < 2u; ++issued) issue(issued);
+      }
+      __syncthreads();
+      uint32_t Hloc = 0, consumed = 0;
+      bool fail = false, timed_out = false;
       for (uint32_t c = 0; c < nchunks; ++c) {
-        const uint32_t base = c * kChunk;
-        const uint32_t n = min(C - base, (uint32_t)kChunk);
-        BoxRec r[kPerThread];
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e) r[e] = nxt[e];
-        unsigned long long qprev = (j0t > 0) ? (nprev >> a.atlas_log2) : ~0ull;
-        if (c + 1 < nchunks) {
-          const uint32_t nb = base + kChunk;
-#pragma unroll
-          for (int e = 0; e < kPerThread; ++e)
-            if (nb + j0t + e < C) nxt[e] = rec[nb + j0t + e];
-          if (j0t > 0 && nb + j0t - 1 < C) nprev = __ldcg(&rec[nb + j0t - 1].P);
+        const uint32_t stg = c & 1u;
+        const bool got = mbar_wait_bounded(&s_bar[stg], (c >> 1) & 1u);
+        if (__syncthreads_or(!got)) {
+          timed_out = true;
+          break;
         }
-        uint32_t flags = 0, cnt = 0;
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e) {
-          const uint32_t j = j0t + e;
-          if (j < n) {
-            const unsigned long long q = r[e].P >> a.atlas_log2;
-            const uint32_t xr = (uint32_t)(r[e].P & (om - 1));
-            s_x[j] = (q % 3ull == 0ull) ? xr : Om - xr - r[e].w;
-            s_w[j] = r[e].w;
-            s_h[j] = r[e].h;
-            if (j == 0 || q != qprev) {
-              flags |= 1u << e;
-              ++cnt;
-            }
-            qprev = q;
-          }
-        }
-        uint32_t nseg;
-        uint32_t at = block_scan_incl<uint32_t>(cnt, ws32, &nseg) - cnt;
-#pragma unroll
-        for (int e = 0; e < kPerThread; ++e)
-          if (flags & (1u << e)) s_seg[at++] = j0t + e;
-        if (tid == 0) {
-          s_seg[nseg] = n;
-          s_nseg = nseg;
-        }
-        __syncthreads();
-        for (uint32_t sgi = 0; sgi < s_nseg; ++sgi) {
-          const uint32_t j0 = s_seg[sgi], nbx = s_seg[sgi + 1] - j0;
+        consumed = c + 1;
+        const uint2* s_rec = reinterpret_cast<const uint2*>(smem_raw + stg * kStageBytes);
+        const uint16_t* s_sg = reinterpret_cast<const uint16_t*>(smem_raw + stg * kStageBytes + kChunk * 8u);
+        // (the clamps keep every shared-memory index inside the stage whatever the list holds)
+        const uint32_t nseg = min((uint32_t)s_sg[0], kChunk), base = c * kChunk;
+        for (uint32_t sgi = 0; sgi < nseg; ++sgi) {
+          const uint32_t j0 = min((uint32_t)s_sg[1 + sgi], kChunk), j1 = min((uint32_t)s_sg[2 + sgi], kChunk);
+          const uint32_t nbx = j1 > j0 ? j1 - j0 : 0u;
+          bool bad = false;
           if (nbx > (uint32_t)kPushThreads) {
             // a thread per box, several boxes per thread
             for (uint32_t jj = tid; jj < nbx; jj += kPushThreads) {
-              const uint32_t j = j0 + jj, x = s_x[j], w = s_w[j];
+              const uint2 r = s_rec[j0 + jj];
+              const uint32_t xr = r.x & 0xFFFFu, w = r.x >> 16, h = r.y & 0x7FFFFFFFu;
+              const uint32_t x = (r.y >> 31) ? xr : Om - xr - w;
               uint32_t mx = 0;
               for (uint32_t u = 0; u < w; ++u) mx = max(mx, F[x + u]);
-              const uint32_t top = mx + s_h[j];
+              const uint32_t top = mx + h;
               for (uint32_t u = 0; u < w; ++u) F[x + u] = top;
-              xy[base + j] = make_uint2(x, mx);
+              xy[base + j0 + jj] = make_uint2(x, mx);
               Hloc = max(Hloc, top);
-              if (top > Om) s_flag = 1;
+              bad |= top > Om;
             }
           } else {
             // a group of g threads per box, g = 32 for <= 32 boxes ... 1 for > 512:
@@ -368,30 +497,48 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
             const int lg = min(max(10 - lgb, 0), 5);
             const uint32_t g = 1u << lg;
             const uint32_t jj = tid >> lg, li = tid & (g - 1u);
-            uint32_t mx = 0, x = 0, w = 0;
+            uint32_t mx = 0, x = 0, w = 0, h = 0;
             if (jj < nbx) {
-              x = s_x[j0 + jj];
-              w = s_w[j0 + jj];
+              const uint2 r = s_rec[j0 + jj];
+              const uint32_t xr = r.x & 0xFFFFu;
+              w = r.x >> 16;
+              h = r.y & 0x7FFFFFFFu;
+              x = (r.y >> 31) ? xr : Om - xr - w;
               for (uint32_t u = li; u < w; u += g) mx = max(mx, F[x + u]);
             }
             for (uint32_t o = 1; o < g; o <<= 1) mx = max(mx, __shfl_xor_sync(0xFFFFFFFFu, mx, o));
             if (jj < nbx) {
-              const uint32_t top = mx + s_h[j0 + jj];
+              const uint32_t top = mx + h;
               for (uint32_t u = li; u < w; u += g) F[x + u] = top;
               if (li == 0) {
                 xy[base + j0 + jj] = make_uint2(x, mx);
                 Hloc = max(Hloc, top);
-                if (top > Om) s_flag = 1;
+                bad = top > Om;
               }
             }
           }
-          __syncthreads();
-          if (s_flag) break;
+          if (__syncthreads_or(bad)) {
+            fail = true;
+            break;
+          }
         }
-        if (s_flag) break;
+        if (fail) break;
+        // every thread is past this chunk's last barrier: its stage is free
+        if (tid == 0 && issued < nchunks) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          issue(issued);
+          ++issued;
+        }
+      }
+      // copies still in flight land before the CTA leaves
+      if (tid == 0)
+        for (uint32_t c = consumed; c < issued; ++c) mbar_wait_bounded(&s_bar[c & 1u], (c >> 1) & 1u);
+      if (timed_out) {
+        if (tid == 0) set_status(p.ctr, FA_E_TIMEOUT);
+        status = FA_E_TIMEOUT;
       }
       H = block_max<uint32_t>(Hloc, ws32);
-      ok = (!s_flag && H <= Om) ? 1u : 0u;
+      ok = (!fail && !timed_out && H <= Om) ? 1u : 0u;
     }
   }
   // publish this candidate; the last CTA selects
@@ -404,29 +551,50 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
   __syncthreads();
   if (!s_last) return;
   __threadfence();
-  if (tid == 0) {
-    uint32_t best = 0, bestOm = 0;
-    int32_t pst = FA_OK;
-    for (uint32_t kk = 1; kk <= gridDim.x; ++kk) {
+  if (tid < 32) {
+    // candidate kk = lane + 1, lane + 33, ...: the best fitting one, and the error
+    // status of the largest kk that reported one
+    uint32_t bk = 0, bOm = 0, bH = 0, ek = 0;
+    int32_t est = FA_OK;
+    for (uint32_t kk = tid + 1; kk <= gridDim.x; kk += 32) {
       const uint4 cv = __ldcg(reinterpret_cast<const uint4*>(p.cand) + (kk - 1));
-      if ((int32_t)cv.w != FA_OK) pst = (int32_t)cv.w;
-      if (!cv.x) continue;
-      if (best == 0 || a.select_mode == FA_SELECT_LARGEST_K ||
-          (unsigned long long)kk * bestOm >= (unsigned long long)best * cv.y) {
-        best = kk;
-        bestOm = cv.y;
+      if ((int32_t)cv.w != FA_OK) {
+        ek = kk;
+        est = (int32_t)cv.w;
+      }
+      if (cv.x && better_cand(kk, cv.y, bk, bOm, a.select_mode)) {
+        bk = kk;
+        bOm = cv.y;
+        bH = cv.z;
       }
     }
-    if (pst == FA_OK && best == 0) pst = FA_E_PACK_FAILED;
-    fa_pack_result r{0, 0, 0, pst, C};
-    if (pst == FA_OK) {
-      const uint4 cv = __ldcg(reinterpret_cast<const uint4*>(p.cand) + (best - 1));
-      r.k = best;
-      r.omega = cv.y;
-      r.height = cv.z;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const uint32_t ok2 = __shfl_xor_sync(0xFFFFFFFFu, bk, o), oO = __shfl_xor_sync(0xFFFFFFFFu, bOm, o);
+      const uint32_t oH = __shfl_xor_sync(0xFFFFFFFFu, bH, o), oek = __shfl_xor_sync(0xFFFFFFFFu, ek, o);
+      const int32_t oest = __shfl_xor_sync(0xFFFFFFFFu, est, o);
+      if (better_cand(ok2, oO, bk, bOm, a.select_mode)) {
+        bk = ok2;
+        bOm = oO;
+        bH = oH;
+      }
+      if (oek > ek) {
+        ek = oek;
+        est = oest;
+      }
     }
-    *a.res = r;
-    p.ctr->pack_done = 0;
+    if (tid == 0) {
+      int32_t pst = est;
+      if (pst == FA_OK && bk == 0) pst = FA_E_PACK_FAILED;
+      fa_pack_result r{0, 0, 0, pst, C};
+      if (pst == FA_OK) {
+        r.k = bk;
+        r.omega = bOm;
+        r.height = bH;
+      }
+      *a.res = r;
+      p.ctr->pack_done = 0;
+    }
   }
 }
 
@@ -436,18 +604,16 @@ __global__ void __launch_bounds__(256) k_pack_place(PackScratch p, PackArgs a) {
   if (__ldcg(&a.res->status) != FA_OK) return;
   const uint32_t C = __ldcg(&a.res->count), kb = __ldcg(&a.res->k) - 1;
   const uint2* bxy = p.xy + (size_t)kb * p.max_boxes;
-  const BoxRec* brec = p.rec + (size_t)kb * p.max_boxes;
+  const uint2* brec = p.rec8 + (size_t)kb * p.max_chunks * kChunk;
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < C; i += gridDim.x * blockDim.x) {
     const uint32_t b = __ldcg(a.order + i);
     const uint2 q = __ldcg(bxy + i);
-    const uint2 wh = __ldcg(reinterpret_cast<const uint2*>(brec + i) + 1);
-    a.place[b] = fa_placement{(int32_t)q.x, (int32_t)q.y, (int32_t)wh.x, (int32_t)wh.y};
+    const uint2 r = __ldcg(brec + i);
+    a.place[b] = fa_placement{(int32_t)q.x, (int32_t)q.y, (int32_t)(r.x >> 16), (int32_t)(r.y & 0x7FFFFFFFu)};
   }
 }
 
-size_t push_smem_bytes(uint32_t front_cap) {
-  return (size_t)(4 * kChunk + 4) * 4 + (size_t)front_cap * 4;
-}
+size_t push_smem_bytes(uint32_t front_cap) { return 2 * (size_t)kStageBytes + (size_t)front_cap * 4; }
 
 }  // namespace
 
@@ -461,10 +627,8 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   if (ctx) mark(ctx, "k_order_binscan", s);
   launch_k(k_order_binscan, 1, 1024, 0, s, p);
   if (ctx) mark(ctx, "k_order_scatter", s);
-  launch_k(k_order_scatter, p.max_tiles, kOrderTile, 0, s, p, fb, ord);
+  launch_k(k_order_scatter, p.max_tiles, kOrderTile, 0, s, p, fa_, fb, ord);
   PackArgs a;
-  a.fa = fa_;
-  a.fb = fb;
   a.order = ord;
   a.atlas_log2 = atlas_log2;
   uint32_t sh = 8;
@@ -477,12 +641,10 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   a.front_cap = (8u * om < kFrontCap) ? 8u * om : kFrontCap;
   a.place = place;
   a.res = res;
-  const uint32_t items = p.max_tiles * n_scales;
-  const unsigned g2 = items < 152u * 2u ? items : 152u * 2u;
-  if (ctx) mark(ctx, "k_pack_boxes", s);
-  launch_k(k_pack_boxes, g2, kThreads, 0, s, p, a, n_scales);
-  if (ctx) mark(ctx, "k_pack_fix", s);
-  launch_k(k_pack_fix, g2, kThreads, 0, s, p, a, n_scales);
+  const uint32_t items = p.max_chunks * n_scales;
+  const unsigned g2 = items < 152u * 2u ? items : 152u * 2u;  // two 512-thread CTAs per SM
+  if (ctx) mark(ctx, "k_pack_scan", s);
+  launch_k(k_pack_scan, g2, kScanThreads, 0, s, p, a, n_scales);
   if (ctx) mark(ctx, "k_pack_push", s);
   launch_k(k_pack_push, n_scales, kPushThreads, push_smem_bytes(a.front_cap), s, p, a);
   if (ctx) mark(ctx, "k_pack_place", s);
@@ -521,7 +683,7 @@ fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, cons
 // at the point where they pack: code running inside a host application's frame
 // callback or plugin slot whose device memory is owned and budgeted by the host,
 // and real-time loops that must not hit cudaMalloc's implicit device
-// synchronization.  The array (about 7.2 MiB, for up to 4096 boxes) stays resident
+// synchronization.  The array (about 4.8 MiB, for up to 4096 boxes) stays resident
 // on every GPU that loads the library, until the process exits.
 
 #include <mutex>
@@ -542,9 +704,11 @@ constexpr size_t kOffRank = align256(kOffCounts + sizeof(uint32_t) * kMaxH * kNo
 constexpr size_t kOffTotal = align256(kOffRank + sizeof(uint32_t) * kNoAllocMaxBoxes);
 constexpr size_t kOffBinstart = align256(kOffTotal + sizeof(uint32_t) * kMaxH);
 constexpr size_t kOffOrder = align256(kOffBinstart + sizeof(uint32_t) * kMaxH);
-constexpr size_t kOffTileTot = align256(kOffOrder + sizeof(uint32_t) * kNoAllocMaxBoxes);
-constexpr size_t kOffRec = align256(kOffTileTot + sizeof(unsigned long long) * kMaxScales * kNoAllocTiles);
-constexpr size_t kOffXY = align256(kOffRec + sizeof(BoxRec) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kOffFs = align256(kOffOrder + sizeof(uint32_t) * kNoAllocMaxBoxes);
+constexpr size_t kOffRec8 = align256(kOffFs + sizeof(uint2) * kNoAllocMaxBoxes);
+constexpr size_t kOffSegs = align256(kOffRec8 + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
+constexpr size_t kOffState = align256(kOffSegs + sizeof(uint16_t) * kMaxScales * kSegStride);
+constexpr size_t kOffXY = align256(kOffState + sizeof(unsigned long long) * kMaxScales);
 constexpr size_t kNoAllocBytes = align256(kOffXY + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
 
 // The scratch of fa_pack_noalloc.  Host code must not use this name as a device
@@ -622,8 +786,11 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   p.ord_total = (uint32_t*)(base + kOffTotal);
   p.ord_binstart = (uint32_t*)(base + kOffBinstart);
   p.order = (uint32_t*)(base + kOffOrder);
-  p.tile_tot = (unsigned long long*)(base + kOffTileTot);
-  p.rec = (BoxRec*)(base + kOffRec);
+  p.max_chunks = kNoAllocMaxBoxes / kChunk;
+  p.fs = (uint2*)(base + kOffFs);
+  p.rec8 = (uint2*)(base + kOffRec8);
+  p.segs = (uint16_t*)(base + kOffSegs);
+  p.scan_state = (unsigned long long*)(base + kOffState);
   p.m = (uint32_t*)(base + kOffM);
   p.xy = (uint2*)(base + kOffXY);
   p.cand = (PackCand*)(base + kOffCand);
