@@ -269,6 +269,17 @@ fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uin
 fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* params,
                          const fa_frame_out* out, fa_stream_t stream);
 
+/* fa_atlas_frame with the view-projection matrix read on the device, when the
+ * kernels run, from d_view_proj (16 floats, row-major as in params->view_proj,
+ * 16-byte aligned, caller-owned); params->view_proj is ignored.  The paper
+ * re-atlases every frame along a camera path (Sec. 6, per-frame timings over
+ * camera paths): a CUDA graph captured from one call of this function serves the
+ * whole path, the caller writing the next camera into d_view_proj (stream-ordered)
+ * before each replay.  Results equal fa_atlas_frame's for the same matrix.
+ * Errors: FA_E_INVALID_ARG (as fa_atlas_frame, or d_view_proj NULL / misaligned). */
+fa_status fa_atlas_frame_dev_matrix(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* params,
+                                    const float* d_view_proj, const fa_frame_out* out, fa_stream_t stream);
+
 /* Synchronize `stream`, read the context's sticky device status word into *out
  * and clear it.  Returns FA_E_CUDA if the stream reported a CUDA error. */
 fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out);

@@ -315,37 +315,59 @@ fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uin
 
 
 
-fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const fa_frame_out* o,
-                         fa_stream_t stream) {
+}  // extern "C"
+
+namespace {
+
+// One frame; the matrix is p->view_proj, or read on the device from d_view_proj.
+fa_status atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
+                      const fa_frame_out* o, fa_stream_t stream) {
   if (!ctx || !mesh || !p || !o || mesh->ctx != ctx) return FA_E_INVALID_ARG;
   if (!o->vt || !o->tri_chart || !o->place || !o->result) return FA_E_INVALID_ARG;
-  fa_status st = check_view(ctx, p->view_proj, p->width, p->height);
+  fa_status st = check_view(ctx, d_view_proj ? d_view_proj : p->view_proj, p->width, p->height);
   if (st == FA_OK) st = check_charts(&o->charts);
   if (st == FA_OK) st = check_pack(ctx, p->atlas_log2, p->n_scales, p->select_mode);
   if (st != FA_OK) return st;
   if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
+  if (d_view_proj && (reinterpret_cast<uintptr_t>(d_view_proj) & 15u)) return FA_E_INVALID_ARG;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  const Mat4 M = to_mat(p->view_proj);
+  const Mat4 M = d_view_proj ? Mat4{} : to_mat(p->view_proj);
+  const float* Md = d_view_proj;
   trace_begin(ctx);
   // k_clear (first kernel of the visibility step) also clears the status word
-  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s)) != FA_OK) return st;
+  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s, Md)) != FA_OK) return st;
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators
   if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, o->vt, &o->charts,
-                                false, s)) != FA_OK)
+                                false, s, Md)) != FA_OK)
     return st;
   if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
                         p->select_mode, o->order, o->place, o->result, s)) != FA_OK)
     return st;
   if (o->uv || o->affine) {
     if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, o->vt, &o->charts, o->place,
-                        o->result, p->atlas_log2, p->n_scales, o->uv, o->affine, s)) != FA_OK)
+                        o->result, p->atlas_log2, p->n_scales, o->uv, o->affine, s, Md)) != FA_OK)
       return st;
   }
   trace_end(ctx, s);
   return FA_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+fa_status fa_atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const fa_frame_out* o,
+                         fa_stream_t stream) {
+  return atlas_frame(ctx, mesh, p, nullptr, o, stream);
+}
+
+fa_status fa_atlas_frame_dev_matrix(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p,
+                                    const float* d_view_proj, const fa_frame_out* o, fa_stream_t stream) {
+  if (!d_view_proj) return FA_E_INVALID_ARG;
+  return atlas_frame(ctx, mesh, p, d_view_proj, o, stream);
 }
 
 fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {

@@ -143,6 +143,15 @@ struct Mat4 {
   float m[16];
 };
 
+// The view-projection matrix read on the device (16 floats, row-major), for frames
+// whose camera is set in device memory when the kernels run.
+__device__ __forceinline__ Mat4 load_mat(const float* __restrict__ p) {
+  Mat4 M;
+#pragma unroll
+  for (int i = 0; i < 16; ++i) M.m[i] = __ldg(p + i);
+  return M;
+}
+
 #define FA_CUDA_TRY(expr)                         \
   do {                                            \
     cudaError_t e_ = (expr);                      \
@@ -269,20 +278,23 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
 // Each returns FA_OK or FA_E_CUDA (launch error) and bumps ctx->launches.
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
-                            uint32_t H, uint32_t* vt, bool reset_status, cudaStream_t s);
+                            uint32_t H, uint32_t* vt, bool reset_status, cudaStream_t s,
+                            const float* Mdev = nullptr);
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
                           cudaStream_t s);
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                               uint32_t H, float ratio, const int32_t* tri_chart,
-                              const uint32_t* vt, const fa_charts* ch, bool reset_boxes, cudaStream_t s);
+                              const uint32_t* vt, const fa_charts* ch, bool reset_boxes, cudaStream_t s,
+                              const float* Mdev = nullptr);
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
                       uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s);
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                     float ratio, const int32_t* tri_chart, const uint32_t* vt, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
-                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s);
+                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s,
+                    const float* Mdev = nullptr);
 fa_status build_adjacency(fa_ctx* ctx, fa_mesh* mesh, cudaStream_t s);
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,

@@ -56,6 +56,7 @@ __device__ __forceinline__ void box_add(Box& b, const CV& c) {
 
 struct BoxArgs {
   Mat4 M;
+  const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
   const uint32_t* vt;
@@ -67,8 +68,10 @@ struct BoxArgs {
   DevCounters* ctr;
 };
 
+template <bool DEV_M>
 __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
   pdl_wait();
+  const Mat4 M = DEV_M ? load_mat(a.Mdev) : a.M;
   if (__ldcg(&a.ctr->status) != 0) return;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwords = (a.T + 31) >> 5;
@@ -86,8 +89,8 @@ __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
     }
     if (c >= 0) {
       const uint32_t* f = a.idx + 3 * (size_t)t;
-      float4 p0 = load_clip(a.M, a.pos, __ldg(f)), p1 = load_clip(a.M, a.pos, __ldg(f + 1)),
-             p2 = load_clip(a.M, a.pos, __ldg(f + 2));
+      float4 p0 = load_clip(M, a.pos, __ldg(f)), p1 = load_clip(M, a.pos, __ldg(f + 1)),
+             p2 = load_clip(M, a.pos, __ldg(f + 2));
       CV v[3] = {{p0.x, p0.y, p0.z, p0.w}, {p1.x, p1.y, p1.z, p1.w}, {p2.x, p2.y, p2.z, p2.w}};
       float d[3] = {__fadd_rn(p0.z, p0.w), __fadd_rn(p1.z, p1.w), __fadd_rn(p2.z, p2.w)};
       const bool all_in = d[0] >= 0.0f && d[1] >= 0.0f && d[2] >= 0.0f;
@@ -206,6 +209,7 @@ __device__ __forceinline__ DF df_div(float a, float b) {
 
 struct UvArgs {
   Mat4 M;
+  const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
   const uint32_t* vt;
@@ -227,8 +231,10 @@ struct UvArgs {
   DevCounters* ctr;
 };
 
+template <bool DEV_M>
 __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
   pdl_wait();
+  const Mat4 M = DEV_M ? load_mat(a.Mdev) : a.M;
   if (__ldcg(&a.ctr->status) != 0 || __ldcg(&a.res->status) != FA_OK) return;
   const uint32_t k = __ldcg(&a.res->k);
   const float om = (float)(1u << a.atlas_log2), Om = (float)__ldcg(&a.res->omega);
@@ -285,7 +291,7 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
     float2* o = reinterpret_cast<float2*>(a.uv + 6 * (size_t)t);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-      const float4 cc = load_clip(a.M, a.pos, __ldg(f + j));
+      const float4 cc = load_clip(M, a.pos, __ldg(f + j));
       if (!(cc.w > 0.0f)) {
         o[j] = make_float2(__int_as_float(0x7fffffff), __int_as_float(0x7fffffff));
         continue;
@@ -311,7 +317,7 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
 
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                               float ratio, const int32_t* tri_chart, const uint32_t* vt,
-                              const fa_charts* ch, bool reset_boxes, cudaStream_t s) {
+                              const fa_charts* ch, bool reset_boxes, cudaStream_t s, const float* Mdev) {
   if (reset_boxes) {
     mark(ctx, "k_box_reset", s);
     launch_k(k_box_reset, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts,
@@ -319,6 +325,7 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
   }
   BoxArgs a;
   a.M = M;
+  a.Mdev = Mdev;
   a.pos = mesh->pos;
   a.idx = mesh->idx;
   a.vt = vt;
@@ -329,7 +336,10 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
   a.max_charts = ctx->cfg.max_charts;
   a.ctr = ctx->ctr;
   mark(ctx, "k_bbox", s);
-  launch_k(k_bbox, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+  if (Mdev)
+    launch_k(k_bbox<true>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+  else
+    launch_k(k_bbox<false>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
   mark(ctx, "k_footprint", s);
   launch_k(k_footprint, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts, ctx->box_enc, ctx->box_full, 0.5f * (float)W, 0.5f * (float)H,
       256.0f * ratio, ch->bbox, ch->fa, ch->fb, ch->rot, ctx->ctr);
@@ -340,9 +350,10 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H, float ratio,
                     const int32_t* tri_chart, const uint32_t* vt, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
-                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s) {
+                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s, const float* Mdev) {
   UvArgs a;
   a.M = M;
+  a.Mdev = Mdev;
   a.pos = mesh->pos;
   a.idx = mesh->idx;
   a.vt = vt;
@@ -364,7 +375,10 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
   a.affine = affine;
   a.ctr = ctx->ctr;
   mark(ctx, "k_uv", s);
-  launch_k(k_uv, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+  if (Mdev)
+    launch_k(k_uv<true>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+  else
+    launch_k(k_uv<false>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }

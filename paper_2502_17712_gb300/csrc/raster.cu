@@ -192,6 +192,7 @@ constexpr uint32_t kMaxFrontBlocks = 152 * 4;
 
 struct RasterArgs {
   Mat4 M;
+  const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
   uint32_t T;
@@ -359,10 +360,10 @@ __device__ __forceinline__ bool surely_empty(const RasterArgs& A, const float4& 
 // route to the clipped list, conservative reject.  Returns 1 when the triangle needs
 // the exact set-up (unclipped; its clip coordinates are left in c[3]), 2 when it must
 // be clipped first, 0 when dropped.
-__device__ __forceinline__ int front_triangle(const RasterArgs& A, uint32_t t, float4* c) {
+__device__ __forceinline__ int front_triangle(const RasterArgs& A, const Mat4& M, uint32_t t, float4* c) {
   const uint32_t* f = A.idx + 3 * (size_t)t;
   const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
-  const float4 c0 = load_clip(A.M, A.pos, i0), c1 = load_clip(A.M, A.pos, i1), c2 = load_clip(A.M, A.pos, i2);
+  const float4 c0 = load_clip(M, A.pos, i0), c1 = load_clip(M, A.pos, i1), c2 = load_clip(M, A.pos, i2);
   // trivial reject: all vertices outside one side plane, or all behind the near plane
   // (no sample can be covered then: see the design notes on exactness)
   if ((c0.x > c0.w && c1.x > c1.w && c2.x > c2.w) || (c0.x < -c0.w && c1.x < -c1.w && c2.x < -c2.w) ||
@@ -421,8 +422,10 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
 
 // Depth pre-pass, front end: one thread per triangle; survivors go to a compact list
 // (warp-aggregated appends) so that the exact set-up runs on full warps.
+template <bool DEV_M>
 __global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
   pdl_wait();
+  const Mat4 M = DEV_M ? load_mat(A.Mdev) : A.M;
   __shared__ uint32_t s_count;
   if (threadIdx.x == 0) s_count = 0;
   __syncthreads();
@@ -433,7 +436,7 @@ __global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
   for (uint32_t base = blockIdx.x * kFrontThreads; base < A.T; base += gridDim.x * kFrontThreads) {
     const uint32_t t = base + threadIdx.x;
     float4 c[3];
-    const int r = t < A.T ? front_triangle(A, t, c) : 0;
+    const int r = t < A.T ? front_triangle(A, M, t, c) : 0;
     const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, r == 1), b2 = __ballot_sync(0xFFFFFFFFu, r == 2);
     if (b1) {
       uint32_t o = 0;
@@ -513,6 +516,7 @@ __device__ __forceinline__ uint32_t surv_slot(const RasterArgs& A, const uint32_
 // Depth pre-pass, exact part: survivors of the front end.  Survivor i writes its
 // candidate record (or an empty marker) at slot i, so no counter is needed; clipped
 // triangles append theirs after slot T.
+template <bool DEV_M>
 __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   pdl_wait();
   __shared__ uint32_t pre[kMaxFrontBlocks + 1];
@@ -596,8 +600,9 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) {
     const uint32_t t = __ldcg(A.clip + i);
     const uint32_t* f = A.idx + 3 * (size_t)t;
-    const float4 c0 = load_clip(A.M, A.pos, __ldg(f)), c1 = load_clip(A.M, A.pos, __ldg(f + 1)),
-                 c2 = load_clip(A.M, A.pos, __ldg(f + 2));
+    const Mat4 M = DEV_M ? load_mat(A.Mdev) : A.M;
+    const float4 c0 = load_clip(M, A.pos, __ldg(f)), c1 = load_clip(M, A.pos, __ldg(f + 1)),
+                 c2 = load_clip(M, A.pos, __ldg(f + 2));
     depth_clipped(A, t, c0, c1, c2);
   }
 }
@@ -687,8 +692,9 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
 }  // namespace
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
-                            uint32_t* vt, bool reset_status, cudaStream_t s) {
+                            uint32_t* vt, bool reset_status, cudaStream_t s, const float* Mdev) {
   RasterArgs A;
+  A.Mdev = Mdev;
   A.M = M;
   A.pos = mesh->pos;
   A.idx = mesh->idx;
@@ -724,9 +730,15 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_front", s);
-  launch_k(k_raster_front, A.front_blocks, kFrontThreads, 0, s, A);
+  if (Mdev)
+    launch_k(k_raster_front<true>, A.front_blocks, kFrontThreads, 0, s, A);
+  else
+    launch_k(k_raster_front<false>, A.front_blocks, kFrontThreads, 0, s, A);
   mark(ctx, "k_raster_exact", s);
-  launch_k(k_raster_exact, 152 * 8, 256, 0, s, A);
+  if (Mdev)
+    launch_k(k_raster_exact<true>, 152 * 8, 256, 0, s, A);
+  else
+    launch_k(k_raster_exact<false>, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_depth_big", s);
   launch_k(k_raster_big<0>, gb, 256, 0, s, A);
   mark(ctx, "k_raster_mark", s);

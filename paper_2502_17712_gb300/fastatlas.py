@@ -35,7 +35,7 @@ FA_SELECT_LARGEST_K = 1
 EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
            "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
            "fa_atlas_frame", "fa_last_device_status", "fa_launch_count", "fa_profile_enable",
-           "fa_profile_read", "fa_pack_noalloc"]
+           "fa_profile_read", "fa_pack_noalloc", "fa_atlas_frame_dev_matrix"]
 
 
 class fa_config(ctypes.Structure):
@@ -110,6 +110,9 @@ def load(path: str = LIB_PATH):
     lib.fa_uv.restype = st
     lib.fa_atlas_frame.argtypes = [P, P, ctypes.POINTER(fa_frame_params), ctypes.POINTER(fa_frame_out), P]
     lib.fa_atlas_frame.restype = st
+    lib.fa_atlas_frame_dev_matrix.argtypes = [P, P, ctypes.POINTER(fa_frame_params), P,
+                                              ctypes.POINTER(fa_frame_out), P]
+    lib.fa_atlas_frame_dev_matrix.restype = st
     lib.fa_last_device_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int32)]
     lib.fa_last_device_status.restype = st
     lib.fa_launch_count.argtypes = [P]
@@ -218,6 +221,12 @@ def fa_uv(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_charts, plac
 def fa_atlas_frame(ctx, mesh, params: fa_frame_params, out: fa_frame_out, stream=None):
     _check(load().fa_atlas_frame(ctx, mesh, ctypes.byref(params), ctypes.byref(out), _stream(stream)),
            "fa_atlas_frame")
+
+
+def fa_atlas_frame_dev_matrix(ctx, mesh, params: fa_frame_params, d_view_proj, out: fa_frame_out,
+                              stream=None):
+    _check(load().fa_atlas_frame_dev_matrix(ctx, mesh, ctypes.byref(params), _ptr(d_view_proj), ctypes.byref(out),
+                                            _stream(stream)), "fa_atlas_frame_dev_matrix")
 
 
 def fa_last_device_status(ctx, stream=None) -> int:
@@ -348,3 +357,13 @@ def atlas_frame(ctx: Context, mesh: Mesh, bufs: FrameBuffers, M, width, height, 
     """Enqueue the whole per-frame path (fa_atlas_frame); results land in ``bufs``."""
     p = frame_params(M, width, height, ratio, atlas_log2, chart_mode, n_scales, select_mode)
     fa_atlas_frame(ctx.handle, mesh.handle, p, bufs.c_out(), stream)
+
+
+def atlas_frame_dev_matrix(ctx: Context, mesh: Mesh, bufs: FrameBuffers, d_view_proj, width, height, ratio,
+                           atlas_log2, chart_mode=FA_CHARTS_EDGE, n_scales=64, select_mode=FA_SELECT_EFFECTIVE,
+                           stream=None):
+    """fa_atlas_frame_dev_matrix: the matrix is the device tensor ``d_view_proj``
+    (16 float32, row-major), read when the kernels run."""
+    p = frame_params(np.eye(4, dtype=np.float32), width, height, ratio, atlas_log2, chart_mode, n_scales,
+                     select_mode)
+    fa_atlas_frame_dev_matrix(ctx.handle, mesh.handle, p, d_view_proj, bufs.c_out(), stream)

@@ -299,3 +299,11 @@ def icosphere_frame(seed: int = 1, n_spheres: int = 200, ratio: float = 1.0):
     """200 displaced icospheres (4,096,000 tris), 1920x1080 view, 2048^2 atlas."""
     sc = icosphere_scene(seed, n_spheres)
     return sc, box_camera(seed, 1920, 1080), dict(width=1920, height=1080, ratio=ratio, atlas_log2=11)
+
+
+def camera_path_frames(seed: int = 1, n_frames: int = 300):
+    """The 64x64-vertex heightfield seen along a closed n_frames-camera spline path,
+    1920x1080 views, ratio 1.0, 2048^2 atlas (one atlas per frame)."""
+    sc = grid_scene(seed)
+    cams = spline_cameras(seed, n_frames, 1920, 1080)
+    return sc, cams, dict(width=1920, height=1080, ratio=1.0, atlas_log2=11)

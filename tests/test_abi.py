@@ -4,6 +4,7 @@ import ctypes
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -56,3 +57,9 @@ def test_host_side_argument_errors(lib):
     lib.fa_mesh_release(None)
     out = ctypes.c_int32()
     assert lib.fa_last_device_status(None, None, ctypes.byref(out)) == F.FA_E_INVALID_ARG
+    # frame entry points reject NULL handles before touching the device
+    params = F.frame_params(np.eye(4, dtype=np.float32), 64, 64, 1.0, 10)
+    fo = F.fa_frame_out()
+    assert lib.fa_atlas_frame(None, None, ctypes.byref(params), ctypes.byref(fo), None) == F.FA_E_INVALID_ARG
+    assert lib.fa_atlas_frame_dev_matrix(None, None, ctypes.byref(params), None, ctypes.byref(fo),
+                                         None) == F.FA_E_INVALID_ARG
