@@ -303,6 +303,59 @@ fa_status fa_profile_enable(fa_ctx* ctx, int enable);
  * Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
 fa_status fa_profile_read(fa_ctx* ctx, int max_n, float* ms, const char** names, int* n_out);
 
+/* ------------------------------------------------------------------ batches
+ *
+ * Many independent views atlased together.  Each view is one frame of the path
+ * above (its own mesh, camera, viewport, ratio and atlas; Sec. 3: one atlas per
+ * view); a batch runs them on lanes, each lane a context with its own stream,
+ * forked from and joined back into the caller's stream.  Results equal
+ * fa_atlas_frame's for every view, whatever the schedule.  A CUDA graph captured
+ * from one fa_atlas_batch call atlases the whole batch in one launch. */
+typedef struct fa_batch fa_batch;
+
+typedef enum {
+  FA_BATCH_ROUND_ROBIN = 0,   /* view i on lane i mod lanes */
+  FA_BATCH_LONGEST_FIRST = 1  /* views by decreasing T + W*H, each to the least-loaded lane */
+} fa_batch_policy;
+
+#define FA_BATCH_MAX_LANES 64u
+
+/* n_lanes contexts of configuration *cfg (device memory: n_lanes times one
+ * context) and their streams; all lanes in use, round robin.
+ * Errors: FA_E_INVALID_ARG (n_lanes 0 or above FA_BATCH_MAX_LANES, bad cfg),
+ * FA_E_OUT_OF_MEMORY, FA_E_CUDA. */
+fa_status fa_batch_create(fa_batch** out, const fa_config* cfg, uint32_t n_lanes);
+
+/* Synchronizes the device and frees the lanes.  Release the batch's meshes first. */
+void fa_batch_destroy(fa_batch* batch);
+
+/* fa_mesh_register for a mesh used in this batch's views (any lane may run it). */
+fa_status fa_batch_mesh_register(fa_batch* batch, const float* d_pos, uint32_t V, const uint32_t* d_idx,
+                                 uint32_t T, fa_mesh** out, fa_stream_t stream);
+
+/* Lanes in use (1 .. n_lanes) and the assignment policy of later calls. */
+fa_status fa_batch_set_schedule(fa_batch* batch, uint32_t lanes, uint32_t policy);
+fa_status fa_batch_get_schedule(const fa_batch* batch, uint32_t* lanes, uint32_t* policy);
+
+/* Enqueue n_views frames: view i = meshes[i] (registered with this batch) with
+ * params[i] into outs[i] (caller-owned, distinct per view).  Every view is checked
+ * on the host before anything is enqueued.  Each view's own result status is in
+ * outs[i].result.  Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_atlas_batch(fa_batch* batch, uint32_t n_views, const fa_mesh* const* meshes,
+                         const fa_frame_params* params, const fa_frame_out* outs, fa_stream_t stream);
+
+/* Schedule autotuner: for lanes in {1, 2, 4, .., n_lanes} and both policies,
+ * capture the batch into a CUDA graph, launch it once, time `reps` launches
+ * (CUDA events, best of) and keep the fastest schedule; *best_ms (may be NULL)
+ * receives its time.  Runs the views (outputs are overwritten) and synchronizes;
+ * not for use inside a capture.  Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_batch_tune(fa_batch* batch, uint32_t n_views, const fa_mesh* const* meshes,
+                        const fa_frame_params* params, const fa_frame_out* outs, uint32_t reps,
+                        float* best_ms);
+
+/* Kernels launched by all lanes since creation. */
+uint64_t fa_batch_launch_count(const fa_batch* batch);
+
 #ifdef __cplusplus
 }
 #endif

@@ -317,12 +317,14 @@ fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uin
 
 }  // extern "C"
 
-namespace {
+namespace fa {
 
-// One frame; the matrix is p->view_proj, or read on the device from d_view_proj.
-fa_status atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
-                      const fa_frame_out* o, fa_stream_t stream) {
-  if (!ctx || !mesh || !p || !o || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+// Host-side checks of one frame on ctx (the mesh may belong to another context of
+// the same device when its sizes fit this one's maxima).
+fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
+                      const fa_frame_out* o) {
+  if (!ctx || !mesh || !p || !o || !mesh->ctx || mesh->ctx->device != ctx->device) return FA_E_INVALID_ARG;
+  if (mesh->T > ctx->cfg.max_tris || mesh->V > ctx->cfg.max_verts) return FA_E_INVALID_ARG;
   if (!o->vt || !o->tri_chart || !o->place || !o->result) return FA_E_INVALID_ARG;
   fa_status st = check_view(ctx, d_view_proj ? d_view_proj : p->view_proj, p->width, p->height);
   if (st == FA_OK) st = check_charts(&o->charts);
@@ -330,8 +332,14 @@ fa_status atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p
   if (st != FA_OK) return st;
   if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
   if (d_view_proj && (reinterpret_cast<uintptr_t>(d_view_proj) & 15u)) return FA_E_INVALID_ARG;
-  DeviceGuard g(ctx->device);
-  cudaStream_t s = (cudaStream_t)stream;
+  return FA_OK;
+}
+
+// The launch sequence of one checked frame (the device must be current); the
+// matrix is p->view_proj, or read on the device from d_view_proj.
+fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
+                        const fa_frame_out* o, cudaStream_t s) {
+  fa_status st;
   const Mat4 M = d_view_proj ? Mat4{} : to_mat(p->view_proj);
   const float* Md = d_view_proj;
   trace_begin(ctx);
@@ -353,6 +361,19 @@ fa_status atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p
   }
   trace_end(ctx, s);
   return FA_OK;
+}
+
+}  // namespace fa
+
+namespace {
+
+fa_status atlas_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
+                      const fa_frame_out* o, fa_stream_t stream) {
+  if (!mesh || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  fa_status st = check_frame(ctx, mesh, p, d_view_proj, o);
+  if (st != FA_OK) return st;
+  DeviceGuard g(ctx->device);
+  return enqueue_frame(ctx, mesh, p, d_view_proj, o, (cudaStream_t)stream);
 }
 
 }  // namespace

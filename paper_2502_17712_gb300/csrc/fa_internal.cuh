@@ -296,6 +296,11 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                     uint32_t n_scales, float* uv, float* affine, cudaStream_t s,
                     const float* Mdev = nullptr);
 fa_status build_adjacency(fa_ctx* ctx, fa_mesh* mesh, cudaStream_t s);
+// One whole frame on ctx: host-side checks, then the launch sequence.
+fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
+                      const fa_frame_out* o);
+fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
+                        const fa_frame_out* o, cudaStream_t s);
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,

@@ -35,7 +35,11 @@ FA_SELECT_LARGEST_K = 1
 EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
            "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
            "fa_atlas_frame", "fa_last_device_status", "fa_launch_count", "fa_profile_enable",
-           "fa_profile_read", "fa_pack_noalloc", "fa_atlas_frame_dev_matrix"]
+           "fa_profile_read", "fa_pack_noalloc", "fa_atlas_frame_dev_matrix", "fa_batch_create",
+           "fa_batch_destroy", "fa_batch_mesh_register", "fa_batch_set_schedule", "fa_batch_get_schedule",
+           "fa_atlas_batch", "fa_batch_tune", "fa_batch_launch_count"]
+
+FA_BATCH_ROUND_ROBIN, FA_BATCH_LONGEST_FIRST = 0, 1
 
 
 class fa_config(ctypes.Structure):
@@ -113,6 +117,24 @@ def load(path: str = LIB_PATH):
     lib.fa_atlas_frame_dev_matrix.argtypes = [P, P, ctypes.POINTER(fa_frame_params), P,
                                               ctypes.POINTER(fa_frame_out), P]
     lib.fa_atlas_frame_dev_matrix.restype = st
+    lib.fa_batch_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(fa_config), u32]
+    lib.fa_batch_create.restype = st
+    lib.fa_batch_destroy.argtypes = [P]
+    lib.fa_batch_destroy.restype = None
+    lib.fa_batch_mesh_register.argtypes = [P, P, u32, P, u32, ctypes.POINTER(P), P]
+    lib.fa_batch_mesh_register.restype = st
+    lib.fa_batch_set_schedule.argtypes = [P, u32, u32]
+    lib.fa_batch_set_schedule.restype = st
+    lib.fa_batch_get_schedule.argtypes = [P, ctypes.POINTER(u32), ctypes.POINTER(u32)]
+    lib.fa_batch_get_schedule.restype = st
+    lib.fa_atlas_batch.argtypes = [P, u32, ctypes.POINTER(P), ctypes.POINTER(fa_frame_params),
+                                   ctypes.POINTER(fa_frame_out), P]
+    lib.fa_atlas_batch.restype = st
+    lib.fa_batch_tune.argtypes = [P, u32, ctypes.POINTER(P), ctypes.POINTER(fa_frame_params),
+                                  ctypes.POINTER(fa_frame_out), u32, ctypes.POINTER(f32)]
+    lib.fa_batch_tune.restype = st
+    lib.fa_batch_launch_count.argtypes = [P]
+    lib.fa_batch_launch_count.restype = ctypes.c_uint64
     lib.fa_last_device_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int32)]
     lib.fa_last_device_status.restype = st
     lib.fa_launch_count.argtypes = [P]
@@ -367,3 +389,83 @@ def atlas_frame_dev_matrix(ctx: Context, mesh: Mesh, bufs: FrameBuffers, d_view_
     p = frame_params(np.eye(4, dtype=np.float32), width, height, ratio, atlas_log2, chart_mode, n_scales,
                      select_mode)
     fa_atlas_frame_dev_matrix(ctx.handle, mesh.handle, p, d_view_proj, bufs.c_out(), stream)
+
+
+# ------------------------------------------------------------------ batches
+
+class Batch:
+    """An fa_batch: n_lanes contexts of one configuration, each with its own stream."""
+
+    def __init__(self, n_lanes, max_tris, max_verts, max_charts=1 << 16, max_width=1920, max_height=1080,
+                 max_atlas_log2=12, min_box=2, gutter=0, device=0):
+        self.cfg = fa_config(max_tris, max_verts, max_charts, max_width, max_height, max_atlas_log2,
+                             min_box, gutter, device)
+        h = ctypes.c_void_p()
+        _check(load().fa_batch_create(ctypes.byref(h), ctypes.byref(self.cfg), n_lanes), "fa_batch_create")
+        self.handle = h.value
+        self.n_lanes = n_lanes
+
+    def close(self):
+        if self.handle:
+            load().fa_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_schedule(self, lanes, policy=FA_BATCH_ROUND_ROBIN):
+        _check(load().fa_batch_set_schedule(self.handle, lanes, policy), "fa_batch_set_schedule")
+
+    def schedule(self):
+        lanes, pol = ctypes.c_uint32(), ctypes.c_uint32()
+        _check(load().fa_batch_get_schedule(self.handle, ctypes.byref(lanes), ctypes.byref(pol)),
+               "fa_batch_get_schedule")
+        return lanes.value, pol.value
+
+    @property
+    def launches(self) -> int:
+        return int(load().fa_batch_launch_count(self.handle))
+
+
+class BatchMesh(Mesh):
+    """A mesh registered with a batch (any lane may atlas it)."""
+
+    def __init__(self, batch: Batch, pos, idx, stream=None):
+        import torch
+        self.ctx = batch
+        self.pos = pos if torch.is_tensor(pos) else torch.as_tensor(np.ascontiguousarray(pos, np.float32)).cuda()
+        idx_np = idx if torch.is_tensor(idx) else np.ascontiguousarray(idx, np.uint32).view(np.int32)
+        self.idx = idx_np if torch.is_tensor(idx_np) else torch.as_tensor(idx_np).cuda()
+        self.T = int(self.idx.shape[0])
+        self.V = int(self.pos.shape[0])
+        h = ctypes.c_void_p()
+        _check(load().fa_batch_mesh_register(batch.handle, _ptr(self.pos), self.V, _ptr(self.idx), self.T,
+                                             ctypes.byref(h), _stream(stream)), "fa_batch_mesh_register")
+        self.handle = h.value
+
+
+def _batch_arrays(meshes, params, bufs):
+    n = len(meshes)
+    mh = (ctypes.c_void_p * n)(*[m.handle for m in meshes])
+    pa = (fa_frame_params * n)(*params)
+    oa = (fa_frame_out * n)(*[b.c_out() for b in bufs])
+    return n, mh, pa, oa
+
+
+def atlas_batch(batch: Batch, meshes, params, bufs, stream=None):
+    """Enqueue fa_atlas_batch: view i = meshes[i] with params[i] (fa_frame_params,
+    see frame_params) into bufs[i]."""
+    n, mh, pa, oa = _batch_arrays(meshes, params, bufs)
+    _check(load().fa_atlas_batch(batch.handle, n, mh, pa, oa, _stream(stream)), "fa_atlas_batch")
+
+
+def batch_tune(batch: Batch, meshes, params, bufs, reps=3):
+    """fa_batch_tune; returns (lanes, policy, best_ms)."""
+    n, mh, pa, oa = _batch_arrays(meshes, params, bufs)
+    ms = ctypes.c_float()
+    _check(load().fa_batch_tune(batch.handle, n, mh, pa, oa, reps, ctypes.byref(ms)), "fa_batch_tune")
+    lanes, pol = batch.schedule()
+    return lanes, pol, ms.value

@@ -307,3 +307,24 @@ def camera_path_frames(seed: int = 1, n_frames: int = 300):
     sc = grid_scene(seed)
     cams = spline_cameras(seed, n_frames, 1920, 1080)
     return sc, cams, dict(width=1920, height=1080, ratio=1.0, atlas_log2=11)
+
+
+BATCH_RESOLUTIONS = ((640, 360), (1280, 720), (1920, 1080), (2560, 1440))
+BATCH_ATLAS_LOG2 = (10, 11, 12)
+
+
+def batch_views(seed: int = 1, n_views: int = 64, min_instances: int = 50, max_instances: int = 400):
+    """n_views independent views: each an instanced heightfield floor with a seeded
+    number of patches in [min_instances, max_instances], a resolution drawn from
+    BATCH_RESOLUTIONS, an atlas side from BATCH_ATLAS_LOG2, ratio 1.0, and a camera
+    on a hemisphere looking at the floor's centre."""
+    rng = np.random.default_rng([seed, 0xBA7C4])
+    views = []
+    for v in range(n_views):
+        n_inst = int(rng.integers(min_instances, max_instances + 1))
+        W, H = BATCH_RESOLUTIONS[int(rng.integers(len(BATCH_RESOLUTIONS)))]
+        log2 = BATCH_ATLAS_LOG2[int(rng.integers(len(BATCH_ATLAS_LOG2)))]
+        sc = instanced_grid_scene(seed * 1009 + v, n_inst)
+        M = hemisphere_camera(seed * 1009 + v, W, H, radius=10.0)
+        views.append((sc, M, dict(width=W, height=H, ratio=1.0, atlas_log2=log2)))
+    return views
