@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-graph", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batched measurement")
+    ap.add_argument("--batch-views", type=int, default=64)
+    ap.add_argument("--batch-lanes", type=int, default=16)
     return ap.parse_args()
 
 
@@ -231,6 +234,77 @@ def cpu_baseline(a, sc, M, p):
             "sample": f"{n} full frame(s) of the workload, single-threaded oracle"}
 
 
+def _pct(v, q):
+    v = sorted(v)
+    return v[min(len(v) - 1, (q * len(v)) // 100)]
+
+
+def run_batched(a, F, S, torch):
+    """64 independent views (instanced heightfield floors of 50-400 patches, mixed
+    resolutions and atlas sides) atlased (1) one after the other through
+    fa_atlas_frame on one context (the plain per-view path) and (2) by one replay of
+    a CUDA graph captured from fa_atlas_batch, with the schedule autotuned first.
+    Per-batch times from CUDA events; the views' data (~2 GB) exceeds the L2."""
+    views = S.batch_views(7, n_views=a.batch_views)
+    maxT = max(sc.T for sc, _, _ in views)
+    maxV = max(sc.V for sc, _, _ in views)
+    kw = dict(max_tris=maxT, max_verts=maxV, max_charts=1 << 16, max_width=2560, max_height=1440,
+              max_atlas_log2=12)
+    batch = F.Batch(a.batch_lanes, **kw)
+    solo = F.Context(**kw)
+    mb = [F.BatchMesh(batch, sc.pos, sc.idx) for sc, _, _ in views]
+    ms = [F.Mesh(solo, sc.pos, sc.idx) for sc, _, _ in views]
+    params = [F.frame_params(M, p["width"], p["height"], p["ratio"], p["atlas_log2"]) for _, M, p in views]
+    out = [F.FrameBuffers.allocate(m.T, m.V, kw["max_charts"]) for m in mb]
+    stream = torch.cuda.current_stream()
+    reps = 10
+
+    def plain():
+        for (sc, M, p), m, b in zip(views, ms, out):
+            F.atlas_frame(solo, m, b, M, p["width"], p["height"], p["ratio"], p["atlas_log2"])
+
+    def timed(fn):
+        fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(e0.elapsed_time(e1))
+        return t
+
+    t_plain = timed(plain)
+    lanes, policy, _ = F.batch_tune(batch, mb, params, out, reps=2)
+    F.atlas_batch(batch, mb, params, out)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        F.atlas_batch(batch, mb, params, out)
+    t_batch = timed(g.replay)
+    ok = all(int(b.result[3]) == 0 for b in out)
+    n0 = batch.launches
+    F.atlas_batch(batch, mb, params, out)
+    torch.cuda.synchronize()
+    launches = batch.launches - n0
+    for m in mb + ms:
+        m.close()
+    batch.close()
+    solo.close()
+    n = len(views)
+    bp50, pp50 = _pct(t_batch, 50), _pct(t_plain, 50)
+    return {"workload": f"{n} views: instanced 64x64 heightfield floors of 50-400 patches, 640x360-2560x1440, "
+                        "atlas 1024-4096, ratio 1, edge charts, 64 scales",
+            "views": n, "triangles": int(sum(sc.T for sc, _, _ in views)),
+            "lanes": lanes, "policy": "longest_first" if policy else "round_robin",
+            "batched_ms_p50": bp50, "batched_ms_p99": _pct(t_batch, 99),
+            "batched_views_per_s": n / (bp50 * 1e-3), "batched_gpu_launches": launches,
+            "plain_ms_p50": pp50, "plain_ms_p99": _pct(t_plain, 99), "plain_views_per_s": n / (pp50 * 1e-3),
+            "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps}
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -362,6 +436,12 @@ def run_ours(a):
         e2e = {"value": whole_job_rate(world, a.steps, e_ms), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
+    batched = None
+    if not a.no_batched:
+        mesh.close()
+        ctx.close()
+        batched = run_batched(a, F, S, torch)
+
     if rank != 0:
         if world > 1:
             dist.barrier()
@@ -401,6 +481,8 @@ def run_ours(a):
             "traced_ms_per_frame": traced_ms / n_traced,
             "ms_p50": srt[len(srt) // 2], "ms_p99": srt[min(len(srt) - 1, (99 * len(srt)) // 100)],
             "roofline": roof, "frame_roofline": frame_roof, "e2e": e2e, "clocks": clk}
+    if not a.no_batched:
+        line["batched"] = batched
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, sc, M, p)
     print(json.dumps(line), flush=True)
