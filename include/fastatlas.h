@@ -356,6 +356,77 @@ fa_status fa_batch_tune(fa_batch* batch, uint32_t n_views, const fa_mesh* const*
 /* Kernels launched by all lanes since creation. */
 uint64_t fa_batch_launch_count(const fa_batch* batch);
 
+/* ------------------------------------------------------------------ serving
+ *
+ * Continuous batching of per-client view requests.  The paper's setting is a
+ * streaming-shading server that re-atlases every client frame (Sec. 1, Sec. 6);
+ * here clients are sessions whose mesh and output buffers stay on the device.
+ * The server owns slots (a context plus a stream each), as many as fit a
+ * device-memory budget.  Requests are queued when submitted and dispatched, in
+ * submission order, to the first free slot once their session has no request on
+ * the GPU; a request that arrives while others run starts as soon as a slot frees
+ * up, and the slots' work overlaps on the device.  Each request runs the
+ * fa_atlas_frame launch sequence, so its results equal those of the same request
+ * alone.  The server is driven from one host thread (submit / poll); it is not
+ * thread-safe. */
+typedef struct fa_server fa_server;
+
+#define FA_SERVER_MAX_SLOTS 64u
+
+/* One finished request, with host steady-clock times in milliseconds since the
+ * server was created (fa_server_now_ms). */
+typedef struct {
+  uint64_t ticket;
+  uint32_t session;
+  uint32_t slot;
+  double submit_ms;    /* fa_server_submit */
+  double dispatch_ms;  /* launched on its slot */
+  double done_ms;      /* completion seen by fa_server_poll */
+} fa_server_done;
+
+/* Up to max_slots slots of configuration *cfg, each admitted only while the
+ * device memory taken so far (slots, then sessions) stays within budget_bytes;
+ * *n_slots (may be NULL) receives the count.  Errors: FA_E_INVALID_ARG,
+ * FA_E_OUT_OF_MEMORY (not even one slot fits), FA_E_CUDA. */
+fa_status fa_server_create(fa_server** out, const fa_config* cfg, uint32_t max_slots, uint64_t budget_bytes,
+                           uint32_t* n_slots);
+
+/* Synchronizes the device, releases the sessions' meshes and frees the slots. */
+void fa_server_destroy(fa_server* server);
+
+/* Open a session: register its mesh (d_pos float[V][3], d_idx uint32[T][3],
+ * caller-owned, kept until the session closes) and remember its default output
+ * buffers *out (may be NULL: every request then passes its own).  Admission: the
+ * registration's device memory must fit the remaining budget.  *session receives
+ * the id.  Errors: FA_E_INVALID_ARG (sizes above the slots' maxima),
+ * FA_E_OUT_OF_MEMORY (budget), FA_E_CUDA. */
+fa_status fa_server_session_open(fa_server* server, const float* d_pos, uint32_t V, const uint32_t* d_idx,
+                                 uint32_t T, const fa_frame_out* out, uint32_t* session);
+
+/* Close an idle session (no request queued or running).  Errors: FA_E_INVALID_ARG. */
+fa_status fa_server_session_close(fa_server* server, uint32_t session);
+
+/* Queue one view request of a session (params as fa_atlas_frame; out = its
+ * outputs, or NULL for the session's default buffers) and dispatch what fits.
+ * Checked on the host first.  *ticket (may be NULL) receives its id.
+ * Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_server_submit(fa_server* server, uint32_t session, const fa_frame_params* params,
+                           const fa_frame_out* out, uint64_t* ticket);
+
+/* Non-blocking: report up to max_done finished requests into done[], free their
+ * slots and dispatch queued requests into them.  *n_done receives the count.  A
+ * request's per-frame status is in its outputs' result record.
+ * Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_server_poll(fa_server* server, fa_server_done* done, uint32_t max_done, uint32_t* n_done);
+
+/* Queued and running requests, the most requests that ran at once, and the
+ * device bytes taken by slots and sessions (any pointer may be NULL). */
+fa_status fa_server_stats(const fa_server* server, uint32_t* queued, uint32_t* running, uint32_t* max_running,
+                          uint64_t* used_bytes);
+
+/* The server's clock: milliseconds since creation (host steady clock). */
+double fa_server_now_ms(const fa_server* server);
+
 #ifdef __cplusplus
 }
 #endif

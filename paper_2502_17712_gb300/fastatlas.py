@@ -37,7 +37,9 @@ EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh
            "fa_atlas_frame", "fa_last_device_status", "fa_launch_count", "fa_profile_enable",
            "fa_profile_read", "fa_pack_noalloc", "fa_atlas_frame_dev_matrix", "fa_batch_create",
            "fa_batch_destroy", "fa_batch_mesh_register", "fa_batch_set_schedule", "fa_batch_get_schedule",
-           "fa_atlas_batch", "fa_batch_tune", "fa_batch_launch_count"]
+           "fa_atlas_batch", "fa_batch_tune", "fa_batch_launch_count", "fa_server_create", "fa_server_destroy",
+           "fa_server_session_open", "fa_server_session_close", "fa_server_submit", "fa_server_poll",
+           "fa_server_stats", "fa_server_now_ms"]
 
 FA_BATCH_ROUND_ROBIN, FA_BATCH_LONGEST_FIRST = 0, 1
 
@@ -73,6 +75,11 @@ class fa_frame_out(ctypes.Structure):
     _fields_ = [("vt", ctypes.c_void_p), ("tri_chart", ctypes.c_void_p), ("vert_chart", ctypes.c_void_p),
                 ("charts", fa_charts), ("order", ctypes.c_void_p), ("place", ctypes.c_void_p),
                 ("result", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("affine", ctypes.c_void_p)]
+
+
+class fa_server_done(ctypes.Structure):
+    _fields_ = [("ticket", ctypes.c_uint64), ("session", ctypes.c_uint32), ("slot", ctypes.c_uint32),
+                ("submit_ms", ctypes.c_double), ("dispatch_ms", ctypes.c_double), ("done_ms", ctypes.c_double)]
 
 
 _lib = None
@@ -135,6 +142,25 @@ def load(path: str = LIB_PATH):
     lib.fa_batch_tune.restype = st
     lib.fa_batch_launch_count.argtypes = [P]
     lib.fa_batch_launch_count.restype = ctypes.c_uint64
+    lib.fa_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(fa_config), u32, ctypes.c_uint64,
+                                     ctypes.POINTER(u32)]
+    lib.fa_server_create.restype = st
+    lib.fa_server_destroy.argtypes = [P]
+    lib.fa_server_destroy.restype = None
+    lib.fa_server_session_open.argtypes = [P, P, u32, P, u32, ctypes.POINTER(fa_frame_out), ctypes.POINTER(u32)]
+    lib.fa_server_session_open.restype = st
+    lib.fa_server_session_close.argtypes = [P, u32]
+    lib.fa_server_session_close.restype = st
+    lib.fa_server_submit.argtypes = [P, u32, ctypes.POINTER(fa_frame_params), ctypes.POINTER(fa_frame_out),
+                                     ctypes.POINTER(ctypes.c_uint64)]
+    lib.fa_server_submit.restype = st
+    lib.fa_server_poll.argtypes = [P, ctypes.POINTER(fa_server_done), u32, ctypes.POINTER(u32)]
+    lib.fa_server_poll.restype = st
+    lib.fa_server_stats.argtypes = [P, ctypes.POINTER(u32), ctypes.POINTER(u32), ctypes.POINTER(u32),
+                                    ctypes.POINTER(ctypes.c_uint64)]
+    lib.fa_server_stats.restype = st
+    lib.fa_server_now_ms.argtypes = [P]
+    lib.fa_server_now_ms.restype = ctypes.c_double
     lib.fa_last_device_status.argtypes = [P, P, ctypes.POINTER(ctypes.c_int32)]
     lib.fa_last_device_status.restype = st
     lib.fa_launch_count.argtypes = [P]
@@ -469,3 +495,71 @@ def batch_tune(batch: Batch, meshes, params, bufs, reps=3):
     _check(load().fa_batch_tune(batch.handle, n, mh, pa, oa, reps, ctypes.byref(ms)), "fa_batch_tune")
     lanes, pol = batch.schedule()
     return lanes, pol, ms.value
+
+
+# ------------------------------------------------------------------ serving
+
+class Server:
+    """An fa_server: slots (context + stream) admitted by a device-memory budget,
+    sessions with device-resident meshes, continuous batching of view requests."""
+
+    def __init__(self, max_slots, budget_bytes, max_tris, max_verts, max_charts=1 << 16, max_width=1920,
+                 max_height=1080, max_atlas_log2=12, min_box=2, gutter=0, device=0):
+        self.cfg = fa_config(max_tris, max_verts, max_charts, max_width, max_height, max_atlas_log2,
+                             min_box, gutter, device)
+        h, n = ctypes.c_void_p(), ctypes.c_uint32()
+        _check(load().fa_server_create(ctypes.byref(h), ctypes.byref(self.cfg), max_slots, int(budget_bytes),
+                                       ctypes.byref(n)), "fa_server_create")
+        self.handle = h.value
+        self.n_slots = n.value
+        self._keep = {}
+
+    def close(self):
+        if self.handle:
+            load().fa_server_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def open_session(self, pos, idx, bufs: "FrameBuffers | None" = None) -> int:
+        import torch
+        pos = pos if torch.is_tensor(pos) else torch.as_tensor(np.ascontiguousarray(pos, np.float32)).cuda()
+        idx = idx if torch.is_tensor(idx) else torch.as_tensor(
+            np.ascontiguousarray(idx, np.uint32).view(np.int32)).cuda()
+        sid = ctypes.c_uint32()
+        out = ctypes.byref(bufs.c_out()) if bufs is not None else None
+        _check(load().fa_server_session_open(self.handle, _ptr(pos), int(pos.shape[0]), _ptr(idx),
+                                             int(idx.shape[0]), out, ctypes.byref(sid)), "fa_server_session_open")
+        self._keep[sid.value] = (pos, idx, bufs)
+        return sid.value
+
+    def close_session(self, sid: int):
+        _check(load().fa_server_session_close(self.handle, sid), "fa_server_session_close")
+        self._keep.pop(sid, None)
+
+    def submit(self, sid: int, params: fa_frame_params, bufs: "FrameBuffers | None" = None) -> int:
+        t = ctypes.c_uint64()
+        out = ctypes.byref(bufs.c_out()) if bufs is not None else None
+        _check(load().fa_server_submit(self.handle, sid, ctypes.byref(params), out, ctypes.byref(t)),
+               "fa_server_submit")
+        return t.value
+
+    def poll(self, max_done=64):
+        arr = (fa_server_done * max_done)()
+        n = ctypes.c_uint32()
+        _check(load().fa_server_poll(self.handle, arr, max_done, ctypes.byref(n)), "fa_server_poll")
+        return [dict(ticket=d.ticket, session=d.session, slot=d.slot, submit_ms=d.submit_ms,
+                     dispatch_ms=d.dispatch_ms, done_ms=d.done_ms) for d in arr[:n.value]]
+
+    def stats(self):
+        q, r, m, b = ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint32(), ctypes.c_uint64()
+        _check(load().fa_server_stats(self.handle, ctypes.byref(q), ctypes.byref(r), ctypes.byref(m),
+                                      ctypes.byref(b)), "fa_server_stats")
+        return dict(queued=q.value, running=r.value, max_running=m.value, used_bytes=b.value)
+
+    def now_ms(self) -> float:
+        return float(load().fa_server_now_ms(self.handle))
