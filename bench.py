@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-batched", action="store_true", help="skip the 64-view batched measurement")
     ap.add_argument("--batch-views", type=int, default=64)
     ap.add_argument("--batch-lanes", type=int, default=16)
+    ap.add_argument("--no-served", action="store_true", help="skip the 16-session served measurement")
+    ap.add_argument("--served-slots", type=int, default=8)
     return ap.parse_args()
 
 
@@ -305,6 +307,77 @@ def run_batched(a, F, S, torch):
             "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps}
 
 
+def run_served(a, F, S, torch):
+    """16 client sessions (displaced-icosphere scenes of 25-200 spheres, 0.5M-4.1M
+    triangles, meshes and outputs resident on the device) send view requests with
+    Poisson arrivals; each request is a 1280x720 / 1920x1080 / 2560x1440 view from
+    a seeded camera into a 2048^2 or 4096^2 atlas.  The same arrival sequence is
+    served (1) with continuous batching on several slots and (2) by the plain
+    per-request path, one slot (requests one at a time, in arrival order).
+    Latency = completion seen on the host - arrival, host steady clock."""
+    import numpy as np
+    rng = np.random.default_rng(0x5E7)
+    res = ((1280, 720), (1920, 1080), (2560, 1440))
+    sessions = [S.icosphere_scene(300 + i, int(rng.integers(25, 201))) for i in range(16)]
+    maxT = max(sc.T for sc in sessions)
+    maxV = max(sc.V for sc in sessions)
+    kw = dict(max_tris=maxT, max_verts=maxV, max_charts=1 << 17, max_width=2560, max_height=1440,
+              max_atlas_log2=12)
+
+    def requests(n, rate, seed):
+        r = np.random.default_rng(seed)
+        arr = np.cumsum(r.exponential(1e3 / rate, n))  # ms
+        out = []
+        for i in range(n):
+            s_ = int(r.integers(16))
+            W, H = res[int(r.integers(3))]
+            log2 = 11 + int(r.integers(2))
+            M = S.box_camera(int(r.integers(1 << 30)), W, H)
+            out.append((float(arr[i]), s_, F.frame_params(M, W, H, 1.0, log2)))
+        return out
+
+    def serve(n_slots, reqs):
+        server = F.Server(n_slots, 64 << 30, **kw)
+        bufs = [F.FrameBuffers.allocate(sc.T, sc.V, kw["max_charts"]) for sc in sessions]
+        sids = [server.open_session(sc.pos, sc.idx, b) for sc, b in zip(sessions, bufs)]
+        # warm-up: one request per session
+        for sid in sids:
+            server.submit(sid, reqs[0][2])
+        n = 0
+        while n < len(sids):
+            n += len(server.poll())
+        t0 = server.now_ms() + 1.0
+        lat, nxt, done, last = [], 0, 0, 0.0
+        submit_at = {}
+        while done < len(reqs):
+            now = server.now_ms() - t0
+            while nxt < len(reqs) and reqs[nxt][0] <= now:
+                tk = server.submit(sids[reqs[nxt][1]], reqs[nxt][2])
+                submit_at[tk] = reqs[nxt][0]
+                nxt += 1
+            for d in server.poll():
+                if d["ticket"] in submit_at:
+                    lat.append(d["done_ms"] - t0 - submit_at.pop(d["ticket"]))
+                    done += 1
+                    last = d["done_ms"] - t0
+        st = server.stats()
+        ok = all(int(b.result[3]) == 0 for b in bufs)
+        server.close()
+        return {"ms_p50": _pct(lat, 50), "ms_p99": _pct(lat, 99), "ms_mean": float(np.mean(lat)),
+                "requests_per_s": len(reqs) / ((last - reqs[0][0]) * 1e-3), "slots": n_slots,
+                "max_running": st["max_running"], "last_frames_packed": ok}
+
+    out = {"workload": "16 sessions of displaced-icosphere scenes (25-200 spheres, 0.5M-4.1M tris), "
+                       "Poisson arrivals, views 1280x720 / 1920x1080 / 2560x1440, atlas 2048 or 4096, ratio 1, "
+                       "edge charts, 64 scales",
+           "triangles_per_session": [int(sc.T) for sc in sessions]}
+    for name, rate, n in (("rate_240_per_s", 240.0, 480), ("rate_4000_per_s", 4000.0, 1200)):
+        reqs = requests(n, rate, int(rate))
+        out[name] = {"offered_per_s": rate, "requests": n,
+                     "continuous_batching": serve(a.served_slots, reqs), "plain": serve(1, reqs)}
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -436,11 +509,14 @@ def run_ours(a):
         e2e = {"value": whole_job_rate(world, a.steps, e_ms), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h}
 
-    batched = None
-    if not a.no_batched:
+    batched = served = None
+    if not (a.no_batched and a.no_served):
         mesh.close()
         ctx.close()
+    if not a.no_batched:
         batched = run_batched(a, F, S, torch)
+    if not a.no_served:
+        served = run_served(a, F, S, torch)
 
     if rank != 0:
         if world > 1:
@@ -483,6 +559,8 @@ def run_ours(a):
             "roofline": roof, "frame_roofline": frame_roof, "e2e": e2e, "clocks": clk}
     if not a.no_batched:
         line["batched"] = batched
+    if not a.no_served:
+        line["served"] = served
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, sc, M, p)
     print(json.dumps(line), flush=True)
