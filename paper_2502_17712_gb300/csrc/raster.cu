@@ -360,10 +360,31 @@ __device__ __forceinline__ bool surely_empty(const RasterArgs& A, const float4& 
 // route to the clipped list, conservative reject.  Returns 1 when the triangle needs
 // the exact set-up (unclipped; its clip coordinates are left in c[3]), 2 when it must
 // be clipped first, 0 when dropped.
-__device__ __forceinline__ int front_triangle(const RasterArgs& A, const Mat4& M, uint32_t t, float4* c) {
-  const uint32_t* f = A.idx + 3 * (size_t)t;
-  const uint32_t i0 = __ldg(f), i1 = __ldg(f + 1), i2 = __ldg(f + 2);
-  const float4 c0 = load_clip(M, A.pos, i0), c1 = load_clip(M, A.pos, i1), c2 = load_clip(M, A.pos, i2);
+struct TriPos {
+  float p[9];  // the three corners' world positions
+};
+
+__device__ __forceinline__ uint3 load_tri(const uint32_t* __restrict__ idx, uint32_t t) {
+  const uint32_t* f = idx + 3 * (size_t)t;
+  return make_uint3(__ldg(f), __ldg(f + 1), __ldg(f + 2));
+}
+
+__device__ __forceinline__ TriPos load_pos(const float* __restrict__ pos, uint3 i) {
+  TriPos q;
+  const uint32_t v[3] = {i.x, i.y, i.z};
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const float* p = pos + 3 * (size_t)v[k];
+    q.p[3 * k] = __ldg(p);
+    q.p[3 * k + 1] = __ldg(p + 1);
+    q.p[3 * k + 2] = __ldg(p + 2);
+  }
+  return q;
+}
+
+__device__ __forceinline__ int front_triangle(const RasterArgs& A, const Mat4& M, const TriPos& q, float4* c) {
+  const float4 c0 = transform(M, q.p[0], q.p[1], q.p[2]), c1 = transform(M, q.p[3], q.p[4], q.p[5]),
+               c2 = transform(M, q.p[6], q.p[7], q.p[8]);
   // trivial reject: all vertices outside one side plane, or all behind the near plane
   // (no sample can be covered then: see the design notes on exactness)
   if ((c0.x > c0.w && c1.x > c1.w && c2.x > c2.w) || (c0.x < -c0.w && c1.x < -c1.w && c2.x < -c2.w) ||
@@ -433,10 +454,20 @@ __global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
   // block b owns survivor slots [b * surv_per_block, (b + 1) * surv_per_block): it sees
   // at most that many triangles, so its region cannot overflow
   const uint32_t region = blockIdx.x * A.surv_per_block;
-  for (uint32_t base = blockIdx.x * kFrontThreads; base < A.T; base += gridDim.x * kFrontThreads) {
+  // software pipeline over this thread's triangles t, t + stride, ...: the indices
+  // are loaded two iterations ahead and the corner positions one iteration ahead, so
+  // that each iteration waits on no dependent load of its own
+  const uint32_t stride = gridDim.x * kFrontThreads;
+  const uint32_t t0 = blockIdx.x * kFrontThreads + threadIdx.x;
+  uint3 idx1 = t0 + stride < A.T ? load_tri(A.idx, t0 + stride) : make_uint3(0u, 0u, 0u);
+  TriPos pos0 = load_pos(A.pos, t0 < A.T ? load_tri(A.idx, t0) : make_uint3(0u, 0u, 0u));
+  for (uint32_t base = blockIdx.x * kFrontThreads; base < A.T; base += stride) {
     const uint32_t t = base + threadIdx.x;
+    const TriPos cur = pos0;
+    pos0 = load_pos(A.pos, idx1);
+    idx1 = t + 2u * stride < A.T ? load_tri(A.idx, t + 2u * stride) : make_uint3(0u, 0u, 0u);
     float4 c[3];
-    const int r = t < A.T ? front_triangle(A, M, t, c) : 0;
+    const int r = t < A.T ? front_triangle(A, M, cur, c) : 0;
     const uint32_t b1 = __ballot_sync(0xFFFFFFFFu, r == 1), b2 = __ballot_sync(0xFFFFFFFFu, r == 2);
     if (b1) {
       uint32_t o = 0;
