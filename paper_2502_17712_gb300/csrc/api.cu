@@ -94,7 +94,7 @@ void fa_destroy(fa_ctx* ctx) {
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
   void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
-                  ctx->label, ctx->cid, ctx->blockcnt,
+                  ctx->label, ctx->cid, ctx->blockcnt, ctx->viscnt, ctx->vis,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
   for (void* p : ptrs)
@@ -152,6 +152,8 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->label, T + V);
   FA_ALLOC(ctx->cid, T);
   FA_ALLOC(ctx->blockcnt, nblocks + 1);
+  FA_ALLOC(ctx->viscnt, nblocks + 1);
+  FA_ALLOC(ctx->vis, T);
   FA_ALLOC(ctx->box_enc, 4 * C);
   FA_ALLOC(ctx->box_full, C);
   FA_ALLOC(pk.ord_counts, (uint64_t)kMaxH * pk.max_tiles);
@@ -238,23 +240,8 @@ fa_status fa_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* d_vt, ui
   return st;
 }
 
-// The box and UV kernels walk the VT words; the standalone calls derive them from
-// tri_chart so that they need no extra argument.
-namespace {
-__global__ void k_vt_from_chart(const int32_t* tri_chart, uint32_t T, uint32_t* vt) {
-  pdl_wait();
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwords = (T + 31) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
-       w += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t t = (w << 5) + lane;
-    const bool v = t < T && tri_chart[t] >= 0;
-    const uint32_t bits = __ballot_sync(0xFFFFFFFFu, v);
-    if (lane == 0) vt[w] = bits;
-  }
-}
-}  // namespace
-
+// The box and UV kernels walk the context's visible-triangle list; the standalone
+// calls build it from tri_chart so that they need no extra argument.
 fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
                           uint32_t height, float ratio, const int32_t* d_tri_chart, const fa_charts* charts,
                           fa_stream_t stream) {
@@ -265,12 +252,10 @@ fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_pro
   if (!(ratio > 0.0f && ratio <= 64.0f)) return FA_E_INVALID_ARG;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t* vt = ctx->bigbits;  // reuse: the raster's queue bits are dead after visibility
   trace_begin(ctx);
-  mark(ctx, "k_vt_from_chart", s);
-  launch_k(k_vt_from_chart, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s, d_tri_chart,
-                                                                                              mesh->T, vt);
-  st = launch_parameterize(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, vt, charts, true, s);
+  st = launch_vis_list(ctx, mesh, d_tri_chart, s);
+  if (st == FA_OK)
+    st = launch_parameterize(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, charts, true, s);
   trace_end(ctx, s);
   return st;
 }
@@ -302,13 +287,11 @@ fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uin
   if (!(ratio > 0.0f && ratio <= 64.0f)) return FA_E_INVALID_ARG;
   DeviceGuard g(ctx->device);
   cudaStream_t s = (cudaStream_t)stream;
-  uint32_t* vt = ctx->bigbits;
   trace_begin(ctx);
-  mark(ctx, "k_vt_from_chart", s);
-  launch_k(k_vt_from_chart, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 8), 256, 0, s, d_tri_chart,
-                                                                                              mesh->T, vt);
-  st = launch_uv(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, vt, charts, d_place, d_res,
-                 atlas_log2, n_scales, d_uv, d_affine, s);
+  st = launch_vis_list(ctx, mesh, d_tri_chart, s);
+  if (st == FA_OK)
+    st = launch_uv(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, charts, d_place, d_res,
+                   atlas_log2, n_scales, d_uv, d_affine, s);
   trace_end(ctx, s);
   return st;
 }
@@ -348,14 +331,14 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators
-  if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, o->vt, &o->charts,
+  if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts,
                                 false, s, Md)) != FA_OK)
     return st;
   if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
                         p->select_mode, o->order, o->place, o->result, s)) != FA_OK)
     return st;
   if (o->uv || o->affine) {
-    if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, o->vt, &o->charts, o->place,
+    if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts, o->place,
                         o->result, p->atlas_log2, p->n_scales, o->uv, o->affine, s, Md)) != FA_OK)
       return st;
   }

@@ -76,6 +76,7 @@ struct UfArgs {
 // global init: afterwards every visible triangle points to a root, and only edges that
 // leave the tile remain for the global hooking.
 constexpr int kTile = 1024;
+constexpr int kLocalThreads = 1024;  // one triangle of the tile per thread
 
 __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
   int32_t cur = lab[x];
@@ -90,7 +91,7 @@ __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
   return cur;
 }
 
-__global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
+__global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
   pdl_wait();
   __shared__ int32_t lab[kTile];
   __shared__ uint32_t vis[kTile / 32];
@@ -104,10 +105,10 @@ __global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
   if (!__syncthreads_or(v != 0u)) return;  // no visible triangle in this tile
   volatile int32_t* vl = lab;
   // start from the smallest visible neighbour inside the tile (Alg. 1, first loop)
-  int32_t nb[kTile / kBlock][3];
+  int32_t nb[kTile / kLocalThreads][3];
 #pragma unroll
-  for (int k = 0; k < kTile / kBlock; ++k) {
-    const uint32_t i = threadIdx.x + k * kBlock;
+  for (int k = 0; k < kTile / kLocalThreads; ++k) {
+    const uint32_t i = threadIdx.x + k * kLocalThreads;
     int32_t l = (int32_t)i;
 #pragma unroll
     for (int j = 0; j < 3; ++j) nb[k][j] = -1;
@@ -128,8 +129,8 @@ __global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
   __syncthreads();
   // hook every in-tile edge once, from its lower end
 #pragma unroll
-  for (int k = 0; k < kTile / kBlock; ++k) {
-    const int32_t i = (int32_t)(threadIdx.x + k * kBlock);
+  for (int k = 0; k < kTile / kLocalThreads; ++k) {
+    const int32_t i = (int32_t)(threadIdx.x + k * kLocalThreads);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int32_t ni = nb[k][j];
@@ -145,7 +146,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_local(UfArgs a) {
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kTile; i += kBlock) {
+  for (uint32_t i = threadIdx.x; i < kTile; i += kLocalThreads) {
     if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
     int32_t r = (int32_t)i, nx;
     while ((nx = vl[r]) != r) r = nx;
@@ -204,16 +205,17 @@ __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* n
 
 // Flatten visible triangles to their root and count roots per block of
 // kPerBlock triangles: warp w of the block owns VT words w, w + 8, w + 16, w + 24.
-__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt) {
+__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt, uint32_t* viscnt) {
   pdl_wait();
-  __shared__ uint32_t cnt[kBlock / 32];
+  __shared__ uint32_t cnt[kBlock / 32], vcnt[kBlock / 32];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
-  uint32_t mine = 0;
+  uint32_t mine = 0, vis = 0;
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
     const uint32_t w = blockIdx.x * (kPerBlock / 32) + k * (kBlock / 32) + wid;
     const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
+    vis += __popc(word);
     if (!((word >> lane) & 1u)) continue;
     const uint32_t t = (w << 5) + lane;
     const int32_t r = find_root(a.label, (int32_t)t);
@@ -221,57 +223,98 @@ __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* block
     mine += (r == (int32_t)t);
   }
   mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-  if (lane == 0) cnt[wid] = mine;
+  if (lane == 0) {
+    cnt[wid] = mine;
+    vcnt[wid] = vis;  // every lane counted the same words
+  }
   __syncthreads();
   if (threadIdx.x == 0) {
-    uint32_t s = 0;
-    for (int i = 0; i < kBlock / 32; ++i) s += cnt[i];
+    uint32_t s = 0, v = 0;
+    for (int i = 0; i < kBlock / 32; ++i) {
+      s += cnt[i];
+      v += vcnt[i];
+    }
     blockcnt[blockIdx.x] = s;
+    viscnt[blockIdx.x] = v;
   }
 }
 
-// Exclusive scan of the per-block root counts (one block); writes the chart count.
-__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blockcnt, uint32_t nblocks,
-                                                      uint32_t* count_out, uint32_t max_charts,
-                                                      DevCounters* ctr) {
-  pdl_wait();
-  __shared__ uint32_t warp_tot[32];
-  __shared__ uint32_t carry;
-  if (threadIdx.x == 0) carry = 0;
+// In-place exclusive scans of the per-block counts a[0..n) and, when given,
+// b[0..n) (one 1024-thread block, both in the same pass); the totals go to a[n],
+// b[n], *ta and *tb.
+__device__ void scan_counts(uint32_t* a, uint32_t* b, uint32_t n, uint32_t* ta, uint32_t* tb) {
+  __shared__ uint2 warp_tot[32];
+  __shared__ uint2 carry;
+  if (threadIdx.x == 0) carry = make_uint2(0u, 0u);
   __syncthreads();
-  for (uint32_t base = 0; base < nblocks; base += 1024) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (uint32_t base = 0; base < n; base += 1024) {
     const uint32_t i = base + threadIdx.x;
-    uint32_t v = i < nblocks ? blockcnt[i] : 0;
-    uint32_t x = v;
+    const uint2 v = make_uint2(i < n ? a[i] : 0u, (b && i < n) ? b[i] : 0u);
+    uint2 x = v;
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
-      if ((threadIdx.x & 31) >= (unsigned)o) x += y;
+      const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, x.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, x.y, o);
+      if (lane >= (unsigned)o) {
+        x.x += y0;
+        x.y += y1;
+      }
     }
-    if ((threadIdx.x & 31) == 31) warp_tot[threadIdx.x >> 5] = x;
+    if (lane == 31) warp_tot[wid] = x;
     __syncthreads();
     if (threadIdx.x < 32) {
-      uint32_t t = warp_tot[threadIdx.x];
+      uint2 t = warp_tot[threadIdx.x];
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
-        uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o);
-        if (threadIdx.x >= (unsigned)o) t += y;
+        const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, t.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, t.y, o);
+        if (threadIdx.x >= (unsigned)o) {
+          t.x += y0;
+          t.y += y1;
+        }
       }
       warp_tot[threadIdx.x] = t;
     }
     __syncthreads();
-    const uint32_t wprefix = (threadIdx.x >= 32) ? warp_tot[(threadIdx.x >> 5) - 1] : 0;
-    if (i < nblocks) blockcnt[i] = carry + wprefix + x - v;
+    const uint2 wp = wid ? warp_tot[wid - 1] : make_uint2(0u, 0u);
+    const uint2 cr = carry;
+    if (i < n) {
+      a[i] = cr.x + wp.x + x.x - v.x;
+      if (b) b[i] = cr.y + wp.y + x.y - v.y;
+    }
     __syncthreads();
-    if (threadIdx.x == 1023) carry += wprefix + x;
+    if (threadIdx.x == 1023) carry = make_uint2(cr.x + wp.x + x.x, cr.y + wp.y + x.y);
     __syncthreads();
   }
   if (threadIdx.x == 0) {
-    blockcnt[nblocks] = carry;
-    ctr->chart_count = carry;
-    *count_out = carry;
-    if (carry > max_charts) set_status(ctr, FA_E_CAPACITY);
+    a[n] = carry.x;
+    *ta = carry.x;
+    if (b) {
+      b[n] = carry.y;
+      *tb = carry.y;
+    }
   }
+  __syncthreads();
+}
+
+// Exclusive scans of the per-block root counts (chart numbering) and visible
+// counts (the visible-triangle list); writes the chart count.
+__global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blockcnt, uint32_t* viscnt, uint32_t nblocks,
+                                                      uint32_t* count_out, uint32_t max_charts,
+                                                      DevCounters* ctr) {
+  pdl_wait();
+  __shared__ uint32_t charts;
+  scan_counts(blockcnt, viscnt, nblocks, &charts, &ctr->n_vis);
+  if (threadIdx.x == 0) {
+    ctr->chart_count = charts;
+    *count_out = charts;
+    if (charts > max_charts) set_status(ctr, FA_E_CAPACITY);
+  }
+}
+
+// Scan of the visible counts alone (the standalone box / UV calls).
+__global__ void __launch_bounds__(1024) k_scan_vis(uint32_t* viscnt, uint32_t nblocks, DevCounters* ctr) {
+  pdl_wait();
+  scan_counts(viscnt, nullptr, nblocks, &ctr->n_vis, nullptr);
 }
 
 // Number the roots in triangle order (same blocking as k_uf_flatten); record the
@@ -314,20 +357,86 @@ __global__ void __launch_bounds__(kBlock) k_number(UfArgs a, const uint32_t* blo
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* cid, int32_t* tri_chart) {
+// The entries of one 1024-triangle block's visible triangles in the list, in
+// triangle order: entry = list start of the block + the visible triangles before
+// it.  words[k] is VT word k * 8 + warp of the block.
+__device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / kBlock], uint32_t start,
+                                            const int32_t (&chart)[kPerBlock / kBlock], uint2* vis) {
+  __shared__ uint32_t wpop[kPerBlock / 32];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k)
+    if (lane == 0) wpop[k * (kBlock / 32) + wid] = __popc(words[k]);
+  __syncthreads();
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t wl = k * (kBlock / 32) + wid;
+    if (!((words[k] >> lane) & 1u)) continue;
+    uint32_t pre = start;
+    for (uint32_t i = 0; i < wl; ++i) pre += wpop[i];
+    pre += __popc(words[k] & ((1u << lane) - 1u));
+    const uint32_t t = ((blockIdx.x * (kPerBlock / 32) + wl) << 5) + lane;
+    vis[pre] = make_uint2(t, (uint32_t)chart[k]);
+  }
+}
+
+// Chart id of every triangle (-1 invisible) and the visible-triangle list (same
+// blocking as k_uf_flatten).
+__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* cid, int32_t* tri_chart,
+                                                      const uint32_t* visstart, uint2* vis) {
   pdl_wait();
   if (__ldcg(&a.ctr->status) != 0) return;
-  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
-       w += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t word = __ldg(a.vt + w);
+  uint32_t words[kPerBlock / kBlock];
+  int32_t chart[kPerBlock / kBlock];
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t w = blockIdx.x * (kPerBlock / 32) + k * (kBlock / 32) + wid;
+    words[k] = w < nwords ? __ldg(a.vt + w) : 0u;
     const uint32_t t = (w << 5) + lane;
-    if (t >= a.T) continue;
     int32_t out = -1;
-    if ((word >> lane) & 1u) out = __ldcg(cid + __ldcg(a.label + t));
-    tri_chart[t] = out;
+    if ((words[k] >> lane) & 1u) out = __ldcg(cid + __ldcg(a.label + t));
+    chart[k] = out;
+    if (w < nwords && t < a.T) tri_chart[t] = out;
   }
+  put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis);
+}
+
+// Standalone path: visible counts per block from a caller's tri_chart ...
+__global__ void __launch_bounds__(kBlock) k_vis_count(const int32_t* tri_chart, uint32_t T, uint32_t* viscnt) {
+  pdl_wait();
+  __shared__ uint32_t vc[kBlock / 32];
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t v = 0;
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t t = blockIdx.x * kPerBlock + (k * (kBlock / 32) + wid) * 32 + lane;
+    v += __popc(__ballot_sync(0xFFFFFFFFu, t < T && tri_chart[t] >= 0));
+  }
+  if (lane == 0) vc[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    uint32_t s = 0;
+    for (int i = 0; i < kBlock / 32; ++i) s += vc[i];
+    viscnt[blockIdx.x] = s;
+  }
+}
+
+// ... and the list itself, after k_scan_vis.
+__global__ void __launch_bounds__(kBlock) k_vis_fill(const int32_t* tri_chart, uint32_t T, const uint32_t* visstart,
+                                                     uint2* vis) {
+  pdl_wait();
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  uint32_t words[kPerBlock / kBlock];
+  int32_t chart[kPerBlock / kBlock];
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t t = blockIdx.x * kPerBlock + (k * (kBlock / 32) + wid) * 32 + lane;
+    chart[k] = t < T ? tri_chart[t] : -1;
+    words[k] = __ballot_sync(0xFFFFFFFFu, chart[k] >= 0);
+  }
+  put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis);
 }
 
 __global__ void k_vert_chart(UfArgs a, const int32_t* cid, int32_t* vert_chart, int vertex_mode) {
@@ -362,7 +471,7 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
     launch_k(k_uf_init_v, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, ctx->label, mesh->T, mesh->V);
   }
   mark(ctx, "k_uf_local", s);
-  launch_k(k_uf_local, (mesh->T + kTile - 1) / kTile, kBlock, 0, s, a);
+  launch_k(k_uf_local, (mesh->T + kTile - 1) / kTile, kLocalThreads, 0, s, a);
   mark(ctx, "k_uf_hook", s);
   launch_k(k_uf_hook, gw, kBlock, 0, s, a, vm);
   if (!vm && mesh->n_nm) {
@@ -371,18 +480,31 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   }
   const uint32_t nb = (mesh->T + kPerBlock - 1) / kPerBlock;
   mark(ctx, "k_uf_flatten", s);
-  launch_k(k_uf_flatten, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt);
+  launch_k(k_uf_flatten, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->viscnt);
   mark(ctx, "k_scan_blocks", s);
-  launch_k(k_scan_blocks, 1, 1024, 0, s, ctx->blockcnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts, ctx->ctr);
+  launch_k(k_scan_blocks, 1, 1024, 0, s, ctx->blockcnt, ctx->viscnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts,
+           ctx->ctr);
   mark(ctx, "k_number", s);
   launch_k(k_number, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->cid, ch->root, ctx->box_enc,
                                           ctx->box_full, ctx->cfg.max_charts);
   mark(ctx, "k_tri_chart", s);
-  launch_k(k_tri_chart, gw, kBlock, 0, s, a, ctx->cid, tri_chart);
+  launch_k(k_tri_chart, nb ? nb : 1, kBlock, 0, s, a, ctx->cid, tri_chart, ctx->viscnt, ctx->vis);
   if (vert_chart) {
     mark(ctx, "k_vert_chart", s);
     launch_k(k_vert_chart, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, a, ctx->cid, vert_chart, vm);
   }
+  FA_CUDA_TRY(cudaGetLastError());
+  return FA_OK;
+}
+
+fa_status launch_vis_list(fa_ctx* ctx, const fa_mesh* mesh, const int32_t* tri_chart, cudaStream_t s) {
+  const uint32_t nb = (mesh->T + kPerBlock - 1) / kPerBlock;
+  mark(ctx, "k_vis_count", s);
+  launch_k(k_vis_count, nb ? nb : 1, kBlock, 0, s, tri_chart, mesh->T, ctx->viscnt);
+  mark(ctx, "k_scan_vis", s);
+  launch_k(k_scan_vis, 1, 1024, 0, s, ctx->viscnt, nb ? nb : 1, ctx->ctr);
+  mark(ctx, "k_vis_fill", s);
+  launch_k(k_vis_fill, nb ? nb : 1, kBlock, 0, s, tri_chart, mesh->T, ctx->viscnt, ctx->vis);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }

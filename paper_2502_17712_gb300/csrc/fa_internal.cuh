@@ -35,6 +35,7 @@ struct DevCounters {
   uint32_t chart_count;    // scratch copy of the frame's chart count
   uint32_t n_groups[kMaxScales];
   uint32_t pack_item;      // next (candidate, chunk) item of the width scan
+  uint32_t n_vis;          // entries of the visible-triangle list
 };
 
 // One queued (large) sub-triangle of the raster: snapped vertices, depths and its
@@ -117,6 +118,8 @@ struct fa_ctx {
   int32_t* label;        // [max_tris + max_verts]
   int32_t* cid;          // [max_tris] chart id of root triangles
   uint32_t* blockcnt;    // [n_blocks + 1]
+  uint32_t* viscnt;      // [n_blocks + 1] visible triangles per 1024-triangle block, then their starts
+  uint2* vis;            // [max_tris] (triangle, chart) of the visible triangles, triangle order
   uint32_t* box_enc;     // [max_charts * 4] ordered-int chart boxes
   uint32_t* box_full;    // [max_charts]
   fa::PackScratch pack;  // order + pack scratch (count filled per call)
@@ -283,19 +286,23 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
                           cudaStream_t s);
+// launch_parameterize and launch_uv read the context's visible-triangle list (built
+// by chartify, or by launch_vis_list).
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                               uint32_t H, float ratio, const int32_t* tri_chart,
-                              const uint32_t* vt, const fa_charts* ch, bool reset_boxes, cudaStream_t s,
+                              const fa_charts* ch, bool reset_boxes, cudaStream_t s,
                               const float* Mdev = nullptr);
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
                       uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s);
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
-                    float ratio, const int32_t* tri_chart, const uint32_t* vt, const fa_charts* ch,
+                    float ratio, const int32_t* tri_chart, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
                     uint32_t n_scales, float* uv, float* affine, cudaStream_t s,
                     const float* Mdev = nullptr);
 fa_status build_adjacency(fa_ctx* ctx, fa_mesh* mesh, cudaStream_t s);
+// The visible-triangle list from a caller's tri_chart (standalone box / UV calls).
+fa_status launch_vis_list(fa_ctx* ctx, const fa_mesh* mesh, const int32_t* tri_chart, cudaStream_t s);
 // One whole frame on ctx: host-side checks, then the launch sequence.
 fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
                       const fa_frame_out* o);

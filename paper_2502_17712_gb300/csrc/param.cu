@@ -59,7 +59,7 @@ struct BoxArgs {
   const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
-  const uint32_t* vt;
+  const uint2* vis;  // (triangle, chart) of the visible triangles
   const int32_t* tri_chart;
   uint32_t T;
   uint32_t* box_enc;
@@ -74,18 +74,19 @@ __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
   const Mat4 M = DEV_M ? load_mat(a.Mdev) : a.M;
   if (__ldcg(&a.ctr->status) != 0) return;
   const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
-       w += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t word = __ldg(a.vt + w);
-    if (word == 0) continue;
-    const uint32_t t = (w << 5) + lane;
+  const uint32_t n = __ldcg(&a.ctr->n_vis);
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); base < n; base += stride) {
+    const uint32_t i = base + lane;
+    uint32_t t = 0;
     int32_t c = -1;
     Box b{__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0xff800000),
           __int_as_float(0xff800000), false};
-    if ((word >> lane) & 1u) {
-      c = __ldcg(a.tri_chart + t);
-      if ((uint32_t)c >= a.max_charts) c = -1;  // not a chart of this context: ignored
+    if (i < n) {
+      const uint2 e = __ldcg(a.vis + i);
+      t = e.x;
+      c = (int32_t)e.y;
+      if ((uint32_t)c >= a.max_charts || t >= a.T) c = -1;  // not a chart of this context: ignored
     }
     if (c >= 0) {
       const uint32_t* f = a.idx + 3 * (size_t)t;
@@ -212,7 +213,7 @@ struct UvArgs {
   const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
-  const uint32_t* vt;
+  const uint2* vis;  // (triangle, chart) of the visible triangles
   const int32_t* tri_chart;
   uint32_t T;
   float hx, hy;
@@ -273,15 +274,13 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
     }
   }
   if (!a.uv) return;
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
-       w += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t word = __ldg(a.vt + w);
-    const uint32_t t = (w << 5) + lane;
-    if (!((word >> lane) & 1u)) continue;
-    const int32_t c = __ldcg(a.tri_chart + t);
-    if (c < 0 || (uint32_t)c >= min(__ldcg(a.count), a.max_charts)) continue;
+  const uint32_t n = __ldcg(&a.ctr->n_vis);
+  const uint32_t C = min(__ldcg(a.count), a.max_charts);
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+    const uint2 e = __ldcg(a.vis + i);
+    const uint32_t t = e.x;
+    const int32_t c = (int32_t)e.y;
+    if (c < 0 || (uint32_t)c >= C || t >= a.T) continue;
     const float4 bb = reinterpret_cast<const float4*>(a.bbox)[c];
     const fa_placement pl = a.place[c];
     const bool r = __ldg(a.rot + c) != 0;
@@ -316,8 +315,8 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
 }  // namespace
 
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
-                              float ratio, const int32_t* tri_chart, const uint32_t* vt,
-                              const fa_charts* ch, bool reset_boxes, cudaStream_t s, const float* Mdev) {
+                              float ratio, const int32_t* tri_chart, const fa_charts* ch, bool reset_boxes,
+                              cudaStream_t s, const float* Mdev) {
   if (reset_boxes) {
     mark(ctx, "k_box_reset", s);
     launch_k(k_box_reset, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts,
@@ -328,7 +327,7 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
   a.Mdev = Mdev;
   a.pos = mesh->pos;
   a.idx = mesh->idx;
-  a.vt = vt;
+  a.vis = ctx->vis;
   a.tri_chart = tri_chart;
   a.T = mesh->T;
   a.box_enc = ctx->box_enc;
@@ -337,9 +336,9 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
   a.ctr = ctx->ctr;
   mark(ctx, "k_bbox", s);
   if (Mdev)
-    launch_k(k_bbox<true>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+    launch_k(k_bbox<true>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
   else
-    launch_k(k_bbox<false>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+    launch_k(k_bbox<false>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
   mark(ctx, "k_footprint", s);
   launch_k(k_footprint, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts, ctx->box_enc, ctx->box_full, 0.5f * (float)W, 0.5f * (float)H,
       256.0f * ratio, ch->bbox, ch->fa, ch->fb, ch->rot, ctx->ctr);
@@ -348,7 +347,7 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
 }
 
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H, float ratio,
-                    const int32_t* tri_chart, const uint32_t* vt, const fa_charts* ch,
+                    const int32_t* tri_chart, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
                     uint32_t n_scales, float* uv, float* affine, cudaStream_t s, const float* Mdev) {
   UvArgs a;
@@ -356,7 +355,7 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
   a.Mdev = Mdev;
   a.pos = mesh->pos;
   a.idx = mesh->idx;
-  a.vt = vt;
+  a.vis = ctx->vis;
   a.tri_chart = tri_chart;
   a.T = mesh->T;
   a.hx = 0.5f * (float)W;
@@ -376,9 +375,9 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
   a.ctr = ctx->ctr;
   mark(ctx, "k_uv", s);
   if (Mdev)
-    launch_k(k_uv<true>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+    launch_k(k_uv<true>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
   else
-    launch_k(k_uv<false>, grid_for((uint64_t)((mesh->T + 31) / 32) * 32, 256, 152 * 16), 256, 0, s, a);
+    launch_k(k_uv<false>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
