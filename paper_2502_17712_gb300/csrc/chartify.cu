@@ -68,6 +68,8 @@ struct UfArgs {
   const int32_t* adj;
   uint32_t T, V;
   int32_t* label;
+  uint2* xedge;    // per tile: the edges (t, n > t) of its visible triangles that leave it
+  uint32_t* xcnt;  // per tile: their count
   DevCounters* ctr;
 };
 
@@ -77,6 +79,7 @@ struct UfArgs {
 // leave the tile remain for the global hooking.
 constexpr int kTile = 1024;
 constexpr int kLocalThreads = 1024;  // one triangle of the tile per thread
+constexpr uint32_t kXCap = 3 * kTile;  // cross-tile edge slots per tile
 
 __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
   int32_t cur = lab[x];
@@ -102,8 +105,14 @@ __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
     v = w < ((a.T + 31) >> 5) ? __ldg(a.vt + w) : 0u;
     vis[threadIdx.x] = v;
   }
-  if (!__syncthreads_or(v != 0u)) return;  // no visible triangle in this tile
+  __shared__ uint32_t s_xc;
+  if (threadIdx.x == 0) s_xc = 0;
+  if (!__syncthreads_or(v != 0u)) {  // no visible triangle in this tile
+    if (threadIdx.x == 0) a.xcnt[blockIdx.x] = 0;
+    return;
+  }
   volatile int32_t* vl = lab;
+  uint2* xe = a.xedge + (size_t)blockIdx.x * kXCap;
   // start from the smallest visible neighbour inside the tile (Alg. 1, first loop)
   int32_t nb[kTile / kLocalThreads][3];
 #pragma unroll
@@ -117,7 +126,11 @@ __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
 #pragma unroll
       for (int j = 0; j < 3; ++j) {
         const int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
-        if (n < (int32_t)base || (uint32_t)n >= base + kTile) continue;
+        if (n < (int32_t)base || (uint32_t)n >= base + kTile) {
+          // leaves the tile: hooked globally (once, from the lower end) if n is visible
+          if (n > (int32_t)t) xe[atomicAdd(&s_xc, 1u)] = make_uint2(t, (uint32_t)n);
+          continue;
+        }
         const uint32_t ni = (uint32_t)n - base;
         if (!((vis[ni >> 5] >> (ni & 31)) & 1u)) continue;
         nb[k][j] = (int32_t)ni;
@@ -152,6 +165,7 @@ __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
     while ((nx = vl[r]) != r) r = nx;
     a.label[base + i] = (int32_t)base + r;
   }
+  if (threadIdx.x == 0) a.xcnt[blockIdx.x] = s_xc;  // all appends precede the last barrier
 }
 
 __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
@@ -160,8 +174,21 @@ __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
     label[T + v] = (int32_t)(T + v);
 }
 
-// Hooking (Alg. 1, second loop): each undirected edge once, from its lower end.
-__global__ void __launch_bounds__(kBlock) k_uf_hook(UfArgs a, int vertex_mode) {
+// Hooking (Alg. 1, second loop), edge mode: the edges that leave a tile, each once
+// from its lower end, when the other end is visible too (edges inside a tile were
+// joined by k_uf_local).  One block per tile.
+__global__ void __launch_bounds__(128) k_uf_hook(UfArgs a) {
+  pdl_wait();
+  const uint32_t n = min(__ldcg(a.xcnt + blockIdx.x), kXCap);
+  const uint2* xe = a.xedge + (size_t)blockIdx.x * kXCap;
+  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+    const uint2 e = __ldcg(xe + i);
+    if (e.y < a.T && vt_bit(a.vt, e.y)) unite(a.label, (int32_t)e.x, (int32_t)e.y, a.ctr);
+  }
+}
+
+// Vertex mode: every visible triangle joins its three vertex nodes T + v.
+__global__ void __launch_bounds__(kBlock) k_uf_hook_v(UfArgs a) {
   pdl_wait();
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t nwords = (a.T + 31) >> 5;
@@ -171,20 +198,10 @@ __global__ void __launch_bounds__(kBlock) k_uf_hook(UfArgs a, int vertex_mode) {
     if (word == 0) continue;
     const uint32_t t = (w << 5) + lane;
     if (!((word >> lane) & 1u)) continue;
-    if (vertex_mode) {
 #pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        uint32_t v = __ldg(a.idx + 3 * (size_t)t + j);
-        unite(a.label, (int32_t)t, (int32_t)(a.T + v), a.ctr);
-      }
-    } else {
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
-        // edges inside a tile were joined by k_uf_local
-        if (n > (int32_t)t && ((uint32_t)n / kTile) != (t / kTile) && vt_bit(a.vt, (uint32_t)n))
-          unite(a.label, (int32_t)t, n, a.ctr);
-      }
+    for (int j = 0; j < 3; ++j) {
+      uint32_t v = __ldg(a.idx + 3 * (size_t)t + j);
+      unite(a.label, (int32_t)t, (int32_t)(a.T + v), a.ctr);
     }
   }
 }
@@ -463,6 +480,8 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   a.T = mesh->T;
   a.V = mesh->V;
   a.label = ctx->label;
+  a.xedge = ctx->xedge;
+  a.xcnt = ctx->xcnt;
   a.ctr = ctx->ctr;
   const int vm = mode == FA_CHARTS_VERTEX;
   const unsigned gw = grid_for((uint64_t)((mesh->T + 31) / 32) * 32, kBlock, 152 * 16);
@@ -473,7 +492,10 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   mark(ctx, "k_uf_local", s);
   launch_k(k_uf_local, (mesh->T + kTile - 1) / kTile, kLocalThreads, 0, s, a);
   mark(ctx, "k_uf_hook", s);
-  launch_k(k_uf_hook, gw, kBlock, 0, s, a, vm);
+  if (vm)
+    launch_k(k_uf_hook_v, gw, kBlock, 0, s, a);
+  else
+    launch_k(k_uf_hook, (mesh->T + kTile - 1) / kTile, 128, 0, s, a);
   if (!vm && mesh->n_nm) {
     mark(ctx, "k_uf_hook_nm", s);
     launch_k(k_uf_hook_nm, grid_for(mesh->n_nm, 256), 256, 0, s, a, mesh->nm_off, mesh->nm_list, mesh->n_nm);

@@ -118,6 +118,8 @@ struct fa_ctx {
   int32_t* label;        // [max_tris + max_verts]
   int32_t* cid;          // [max_tris] chart id of root triangles
   uint32_t* blockcnt;    // [n_blocks + 1]
+  uint2* xedge;          // [n_blocks][3072] cross-tile edges of the local union-find
+  uint32_t* xcnt;        // [n_blocks] their counts
   uint32_t* viscnt;      // [n_blocks + 1] visible triangles per 1024-triangle block, then their starts
   uint2* vis;            // [max_tris] (triangle, chart) of the visible triangles, triangle order
   uint32_t* box_enc;     // [max_charts * 4] ordered-int chart boxes
