@@ -534,12 +534,25 @@ __device__ uint32_t surv_prefix(const RasterArgs& A, uint32_t* pre) {
 }
 
 // Survivor slot of dense index v: block b with pre[b] <= v < pre[b + 1].
-__device__ __forceinline__ uint32_t surv_slot(const RasterArgs& A, const uint32_t* pre, uint32_t v) {
-  uint32_t lo = 0, hi = A.front_blocks;  // pre[lo] <= v < pre[hi]
+// Survivor slot of dense index v: block b with pre[b] <= v < pre[b + 1].  vfirst <=
+// v is the warp's first index, the same in every lane: its search reads the same
+// shared words in all lanes (broadcasts), and a lane searches on its own only when
+// v lies in a later region than vfirst.
+__device__ __forceinline__ uint32_t surv_slot(const RasterArgs& A, const uint32_t* pre, uint32_t v,
+                                              uint32_t vfirst) {
+  uint32_t lo = 0, hi = A.front_blocks;  // pre[lo] <= vfirst < pre[hi]
   while (hi - lo > 1) {
     const uint32_t mid = (lo + hi) >> 1;
-    if (pre[mid] <= v) lo = mid;
+    if (pre[mid] <= vfirst) lo = mid;
     else hi = mid;
+  }
+  if (v >= pre[lo + 1]) {
+    hi = A.front_blocks;
+    while (hi - lo > 1) {
+      const uint32_t mid = (lo + hi) >> 1;
+      if (pre[mid] <= v) lo = mid;
+      else hi = mid;
+    }
   }
   return lo * A.surv_per_block + (v - pre[lo]);
 }
@@ -556,7 +569,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   const uint32_t stride = gridDim.x * blockDim.x;
   for (uint32_t wbase = blockIdx.x * blockDim.x + (threadIdx.x & ~31u); wbase < n; wbase += stride) {
     const uint32_t v = wbase + lane;
-    const uint32_t i = v < n ? surv_slot(A, pre, v) : 0u;
+    const uint32_t i = v < n ? surv_slot(A, pre, v, wbase) : 0u;
     Exact E;
     uint32_t t = 0, tiles = 0;
     int kind = 0;  // 0 nothing, 1 small, 2 large
@@ -640,7 +653,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
 
 // Marking pass over the candidate list: a record is visible when one of its samples
 // has key <= the depth buffer; visible bits are OR-ed per VT word and warp.
-__global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
+__global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
   pdl_wait();
   __shared__ uint32_t pre[kMaxFrontBlocks + 1];
   if (__ldcg(&A.ctr->status) != 0) return;
@@ -653,7 +666,7 @@ __global__ void __launch_bounds__(256) k_raster_mark(RasterArgs A) {
     bool vis = false;
     uint32_t t = 0xFFFFFFFFu;
     if (k < n) {
-      const uint32_t i = k < ns ? surv_slot(A, pre, k) : A.clip_base + (k - ns);
+      const uint32_t i = k < ns ? surv_slot(A, pre, k, base + (threadIdx.x & ~31u)) : A.clip_base + (k - ns);
       const float4* s = reinterpret_cast<const float4*>(A.cand + i);
       const float4 fb = __ldcs(s + 1);
       const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
