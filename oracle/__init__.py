@@ -61,7 +61,7 @@ def _load():
         lib.or_visibility.argtypes = [P, P, P, i, i, i, P, P]
         lib.or_chartify.argtypes = [P, i, i, P, i, P, P, i, P]
         lib.or_chartify.restype = i
-        lib.or_parameterize.argtypes = [P, P, P, i, i, i, f, P, i, P, P, P, P]
+        lib.or_parameterize.argtypes = [P, P, P, i, i, i, f, P, i, P, P, P, P, ctypes.c_uint32, P]
         lib.or_order.argtypes = [P, i, P]
         lib.or_pack_candidate.argtypes = [P, P, P, i, i, i, i, i, i, P, P, P, P, P, P, P]
         lib.or_pack.argtypes = [P, P, i, i, i, i, i, i, P, ctypes.POINTER(PackResult), P, P, P]
@@ -149,22 +149,27 @@ def chartify(idx, V, vt, mode=0, max_charts=1 << 24):
 
 @dataclass
 class Footprints:
-    bbox: np.ndarray  # float32 [C, 4] xmin, ymin, xmax, ymax (NDC)
-    fa: np.ndarray    # uint32 [C] (1/256 texel), fa <= fb
+    bbox: np.ndarray     # float32 [C, 4] xmin, ymin, xmax, ymax (NDC)
+    fa: np.ndarray       # uint32 [C] (1/256 texel), fa <= fb
     fb: np.ndarray
-    rot: np.ndarray   # uint8 [C]
+    rot: np.ndarray      # uint8 [C]
+    partial: np.ndarray  # uint32 [ceil(T/32)] partial-visibility bits of the visible triangles
 
 
-def parameterize(M, pos, idx, width, height, ratio, tri_chart, C):
+BOX_FRUSTUM_CLIP = 1  # flags bit: best single frustum plane clip for the boxes (Sec. 5.2)
+
+
+def parameterize(M, pos, idx, width, height, ratio, tri_chart, C, flags=0):
     pos, idx = _f32(pos), _u32(idx)
     bbox = np.empty((C, 4), np.float32)
     fa = np.empty(C, np.uint32)
     fb = np.empty(C, np.uint32)
     rot = np.empty(C, np.uint8)
+    partial = np.empty((idx.shape[0] + 31) // 32, np.uint32)
     _load().or_parameterize(_p(_f32(M)), _p(pos), _p(idx), idx.shape[0], width, height,
                             float(ratio), _p(np.ascontiguousarray(tri_chart, np.int32)), C,
-                            _p(bbox), _p(fa), _p(fb), _p(rot))
-    return Footprints(bbox, fa, fb, rot)
+                            _p(bbox), _p(fa), _p(fb), _p(rot), int(flags), _p(partial))
+    return Footprints(bbox, fa, fb, rot, partial)
 
 
 def order(fb):
@@ -241,12 +246,12 @@ class Frame:
 
 
 def atlas_frame(M, pos, idx, width, height, ratio, atlas_log2, mode=0, n_scales=64,
-                min_box=2, gutter=0, select_mode=0, vt=None):
+                min_box=2, gutter=0, select_mode=0, vt=None, flags=0):
     """The whole per-frame path, step by step."""
     if vt is None:
         vt = visibility(M, pos, idx, width, height)
     ch = chartify(idx, pos.shape[0], vt, mode)
-    fp = parameterize(M, pos, idx, width, height, ratio, ch.tri_chart, ch.C)
+    fp = parameterize(M, pos, idx, width, height, ratio, ch.tri_chart, ch.C, flags)
     od = order(fp.fb)
     pk = pack(fp.fa, fp.fb, atlas_log2, n_scales, min_box, gutter, select_mode)
     u, aff = uv(M, pos, idx, width, height, ratio, ch.tri_chart, fp, pk, atlas_log2, n_scales, gutter)

@@ -12,7 +12,8 @@
 //   transform        clip = M . [p, 1]                           [Sec. 5.2]
 //   visibility       depth pre-pass + "<=" marking pass           [Sec. 5.1, App. A]
 //   chartify         connected components of visible triangles    [Sec. 5.1, App. A, Alg. 1]
-//   parameterize     near-clip + Blinn-clamped NDC box, viewport
+//   parameterize     near-clip (or best single frustum plane) + Blinn-clamped NDC
+//                    box, viewport; partial-visibility bits
 //                    size, quantized footprint, rotate tall        [Sec. 5.2, Sec. 4.1]
 //   order            (height desc, root asc)                      [Sec. 4.1]
 //   pack             64 candidate scales: prefix-sum fold, overflow
@@ -67,6 +68,18 @@ float plane_dist(const Clip& c, int pl) {
   }
 }
 
+// Signed distance to frustum plane `pl` of the box variant (inside iff >= 0):
+//   0 left x >= -w, 1 right x <= w, 2 bottom y >= -w, 3 top y <= w, 4 far z <= w.
+float frustum_dist(const Clip& c, int pl) {
+  switch (pl) {
+    case 0: return c.x + c.w;
+    case 1: return c.w - c.x;
+    case 2: return c.y + c.w;
+    case 3: return c.w - c.y;
+    default: return c.w - c.z;
+  }
+}
+
 // Point on segment a->b where the plane is crossed; a is the inside end.
 Clip intersect(const Clip& a, const Clip& b, float da, float db) {
   float t = da / (da - db);
@@ -86,6 +99,24 @@ std::vector<Clip> clip_poly(const std::vector<Clip>& in, int pl) {
     const Clip& c = in[i];
     const Clip& nx = in[(i + 1) % n];
     float dc = plane_dist(c, pl), dn = plane_dist(nx, pl);
+    bool ic = dc >= 0.0f, in_ = dn >= 0.0f;
+    if (ic) out.push_back(c);
+    if (ic != in_) {
+      if (ic) out.push_back(intersect(c, nx, dc, dn));
+      else out.push_back(intersect(nx, c, dn, dc));
+    }
+  }
+  return out;
+}
+
+// Sutherland-Hodgman against one frustum plane of the box variant.
+std::vector<Clip> clip_frustum(const std::vector<Clip>& in, int pl) {
+  std::vector<Clip> out;
+  size_t n = in.size();
+  for (size_t i = 0; i < n; ++i) {
+    const Clip& c = in[i];
+    const Clip& nx = in[(i + 1) % n];
+    float dc = frustum_dist(c, pl), dn = frustum_dist(nx, pl);
     bool ic = dc >= 0.0f, in_ = dn >= 0.0f;
     if (ic) out.push_back(c);
     if (ic != in_) {
@@ -185,11 +216,9 @@ void raster_triangle(const float* M, const float* p0, const float* p1, const flo
 
 // Near-plane clip (only), then Blinn's clamp x,y to [-w, w] and divide.
 // Returns false when a vertex with w <= 0 survives (box becomes [-1,1]^2).
-bool blinn_box(const float* M, const float* p0, const float* p1, const float* p2, float box[4],
-               bool* any) {
-  std::vector<Clip> poly = {transform(M, p0), transform(M, p1), transform(M, p2)};
-  poly = clip_poly(poly, 0);
-  *any = poly.size() >= 3;
+// Blinn's estimator over a polygon: clamp x, y to [-w, w], divide by w, and widen
+// box[4] = (xmin, ymin, xmax, ymax).  False when a vertex has w <= 0.
+bool blinn_add(const std::vector<Clip>& poly, float box[4]) {
   for (const Clip& c : poly) {
     if (!(c.w > 0.0f)) return false;
     float x = c.x, y = c.y;
@@ -206,6 +235,56 @@ bool blinn_box(const float* M, const float* p0, const float* p1, const float* p2
     box[3] = std::max(box[3], ny);
   }
   return true;
+}
+
+// Conservative NDC box of one visible triangle (Sec. 5.2), widening box[4]: clip
+// against the near plane when the triangle crosses it, then Blinn's clamp.  With
+// frustum_clip, a triangle that does not cross the near plane is instead clipped
+// against the one frustum plane (left, right, bottom, top, far) whose single-plane
+// clip gives the smallest Blinn box, area (xmax - xmin) * (ymax - ymin) in fp32,
+// ties to the first plane in that order (a plane the triangle does not cross leaves
+// it whole).  False when the box must become [-1, 1]^2 (a vertex with w <= 0).
+bool blinn_box(const float* M, const float* p0, const float* p1, const float* p2, float box[4],
+               bool* any, bool frustum_clip) {
+  std::vector<Clip> tri = {transform(M, p0), transform(M, p1), transform(M, p2)};
+  const bool crosses_near = plane_dist(tri[0], 0) < 0.0f || plane_dist(tri[1], 0) < 0.0f ||
+                            plane_dist(tri[2], 0) < 0.0f;
+  std::vector<Clip> poly = clip_poly(tri, 0);
+  *any = poly.size() >= 3;
+  if (!frustum_clip || crosses_near) return blinn_add(poly, box);
+  const float inf = std::numeric_limits<float>::infinity();
+  float best[4] = {inf, inf, -inf, -inf};
+  bool best_ok = true, have = false;
+  float best_area = 0.0f;
+  for (int pl = 0; pl < 5; ++pl) {
+    std::vector<Clip> cp = clip_frustum(tri, pl);
+    if (cp.size() < 3) continue;  // wholly outside this plane: not a candidate
+    float b[4] = {inf, inf, -inf, -inf};
+    const bool ok = blinn_add(cp, b);
+    const float area = ok ? (b[2] - b[0]) * (b[3] - b[1]) : inf;
+    if (!have || area < best_area) {
+      have = true;
+      best_area = area;
+      best_ok = ok;
+      for (int k = 0; k < 4; ++k) best[k] = b[k];
+    }
+  }
+  if (!have) return blinn_add(tri, box);
+  if (!best_ok) return false;
+  for (int k = 0; k < 2; ++k) box[k] = std::min(box[k], best[k]);
+  for (int k = 2; k < 4; ++k) box[k] = std::max(box[k], best[k]);
+  return true;
+}
+
+// Partial visibility (Sec. 6, temporal re-use): a vertex with max(|x|, |y|) >= w in
+// clip coordinates.
+bool partially_visible(const float* M, const float* p0, const float* p1, const float* p2) {
+  const float* p[3] = {p0, p1, p2};
+  for (int k = 0; k < 3; ++k) {
+    const Clip c = transform(M, p[k]);
+    if (std::max(std::fabs(c.x), std::fabs(c.y)) >= c.w) return true;
+  }
+  return false;
 }
 
 }  // namespace
@@ -341,7 +420,7 @@ int or_chartify(const uint32_t* idx, int T, int V, const uint32_t* vt, int mode,
 // sides after the rotate-tall step, rot[c] = 1 when the box was rotated 90 degrees.
 void or_parameterize(const float* M, const float* pos, const uint32_t* idx, int T, int Wv, int Hv,
                      float ratio, const int32_t* tri_chart, int C, float* bbox, uint32_t* fa,
-                     uint32_t* fb, uint8_t* rot) {
+                     uint32_t* fb, uint8_t* rot, uint32_t flags, uint32_t* partial) {
   const float inf = std::numeric_limits<float>::infinity();
   std::vector<uint8_t> full(C, 0);
   for (int c = 0; c < C; ++c) {
@@ -350,13 +429,17 @@ void or_parameterize(const float* M, const float* pos, const uint32_t* idx, int 
     bbox[4 * c + 2] = -inf;
     bbox[4 * c + 3] = -inf;
   }
+  if (partial)
+    for (int w = 0; w < (T + 31) / 32; ++w) partial[w] = 0u;
   for (int t = 0; t < T; ++t) {
     int c = tri_chart[t];
     if (c < 0) continue;
     const uint32_t* f = idx + 3 * (size_t)t;
     bool any;
-    if (!blinn_box(M, pos + 3 * f[0], pos + 3 * f[1], pos + 3 * f[2], bbox + 4 * c, &any))
+    if (!blinn_box(M, pos + 3 * f[0], pos + 3 * f[1], pos + 3 * f[2], bbox + 4 * c, &any, (flags & 1u) != 0))
       full[c] = 1;
+    if (partial && partially_visible(M, pos + 3 * f[0], pos + 3 * f[1], pos + 3 * f[2]))
+      partial[t >> 5] |= 1u << (t & 31);
   }
   const float hx = 0.5f * (float)Wv, hy = 0.5f * (float)Hv, s = 256.0f * ratio;
   for (int c = 0; c < C; ++c) {
