@@ -112,7 +112,16 @@ typedef struct {
   uint32_t chart_mode;  /* fa_chart_mode                                           */
   uint32_t n_scales;    /* candidate scales k / n, k = 1..n; n in {1,2,4,...,64}   */
   uint32_t select_mode; /* fa_select_mode                                          */
+  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP or 0                                */
 } fa_frame_params;
+
+/* fa_frame_params.flags / fa_parameterize flags.  FA_BOX_FRUSTUM_CLIP: a visible
+ * triangle that does not cross the near plane is clipped against the one frustum
+ * plane (left, right, bottom, top, far, in this order) whose single-plane clip
+ * gives the smallest Blinn box, fp32 area (xmax - xmin) * (ymax - ymin), ties to
+ * the earlier plane, before Blinn's clamp (Sec. 5.2: the second clip whose details
+ * the paper leaves to its supplementary material).  Tighter, still conservative. */
+#define FA_BOX_FRUSTUM_CLIP 1u
 
 /* All outputs of fa_atlas_frame (caller-owned device memory). */
 typedef struct {
@@ -130,6 +139,9 @@ typedef struct {
   float* affine;          /* [max_charts][6] (a11, a12, b1, a21, a22, b2):
                              uv = A . ndc + b, i.e. uv * w = A . (x, y) + b * w;
                              may be NULL                                            */
+  uint32_t* partial;      /* [ceil(T/32)] partially visible triangles (visible, with a
+                             vertex where max(|x|, |y|) >= w in clip coordinates;
+                             Sec. 6 temporal re-use shades these again); may be NULL */
 } fa_frame_out;
 
 /* Library version (major * 10000 + minor * 100 + patch). */
@@ -195,10 +207,13 @@ fa_status fa_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* d_vt, ui
  * makes the box [-1,1]^2).  The box's viewport size is scaled by `ratio`,
  * quantized up to 1/256 texel, and rotated to stand tall (fa <= fb, rot = 1 when
  * the width exceeded the height).  Reads charts->count; writes bbox, fa, fb, rot.
+ * flags: FA_BOX_FRUSTUM_CLIP or 0.  d_partial (may be NULL): [ceil(T/32)] bits of
+ * the partially visible triangles (see fa_frame_out.partial), cleared first.
  * Errors: FA_E_INVALID_ARG. */
 fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16],
                           uint32_t width, uint32_t height, float ratio,
-                          const int32_t* d_tri_chart, const fa_charts* charts, fa_stream_t stream);
+                          const int32_t* d_tri_chart, const fa_charts* charts, uint32_t flags,
+                          uint32_t* d_partial, fa_stream_t stream);
 
 /* Packing (Sec. 4.1-4.3).  Inputs: d_count[0] boxes with footprints d_fa, d_fb in
  * 1/256 texel (the box index is the tie-break of the order, so pass boxes by

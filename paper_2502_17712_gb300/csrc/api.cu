@@ -246,8 +246,9 @@ fa_status fa_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* d_vt, ui
 // calls build it from tri_chart so that they need no extra argument.
 fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
                           uint32_t height, float ratio, const int32_t* d_tri_chart, const fa_charts* charts,
-                          fa_stream_t stream) {
+                          uint32_t flags, uint32_t* d_partial, fa_stream_t stream) {
   if (!ctx || !mesh || !d_tri_chart || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  if (flags & ~FA_BOX_FRUSTUM_CLIP) return FA_E_INVALID_ARG;
   fa_status st = check_view(ctx, view_proj, width, height);
   if (st == FA_OK) st = check_charts(charts);
   if (st != FA_OK) return st;
@@ -257,7 +258,8 @@ fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_pro
   trace_begin(ctx);
   st = launch_vis_list(ctx, mesh, d_tri_chart, s);
   if (st == FA_OK)
-    st = launch_parameterize(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, charts, true, s);
+    st = launch_parameterize(ctx, mesh, to_mat(view_proj), width, height, ratio, d_tri_chart, charts, true, flags,
+                             d_partial, s);
   trace_end(ctx, s);
   return st;
 }
@@ -316,6 +318,7 @@ fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_par
   if (st == FA_OK) st = check_pack(ctx, p->atlas_log2, p->n_scales, p->select_mode);
   if (st != FA_OK) return st;
   if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
+  if (p->flags & ~FA_BOX_FRUSTUM_CLIP) return FA_E_INVALID_ARG;
   if (d_view_proj && (reinterpret_cast<uintptr_t>(d_view_proj) & 15u)) return FA_E_INVALID_ARG;
   return FA_OK;
 }
@@ -334,7 +337,7 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
     return st;
   // k_number of chartify already reset the chart-box accumulators
   if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts,
-                                false, s, Md)) != FA_OK)
+                                false, p->flags, o->partial, s, Md)) != FA_OK)
     return st;
   if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
                         p->select_mode, o->order, o->place, o->result, s)) != FA_OK)

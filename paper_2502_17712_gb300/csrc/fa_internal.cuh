@@ -292,8 +292,8 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
 // by chartify, or by launch_vis_list).
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                               uint32_t H, float ratio, const int32_t* tri_chart,
-                              const fa_charts* ch, bool reset_boxes, cudaStream_t s,
-                              const float* Mdev = nullptr);
+                              const fa_charts* ch, bool reset_boxes, uint32_t flags, uint32_t* partial,
+                              cudaStream_t s, const float* Mdev = nullptr);
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
                       uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s);

@@ -1,7 +1,9 @@
 // Chart boxes, footprints and UVs.
 //
 // k_bbox (Sec. 5.2): per visible triangle, clip against the near plane when it
-//   crosses it, clamp each vertex to [-w, w] and divide (Blinn's estimator), then
+//   crosses it (otherwise, with FA_BOX_FRUSTUM_CLIP, against the one frustum plane
+//   that shrinks its box most), clamp each vertex to [-w, w] and divide (Blinn's
+//   estimator); optionally the partial-visibility bits (Sec. 6); then
 //   a warp-segmented min / max per chart (__match_any_sync + __reduce_*_sync) and one
 //   atomic per chart and warp on order-preserving integer encodings (exact and
 //   order independent).
@@ -56,6 +58,8 @@ __device__ __forceinline__ void box_add(Box& b, const CV& c) {
 
 struct BoxArgs {
   Mat4 M;
+  uint32_t frustum_clip;  // FA_BOX_FRUSTUM_CLIP
+  uint32_t* partial;      // partial-visibility bits, or null
   const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
@@ -67,6 +71,67 @@ struct BoxArgs {
   uint32_t max_charts;
   DevCounters* ctr;
 };
+
+// Signed distance to frustum plane pl (inside iff >= 0): 0 left x >= -w, 1 right
+// x <= w, 2 bottom y >= -w, 3 top y <= w, 4 far z <= w.
+__device__ __forceinline__ float frustum_dist(const CV& c, int pl) {
+  switch (pl) {
+    case 0: return __fadd_rn(c.x, c.w);
+    case 1: return __fsub_rn(c.w, c.x);
+    case 2: return __fadd_rn(c.y, c.w);
+    case 3: return __fsub_rn(c.w, c.y);
+    default: return __fsub_rn(c.w, c.z);
+  }
+}
+
+// Box of a triangle that does not cross the near plane, clipped first against the
+// one frustum plane whose clip gives the smallest Blinn box (fp32 area, ties to the
+// first plane in the order above; a plane the triangle does not cross leaves it
+// whole; a plane it lies wholly outside of is no candidate).
+__device__ __forceinline__ void box_frustum(Box& b, const CV (&v)[3]) {
+  const float inf = __int_as_float(0x7f800000);
+  Box best{inf, inf, -inf, -inf, false};
+  float best_area = inf;
+  bool have = false;
+#pragma unroll
+  for (int pl = 0; pl < 5; ++pl) {
+    const float d[3] = {frustum_dist(v[0], pl), frustum_dist(v[1], pl), frustum_dist(v[2], pl)};
+    Box cb{inf, inf, -inf, -inf, false};
+    int np = 0;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int nx = (i + 1) % 3;
+      const bool ic = d[i] >= 0.0f, in_ = d[nx] >= 0.0f;
+      if (ic) {
+        box_add(cb, v[i]);
+        ++np;
+      }
+      if (ic != in_) {
+        box_add(cb, ic ? lerp_in_out(v[i], v[nx], d[i], d[nx]) : lerp_in_out(v[nx], v[i], d[nx], d[i]));
+        ++np;
+      }
+    }
+    if (np < 3) continue;
+    const float area = cb.full ? inf : __fmul_rn(__fsub_rn(cb.xmax, cb.xmin), __fsub_rn(cb.ymax, cb.ymin));
+    if (!have || area < best_area) {
+      have = true;
+      best_area = area;
+      best = cb;
+    }
+  }
+  if (!have) {
+    box_add(b, v[0]);
+    box_add(b, v[1]);
+    box_add(b, v[2]);
+  } else if (best.full) {
+    b.full = true;
+  } else {
+    b.xmin = fminf(b.xmin, best.xmin);
+    b.ymin = fminf(b.ymin, best.ymin);
+    b.xmax = fmaxf(b.xmax, best.xmax);
+    b.ymax = fmaxf(b.ymax, best.ymax);
+  }
+}
 
 template <bool DEV_M>
 __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
@@ -82,6 +147,7 @@ __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
     int32_t c = -1;
     Box b{__int_as_float(0x7f800000), __int_as_float(0x7f800000), __int_as_float(0xff800000),
           __int_as_float(0xff800000), false};
+    bool pv = false;  // partially visible (Sec. 6): a vertex with max(|x|, |y|) >= w
     if (i < n) {
       const uint2 e = __ldcg(a.vis + i);
       t = e.x;
@@ -95,7 +161,13 @@ __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
       CV v[3] = {{p0.x, p0.y, p0.z, p0.w}, {p1.x, p1.y, p1.z, p1.w}, {p2.x, p2.y, p2.z, p2.w}};
       float d[3] = {__fadd_rn(p0.z, p0.w), __fadd_rn(p1.z, p1.w), __fadd_rn(p2.z, p2.w)};
       const bool all_in = d[0] >= 0.0f && d[1] >= 0.0f && d[2] >= 0.0f;
-      if (all_in) {
+      if (a.partial) {
+        pv = fmaxf(fabsf(p0.x), fabsf(p0.y)) >= p0.w || fmaxf(fabsf(p1.x), fabsf(p1.y)) >= p1.w ||
+             fmaxf(fabsf(p2.x), fabsf(p2.y)) >= p2.w;
+      }
+      if (all_in && a.frustum_clip) {
+        box_frustum(b, v);
+      } else if (all_in) {
         box_add(b, v[0]);
         box_add(b, v[1]);
         box_add(b, v[2]);
@@ -123,6 +195,12 @@ __global__ void __launch_bounds__(256) k_bbox(BoxArgs a) {
       atomicMax(be + 2, e2);
       atomicMax(be + 3, e3);
       if (fl) atomicOr(a.box_full + c, 1u);
+    }
+    if (a.partial) {  // OR the bits of one word once per warp
+      const uint32_t word = pv ? (t >> 5) : 0xFFFFFFFFu;
+      const uint32_t wp = __match_any_sync(0xFFFFFFFFu, word);
+      const uint32_t bits = __reduce_or_sync(wp, pv ? (1u << (t & 31)) : 0u);
+      if (pv && (__ffs(wp) - 1) == (int)lane) atomicOr(a.partial + word, bits);
     }
   }
 }
@@ -316,7 +394,8 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
 
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                               float ratio, const int32_t* tri_chart, const fa_charts* ch, bool reset_boxes,
-                              cudaStream_t s, const float* Mdev) {
+                              uint32_t flags, uint32_t* partial, cudaStream_t s, const float* Mdev) {
+  if (partial) FA_CUDA_TRY(cudaMemsetAsync(partial, 0, (size_t)((mesh->T + 31) / 32) * 4, s));
   if (reset_boxes) {
     mark(ctx, "k_box_reset", s);
     launch_k(k_box_reset, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts,
@@ -325,6 +404,8 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
   BoxArgs a;
   a.M = M;
   a.Mdev = Mdev;
+  a.frustum_clip = (flags & FA_BOX_FRUSTUM_CLIP) ? 1u : 0u;
+  a.partial = partial;
   a.pos = mesh->pos;
   a.idx = mesh->idx;
   a.vis = ctx->vis;

@@ -31,6 +31,7 @@ FA_CHARTS_EDGE = 0
 FA_CHARTS_VERTEX = 1
 FA_SELECT_EFFECTIVE = 0
 FA_SELECT_LARGEST_K = 1
+FA_BOX_FRUSTUM_CLIP = 1
 
 EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
            "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
@@ -68,13 +69,14 @@ class fa_pack_result(ctypes.Structure):
 class fa_frame_params(ctypes.Structure):
     _fields_ = [("view_proj", ctypes.c_float * 16), ("width", ctypes.c_uint32), ("height", ctypes.c_uint32),
                 ("ratio", ctypes.c_float), ("atlas_log2", ctypes.c_uint32), ("chart_mode", ctypes.c_uint32),
-                ("n_scales", ctypes.c_uint32), ("select_mode", ctypes.c_uint32)]
+                ("n_scales", ctypes.c_uint32), ("select_mode", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
 
 
 class fa_frame_out(ctypes.Structure):
     _fields_ = [("vt", ctypes.c_void_p), ("tri_chart", ctypes.c_void_p), ("vert_chart", ctypes.c_void_p),
                 ("charts", fa_charts), ("order", ctypes.c_void_p), ("place", ctypes.c_void_p),
-                ("result", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("affine", ctypes.c_void_p)]
+                ("result", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("affine", ctypes.c_void_p),
+                ("partial", ctypes.c_void_p)]
 
 
 class fa_server_done(ctypes.Structure):
@@ -113,7 +115,7 @@ def load(path: str = LIB_PATH):
     lib.fa_visibility.restype = st
     lib.fa_chartify.argtypes = [P, P, P, u32, P, P, ctypes.POINTER(fa_charts), P]
     lib.fa_chartify.restype = st
-    lib.fa_parameterize.argtypes = [P, P, P, u32, u32, f32, P, ctypes.POINTER(fa_charts), P]
+    lib.fa_parameterize.argtypes = [P, P, P, u32, u32, f32, P, ctypes.POINTER(fa_charts), u32, P, P]
     lib.fa_parameterize.restype = st
     lib.fa_pack.argtypes = [P, P, P, P, u32, u32, u32, P, P, P, P]
     lib.fa_pack.restype = st
@@ -241,9 +243,11 @@ def fa_chartify(ctx, mesh, vt, mode, tri_chart, vert_chart, charts: fa_charts, s
                               ctypes.byref(charts), _stream(stream)), "fa_chartify")
 
 
-def fa_parameterize(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_charts, stream=None):
+def fa_parameterize(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_charts, flags=0, partial=None,
+                    stream=None):
     _check(load().fa_parameterize(ctx, mesh, _mat(M), width, height, float(ratio), _ptr(tri_chart),
-                                  ctypes.byref(charts), _stream(stream)), "fa_parameterize")
+                                  ctypes.byref(charts), int(flags), _ptr(partial), _stream(stream)),
+           "fa_parameterize")
 
 
 def fa_pack(ctx, fa, fb, count, atlas_log2, n_scales, select_mode, order, place, res, stream=None):
@@ -372,9 +376,10 @@ class FrameBuffers:
     result: object
     uv: object
     affine: object
+    partial: object = None
 
     @staticmethod
-    def allocate(T, V, max_charts, uv=True, vert_chart=False, device="cuda"):
+    def allocate(T, V, max_charts, uv=True, vert_chart=False, partial=False, device="cuda"):
         import torch
         i32, u8, f32 = torch.int32, torch.uint8, torch.float32
         z = lambda *s, dt=i32: torch.zeros(*s, dtype=dt, device=device)
@@ -383,7 +388,7 @@ class FrameBuffers:
             root=z(max_charts), bbox=z(max_charts, 4, dt=f32), fa=z(max_charts), fb=z(max_charts),
             rot=z(max_charts, dt=u8), count=z(1), order=z(max_charts), place=z(max_charts, 4),
             result=z(5), uv=torch.full((T, 3, 2), float("nan"), dtype=f32, device=device) if uv else None,
-            affine=z(max_charts, 6, dt=f32))
+            affine=z(max_charts, 6, dt=f32), partial=z((T + 31) // 32) if partial else None)
 
     def charts(self) -> fa_charts:
         return fa_charts(_ptr(self.root), _ptr(self.bbox), _ptr(self.fa), _ptr(self.fb), _ptr(self.rot),
@@ -392,18 +397,19 @@ class FrameBuffers:
     def c_out(self) -> fa_frame_out:
         return fa_frame_out(_ptr(self.vt), _ptr(self.tri_chart), _ptr(self.vert_chart), self.charts(),
                             _ptr(self.order), _ptr(self.place), _ptr(self.result), _ptr(self.uv),
-                            _ptr(self.affine))
+                            _ptr(self.affine), _ptr(self.partial))
 
 
 def frame_params(M, width, height, ratio, atlas_log2, chart_mode=FA_CHARTS_EDGE, n_scales=64,
-                 select_mode=FA_SELECT_EFFECTIVE) -> fa_frame_params:
-    return fa_frame_params(_mat(M), width, height, float(ratio), atlas_log2, chart_mode, n_scales, select_mode)
+                 select_mode=FA_SELECT_EFFECTIVE, flags=0) -> fa_frame_params:
+    return fa_frame_params(_mat(M), width, height, float(ratio), atlas_log2, chart_mode, n_scales, select_mode,
+                           flags)
 
 
 def atlas_frame(ctx: Context, mesh: Mesh, bufs: FrameBuffers, M, width, height, ratio, atlas_log2,
-                chart_mode=FA_CHARTS_EDGE, n_scales=64, select_mode=FA_SELECT_EFFECTIVE, stream=None):
+                chart_mode=FA_CHARTS_EDGE, n_scales=64, select_mode=FA_SELECT_EFFECTIVE, stream=None, flags=0):
     """Enqueue the whole per-frame path (fa_atlas_frame); results land in ``bufs``."""
-    p = frame_params(M, width, height, ratio, atlas_log2, chart_mode, n_scales, select_mode)
+    p = frame_params(M, width, height, ratio, atlas_log2, chart_mode, n_scales, select_mode, flags)
     fa_atlas_frame(ctx.handle, mesh.handle, p, bufs.c_out(), stream)
 
 

@@ -27,11 +27,11 @@ def F():
     return fastatlas
 
 
-def run_gpu(F, ctx, mesh, M, W, H, ratio, log2, mode=0, n_scales=64, select_mode=0, bufs=None):
+def run_gpu(F, ctx, mesh, M, W, H, ratio, log2, mode=0, n_scales=64, select_mode=0, bufs=None, flags=0):
     import torch
     if bufs is None:
-        bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts, vert_chart=True)
-    F.atlas_frame(ctx, mesh, bufs, M, W, H, ratio, log2, mode, n_scales, select_mode)
+        bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts, vert_chart=True, partial=True)
+    F.atlas_frame(ctx, mesh, bufs, M, W, H, ratio, log2, mode, n_scales, select_mode, flags=flags)
     torch.cuda.synchronize()
     st = ctx.device_status()
     return bufs, st
@@ -41,9 +41,10 @@ def to_np(t):
     return t.cpu().numpy()
 
 
-def compare_frame(sc, M, W, H, ratio, log2, bufs, status, mode=0, n_scales=64, select_mode=0, vt=None):
+def compare_frame(sc, M, W, H, ratio, log2, bufs, status, mode=0, n_scales=64, select_mode=0, vt=None,
+                  flags=0):
     fr = O.atlas_frame(M, sc.pos, sc.idx, W, H, ratio, log2, mode=mode, n_scales=n_scales,
-                       select_mode=select_mode, vt=vt)
+                       select_mode=select_mode, vt=vt, flags=flags)
     assert status == 0
     T = sc.T
     gvt = to_np(bufs.vt).view(np.uint32)
@@ -60,6 +61,9 @@ def compare_frame(sc, M, W, H, ratio, log2, bufs, status, mode=0, n_scales=64, s
     assert (to_np(bufs.fa)[:C].view(np.uint32) == fr.fp.fa).all()
     assert (to_np(bufs.fb)[:C].view(np.uint32) == fr.fp.fb).all()
     assert (to_np(bufs.rot)[:C] == fr.fp.rot).all()
+    if bufs.partial is not None:
+        gp = to_np(bufs.partial).view(np.uint32)
+        assert (gp == fr.fp.partial).all(), f"partial bits differ in {int((gp != fr.fp.partial).sum())} words"
     assert (to_np(bufs.order)[:C].view(np.uint32) == fr.order).all()
     res = to_np(bufs.result).view(np.uint32)
     assert int(res[3]) == fr.pk.status
@@ -283,3 +287,54 @@ def test_icosphere_frame_full_size(F, sphere_frame, mode):
     compare_frame(sc, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], bufs, st, mode)
     mesh.close()
     ctx.close()
+
+
+# ---------------------------------------------------------------- box variant, partial bits
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_frustum_clip_boxes_heightfield(F, small_ctx, seed):
+    sc, M, p = S.heightfield_frame(seed)
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    args = (p["width"], p["height"], p["ratio"], p["atlas_log2"])
+    bufs, st = run_gpu(F, small_ctx, mesh, M, *args, flags=F.FA_BOX_FRUSTUM_CLIP)
+    compare_frame(sc, M, *args, bufs, st, flags=F.FA_BOX_FRUSTUM_CLIP)
+
+
+def test_frustum_clip_boxes_icospheres(F):
+    sc, M, p = S.icosphere_frame(3, 30)
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 16, max_width=1920, max_height=1080,
+                    max_atlas_log2=11)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    args = (p["width"], p["height"], p["ratio"], p["atlas_log2"])
+    for flags in (0, F.FA_BOX_FRUSTUM_CLIP):
+        bufs, st = run_gpu(F, ctx, mesh, M, *args, flags=flags)
+        fr = compare_frame(sc, M, *args, bufs, st, flags=flags)
+        assert int(fr.fp.partial.astype(np.uint64).sum()) > 0  # the view cuts some charts
+    mesh.close()
+    ctx.close()
+
+
+def test_standalone_parameterize_flags_and_partial(F, small_ctx):
+    import torch
+    sc = S.grid_scene(9)
+    W, H = 640, 360
+    M = S.hemisphere_camera(9, W, H, radius=1.6)  # close: the view cuts the floor
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, 10)
+    assert st == 0
+    tc = bufs.tri_chart.clone()
+    C = int(bufs.count[0])
+    for flags in (0, F.FA_BOX_FRUSTUM_CLIP):
+        b = F.FrameBuffers.allocate(mesh.T, mesh.V, small_ctx.cfg.max_charts, partial=True)
+        b.count.copy_(bufs.count)
+        F.fa_parameterize(small_ctx.handle, mesh.handle, M, W, H, 1.0, tc, b.charts(), flags=flags,
+                          partial=b.partial)
+        torch.cuda.synchronize()
+        assert small_ctx.device_status() == 0
+        fp = O.parameterize(M, sc.pos, sc.idx, W, H, 1.0, to_np(tc), C, flags)
+        assert (to_np(b.bbox)[:C].view(np.uint32) == fp.bbox.view(np.uint32)).all()
+        assert (to_np(b.fa)[:C].view(np.uint32) == fp.fa).all()
+        assert (to_np(b.fb)[:C].view(np.uint32) == fp.fb).all()
+        assert (to_np(b.partial).view(np.uint32) == fp.partial).all()
+        assert int(fp.partial.astype(np.uint64).sum()) > 0
+    mesh.close()
