@@ -57,8 +57,8 @@ def _load():
         i = ctypes.c_int
         f = ctypes.c_float
         lib.or_transform.argtypes = [P, P, i, P]
-        lib.or_raster_triangle.argtypes = [P, P, P, P, i, i, P, P]
-        lib.or_visibility.argtypes = [P, P, P, i, i, i, P, P]
+        lib.or_raster_triangle.argtypes = [P, P, P, P, i, i, P, P, i]
+        lib.or_visibility.argtypes = [P, P, P, i, i, i, P, P, i]
         lib.or_chartify.argtypes = [P, i, i, P, i, P, P, i, P]
         lib.or_chartify.restype = i
         lib.or_parameterize.argtypes = [P, P, P, i, i, i, f, P, i, P, P, P, P, ctypes.c_uint32, P]
@@ -91,22 +91,27 @@ def transform(M, pos):
     return out
 
 
-def raster_triangle(M, p0, p1, p2, width, height):
-    """Coverage mask and min depth key of one triangle (row py from the bottom)."""
+def raster_triangle(M, p0, p1, p2, width, height, conservative=False):
+    """Coverage mask and min depth key of one triangle (row py from the bottom):
+    sample coverage, or the marking pass's conservative coverage."""
     cover = np.empty((height, width), np.uint8)
     key = np.empty((height, width), np.uint32)
     _load().or_raster_triangle(_p(_f32(M)), _p(_f32(p0)), _p(_f32(p1)), _p(_f32(p2)),
-                               width, height, _p(cover), _p(key))
+                               width, height, _p(cover), _p(key), int(bool(conservative)))
     return cover.astype(bool), key
 
 
-def visibility(M, pos, idx, width, height, return_zbuf=False):
+VIS_CONSERVATIVE = 2  # flags bit: conservative coverage in the marking pass (App. A)
+
+
+def visibility(M, pos, idx, width, height, return_zbuf=False, conservative=False):
     """VT bitmask (uint32[ceil(T/32)]) and optionally the depth-key buffer [H][W]."""
     pos, idx = _f32(pos), _u32(idx)
     T = idx.shape[0]
     vt = np.zeros((T + 31) // 32, np.uint32)
     zb = np.empty((height, width), np.uint32)
-    _load().or_visibility(_p(_f32(M)), _p(pos), _p(idx), T, width, height, _p(vt), _p(zb))
+    _load().or_visibility(_p(_f32(M)), _p(pos), _p(idx), T, width, height, _p(vt), _p(zb),
+                          int(bool(conservative)))
     return (vt, zb) if return_zbuf else vt
 
 
@@ -249,7 +254,7 @@ def atlas_frame(M, pos, idx, width, height, ratio, atlas_log2, mode=0, n_scales=
                 min_box=2, gutter=0, select_mode=0, vt=None, flags=0):
     """The whole per-frame path, step by step."""
     if vt is None:
-        vt = visibility(M, pos, idx, width, height)
+        vt = visibility(M, pos, idx, width, height, conservative=bool(flags & VIS_CONSERVATIVE))
     ch = chartify(idx, pos.shape[0], vt, mode)
     fp = parameterize(M, pos, idx, width, height, ratio, ch.tri_chart, ch.C, flags)
     od = order(fp.fb)

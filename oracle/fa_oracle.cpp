@@ -214,6 +214,85 @@ void raster_triangle(const float* M, const float* p0, const float* p1, const flo
   }
 }
 
+// Conservative coverage of one mesh triangle for the marking pass (App. A marks with
+// conservative rasterization): the same clipping, snapping, fan and culling as
+// raster_triangle; a pixel is covered when its closed square meets the closed
+// sub-triangle (for each edge, the edge function at the square corner where it is
+// largest is >= 0; the pixel range is that of the sub-triangle's bounding box).
+// Depth: at a pixel whose centre the sample rule covers, the pre-pass depth there;
+// otherwise the plane extrapolated to the centre, clamped to the sub-triangle's
+// vertex depths.  fn(px, py, key) per covered pixel with a depth in [-1, 1].
+template <class Fn>
+void raster_conservative(const float* M, const float* p0, const float* p1, const float* p2,
+                         int Wv, int Hv, Fn&& fn) {
+  std::vector<Clip> poly = {transform(M, p0), transform(M, p1), transform(M, p2)};
+  for (int pl = 0; pl < 5 && poly.size() >= 3; ++pl) poly = clip_poly(poly, pl);
+  if (poly.size() < 3) return;
+  for (const Clip& c : poly)
+    if (!(c.w > 0.0f)) return;
+  const float hx = 0.5f * (float)Wv, hy = 0.5f * (float)Hv;
+  std::vector<SVert> sv;
+  for (const Clip& c : poly) {
+    float nx = c.x / c.w, ny = c.y / c.w, zn = c.z / c.w;
+    float xs = (nx + 1.0f) * hx, ys = (ny + 1.0f) * hy;
+    SVert s;
+    s.X = (int64_t)std::llrint((double)(xs * 256.0f));
+    s.Y = (int64_t)std::llrint((double)(ys * 256.0f));
+    s.zn = zn;
+    sv.push_back(s);
+  }
+  for (size_t i = 1; i + 1 < sv.size(); ++i) {
+    const SVert& a = sv[0];
+    const SVert& b = sv[i];
+    const SVert& c = sv[i + 1];
+    int64_t A = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
+    if (A <= 0) continue;  // back face or zero area
+    float invA = 1.0f / (float)A;
+    const float zmin = std::min({a.zn, b.zn, c.zn}), zmax = std::max({a.zn, b.zn, c.zn});
+    int64_t xmn = std::min({a.X, b.X, c.X}), xmx = std::max({a.X, b.X, c.X});
+    int64_t ymn = std::min({a.Y, b.Y, c.Y}), ymx = std::max({a.Y, b.Y, c.Y});
+    // squares [px, px + 1] meeting [xmn, xmx] (in pixels): ceil(xmn) - 1 .. floor(xmx)
+    int64_t px0 = -floor_div(-xmn, kSub) - 1, px1 = floor_div(xmx, kSub);
+    int64_t py0 = -floor_div(-ymn, kSub) - 1, py1 = floor_div(ymx, kSub);
+    px0 = std::max<int64_t>(px0, 0);
+    py0 = std::max<int64_t>(py0, 0);
+    px1 = std::min<int64_t>(px1, Wv - 1);
+    py1 = std::min<int64_t>(py1, Hv - 1);
+    bool tl0 = top_left(b, c), tl1 = top_left(c, a), tl2 = top_left(a, b);
+    const SVert* ea[3] = {&b, &c, &a};
+    const SVert* eb[3] = {&c, &a, &b};
+    for (int64_t py = py0; py <= py1; ++py) {
+      for (int64_t px = px0; px <= px1; ++px) {
+        bool meets = true;
+        for (int k = 0; k < 3 && meets; ++k) {
+          const SVert& u = *ea[k];
+          const SVert& v = *eb[k];
+          // E(x, y) = (v.X - u.X)(y - u.Y) - (v.Y - u.Y)(x - u.X): largest at the corner
+          // with x high iff -(v.Y - u.Y) > 0 and y high iff (v.X - u.X) > 0
+          const int64_t cx = (u.Y - v.Y) > 0 ? (px + 1) * kSub : px * kSub;
+          const int64_t cy = (v.X - u.X) > 0 ? (py + 1) * kSub : py * kSub;
+          meets = edge_fn(u, v, cx, cy) >= 0;
+        }
+        if (!meets) continue;
+        int64_t sx = px * kSub + kSub / 2, sy = py * kSub + kSub / 2;
+        int64_t e0 = edge_fn(b, c, sx, sy);
+        int64_t e1 = edge_fn(c, a, sx, sy);
+        int64_t e2 = edge_fn(a, b, sx, sy);
+        bool in = (e0 > 0 || (e0 == 0 && tl0)) && (e1 > 0 || (e1 == 0 && tl1)) &&
+                  (e2 > 0 || (e2 == 0 && tl2));
+        float f0 = (float)e0, f1 = (float)e1, f2 = (float)e2;
+        float s = f0 * a.zn;
+        s = s + f1 * b.zn;
+        s = s + f2 * c.zn;
+        float d = s * invA;
+        if (!in) d = std::min(std::max(d, zmin), zmax);
+        if (!(d >= -1.0f && d <= 1.0f)) continue;
+        fn((int)px, (int)py, depth_key(d));
+      }
+    }
+  }
+}
+
 // Near-plane clip (only), then Blinn's clamp x,y to [-w, w] and divide.
 // Returns false when a vertex with w <= 0 survives (box becomes [-1,1]^2).
 // Blinn's estimator over a polygon: clamp x, y to [-w, w], divide by w, and widen
@@ -311,24 +390,29 @@ void or_transform(const float* M, const float* pos, int V, float* clip) {
   }
 }
 
-// Coverage of a single triangle: cover[py*Wv+px] = 1 and key[...] = min depth key.
+// Coverage of a single triangle: cover[py*Wv+px] = 1 and key[...] = min depth key;
+// sample coverage, or the conservative coverage of the marking pass.
 void or_raster_triangle(const float* M, const float* p0, const float* p1, const float* p2, int Wv,
-                        int Hv, uint8_t* cover, uint32_t* key) {
+                        int Hv, uint8_t* cover, uint32_t* key, int conservative) {
   for (int i = 0; i < Wv * Hv; ++i) {
     cover[i] = 0;
     key[i] = 0xFFFFFFFFu;
   }
-  raster_triangle(M, p0, p1, p2, Wv, Hv, [&](int px, int py, uint32_t k) {
+  auto put = [&](int px, int py, uint32_t k) {
     size_t o = (size_t)py * Wv + px;
     cover[o] = 1;
     key[o] = std::min(key[o], k);
-  });
+  };
+  if (conservative)
+    raster_conservative(M, p0, p1, p2, Wv, Hv, put);
+  else
+    raster_triangle(M, p0, p1, p2, Wv, Hv, put);
 }
 
 // Depth pre-pass then marking pass with the "<=" test (App. A, Detecting Visible
 // Triangles).  vt: ceil(T/32) words, bit t%32 of word t/32.  zbuf may be null.
 void or_visibility(const float* M, const float* pos, const uint32_t* idx, int T, int Wv, int Hv,
-                   uint32_t* vt, uint32_t* zbuf_out) {
+                   uint32_t* vt, uint32_t* zbuf_out, int conservative) {
   std::vector<uint32_t> zb((size_t)Wv * Hv, 0xFFFFFFFFu);
   for (int t = 0; t < T; ++t) {
     const uint32_t* f = idx + 3 * (size_t)t;
@@ -343,10 +427,13 @@ void or_visibility(const float* M, const float* pos, const uint32_t* idx, int T,
   for (int t = 0; t < T; ++t) {
     const uint32_t* f = idx + 3 * (size_t)t;
     bool vis = false;
-    raster_triangle(M, pos + 3 * f[0], pos + 3 * f[1], pos + 3 * f[2], Wv, Hv,
-                    [&](int px, int py, uint32_t k) {
-                      if (k <= zb[(size_t)py * Wv + px]) vis = true;
-                    });
+    auto test = [&](int px, int py, uint32_t k) {
+      if (k <= zb[(size_t)py * Wv + px]) vis = true;
+    };
+    if (conservative)
+      raster_conservative(M, pos + 3 * f[0], pos + 3 * f[1], pos + 3 * f[2], Wv, Hv, test);
+    else
+      raster_triangle(M, pos + 3 * f[0], pos + 3 * f[1], pos + 3 * f[2], Wv, Hv, test);
     if (vis) vt[t >> 5] |= 1u << (t & 31);
   }
   if (zbuf_out) std::memcpy(zbuf_out, zb.data(), zb.size() * 4);
