@@ -112,7 +112,7 @@ typedef struct {
   uint32_t chart_mode;  /* fa_chart_mode                                           */
   uint32_t n_scales;    /* candidate scales k / n, k = 1..n; n in {1,2,4,...,64}   */
   uint32_t select_mode; /* fa_select_mode                                          */
-  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP or 0                                */
+  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE, or 0          */
 } fa_frame_params;
 
 /* fa_frame_params.flags / fa_parameterize flags.  FA_BOX_FRUSTUM_CLIP: a visible
@@ -122,6 +122,15 @@ typedef struct {
  * the earlier plane, before Blinn's clamp (Sec. 5.2: the second clip whose details
  * the paper leaves to its supplementary material).  Tighter, still conservative. */
 #define FA_BOX_FRUSTUM_CLIP 1u
+
+/* fa_frame_params.flags / fa_visibility flags.  FA_VIS_CONSERVATIVE: the marking
+ * pass rasterizes conservatively, as the paper's does (App. A): a pixel counts
+ * when its closed square meets the closed (snapped, culled) sub-triangle, with the
+ * pre-pass depth where the sample rule covers its centre and otherwise the plane
+ * extrapolated to the centre and clamped to the sub-triangle's vertex depths; the
+ * triangle is visible when such a pixel passes the "<=" test.  The depth pre-pass
+ * keeps the sample rule.  Marks a superset of the default's triangles. */
+#define FA_VIS_CONSERVATIVE 2u
 
 /* All outputs of fa_atlas_frame (caller-owned device memory). */
 typedef struct {
@@ -183,10 +192,13 @@ void fa_mesh_release(fa_mesh* mesh);
  * depth test.  Samples are pixel centres; coverage uses the top-left rule on
  * vertices snapped to 1/256 pixel after clipping against the near plane and a
  * guard band |x|, |y| <= 64 w; back faces and zero-area triangles are culled.
+ * flags: 0, or FA_VIS_CONSERVATIVE for the conservative marking pass.
  * d_vt: uint32[ceil(T/32)], bit t%32 of word t/32 (fully overwritten).
- * Errors: FA_E_INVALID_ARG (viewport above the context maximum, NULL pointers). */
+ * Errors: FA_E_INVALID_ARG (viewport above the context maximum, NULL pointers,
+ * unknown flags). */
 fa_status fa_visibility(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16],
-                        uint32_t width, uint32_t height, uint32_t* d_vt, fa_stream_t stream);
+                        uint32_t width, uint32_t height, uint32_t flags, uint32_t* d_vt,
+                        fa_stream_t stream);
 
 /* Charts (Sec. 5.1; App. A "GPU Union Find", Alg. 1): connected components of
  * the visible triangles under shared edges (FA_CHARTS_EDGE) or shared vertices

@@ -218,13 +218,15 @@ void fa_mesh_release(fa_mesh* m) {
 }
 
 fa_status fa_visibility(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
-                        uint32_t height, uint32_t* d_vt, fa_stream_t stream) {
+                        uint32_t height, uint32_t flags, uint32_t* d_vt, fa_stream_t stream) {
   if (!ctx || !mesh || !d_vt || mesh->ctx != ctx) return FA_E_INVALID_ARG;
+  if (flags & ~FA_VIS_CONSERVATIVE) return FA_E_INVALID_ARG;
   fa_status st = check_view(ctx, view_proj, width, height);
   if (st != FA_OK) return st;
   DeviceGuard g(ctx->device);
   trace_begin(ctx);
-  st = launch_visibility(ctx, mesh, to_mat(view_proj), width, height, d_vt, false, (cudaStream_t)stream);
+  st = launch_visibility(ctx, mesh, to_mat(view_proj), width, height, d_vt, false, (cudaStream_t)stream, nullptr,
+                         (flags & FA_VIS_CONSERVATIVE) != 0);
   trace_end(ctx, (cudaStream_t)stream);
   return st;
 }
@@ -318,7 +320,7 @@ fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_par
   if (st == FA_OK) st = check_pack(ctx, p->atlas_log2, p->n_scales, p->select_mode);
   if (st != FA_OK) return st;
   if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
-  if (p->flags & ~FA_BOX_FRUSTUM_CLIP) return FA_E_INVALID_ARG;
+  if (p->flags & ~(FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE)) return FA_E_INVALID_ARG;
   if (d_view_proj && (reinterpret_cast<uintptr_t>(d_view_proj) & 15u)) return FA_E_INVALID_ARG;
   return FA_OK;
 }
@@ -332,7 +334,9 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   const float* Md = d_view_proj;
   trace_begin(ctx);
   // k_clear (first kernel of the visibility step) also clears the status word
-  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s, Md)) != FA_OK) return st;
+  if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s, Md,
+                              (p->flags & FA_VIS_CONSERVATIVE) != 0)) != FA_OK)
+    return st;
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators

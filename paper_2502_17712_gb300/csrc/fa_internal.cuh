@@ -284,7 +284,7 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                             uint32_t H, uint32_t* vt, bool reset_status, cudaStream_t s,
-                            const float* Mdev = nullptr);
+                            const float* Mdev = nullptr, bool conservative = false);
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
                           cudaStream_t s);

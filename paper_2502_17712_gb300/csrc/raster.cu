@@ -90,14 +90,21 @@ struct Setup {
   int px0, py0, px1, py1;
 };
 
-__device__ __forceinline__ Setup setup(const SV& a, const SV& b, const SV& c, int W, int H) {
+__device__ __forceinline__ Setup setup(const SV& a, const SV& b, const SV& c, int W, int H, bool cons) {
   Setup s;
   s.A = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
   int64_t xmn = min(a.X, min(b.X, c.X)), xmx = max(a.X, max(b.X, c.X));
   int64_t ymn = min(a.Y, min(b.Y, c.Y)), ymx = max(a.Y, max(b.Y, c.Y));
-  // first / last pixel whose centre 256 p + 128 lies in [min, max]
+  // sample rule: first / last pixel whose centre 256 p + 128 lies in [min, max];
+  // conservative marking: first / last pixel whose square [256 p, 256 p + 256] meets it
   int64_t px0 = -((128 - xmn) >> 8), px1 = (xmx - 128) >> 8;
   int64_t py0 = -((128 - ymn) >> 8), py1 = (ymx - 128) >> 8;
+  if (cons) {
+    px0 = -((-xmn) >> 8) - 1;
+    px1 = xmx >> 8;
+    py0 = -((-ymn) >> 8) - 1;
+    py1 = ymx >> 8;
+  }
   s.px0 = (int)(px0 > 0 ? px0 : 0);
   s.py0 = (int)(py0 > 0 ? py0 : 0);
   s.px1 = (int)(px1 < W - 1 ? px1 : W - 1);
@@ -130,18 +137,35 @@ __device__ __forceinline__ Edges edges_at(const SV& a, const SV& b, const SV& c,
   return E;
 }
 
-// Test and shade one sample with edge values e: covered (top-left rule) and a depth
-// in [-1, 1].  PASS 0: atomicMin the depth key; PASS 1: return key <= zbuf.
+// Test and shade one pixel with edge values e at its sample.  PASS 0: covered (top-
+// left rule) with a depth in [-1, 1]: atomicMin the depth key.  PASS 1: the same
+// test, return key <= zbuf.  PASS 2 (conservative marking, App. A): the pixel's
+// closed square meets the closed triangle (each edge function is >= 0 at the
+// square corner where it is largest: e + (|dx| + |dy|) / 2, a half pixel each way);
+// the depth is the sample's where the sample rule covers the centre, else the plane
+// at the centre clamped to [zmin, zmax]; return key <= zbuf when it is in [-1, 1].
 template <int PASS>
 __device__ __forceinline__ bool sample(const Edges& E, const int64_t* e, const SV& a, const SV& b, const SV& c,
-                                       float invA, uint32_t* __restrict__ z) {
+                                       float invA, uint32_t* __restrict__ z, float zmin = 0.0f,
+                                       float zmax = 0.0f) {
   const bool in = (e[0] > 0 || (e[0] == 0 && E.tl[0])) && (e[1] > 0 || (e[1] == 0 && E.tl[1])) &&
                   (e[2] > 0 || (e[2] == 0 && E.tl[2]));
-  if (!in) return false;
+  if (PASS == 2) {
+    bool meets = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t ax = E.dx[i] < 0 ? -E.dx[i] : E.dx[i], ay = E.dy[i] < 0 ? -E.dy[i] : E.dy[i];
+      meets = meets && (e[i] + ((ax + ay) >> 1) >= 0);
+    }
+    if (!meets) return false;
+  } else if (!in) {
+    return false;
+  }
   float s = __fmul_rn(ll2float_rn(e[0]), a.zn);
   s = __fadd_rn(s, __fmul_rn(ll2float_rn(e[1]), b.zn));
   s = __fadd_rn(s, __fmul_rn(ll2float_rn(e[2]), c.zn));
-  const float d = __fmul_rn(s, invA);
+  float d = __fmul_rn(s, invA);
+  if (PASS == 2 && !in) d = fminf(fmaxf(d, zmin), zmax);
   if (!(d >= -1.0f && d <= 1.0f)) return false;
   const uint32_t key = ordered(d);
   if (PASS == 0) {
@@ -157,6 +181,7 @@ template <int PASS>
 __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, int px0, int py0,
                             int px1, int py1, uint32_t* __restrict__ zbuf, int W) {
   const Edges E = edges_at(a, b, c, px0, py0);
+  const float zmin = fminf(a.zn, fminf(b.zn, c.zn)), zmax = fmaxf(a.zn, fmaxf(b.zn, c.zn));
   int64_t er[3] = {E.e[0], E.e[1], E.e[2]};
   bool vis = false;  // PASS 1: no early exit, so the depth loads can overlap
   for (int py = py0; py <= py1; ++py) {
@@ -164,7 +189,7 @@ __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, i
     uint32_t* zrow = zbuf + (size_t)py * W;
 #pragma unroll 2
     for (int px = px0; px <= px1; ++px) {
-      vis |= sample<PASS>(E, e, a, b, c, invA, zrow + px);
+      vis |= sample<PASS>(E, e, a, b, c, invA, zrow + px, zmin, zmax);
       e[0] += E.dx[0];
       e[1] += E.dx[1];
       e[2] += E.dx[2];
@@ -192,6 +217,7 @@ constexpr uint32_t kMaxFrontBlocks = 152 * 4;
 
 struct RasterArgs {
   Mat4 M;
+  int cons;  // conservative marking (FA_VIS_CONSERVATIVE): conservative pixel boxes
   const float* Mdev;  // when set, the matrix is read here on the device instead of M
   const float* pos;
   const uint32_t* idx;
@@ -244,7 +270,7 @@ __device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, C
   uint64_t tiles = 0;
   bool big = false;
   for (int i = 1; i + 1 < n; ++i) {
-    Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
+    Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H, A.cons);
     if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
     int w = s.px1 - s.px0 + 1, h = s.py1 - s.py0 + 1;
     if (w * h > kSmallMaxPix) big = true;
@@ -258,7 +284,7 @@ __device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, C
     if (e0 + nq <= A.queue_cap && tile + tiles <= A.tile_cap) {
       int q = 0;
       for (int i = 1; i + 1 < n; ++i) {
-        Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
+        Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H, A.cons);
         if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
         BigTri bt;
         bt.X[0] = (int32_t)sv[0].X; bt.X[1] = (int32_t)sv[i].X; bt.X[2] = (int32_t)sv[i + 1].X;
@@ -289,7 +315,7 @@ __device__ int depth_fan(const RasterArgs& A, uint32_t t, const SV* sv, int n, C
   }
   int nout = 0;
   for (int i = 1; i + 1 < n; ++i) {
-    Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H);
+    Setup s = setup(sv[0], sv[i], sv[i + 1], A.W, A.H, A.cons);
     if (s.A <= 0 || s.px1 < s.px0 || s.py1 < s.py0) continue;
     float invA = __fdiv_rn(1.0f, ll2float_rn(s.A));
     raster_rect<0>(sv[0], sv[i], sv[i + 1], invA, s.px0, s.py0, s.px1, s.py1, A.zbuf, A.W);
@@ -343,8 +369,11 @@ __device__ __forceinline__ bool surely_empty(const RasterArgs& A, const float4& 
   // pixel centres p + 0.5 inside the widened box, clamped to the viewport
   const float lo_x = fminf(x0, fminf(x1, x2)) - mx, hi_x = fmaxf(x0, fmaxf(x1, x2)) + mx;
   const float lo_y = fminf(y0, fminf(y1, y2)) - my, hi_y = fmaxf(y0, fmaxf(y1, y2)) + my;
-  const float px0 = fmaxf(ceilf(lo_x - 0.5f), 0.0f), px1 = fminf(floorf(hi_x - 0.5f), (float)(A.W - 1));
-  const float py0 = fmaxf(ceilf(lo_y - 0.5f), 0.0f), py1 = fminf(floorf(hi_y - 0.5f), (float)(A.H - 1));
+  // (conservative marking: pixels whose squares meet the widened box)
+  const float px0 = fmaxf(A.cons ? ceilf(lo_x) - 1.0f : ceilf(lo_x - 0.5f), 0.0f);
+  const float px1 = fminf(A.cons ? floorf(hi_x) : floorf(hi_x - 0.5f), (float)(A.W - 1));
+  const float py0 = fmaxf(A.cons ? ceilf(lo_y) - 1.0f : ceilf(lo_y - 0.5f), 0.0f);
+  const float py1 = fminf(A.cons ? floorf(hi_y) : floorf(hi_y - 0.5f), (float)(A.H - 1));
   if (px0 > px1 || py0 > py1) return true;
   // signed doubled area in px^2 against its error bound
   const float e1x = x1 - x0, e1y = y1 - y0, e2x = x2 - x0, e2y = y2 - y0;
@@ -418,7 +447,7 @@ __device__ __forceinline__ Exact exact_setup(const RasterArgs& A, const float4& 
   E.a = project(CV{c0.x, c0.y, c0.z, c0.w}, A.hx, A.hy);
   E.b = project(CV{c1.x, c1.y, c1.z, c1.w}, A.hx, A.hy);
   E.c = project(CV{c2.x, c2.y, c2.z, c2.w}, A.hx, A.hy);
-  E.s = setup(E.a, E.b, E.c, A.W, A.H);
+  E.s = setup(E.a, E.b, E.c, A.W, A.H, A.cons);
   return E;
 }
 
@@ -678,8 +707,10 @@ __global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
         t = __float_as_uint(fc.w);
         const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
         const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
-        vis = raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
-                             (int)(b1 >> 16), A.zbuf, A.W);
+        vis = A.cons ? raster_rect<2>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
+                                      (int)(b1 >> 16), A.zbuf, A.W)
+                     : raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
+                                      (int)(b1 >> 16), A.zbuf, A.W);
       }
     }
     const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
@@ -693,7 +724,7 @@ __global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
 template <int PASS>
 __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
   pdl_wait();
-  if (PASS == 1 && __ldcg(&A.ctr->status) != 0) return;
+  if (PASS >= 1 && __ldcg(&A.ctr->status) != 0) return;
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -716,18 +747,20 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
     SV a{q.X[0], q.Y[0], q.zn[0]}, b{q.X[1], q.Y[1], q.zn[1]}, c{q.X[2], q.Y[2], q.zn[2]};
     const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
     const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
+    const float zmin = fminf(a.zn, fminf(b.zn, c.zn)), zmax = fmaxf(a.zn, fmaxf(b.zn, c.zn));
     bool vis = false;
     const int px = bx + (int)(lane % kBigTile), py_first = by + (int)(lane / kBigTile);
     const Edges E = edges_at(a, b, c, px, py_first);
     int64_t e[3] = {E.e[0], E.e[1], E.e[2]};
 #pragma unroll 1
     for (int py = py_first; py < by + kBigTile; py += 32 / kBigTile) {
-      if (px <= px1 && py <= py1) vis |= sample<PASS>(E, e, a, b, c, invA, A.zbuf + (size_t)py * A.W + px);
+      if (px <= px1 && py <= py1)
+        vis |= sample<PASS>(E, e, a, b, c, invA, A.zbuf + (size_t)py * A.W + px, zmin, zmax);
       e[0] += E.dy[0] * (32 / kBigTile);
       e[1] += E.dy[1] * (32 / kBigTile);
       e[2] += E.dy[2] * (32 / kBigTile);
     }
-    if (PASS == 1) {
+    if (PASS >= 1) {
       if (__any_sync(0xFFFFFFFFu, vis) && lane == 0) atomicOr(A.vt + (q.tri >> 5), 1u << (q.tri & 31));
     }
   }
@@ -736,8 +769,9 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
 }  // namespace
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
-                            uint32_t* vt, bool reset_status, cudaStream_t s, const float* Mdev) {
+                            uint32_t* vt, bool reset_status, cudaStream_t s, const float* Mdev, bool cons) {
   RasterArgs A;
+  A.cons = cons ? 1 : 0;
   A.Mdev = Mdev;
   A.M = M;
   A.pos = mesh->pos;
@@ -788,7 +822,10 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   mark(ctx, "k_raster_mark", s);
   launch_k(k_raster_mark, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_mark_big", s);
-  launch_k(k_raster_big<1>, gb, 256, 0, s, A);
+  if (cons)
+    launch_k(k_raster_big<2>, gb, 256, 0, s, A);
+  else
+    launch_k(k_raster_big<1>, gb, 256, 0, s, A);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }

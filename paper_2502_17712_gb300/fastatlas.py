@@ -32,6 +32,7 @@ FA_CHARTS_VERTEX = 1
 FA_SELECT_EFFECTIVE = 0
 FA_SELECT_LARGEST_K = 1
 FA_BOX_FRUSTUM_CLIP = 1
+FA_VIS_CONSERVATIVE = 2
 
 EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
            "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
@@ -111,7 +112,7 @@ def load(path: str = LIB_PATH):
     lib.fa_mesh_register.restype = st
     lib.fa_mesh_release.argtypes = [P]
     lib.fa_mesh_release.restype = None
-    lib.fa_visibility.argtypes = [P, P, P, u32, u32, P, P]
+    lib.fa_visibility.argtypes = [P, P, P, u32, u32, u32, P, P]
     lib.fa_visibility.restype = st
     lib.fa_chartify.argtypes = [P, P, P, u32, P, P, ctypes.POINTER(fa_charts), P]
     lib.fa_chartify.restype = st
@@ -234,8 +235,9 @@ def fa_mesh_release(mesh: int):
     load().fa_mesh_release(mesh)
 
 
-def fa_visibility(ctx, mesh, M, width, height, vt, stream=None):
-    _check(load().fa_visibility(ctx, mesh, _mat(M), width, height, _ptr(vt), _stream(stream)), "fa_visibility")
+def fa_visibility(ctx, mesh, M, width, height, vt, stream=None, flags=0):
+    _check(load().fa_visibility(ctx, mesh, _mat(M), width, height, int(flags), _ptr(vt), _stream(stream)),
+           "fa_visibility")
 
 
 def fa_chartify(ctx, mesh, vt, mode, tri_chart, vert_chart, charts: fa_charts, stream=None):

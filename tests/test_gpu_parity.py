@@ -338,3 +338,49 @@ def test_standalone_parameterize_flags_and_partial(F, small_ctx):
         assert (to_np(b.partial).view(np.uint32) == fp.partial).all()
         assert int(fp.partial.astype(np.uint64).sum()) > 0
     mesh.close()
+
+
+# ---------------------------------------------------------------- conservative marking
+
+@pytest.mark.parametrize("seed", [1, 2, 3])
+def test_conservative_marking_heightfield(F, small_ctx, seed):
+    sc, M, p = S.heightfield_frame(seed)
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    args = (p["width"], p["height"], p["ratio"], p["atlas_log2"])
+    bufs, st = run_gpu(F, small_ctx, mesh, M, *args, flags=F.FA_VIS_CONSERVATIVE)
+    fr = compare_frame(sc, M, *args, bufs, st, flags=F.FA_VIS_CONSERVATIVE)
+    plain = O.visibility(M, sc.pos, sc.idx, p["width"], p["height"])
+    assert int(np.unpackbits(fr.vt.view(np.uint8)).sum()) > int(np.unpackbits(plain.view(np.uint8)).sum())
+
+
+def test_conservative_marking_big_and_clipped(F, small_ctx):
+    flags = F.FA_VIS_CONSERVATIVE | F.FA_BOX_FRUSTUM_CLIP
+    sc = S.grid_scene(7)
+    M = S.spline_cameras(7, 5, 1920, 1080)[2]  # large triangles: the tile rasterizer
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, small_ctx, mesh, M, 1920, 1080, 1.0, 11, flags=flags)
+    compare_frame(sc, M, 1920, 1080, 1.0, 11, bufs, st, flags=flags)
+    sc = S.instanced_grid_scene(3, 6, n=24)  # near plane and guard band crossings
+    W, H = 640, 360
+    for eye in [(0.1, 0.2, 0.12), (-0.5, 0.3, 0.06)]:
+        M = S.view_proj(eye, (eye[0] + 1.0, eye[1] + 0.4, -0.2), (0, 0, 1), W, H, near=0.05)
+        mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+        bufs, st = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, 10, flags=flags)
+        compare_frame(sc, M, W, H, 1.0, 10, bufs, st, flags=flags)
+
+
+def test_conservative_marking_icospheres_and_standalone(F):
+    import torch
+    sc, M, p = S.icosphere_frame(4, 20)
+    W, H = p["width"], p["height"]
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 16, max_width=W, max_height=H,
+                    max_atlas_log2=11)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    bufs, st = run_gpu(F, ctx, mesh, M, W, H, 1.0, 11, flags=F.FA_VIS_CONSERVATIVE)
+    compare_frame(sc, M, W, H, 1.0, 11, bufs, st, flags=F.FA_VIS_CONSERVATIVE)
+    vt = torch.zeros_like(bufs.vt)
+    F.fa_visibility(ctx.handle, mesh.handle, M, W, H, vt, flags=F.FA_VIS_CONSERVATIVE)
+    torch.cuda.synchronize()
+    assert torch.equal(vt, bufs.vt)
+    mesh.close()
+    ctx.close()
