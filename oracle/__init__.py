@@ -64,7 +64,7 @@ def _load():
         lib.or_parameterize.argtypes = [P, P, P, i, i, i, f, P, i, P, P, P, P, ctypes.c_uint32, P]
         lib.or_order.argtypes = [P, i, P]
         lib.or_pack_candidate.argtypes = [P, P, P, i, i, i, i, i, i, P, P, P, P, P, P, P]
-        lib.or_pack.argtypes = [P, P, i, i, i, i, i, i, P, ctypes.POINTER(PackResult), P, P, P]
+        lib.or_pack.argtypes = [P, P, i, i, i, i, i, i, P, ctypes.POINTER(PackResult), P, P, P, i]
         lib.or_uv.argtypes = [P, P, P, i, i, i, f, P, i, P, P, P, ctypes.POINTER(PackResult),
                               i, i, i, P, P]
         _lib = lib
@@ -102,6 +102,11 @@ def raster_triangle(M, p0, p1, p2, width, height, conservative=False):
 
 
 VIS_CONSERVATIVE = 2  # flags bit: conservative coverage in the marking pass (App. A)
+
+
+def LOWRES(d):
+    """flags field: the packing also serves the atlas scaled by 2^-d (Sec. 7)."""
+    return (int(d) & 7) << 8
 
 
 def visibility(M, pos, idx, width, height, return_zbuf=False, conservative=False):
@@ -210,7 +215,7 @@ class Packing:
     raw: PackResult
 
 
-def pack(fa, fb, atlas_log2, n_scales=64, min_box=2, gutter=0, select_mode=0):
+def pack(fa, fb, atlas_log2, n_scales=64, min_box=2, gutter=0, select_mode=0, lowres_log2=0):
     fa, fb = _u32(fa), _u32(fb)
     C = fa.shape[0]
     place = np.zeros((C, 4), np.int32)
@@ -219,7 +224,7 @@ def pack(fa, fb, atlas_log2, n_scales=64, min_box=2, gutter=0, select_mode=0):
     ch = np.empty(n_scales, np.uint64)
     ck = np.empty(n_scales, np.int32)
     _load().or_pack(_p(fa), _p(fb), C, atlas_log2, n_scales, min_box, gutter, select_mode,
-                    _p(place), ctypes.byref(res), _p(co), _p(ch), _p(ck))
+                    _p(place), ctypes.byref(res), _p(co), _p(ch), _p(ck), int(lowres_log2))
     return Packing(place, res.k, res.omega, res.height, res.status, co, ch, ck.astype(bool), res)
 
 
@@ -258,6 +263,6 @@ def atlas_frame(M, pos, idx, width, height, ratio, atlas_log2, mode=0, n_scales=
     ch = chartify(idx, pos.shape[0], vt, mode)
     fp = parameterize(M, pos, idx, width, height, ratio, ch.tri_chart, ch.C, flags)
     od = order(fp.fb)
-    pk = pack(fp.fa, fp.fb, atlas_log2, n_scales, min_box, gutter, select_mode)
+    pk = pack(fp.fa, fp.fb, atlas_log2, n_scales, min_box, gutter, select_mode, (flags >> 8) & 7)
     u, aff = uv(M, pos, idx, width, height, ratio, ch.tri_chart, fp, pk, atlas_log2, n_scales, gutter)
     return Frame(vt, ch, fp, od, pk, u, aff)

@@ -622,9 +622,15 @@ void or_pack_candidate(const uint32_t* fa, const uint32_t* fb, const uint32_t* o
 // integer compare, ties to the larger k), select_mode 1 takes the largest fitting k.
 // place[c] = (x, y, w, h) in the chosen candidate's virtual Omega x Omega grid, in
 // chart order.  cand_* (optional, n_scales entries) report every candidate.
+// Multi-atlas from one packing (Sec. 7, depth of field / foveated rendering): with
+// lowres_log2 = d > 0 the packing must also serve an atlas scaled by 2^-d.  Two
+// charts' contents are at least 2 gutter virtual texels apart, alpha * 2 * gutter
+// atlas texels, 2^-d of that in the low-resolution atlas; they share no
+// low-resolution texel when that gap is >= 1, i.e. 2 * gutter * omega >= Omega * 2^d,
+// which a candidate must then satisfy besides H <= Omega.
 void or_pack(const uint32_t* fa, const uint32_t* fb, int C, int atlas_log2, int n_scales,
              int min_box, int gutter, int select_mode, int32_t* place, or_pack_result* res,
-             uint64_t* cand_omega, uint64_t* cand_height, int32_t* cand_ok) {
+             uint64_t* cand_omega, uint64_t* cand_height, int32_t* cand_ok, int lowres_log2) {
   std::vector<uint32_t> order(C);
   or_order(fb, C, order.data());
   std::vector<uint64_t> Om(n_scales + 1), Hk(n_scales + 1);
@@ -633,6 +639,7 @@ void or_pack(const uint32_t* fa, const uint32_t* fb, int C, int atlas_log2, int 
   for (int k = 1; k <= n_scales; ++k) {
     or_pack_candidate(fa, fb, order.data(), C, atlas_log2, k, n_scales, min_box, gutter, x.data(),
                       y.data(), w.data(), h.data(), &Om[k], &Hk[k], &ok[k]);
+    if (lowres_log2 > 0 && (Om[k] << lowres_log2) > 2ull * (uint64_t)gutter * (1ull << atlas_log2)) ok[k] = 0;
     if (cand_omega) cand_omega[k - 1] = Om[k];
     if (cand_height) cand_height[k - 1] = Hk[k];
     if (cand_ok) cand_ok[k - 1] = ok[k];

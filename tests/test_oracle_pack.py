@@ -197,3 +197,47 @@ def test_determinism():
     a = O.pack(fa, fb, 11)
     b = O.pack(fa.copy(), fb.copy(), 11)
     assert (a.place == b.place).all() and a.k == b.k and a.omega == b.omega
+
+
+# ---------------------------------------------------------------- one packing, two atlases
+
+def _lowres_texels(pk, omega, gutter, d, fa, fb, n_scales):
+    """Low-resolution texel ranges [x0, x1) x [y0, y1) of each chart's content: the
+    content of box (x, y, w, h) spans [x + g, x + w - g) virtual texels, alpha = omega /
+    Omega maps them to the atlas and 2^-d to the low-resolution atlas (exact
+    rationals); the texels touched are floor(start) .. ceil(end) - 1."""
+    from fractions import Fraction
+    a = Fraction(omega, pk.omega) / (1 << d)
+    out = []
+    for x, y, w, h in pk.place:
+        x0, x1 = a * (int(x) + gutter), a * (int(x) + int(w) - gutter)
+        y0, y1 = a * (int(y) + gutter), a * (int(y) + int(h) - gutter)
+        out.append((x0.__floor__(), -((-x1).__floor__()), y0.__floor__(), -((-y1).__floor__())))
+    return out
+
+
+@pytest.mark.parametrize("d,gutter,seed", [(2, 2, 0), (3, 4, 1), (3, 8, 2), (2, 3, 3)])
+def test_lowres_packing_keeps_charts_apart(d, gutter, seed):
+    fa, fb = S.lognormal_boxes(seed, 300, mean_texels=40.0)
+    L = 12
+    pk = O.pack(fa, fb, L, 64, 2, gutter, 0, d)
+    assert pk.status == 0
+    assert (pk.omega << d) <= 2 * gutter * (1 << L)
+    r = _lowres_texels(pk, 1 << L, gutter, d, fa, fb, 64)
+    for i in range(len(r)):
+        for j in range(i + 1, len(r)):
+            a, b = r[i], r[j]
+            overlap = a[0] < b[1] and b[0] < a[1] and a[2] < b[3] and b[2] < a[3]
+            assert not overlap, (i, j, a, b)
+    # every candidate the constraint rejected broke it; the unconstrained choice is
+    # at least as large a scale
+    free = O.pack(fa, fb, L, 64, 2, gutter, 0, 0)
+    assert free.status == 0 and free.k * pk.omega >= pk.k * free.omega
+    for k in range(64):
+        if free.cand_ok[k] and not pk.cand_ok[k]:
+            assert (int(pk.cand_omega[k]) << d) > 2 * gutter * (1 << L)
+
+
+def test_lowres_without_gutter_fails():
+    fa, fb = S.lognormal_boxes(5, 50)
+    assert O.pack(fa, fb, 11, 64, 2, 0, 0, 3).status == 4
