@@ -112,7 +112,7 @@ typedef struct {
   uint32_t chart_mode;  /* fa_chart_mode                                           */
   uint32_t n_scales;    /* candidate scales k / n, k = 1..n; n in {1,2,4,...,64}   */
   uint32_t select_mode; /* fa_select_mode                                          */
-  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE, or 0          */
+  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE | FA_LOWRES(d) */
 } fa_frame_params;
 
 /* fa_frame_params.flags / fa_parameterize flags.  FA_BOX_FRUSTUM_CLIP: a visible
@@ -131,6 +131,15 @@ typedef struct {
  * triangle is visible when such a pixel passes the "<=" test.  The depth pre-pass
  * keeps the sample rule.  Marks a superset of the default's triangles. */
 #define FA_VIS_CONSERVATIVE 2u
+
+/* fa_frame_params.flags bits 8..10: one packing, two atlases (Sec. 7: depth of
+ * field and foveated rendering shade a second atlas of the same packing scaled by
+ * 2^-d).  With d > 0 a candidate is accepted only if also
+ * 2 * gutter * omega >= Omega * 2^d: the contents of two charts, at least
+ * 2 * gutter virtual texels (2 * gutter * omega / Omega atlas texels) apart, then
+ * share no texel of the scaled atlas.  Needs a context gutter > 0.  The scaled
+ * atlas's UVs are the UVs times 2^-d (exact in fp32). */
+#define FA_LOWRES(d) ((((uint32_t)(d)) & 7u) << 8)
 
 /* All outputs of fa_atlas_frame (caller-owned device memory). */
 typedef struct {
@@ -240,12 +249,13 @@ fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_pro
  * to *d_res and its placements (chart order) to d_place; d_order (may be NULL)
  * receives the packing order.  No fitting candidate: d_res->status =
  * FA_E_PACK_FAILED.  A candidate with Omega above the frontline capacity
- * min(8 omega, 32768) sets FA_E_CAPACITY.
+ * min(8 omega, 32768) sets FA_E_CAPACITY.  lowres_log2 = d > 0: candidates must
+ * also serve the atlas scaled by 2^-d (see FA_LOWRES); 0 for none.
  * Errors: FA_E_INVALID_ARG (atlas_log2 out of range, n_scales not a power of two
- * in [1, 64], select_mode unknown, NULL pointers). */
+ * in [1, 64], select_mode unknown, lowres_log2 > 7, NULL pointers). */
 fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const uint32_t* d_count,
                   uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* d_order,
-                  fa_placement* d_place, fa_pack_result* d_res, fa_stream_t stream);
+                  fa_placement* d_place, fa_pack_result* d_res, uint32_t lowres_log2, fa_stream_t stream);
 
 /* Packing without any allocation.  The paper has no counterpart: this is a
  * service for callers that may not allocate device memory where they pack, such as

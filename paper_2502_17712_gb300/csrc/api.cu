@@ -268,14 +268,14 @@ fa_status fa_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const float view_pro
 
 fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const uint32_t* d_count,
                   uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* d_order,
-                  fa_placement* d_place, fa_pack_result* d_res, fa_stream_t stream) {
-  if (!ctx || !d_fa || !d_fb || !d_count || !d_place || !d_res) return FA_E_INVALID_ARG;
+                  fa_placement* d_place, fa_pack_result* d_res, uint32_t lowres_log2, fa_stream_t stream) {
+  if (!ctx || !d_fa || !d_fb || !d_count || !d_place || !d_res || lowres_log2 > 7) return FA_E_INVALID_ARG;
   fa_status st = check_pack(ctx, atlas_log2, n_scales, select_mode);
   if (st != FA_OK) return st;
   DeviceGuard g(ctx->device);
   trace_begin(ctx);
   st = launch_pack(ctx, d_fa, d_fb, d_count, atlas_log2, n_scales, select_mode, d_order, d_place, d_res,
-                   (cudaStream_t)stream);
+                   (cudaStream_t)stream, lowres_log2);
   trace_end(ctx, (cudaStream_t)stream);
   return st;
 }
@@ -320,7 +320,7 @@ fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_par
   if (st == FA_OK) st = check_pack(ctx, p->atlas_log2, p->n_scales, p->select_mode);
   if (st != FA_OK) return st;
   if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
-  if (p->flags & ~(FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE)) return FA_E_INVALID_ARG;
+  if (p->flags & ~(FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE | FA_LOWRES(7))) return FA_E_INVALID_ARG;
   if (d_view_proj && (reinterpret_cast<uintptr_t>(d_view_proj) & 15u)) return FA_E_INVALID_ARG;
   return FA_OK;
 }
@@ -344,7 +344,7 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
                                 false, p->flags, o->partial, s, Md)) != FA_OK)
     return st;
   if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
-                        p->select_mode, o->order, o->place, o->result, s)) != FA_OK)
+                        p->select_mode, o->order, o->place, o->result, s, (p->flags >> 8) & 7u)) != FA_OK)
     return st;
   if (o->uv || o->affine) {
     if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts, o->place,

@@ -296,7 +296,8 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
                               cudaStream_t s, const float* Mdev = nullptr);
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
-                      uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s);
+                      uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s,
+                      uint32_t lowres_log2 = 0);
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                     float ratio, const int32_t* tri_chart, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
@@ -313,7 +314,7 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
-                              cudaStream_t s);
+                              cudaStream_t s, uint32_t lowres_log2);
 fa_status pack_set_smem_limit();
 
 }  // namespace fa

@@ -187,6 +187,7 @@ __global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, con
 struct PackArgs {
   const uint32_t* order;
   uint32_t atlas_log2;
+  uint32_t lowres_log2;  // > 0: the packing must also serve the atlas scaled by 2^-lowres_log2
   uint32_t shift;  // log2(256 * n_scales)
   uint32_t min_box;
   uint32_t gutter;
@@ -539,6 +540,9 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       }
       H = block_max<uint32_t>(Hloc, ws32);
       ok = (!fail && !timed_out && H <= Om) ? 1u : 0u;
+      // one packing, two atlases (Sec. 7): contents at least 2 gutter * alpha texels
+      // apart stay a whole texel apart at 2^-d when 2 * gutter * omega >= Omega * 2^d
+      if (a.lowres_log2 && ((unsigned long long)Om << a.lowres_log2) > 2ull * a.gutter * om) ok = 0u;
     }
   }
   // publish this candidate; the last CTA selects
@@ -620,7 +624,7 @@ size_t push_smem_bytes(uint32_t front_cap) { return 2 * (size_t)kStageBytes + (s
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
-                              cudaStream_t s) {
+                              cudaStream_t s, uint32_t lowres_log2) {
   uint32_t* ord = order ? order : p.order;
   if (ctx) mark(ctx, "k_order_tile", s);
   launch_k(k_order_tile, p.max_tiles, kOrderTile, 0, s, p, fb);
@@ -631,6 +635,7 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   PackArgs a;
   a.order = ord;
   a.atlas_log2 = atlas_log2;
+  a.lowres_log2 = lowres_log2;
   uint32_t sh = 8;
   while ((1u << (sh - 8)) < n_scales) ++sh;
   a.shift = sh;
@@ -661,7 +666,7 @@ fa_status pack_set_smem_limit() {
 
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* order,
-                      fa_placement* place, fa_pack_result* res, cudaStream_t s) {
+                      fa_placement* place, fa_pack_result* res, cudaStream_t s, uint32_t lowres_log2) {
   if (!ctx->pack_smem_set) {
     fa_status st = pack_set_smem_limit();
     if (st != FA_OK) return st;
@@ -670,7 +675,7 @@ fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, cons
   PackScratch p = ctx->pack;
   p.count = count;
   return launch_pack_kernels(ctx, p, fa_, fb, atlas_log2, n_scales, select_mode, ctx->cfg.min_box,
-                             ctx->cfg.gutter, order, place, res, s);
+                             ctx->cfg.gutter, order, place, res, s, lowres_log2);
 }
 
 }  // namespace fa
@@ -796,5 +801,5 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   p.cand = (PackCand*)(base + kOffCand);
   launch_k(k_noalloc_reset, 1, 256, 0, s, p.ctr, (uint32_t*)p.count, p.ord_total, n);
   return launch_pack_kernels(nullptr, p, d_fa, d_fb, atlas_log2, n_scales, select_mode, min_box, gutter, d_order,
-                             d_place, d_res, s);
+                             d_place, d_res, s, 0u);
 }

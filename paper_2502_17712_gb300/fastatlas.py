@@ -34,6 +34,11 @@ FA_SELECT_LARGEST_K = 1
 FA_BOX_FRUSTUM_CLIP = 1
 FA_VIS_CONSERVATIVE = 2
 
+
+def FA_LOWRES(d):
+    """Frame flags field: the packing also serves the atlas scaled by 2^-d (Sec. 7)."""
+    return (int(d) & 7) << 8
+
 EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh_register",
            "fa_mesh_release", "fa_visibility", "fa_chartify", "fa_parameterize", "fa_pack", "fa_uv",
            "fa_atlas_frame", "fa_last_device_status", "fa_launch_count", "fa_profile_enable",
@@ -118,7 +123,7 @@ def load(path: str = LIB_PATH):
     lib.fa_chartify.restype = st
     lib.fa_parameterize.argtypes = [P, P, P, u32, u32, f32, P, ctypes.POINTER(fa_charts), u32, P, P]
     lib.fa_parameterize.restype = st
-    lib.fa_pack.argtypes = [P, P, P, P, u32, u32, u32, P, P, P, P]
+    lib.fa_pack.argtypes = [P, P, P, P, u32, u32, u32, P, P, P, u32, P]
     lib.fa_pack.restype = st
     lib.fa_uv.argtypes = [P, P, P, u32, u32, f32, P, ctypes.POINTER(fa_charts), P, P, u32, u32, P, P, P]
     lib.fa_uv.restype = st
@@ -252,9 +257,10 @@ def fa_parameterize(ctx, mesh, M, width, height, ratio, tri_chart, charts: fa_ch
            "fa_parameterize")
 
 
-def fa_pack(ctx, fa, fb, count, atlas_log2, n_scales, select_mode, order, place, res, stream=None):
+def fa_pack(ctx, fa, fb, count, atlas_log2, n_scales, select_mode, order, place, res, stream=None,
+            lowres_log2=0):
     _check(load().fa_pack(ctx, _ptr(fa), _ptr(fb), _ptr(count), atlas_log2, n_scales, select_mode, _ptr(order),
-                          _ptr(place), _ptr(res), _stream(stream)), "fa_pack")
+                          _ptr(place), _ptr(res), int(lowres_log2), _stream(stream)), "fa_pack")
 
 
 def fa_pack_noalloc(fa, fb, n, atlas_log2, n_scales, select_mode, min_box, gutter, order, place, res,

@@ -42,9 +42,9 @@ def to_np(t):
 
 
 def compare_frame(sc, M, W, H, ratio, log2, bufs, status, mode=0, n_scales=64, select_mode=0, vt=None,
-                  flags=0):
+                  flags=0, gutter=0):
     fr = O.atlas_frame(M, sc.pos, sc.idx, W, H, ratio, log2, mode=mode, n_scales=n_scales,
-                       select_mode=select_mode, vt=vt, flags=flags)
+                       select_mode=select_mode, vt=vt, flags=flags, gutter=gutter)
     assert status == 0
     T = sc.T
     gvt = to_np(bufs.vt).view(np.uint32)
@@ -382,5 +382,42 @@ def test_conservative_marking_icospheres_and_standalone(F):
     F.fa_visibility(ctx.handle, mesh.handle, M, W, H, vt, flags=F.FA_VIS_CONSERVATIVE)
     torch.cuda.synchronize()
     assert torch.equal(vt, bufs.vt)
+    mesh.close()
+    ctx.close()
+
+
+# ---------------------------------------------------------------- one packing, two atlases
+
+@pytest.mark.parametrize("d,gutter,seed", [(2, 2, 0), (3, 4, 1), (3, 8, 2)])
+def test_pack_lowres_matches_oracle(F, d, gutter, seed):
+    import torch
+    fa, fb = S.lognormal_boxes(seed, 2000, mean_texels=30.0)
+    n, L = len(fa), 12
+    ctx = F.Context(max_tris=64, max_verts=64, max_charts=4096, max_atlas_log2=L, gutter=gutter)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    place = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    F.fa_pack(ctx.handle, d_fa, d_fb, cnt, L, 64, 0, None, place, res, lowres_log2=d)
+    torch.cuda.synchronize()
+    pk = O.pack(fa, fb, L, 64, 2, gutter, 0, d)
+    r = to_np(res).view(np.uint32)
+    assert (int(r[3]), int(r[0]), int(r[1]), int(r[2])) == (pk.status, pk.k, pk.omega, pk.height)
+    assert (to_np(place) == pk.place).all()
+    assert (pk.omega << d) <= 2 * gutter * (1 << L)
+    ctx.close()
+
+
+def test_lowres_frame_matches_oracle(F):
+    sc, M, p = S.heightfield_frame(2)
+    gutter, flags = 4, F.FA_LOWRES(3)
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 14, max_width=p["width"],
+                    max_height=p["height"], max_atlas_log2=p["atlas_log2"], gutter=gutter)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    args = (p["width"], p["height"], p["ratio"], p["atlas_log2"])
+    bufs, st = run_gpu(F, ctx, mesh, M, *args, flags=flags)
+    fr = compare_frame(sc, M, *args, bufs, st, flags=flags, gutter=gutter)
+    assert fr.pk.status == 0 and (fr.pk.omega << 3) <= 2 * gutter * (1 << p["atlas_log2"])
     mesh.close()
     ctx.close()
