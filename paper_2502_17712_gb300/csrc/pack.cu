@@ -518,12 +518,16 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
               }
             }
           }
-          if (__syncthreads_or(bad)) {
-            fail = true;
-            break;
-          }
+          fail |= bad;
+          __syncthreads();
         }
-        if (fail) break;
+        // a candidate that no longer fits stops at the end of the chunk (one
+        // reduction per chunk; a box may rest above Omega meanwhile, which only
+        // raises later rests: every index stays inside [0, Omega))
+        if (__syncthreads_or(fail)) {
+          fail = true;
+          break;
+        }
         // every thread is past this chunk's last barrier: its stage is free
         if (tid == 0 && issued < nchunks) {
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
