@@ -340,11 +340,13 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators
+  // the footprints are computed by the first order kernel
   if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts,
-                                false, p->flags, o->partial, s, Md)) != FA_OK)
+                                false, p->flags, o->partial, s, Md, false)) != FA_OK)
     return st;
+  const FootArgs foot = foot_args(ctx, p->width, p->height, p->ratio, &o->charts);
   if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
-                        p->select_mode, o->order, o->place, o->result, s, (p->flags >> 8) & 7u)) != FA_OK)
+                        p->select_mode, o->order, o->place, o->result, s, (p->flags >> 8) & 7u, &foot)) != FA_OK)
     return st;
   if (o->uv || o->affine) {
     if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts, o->place,

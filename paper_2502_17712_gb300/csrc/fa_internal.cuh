@@ -216,6 +216,43 @@ __device__ __forceinline__ float unordered(uint32_t k) {
   return __uint_as_float(u);
 }
 
+// Footprint of chart c from its box accumulators (Sec. 5.2, Sec. 4.1): the box
+// (full: [-1, 1]^2), its viewport size scaled by 256 * ratio and rounded up to 1/256
+// texel, rotated to stand tall.  Written to bbox / fa / fb / rot; returns fb.
+struct FootArgs {
+  const uint32_t* box_enc;
+  const uint32_t* box_full;
+  float hx, hy, s256;
+  float* bbox;
+  uint32_t* fa;
+  uint32_t* fb;
+  uint8_t* rot;
+};
+
+__device__ __forceinline__ uint32_t chart_footprint(const FootArgs& f, uint32_t c) {
+  float x0, y0, x1, y1;
+  if (__ldcg(f.box_full + c)) {
+    x0 = y0 = -1.0f;
+    x1 = y1 = 1.0f;
+  } else {
+    const uint4 e = __ldcg(reinterpret_cast<const uint4*>(f.box_enc) + c);
+    x0 = unordered(e.x);
+    y0 = unordered(e.y);
+    x1 = unordered(e.z);
+    y1 = unordered(e.w);
+  }
+  reinterpret_cast<float4*>(f.bbox)[c] = make_float4(x0, y0, x1, y1);
+  const float wpx = __fmul_rn(__fsub_rn(x1, x0), f.hx);
+  const float hpx = __fmul_rn(__fsub_rn(y1, y0), f.hy);
+  const uint32_t fw = __float2uint_rz(ceilf(__fmul_rn(f.s256, wpx)));
+  const uint32_t fh = __float2uint_rz(ceilf(__fmul_rn(f.s256, hpx)));
+  const bool r = fw > fh;
+  f.rot[c] = r ? 1 : 0;
+  f.fa[c] = r ? fh : fw;
+  f.fb[c] = r ? fw : fh;
+  return r ? fw : fh;
+}
+
 __device__ __forceinline__ void set_status(DevCounters* c, int32_t s) {
   atomicCAS(&c->status, 0, s);
 }
@@ -293,11 +330,14 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                               uint32_t H, float ratio, const int32_t* tri_chart,
                               const fa_charts* ch, bool reset_boxes, uint32_t flags, uint32_t* partial,
-                              cudaStream_t s, const float* Mdev = nullptr);
+                              cudaStream_t s, const float* Mdev = nullptr, bool footprint = true);
+// Footprint inputs / outputs of the charts of ch (fused into the first order kernel
+// on the frame path).
+FootArgs foot_args(fa_ctx* ctx, uint32_t W, uint32_t H, float ratio, const fa_charts* ch);
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
                       uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s,
-                      uint32_t lowres_log2 = 0);
+                      uint32_t lowres_log2 = 0, const FootArgs* foot = nullptr);
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                     float ratio, const int32_t* tri_chart, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
@@ -314,7 +354,7 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
-                              cudaStream_t s, uint32_t lowres_log2);
+                              cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot);
 fa_status pack_set_smem_limit();
 
 }  // namespace fa

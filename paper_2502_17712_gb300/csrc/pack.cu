@@ -78,7 +78,11 @@ __device__ __forceinline__ T block_max(T v, T* warp_vals) {
 
 // ------------------------------------------------------------------ order
 
-__global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const uint32_t* __restrict__ fb) {
+// FOOT: the charts' footprints are computed here from their box accumulators
+// (written out, and their heights used as the keys) instead of read from fb.
+template <bool FOOT>
+__global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const uint32_t* __restrict__ fb,
+                                                           FootArgs foot) {
   pdl_wait();
   __shared__ uint32_t key[kOrderTile];
   __shared__ uint16_t first[kMaxH];
@@ -89,7 +93,9 @@ __global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const 
   if (blockIdx.x >= ntiles) return;
   const uint32_t tid = threadIdx.x;
   const uint32_t i = blockIdx.x * kOrderTile + tid;
-  key[tid] = i < C ? (height_bin(__ldg(fb + i)) << 10) | tid : 0xFFFFFFFFu;
+  uint32_t fbi = 0;
+  if (i < C) fbi = FOOT ? chart_footprint(foot, i) : __ldg(fb + i);
+  key[tid] = i < C ? (height_bin(fbi) << 10) | tid : 0xFFFFFFFFu;
   uint32_t* row = p.ord_counts + (size_t)blockIdx.x * kMaxH;
   for (uint32_t b = tid; b < kMaxH; b += kOrderTile) row[b] = 0;
   __syncthreads();
@@ -628,10 +634,13 @@ size_t push_smem_bytes(uint32_t front_cap) { return 2 * (size_t)kStageBytes + (s
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
-                              cudaStream_t s, uint32_t lowres_log2) {
+                              cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot) {
   uint32_t* ord = order ? order : p.order;
   if (ctx) mark(ctx, "k_order_tile", s);
-  launch_k(k_order_tile, p.max_tiles, kOrderTile, 0, s, p, fb);
+  if (foot)
+    launch_k(k_order_tile<true>, p.max_tiles, kOrderTile, 0, s, p, fb, *foot);
+  else
+    launch_k(k_order_tile<false>, p.max_tiles, kOrderTile, 0, s, p, fb, FootArgs{});
   if (ctx) mark(ctx, "k_order_binscan", s);
   launch_k(k_order_binscan, 1, 1024, 0, s, p);
   if (ctx) mark(ctx, "k_order_scatter", s);
@@ -670,7 +679,8 @@ fa_status pack_set_smem_limit() {
 
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* order,
-                      fa_placement* place, fa_pack_result* res, cudaStream_t s, uint32_t lowres_log2) {
+                      fa_placement* place, fa_pack_result* res, cudaStream_t s, uint32_t lowres_log2,
+                      const FootArgs* foot) {
   if (!ctx->pack_smem_set) {
     fa_status st = pack_set_smem_limit();
     if (st != FA_OK) return st;
@@ -679,7 +689,7 @@ fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, cons
   PackScratch p = ctx->pack;
   p.count = count;
   return launch_pack_kernels(ctx, p, fa_, fb, atlas_log2, n_scales, select_mode, ctx->cfg.min_box,
-                             ctx->cfg.gutter, order, place, res, s, lowres_log2);
+                             ctx->cfg.gutter, order, place, res, s, lowres_log2, foot);
 }
 
 }  // namespace fa
@@ -805,5 +815,5 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   p.cand = (PackCand*)(base + kOffCand);
   launch_k(k_noalloc_reset, 1, 256, 0, s, p.ctr, (uint32_t*)p.count, p.ord_total, n);
   return launch_pack_kernels(nullptr, p, d_fa, d_fb, atlas_log2, n_scales, select_mode, min_box, gutter, d_order,
-                             d_place, d_res, s, 0u);
+                             d_place, d_res, s, 0u, nullptr);
 }

@@ -214,33 +214,12 @@ __global__ void k_box_reset(const uint32_t* count, uint32_t max_charts, uint32_t
   }
 }
 
-__global__ void k_footprint(const uint32_t* count, uint32_t max_charts, const uint32_t* box_enc,
-                            const uint32_t* box_full, float hx, float hy, float s256, float* bbox,
-                            uint32_t* fa_, uint32_t* fb, uint8_t* rot, DevCounters* ctr) {
+__global__ void k_footprint(const uint32_t* count, uint32_t max_charts, FootArgs f, DevCounters* ctr) {
   pdl_wait();
   if (__ldcg(&ctr->status) != 0) return;
   const uint32_t C = min(__ldcg(count), max_charts);
-  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
-    float x0, y0, x1, y1;
-    if (__ldcg(box_full + c)) {
-      x0 = y0 = -1.0f;
-      x1 = y1 = 1.0f;
-    } else {
-      x0 = unordered(__ldcg(box_enc + 4 * c + 0));
-      y0 = unordered(__ldcg(box_enc + 4 * c + 1));
-      x1 = unordered(__ldcg(box_enc + 4 * c + 2));
-      y1 = unordered(__ldcg(box_enc + 4 * c + 3));
-    }
-    reinterpret_cast<float4*>(bbox)[c] = make_float4(x0, y0, x1, y1);
-    const float wpx = __fmul_rn(__fsub_rn(x1, x0), hx);
-    const float hpx = __fmul_rn(__fsub_rn(y1, y0), hy);
-    const uint32_t fw = __float2uint_rz(ceilf(__fmul_rn(s256, wpx)));
-    const uint32_t fh = __float2uint_rz(ceilf(__fmul_rn(s256, hpx)));
-    const bool r = fw > fh;
-    rot[c] = r ? 1 : 0;
-    fa_[c] = r ? fh : fw;
-    fb[c] = r ? fw : fh;
-  }
+  for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x)
+    chart_footprint(f, c);
 }
 
 // ------------------------------------------------------------ compensated fp32
@@ -392,9 +371,24 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
 
 }  // namespace
 
+FootArgs foot_args(fa_ctx* ctx, uint32_t W, uint32_t H, float ratio, const fa_charts* ch) {
+  FootArgs f;
+  f.box_enc = ctx->box_enc;
+  f.box_full = ctx->box_full;
+  f.hx = 0.5f * (float)W;
+  f.hy = 0.5f * (float)H;
+  f.s256 = 256.0f * ratio;
+  f.bbox = ch->bbox;
+  f.fa = ch->fa;
+  f.fb = ch->fb;
+  f.rot = ch->rot;
+  return f;
+}
+
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                               float ratio, const int32_t* tri_chart, const fa_charts* ch, bool reset_boxes,
-                              uint32_t flags, uint32_t* partial, cudaStream_t s, const float* Mdev) {
+                              uint32_t flags, uint32_t* partial, cudaStream_t s, const float* Mdev,
+                              bool footprint) {
   if (partial) FA_CUDA_TRY(cudaMemsetAsync(partial, 0, (size_t)((mesh->T + 31) / 32) * 4, s));
   if (reset_boxes) {
     mark(ctx, "k_box_reset", s);
@@ -420,9 +414,11 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
     launch_k(k_bbox<true>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
   else
     launch_k(k_bbox<false>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
-  mark(ctx, "k_footprint", s);
-  launch_k(k_footprint, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts, ctx->box_enc, ctx->box_full, 0.5f * (float)W, 0.5f * (float)H,
-      256.0f * ratio, ch->bbox, ch->fa, ch->fb, ch->rot, ctx->ctr);
+  if (footprint) {
+    mark(ctx, "k_footprint", s);
+    launch_k(k_footprint, grid_for(ctx->cfg.max_charts, 256, 152 * 4), 256, 0, s, ch->count, ctx->cfg.max_charts,
+             foot_args(ctx, W, H, ratio, ch), ctx->ctr);
+  }
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
