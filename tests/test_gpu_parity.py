@@ -421,3 +421,25 @@ def test_lowres_frame_matches_oracle(F):
     assert fr.pk.status == 0 and (fr.pk.omega << 3) <= 2 * gutter * (1 << p["atlas_log2"])
     mesh.close()
     ctx.close()
+
+
+# ---------------------------------------------------------------- depth ties
+
+def test_coplanar_duplicates_tie_exactly(F, small_ctx):
+    """Duplicated triangles give equal depth keys at the same pixels: every copy of a
+    visible triangle is visible (the "<=" test); two and three copies."""
+    sc = S.grid_scene(4)
+    rng = np.random.default_rng(4)
+    dup2 = rng.choice(sc.T, 300, replace=False)
+    dup3 = rng.choice(sc.T, 100, replace=False)
+    idx = np.concatenate([sc.idx, sc.idx[dup2], sc.idx[dup3], sc.idx[dup3]]).astype(np.uint32)
+    M = S.hemisphere_camera(4, 640, 360)
+    mesh = F.Mesh(small_ctx, sc.pos, idx)
+    bufs, st = run_gpu(F, small_ctx, mesh, M, 640, 360, 1.0, 10)
+    sc2 = S.Scene(sc.pos, idx)
+    fr = compare_frame(sc2, M, 640, 360, 1.0, 10, bufs, st)
+    vis = O.vt_to_bool(fr.vt, idx.shape[0])
+    T = sc.T
+    assert (vis[T:T + 300] == vis[dup2]).all() and vis[dup2].any()
+    assert (vis[T + 300:T + 400] == vis[dup3]).all() and (vis[T + 400:] == vis[dup3]).all()
+    mesh.close()
