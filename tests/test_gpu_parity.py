@@ -443,3 +443,57 @@ def test_coplanar_duplicates_tie_exactly(F, small_ctx):
     assert (vis[T:T + 300] == vis[dup2]).all() and vis[dup2].any()
     assert (vis[T + 300:T + 400] == vis[dup3]).all() and (vis[T + 400:] == vis[dup3]).all()
     mesh.close()
+
+
+# ---------------------------------------------------------------- edge cases
+
+def test_pack_empty_box_set(F):
+    import torch
+    ctx = F.Context(max_tris=64, max_verts=64, max_charts=4096, max_atlas_log2=11)
+    d = torch.zeros(4096, dtype=torch.int32, device="cuda")
+    cnt = torch.zeros(1, dtype=torch.int32, device="cuda")
+    place = torch.full((4096, 4), -7, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    for sel in (0, 1):
+        F.fa_pack(ctx.handle, d, d, cnt, 11, 64, sel, None, place, res)
+        torch.cuda.synchronize()
+        pk = O.pack(np.zeros(0, np.uint32), np.zeros(0, np.uint32), 11, 64, 2, 0, sel)
+        r = to_np(res).view(np.uint32)
+        assert (int(r[3]), int(r[0]), int(r[1]), int(r[2]), int(r[4])) == (pk.status, pk.k, pk.omega, pk.height, 0)
+    assert (to_np(place) == -7).all()  # nothing written
+    ctx.close()
+
+
+def test_single_triangle_mesh_and_charts_at_capacity(F):
+    # one triangle filling part of the view: one chart, at max_charts = 1 exactly
+    pos = np.array([[-0.5, -0.5, 0.0], [0.5, -0.4, 0.1], [0.0, 0.6, -0.1]], np.float32)
+    idx = np.array([[0, 1, 2]], np.uint32)
+    M = S.view_proj((0, 0, 2), (0, 0, 0), (0, 1, 0), 320, 240)
+    ctx = F.Context(max_tris=1, max_verts=3, max_charts=1, max_width=320, max_height=240, max_atlas_log2=9)
+    mesh = F.Mesh(ctx, pos, idx)
+    bufs, st = run_gpu(F, ctx, mesh, M, 320, 240, 1.0, 9)
+    fr = compare_frame(S.Scene(pos, idx), M, 320, 240, 1.0, 9, bufs, st)
+    assert fr.charts.C == 1 and fr.pk.status == 0
+    mesh.close()
+    ctx.close()
+
+
+def test_chart_count_one_above_capacity(F, small_ctx):
+    # two separate triangles but room for one chart: the count is reported, status
+    # FA_E_CAPACITY, no chart writes beyond the capacity
+    import torch
+    pos = np.array([[-0.9, -0.5, 0], [-0.4, -0.5, 0], [-0.6, 0.2, 0],
+                    [0.4, -0.5, 0], [0.9, -0.5, 0], [0.6, 0.2, 0]], np.float32)
+    idx = np.array([[0, 1, 2], [3, 4, 5]], np.uint32)
+    M = np.eye(4, dtype=np.float32)
+    ctx = F.Context(max_tris=2, max_verts=6, max_charts=1, max_width=64, max_height=64, max_atlas_log2=8)
+    mesh = F.Mesh(ctx, pos, idx)
+    b = F.FrameBuffers.allocate(2, 6, 1)
+    F.atlas_frame(ctx, mesh, b, M, 64, 64, 1.0, 8)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == F.FA_E_CAPACITY
+    assert int(b.count[0]) == 2
+    r = to_np(b.result).view(np.uint32)
+    assert int(r[3]) == F.FA_E_CAPACITY
+    mesh.close()
+    ctx.close()
