@@ -84,46 +84,39 @@ template <bool FOOT>
 __global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const uint32_t* __restrict__ fb,
                                                            FootArgs foot) {
   pdl_wait();
-  __shared__ uint32_t key[kOrderTile];
-  __shared__ uint16_t first[kMaxH];
+  __shared__ uint32_t hist[kMaxH];  // boxes of each height bin seen so far in this tile
   if (__ldcg(&p.ctr->status) != 0) return;
   const uint32_t C = __ldcg(p.count);
   if (C > p.max_boxes) return;
   const uint32_t ntiles = (C + kOrderTile - 1) / kOrderTile;
   if (blockIdx.x >= ntiles) return;
-  const uint32_t tid = threadIdx.x;
+  const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const uint32_t i = blockIdx.x * kOrderTile + tid;
   uint32_t fbi = 0;
   if (i < C) fbi = FOOT ? chart_footprint(foot, i) : __ldg(fb + i);
-  key[tid] = i < C ? (height_bin(fbi) << 10) | tid : 0xFFFFFFFFu;
-  uint32_t* row = p.ord_counts + (size_t)blockIdx.x * kMaxH;
-  for (uint32_t b = tid; b < kMaxH; b += kOrderTile) row[b] = 0;
-  __syncthreads();
-  for (uint32_t size = 2; size <= kOrderTile; size <<= 1) {  // bitonic sort, ascending
-    for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
-      const uint32_t j = tid ^ stride;
-      if (j > tid) {
-        const uint32_t a = key[tid], b = key[j];
-        if ((a > b) == ((tid & size) == 0)) {
-          key[tid] = b;
-          key[j] = a;
-        }
-      }
-      __syncthreads();
+  const uint32_t bin = i < C ? height_bin(fbi) : kMaxH;  // kMaxH: no box
+  for (uint32_t b = tid; b < kMaxH; b += kOrderTile) hist[b] = 0;
+  // stable rank inside the tile: the warps take their turn in index order; inside a
+  // warp, the lanes with the same bin are ranked by lane
+  const uint32_t peers = __match_any_sync(0xFFFFFFFFu, bin);
+  const uint32_t before = __popc(peers & ((1u << lane) - 1u));
+  const bool leader = before == 0u;
+  uint32_t r = 0;
+  for (uint32_t w = 0; w < (uint32_t)(kOrderTile / 32); ++w) {
+    __syncthreads();
+    if (wid == w && bin < kMaxH) {
+      r = hist[bin] + before;
+      __syncwarp(peers);
+      if (leader) hist[bin] = r + __popc(peers);
     }
   }
-  const uint32_t k = key[tid];
-  const bool valid = k != 0xFFFFFFFFu;
-  const uint32_t bin = k >> 10;
-  if (valid && (tid == 0 || (key[tid - 1] >> 10) != bin)) first[bin] = (uint16_t)tid;
   __syncthreads();
-  if (valid) {
-    const uint32_t r = tid - first[bin];
-    p.ord_rank[blockIdx.x * kOrderTile + (k & 1023u)] = r;
-    if (tid == kOrderTile - 1 || (key[tid + 1] >> 10) != bin) {
-      row[bin] = r + 1;
-      atomicAdd(p.ord_total + bin, r + 1);
-    }
+  if (bin < kMaxH) p.ord_rank[i] = r;
+  uint32_t* row = p.ord_counts + (size_t)blockIdx.x * kMaxH;
+  for (uint32_t b = tid; b < kMaxH; b += kOrderTile) {
+    const uint32_t c = hist[b];
+    row[b] = c;
+    if (c) atomicAdd(p.ord_total + b, c);
   }
 }
 
