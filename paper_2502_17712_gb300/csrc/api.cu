@@ -94,7 +94,7 @@ void fa_destroy(fa_ctx* ctx) {
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
   void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
-                  ctx->label, ctx->cid, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt,
+                  ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
   for (void* p : ptrs)
@@ -150,7 +150,7 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   if (st == FA_OK) st = alloc((float4**)&ctx->surv_clip, (size_t)ctx->surv_cap * 3);
   FA_ALLOC(ctx->clip, T);
   FA_ALLOC(ctx->label, T + V);
-  FA_ALLOC(ctx->cid, T);
+  FA_ALLOC(ctx->wordroots, (T + 31) / 32);
   FA_ALLOC(ctx->blockcnt, nblocks + 1);
   FA_ALLOC(ctx->viscnt, nblocks + 1);
   FA_ALLOC(ctx->xedge, nblocks * 3072);

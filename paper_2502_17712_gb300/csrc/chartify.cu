@@ -3,7 +3,9 @@
 // initialise each visible triangle to the smallest visible neighbour, hook roots
 // with atomicCAS so the larger root always points to the smaller one, then flatten.
 // The root of a component is therefore its smallest triangle id.  Charts are
-// numbered by ascending root with a block-count scan.
+// numbered by ascending root: the flatten pass counts the roots per 1024-triangle
+// block and records each VT word's root bits, a scan gives each block's first chart,
+// and a root's chart is that plus the roots before it inside its block.
 //
 // Edge mode joins triangles across shared edges (the adjacency built at mesh
 // registration, plus the incidence lists of non-manifold edges).  Vertex mode
@@ -222,38 +224,56 @@ __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* n
 
 // Flatten visible triangles to their root and count roots per block of
 // kPerBlock triangles: warp w of the block owns VT words w, w + 8, w + 16, w + 24.
-__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt, uint32_t* viscnt) {
+__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt, uint32_t* viscnt,
+                                                       uint2* wordroots) {
   pdl_wait();
-  __shared__ uint32_t cnt[kBlock / 32], vcnt[kBlock / 32];
+  __shared__ uint32_t wc[kPerBlock / 32], vcnt[kBlock / 32];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
-  uint32_t mine = 0, vis = 0;
+  uint32_t vis = 0, rb[kPerBlock / kBlock];
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t w = blockIdx.x * (kPerBlock / 32) + k * (kBlock / 32) + wid;
+    const uint32_t wl = k * (kBlock / 32) + wid;
+    const uint32_t w = blockIdx.x * (kPerBlock / 32) + wl;
     const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
     vis += __popc(word);
-    if (!((word >> lane) & 1u)) continue;
-    const uint32_t t = (w << 5) + lane;
-    const int32_t r = find_root(a.label, (int32_t)t);
-    a.label[t] = r;
-    mine += (r == (int32_t)t);
+    bool root = false;
+    if ((word >> lane) & 1u) {
+      const uint32_t t = (w << 5) + lane;
+      const int32_t r = find_root(a.label, (int32_t)t);
+      a.label[t] = r;
+      root = r == (int32_t)t;
+    }
+    rb[k] = __ballot_sync(0xFFFFFFFFu, root);
+    if (lane == 0) wc[wl] = __popc(rb[k]);
   }
-  mine = __reduce_add_sync(0xFFFFFFFFu, mine);
-  if (lane == 0) {
-    cnt[wid] = mine;
-    vcnt[wid] = vis;  // every lane counted the same words
-  }
+  if (lane == 0) vcnt[wid] = vis;  // every lane counted the same words
   __syncthreads();
+  // per VT word: its root bits and the roots of the block's earlier words
+#pragma unroll
+  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
+    const uint32_t wl = k * (kBlock / 32) + wid;
+    const uint32_t w = blockIdx.x * (kPerBlock / 32) + wl;
+    if (lane == 0 && w < nwords) {
+      uint32_t pre = 0;
+      for (uint32_t i = 0; i < wl; ++i) pre += wc[i];
+      wordroots[w] = make_uint2(rb[k], pre);
+    }
+  }
   if (threadIdx.x == 0) {
     uint32_t s = 0, v = 0;
-    for (int i = 0; i < kBlock / 32; ++i) {
-      s += cnt[i];
-      v += vcnt[i];
-    }
+    for (int i = 0; i < kPerBlock / 32; ++i) s += wc[i];
+    for (int i = 0; i < kBlock / 32; ++i) v += vcnt[i];
     blockcnt[blockIdx.x] = s;
     viscnt[blockIdx.x] = v;
   }
+}
+
+// Chart of root triangle r: the roots before its block (scanned block counts),
+// before its word inside the block, and before it inside its word.
+__device__ __forceinline__ uint32_t chart_of_root(const uint32_t* blockcnt, const uint2* wordroots, uint32_t r) {
+  const uint2 wr = __ldcg(wordroots + (r >> 5));
+  return __ldcg(blockcnt + r / kPerBlock) + wr.y + __popc(wr.x & ((1u << (r & 31)) - 1u));
 }
 
 // In-place exclusive scans of the per-block counts a[0..n) and, when given,
@@ -334,46 +354,6 @@ __global__ void __launch_bounds__(1024) k_scan_vis(uint32_t* viscnt, uint32_t nb
   scan_counts(viscnt, nullptr, nblocks, &ctr->n_vis, nullptr);
 }
 
-// Number the roots in triangle order (same blocking as k_uf_flatten); record the
-// chart's root and reset its box accumulators.
-__global__ void __launch_bounds__(kBlock) k_number(UfArgs a, const uint32_t* blockcnt, int32_t* cid,
-                                                   uint32_t* roots, uint32_t* box_enc,
-                                                   uint32_t* box_full, uint32_t max_charts) {
-  pdl_wait();
-  __shared__ uint32_t wcount[kPerBlock / 32];
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  // roots of each of the block's 32 words (word order = triangle order)
-  uint32_t rbits[kPerBlock / kBlock];
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t wl = k * (kBlock / 32) + wid;
-    const uint32_t w = blockIdx.x * (kPerBlock / 32) + wl;
-    const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
-    bool root = false;
-    if ((word >> lane) & 1u) root = __ldcg(a.label + (w << 5) + lane) == (int32_t)((w << 5) + lane);
-    rbits[k] = __ballot_sync(0xFFFFFFFFu, root);
-    if (lane == 0) wcount[wl] = __popc(rbits[k]);
-  }
-  __syncthreads();
-  const uint32_t base = __ldcg(blockcnt + blockIdx.x);
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t wl = k * (kBlock / 32) + wid;
-    if (!((rbits[k] >> lane) & 1u)) continue;
-    uint32_t pre = base;
-    for (uint32_t i = 0; i < wl; ++i) pre += wcount[i];
-    pre += __popc(rbits[k] & ((1u << lane) - 1u));
-    const uint32_t t = ((blockIdx.x * (kPerBlock / 32) + wl) << 5) + lane;
-    if (pre < max_charts) {
-      cid[t] = (int32_t)pre;
-      roots[pre] = t;
-      reinterpret_cast<uint4*>(box_enc)[pre] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
-      box_full[pre] = 0u;
-    }
-  }
-}
-
 // The entries of one 1024-triangle block's visible triangles in the list, in
 // triangle order: entry = list start of the block + the visible triangles before
 // it.  words[k] is VT word k * 8 + warp of the block.
@@ -397,9 +377,12 @@ __device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / 
   }
 }
 
-// Chart id of every triangle (-1 invisible) and the visible-triangle list (same
-// blocking as k_uf_flatten).
-__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* cid, int32_t* tri_chart,
+// Chart id of every triangle (-1 invisible; charts numbered by ascending root) and
+// the visible-triangle list (same blocking as k_uf_flatten); each root records
+// itself as its chart's root and resets the chart's box accumulators.
+__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots,
+                                                      int32_t* tri_chart, uint32_t* roots, uint32_t* box_enc,
+                                                      uint32_t* box_full, uint32_t max_charts,
                                                       const uint32_t* visstart, uint2* vis) {
   pdl_wait();
   if (__ldcg(&a.ctr->status) != 0) return;
@@ -413,7 +396,16 @@ __global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const int32_t* c
     words[k] = w < nwords ? __ldg(a.vt + w) : 0u;
     const uint32_t t = (w << 5) + lane;
     int32_t out = -1;
-    if ((words[k] >> lane) & 1u) out = __ldcg(cid + __ldcg(a.label + t));
+    if ((words[k] >> lane) & 1u) {
+      const uint32_t r = (uint32_t)__ldcg(a.label + t);
+      const uint32_t c = chart_of_root(blockcnt, wordroots, r);
+      out = (int32_t)c;
+      if (r == t && c < max_charts) {
+        roots[c] = t;
+        reinterpret_cast<uint4*>(box_enc)[c] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+        box_full[c] = 0u;
+      }
+    }
     chart[k] = out;
     if (w < nwords && t < a.T) tri_chart[t] = out;
   }
@@ -456,14 +448,15 @@ __global__ void __launch_bounds__(kBlock) k_vis_fill(const int32_t* tri_chart, u
   put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis);
 }
 
-__global__ void k_vert_chart(UfArgs a, const int32_t* cid, int32_t* vert_chart, int vertex_mode) {
+__global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots, int32_t* vert_chart,
+                             int vertex_mode) {
   pdl_wait();
   if (__ldcg(&a.ctr->status) != 0) return;
   for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
     int32_t out = -1;
     if (vertex_mode) {
       int32_t r = find_root(a.label, (int32_t)(a.T + v));
-      if (r < (int32_t)a.T) out = __ldcg(cid + r);
+      if (r < (int32_t)a.T) out = (int32_t)chart_of_root(blockcnt, wordroots, (uint32_t)r);
     }
     vert_chart[v] = out;
   }
@@ -502,18 +495,17 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   }
   const uint32_t nb = (mesh->T + kPerBlock - 1) / kPerBlock;
   mark(ctx, "k_uf_flatten", s);
-  launch_k(k_uf_flatten, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->viscnt);
+  launch_k(k_uf_flatten, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->viscnt, ctx->wordroots);
   mark(ctx, "k_scan_blocks", s);
   launch_k(k_scan_blocks, 1, 1024, 0, s, ctx->blockcnt, ctx->viscnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts,
            ctx->ctr);
-  mark(ctx, "k_number", s);
-  launch_k(k_number, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->cid, ch->root, ctx->box_enc,
-                                          ctx->box_full, ctx->cfg.max_charts);
   mark(ctx, "k_tri_chart", s);
-  launch_k(k_tri_chart, nb ? nb : 1, kBlock, 0, s, a, ctx->cid, tri_chart, ctx->viscnt, ctx->vis);
+  launch_k(k_tri_chart, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->wordroots, tri_chart, ch->root,
+           ctx->box_enc, ctx->box_full, ctx->cfg.max_charts, ctx->viscnt, ctx->vis);
   if (vert_chart) {
     mark(ctx, "k_vert_chart", s);
-    launch_k(k_vert_chart, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, a, ctx->cid, vert_chart, vm);
+    launch_k(k_vert_chart, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, a, ctx->blockcnt, ctx->wordroots,
+             vert_chart, vm);
   }
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;

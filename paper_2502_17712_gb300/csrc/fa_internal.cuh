@@ -116,7 +116,7 @@ struct fa_ctx {
   void* surv_clip;       // [max_tris][3] float4 clip coordinates of the survivors
   uint32_t* clip;        // [max_tris] triangles to clip
   int32_t* label;        // [max_tris + max_verts]
-  int32_t* cid;          // [max_tris] chart id of root triangles
+  uint2* wordroots;      // [ceil(max_tris / 32)] per VT word: root bits, roots before it in its block
   uint32_t* blockcnt;    // [n_blocks + 1]
   uint2* xedge;          // [n_blocks][3072] cross-tile edges of the local union-find
   uint32_t* xcnt;        // [n_blocks] their counts
