@@ -95,7 +95,7 @@ void fa_destroy(fa_ctx* ctx) {
   const PackScratch& p = ctx->pack;
   void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
                   ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt,
-                  ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total, p.ord_binstart,
+                  ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -161,7 +161,6 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(pk.ord_counts, (uint64_t)kMaxH * pk.max_tiles);
   FA_ALLOC(pk.ord_rank, C);
   FA_ALLOC(pk.ord_total, kMaxH);
-  FA_ALLOC(pk.ord_binstart, kMaxH);
   FA_ALLOC(pk.order, C);
   FA_ALLOC(pk.fs, (uint64_t)pk.max_chunks * kChunk);
   FA_ALLOC(pk.rec8, (uint64_t)kMaxScales * pk.max_chunks * kChunk);
@@ -345,12 +344,15 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
                                 false, p->flags, o->partial, s, Md, false)) != FA_OK)
     return st;
   const FootArgs foot = foot_args(ctx, p->width, p->height, p->ratio, &o->charts);
+  // with UVs, the UV kernel also writes the placements
+  const bool uv = o->uv || o->affine;
   if ((st = launch_pack(ctx, o->charts.fa, o->charts.fb, o->charts.count, p->atlas_log2, p->n_scales,
-                        p->select_mode, o->order, o->place, o->result, s, (p->flags >> 8) & 7u, &foot)) != FA_OK)
+                        p->select_mode, o->order, o->place, o->result, s, (p->flags >> 8) & 7u, &foot,
+                        !uv)) != FA_OK)
     return st;
-  if (o->uv || o->affine) {
+  if (uv) {
     if ((st = launch_uv(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts, o->place,
-                        o->result, p->atlas_log2, p->n_scales, o->uv, o->affine, s, Md)) != FA_OK)
+                        o->result, p->atlas_log2, p->n_scales, o->uv, o->affine, s, Md, true)) != FA_OK)
       return st;
   }
   trace_end(ctx, s);

@@ -75,7 +75,6 @@ struct PackScratch {
   uint32_t* ord_counts;         // [max_tiles][kMaxH]
   uint32_t* ord_rank;           // [max_boxes]
   uint32_t* ord_total;          // [kMaxH], zero between calls
-  uint32_t* ord_binstart;       // [kMaxH]
   uint32_t* order;              // [max_boxes] when the caller passes none
   uint32_t max_chunks;          // ceil(max_boxes / kChunk)
   uint2* fs;                    // [max_chunks * kChunk] footprints (fa, fb) in box order
@@ -337,12 +336,12 @@ FootArgs foot_args(fa_ctx* ctx, uint32_t W, uint32_t H, float ratio, const fa_ch
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode,
                       uint32_t* order, fa_placement* place, fa_pack_result* res, cudaStream_t s,
-                      uint32_t lowres_log2 = 0, const FootArgs* foot = nullptr);
+                      uint32_t lowres_log2 = 0, const FootArgs* foot = nullptr, bool write_place = true);
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
                     float ratio, const int32_t* tri_chart, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
                     uint32_t n_scales, float* uv, float* affine, cudaStream_t s,
-                    const float* Mdev = nullptr);
+                    const float* Mdev = nullptr, bool from_candidates = false);
 fa_status build_adjacency(fa_ctx* ctx, fa_mesh* mesh, cudaStream_t s);
 // The visible-triangle list from a caller's tri_chart (standalone box / UV calls).
 fa_status launch_vis_list(fa_ctx* ctx, const fa_mesh* mesh, const int32_t* tri_chart, cudaStream_t s);
@@ -354,7 +353,7 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
-                              cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot);
+                              cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot, bool write_place);
 fa_status pack_set_smem_limit();
 
 }  // namespace fa

@@ -3,10 +3,11 @@
 // Order: stable counting sort of the boxes by integer height
 //   h0 = clamp(ceil(fb / 256), 1, 8192), tallest first, ties by box index (the
 //   boxes arrive numbered by ascending root, so this is the paper's
-//   (height, lowest triangle id) order).  k_order_tile bitonic-sorts the
-//   (bin, index) keys of each 1024-box tile, giving stable in-tile ranks, a per-bin
-//   count row per tile and global bin totals; k_order_binscan scans the totals;
-//   k_order_scatter adds, for each box, the counts of its bin in earlier tiles.
+//   (height, lowest triangle id) order).  k_order_tile ranks the boxes of each
+//   1024-box tile stably inside their height bin (a shared-memory histogram the
+//   warps update in index order) and writes a per-bin count row per tile and the
+//   global bin totals; k_order_scatter scans the totals (every block) and adds, for
+//   each box, the counts of its bin in earlier tiles.
 //   This replaces the paper's cuckoo-hash bucketing with the same result contract
 //   (deterministic, identical for identical frames).
 //
@@ -120,13 +121,26 @@ __global__ void __launch_bounds__(kOrderTile) k_order_tile(PackScratch p, const 
   }
 }
 
-// binstart = exclusive scan of the bin totals; the totals are cleared for the next call.
-__global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
+// Each block scans the bin totals itself (exclusive, in shared memory), then places
+// its boxes: bin start + the bin's boxes in earlier tiles + the rank in the tile.
+// Block 0 also clears the width scan's look-back state, work counter and overflows
+// (k_pack_scan runs next; it clears the bin totals for the next call).
+__global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, const uint32_t* __restrict__ fa,
+                                                              const uint32_t* __restrict__ fb, uint32_t* order) {
   pdl_wait();
+  __shared__ uint32_t binstart[kMaxH];
   __shared__ uint32_t wt[32];
   if (__ldcg(&p.ctr->status) != 0) return;
-  constexpr uint32_t kPer = kMaxH / 1024;
-  uint4* t4 = reinterpret_cast<uint4*>(p.ord_total) + threadIdx.x * (kPer / 4);
+  const uint32_t C = __ldcg(p.count);
+  if (C > p.max_boxes) return;
+  if (blockIdx.x == 0) {  // also with no boxes: the push reads the overflows
+    for (uint32_t i = threadIdx.x; i < kMaxScales * p.max_chunks; i += blockDim.x) p.scan_state[i] = 0ull;
+    if (threadIdx.x < kMaxScales) p.m[threadIdx.x] = 0u;
+    if (threadIdx.x == 0) p.ctr->pack_item = 0u;
+  }
+  if (blockIdx.x * kOrderTile >= C) return;
+  constexpr uint32_t kPer = kMaxH / kOrderTile;
+  const uint4* t4 = reinterpret_cast<const uint4*>(p.ord_total) + threadIdx.x * (kPer / 4);
   uint32_t v[kPer];
 #pragma unroll
   for (uint32_t j = 0; j < kPer / 4; ++j) {
@@ -135,40 +149,22 @@ __global__ void __launch_bounds__(1024) k_order_binscan(PackScratch p) {
     v[4 * j + 1] = q.y;
     v[4 * j + 2] = q.z;
     v[4 * j + 3] = q.w;
-    t4[j] = make_uint4(0, 0, 0, 0);
   }
-  // the pack's look-back state, work counter and overflows start at zero
-  for (uint32_t i = threadIdx.x; i < kMaxScales * p.max_chunks; i += blockDim.x) p.scan_state[i] = 0ull;
-  if (threadIdx.x < kMaxScales) p.m[threadIdx.x] = 0u;
-  if (threadIdx.x == 0) p.ctr->pack_item = 0u;
   uint32_t sum = 0;
 #pragma unroll
   for (uint32_t j = 0; j < kPer; ++j) sum += v[j];
   uint32_t tot;
-  const uint32_t incl = block_scan_incl<uint32_t>(sum, wt, &tot);
-  uint32_t run = incl - sum;
-  uint4* b4 = reinterpret_cast<uint4*>(p.ord_binstart) + threadIdx.x * (kPer / 4);
+  uint32_t run = block_scan_incl<uint32_t>(sum, wt, &tot) - sum;
 #pragma unroll
-  for (uint32_t j = 0; j < kPer / 4; ++j) {
-    uint4 q;
-    q.x = run; run += v[4 * j];
-    q.y = run; run += v[4 * j + 1];
-    q.z = run; run += v[4 * j + 2];
-    q.w = run; run += v[4 * j + 3];
-    b4[j] = q;
+  for (uint32_t j = 0; j < kPer; ++j) {
+    binstart[threadIdx.x * kPer + j] = run;
+    run += v[j];
   }
-}
-
-__global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, const uint32_t* __restrict__ fa,
-                                                              const uint32_t* __restrict__ fb, uint32_t* order) {
-  pdl_wait();
-  if (__ldcg(&p.ctr->status) != 0) return;
-  const uint32_t C = __ldcg(p.count);
-  if (C > p.max_boxes) return;
+  __syncthreads();
   const uint32_t i = blockIdx.x * kOrderTile + threadIdx.x;
   if (i >= C) return;
   const uint32_t bin = height_bin(__ldg(fb + i));
-  uint32_t pos = __ldcg(p.ord_binstart + bin) + __ldcg(p.ord_rank + i);
+  uint32_t pos = binstart[bin] + p.ord_rank[i];
   uint32_t t = 0;
   for (; t + 4 <= blockIdx.x; t += 4) {
     const uint32_t* c = p.ord_counts + (size_t)t * kMaxH + bin;
@@ -179,6 +175,7 @@ __global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, con
     order[pos] = i;
     p.fs[pos] = make_uint2(__ldg(fa + i), __ldg(fb + i));
   }
+  p.ord_rank[i] = pos;  // from here on: the box's position in the order
 }
 
 // ------------------------------------------------------------------ pack
@@ -224,6 +221,9 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* q, unsigned l
 
 __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackArgs a, uint32_t n_scales) {
   pdl_wait();
+  // the order's bin totals were last read by k_order_scatter: clear them for the next call
+  if (blockIdx.x == 0)
+    for (uint32_t b = threadIdx.x; b < kMaxH; b += blockDim.x) p.ord_total[b] = 0u;
   __shared__ unsigned long long ws64[32];
   __shared__ uint32_t ws32[32];
   __shared__ uint32_t s_lastw[kScanThreads / 32];
@@ -627,15 +627,13 @@ size_t push_smem_bytes(uint32_t front_cap) { return 2 * (size_t)kStageBytes + (s
 fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t* fa_, const uint32_t* fb,
                               uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t min_box,
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
-                              cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot) {
+                              cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot, bool write_place) {
   uint32_t* ord = order ? order : p.order;
   if (ctx) mark(ctx, "k_order_tile", s);
   if (foot)
     launch_k(k_order_tile<true>, p.max_tiles, kOrderTile, 0, s, p, fb, *foot);
   else
     launch_k(k_order_tile<false>, p.max_tiles, kOrderTile, 0, s, p, fb, FootArgs{});
-  if (ctx) mark(ctx, "k_order_binscan", s);
-  launch_k(k_order_binscan, 1, 1024, 0, s, p);
   if (ctx) mark(ctx, "k_order_scatter", s);
   launch_k(k_order_scatter, p.max_tiles, kOrderTile, 0, s, p, fa_, fb, ord);
   PackArgs a;
@@ -658,8 +656,10 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   launch_k(k_pack_scan, g2, kScanThreads, 0, s, p, a, n_scales);
   if (ctx) mark(ctx, "k_pack_push", s);
   launch_k(k_pack_push, n_scales, kPushThreads, push_smem_bytes(a.front_cap), s, p, a);
-  if (ctx) mark(ctx, "k_pack_place", s);
-  launch_k(k_pack_place, 152 * 2, 256, 0, s, p, a);
+  if (write_place) {
+    if (ctx) mark(ctx, "k_pack_place", s);
+    launch_k(k_pack_place, 152 * 2, 256, 0, s, p, a);
+  }
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
@@ -673,7 +673,7 @@ fa_status pack_set_smem_limit() {
 fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, const uint32_t* count,
                       uint32_t atlas_log2, uint32_t n_scales, uint32_t select_mode, uint32_t* order,
                       fa_placement* place, fa_pack_result* res, cudaStream_t s, uint32_t lowres_log2,
-                      const FootArgs* foot) {
+                      const FootArgs* foot, bool write_place) {
   if (!ctx->pack_smem_set) {
     fa_status st = pack_set_smem_limit();
     if (st != FA_OK) return st;
@@ -682,7 +682,7 @@ fa_status launch_pack(fa_ctx* ctx, const uint32_t* fa_, const uint32_t* fb, cons
   PackScratch p = ctx->pack;
   p.count = count;
   return launch_pack_kernels(ctx, p, fa_, fb, atlas_log2, n_scales, select_mode, ctx->cfg.min_box,
-                             ctx->cfg.gutter, order, place, res, s, lowres_log2, foot);
+                             ctx->cfg.gutter, order, place, res, s, lowres_log2, foot, write_place);
 }
 
 }  // namespace fa
@@ -714,8 +714,7 @@ constexpr size_t kOffM = align256(kOffCand + sizeof(PackCand) * kMaxScales);
 constexpr size_t kOffCounts = align256(kOffM + sizeof(uint32_t) * kMaxScales);
 constexpr size_t kOffRank = align256(kOffCounts + sizeof(uint32_t) * kMaxH * kNoAllocTiles);
 constexpr size_t kOffTotal = align256(kOffRank + sizeof(uint32_t) * kNoAllocMaxBoxes);
-constexpr size_t kOffBinstart = align256(kOffTotal + sizeof(uint32_t) * kMaxH);
-constexpr size_t kOffOrder = align256(kOffBinstart + sizeof(uint32_t) * kMaxH);
+constexpr size_t kOffOrder = align256(kOffTotal + sizeof(uint32_t) * kMaxH);
 constexpr size_t kOffFs = align256(kOffOrder + sizeof(uint32_t) * kNoAllocMaxBoxes);
 constexpr size_t kOffRec8 = align256(kOffFs + sizeof(uint2) * kNoAllocMaxBoxes);
 constexpr size_t kOffSegs = align256(kOffRec8 + sizeof(uint2) * kMaxScales * kNoAllocMaxBoxes);
@@ -796,7 +795,6 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   p.ord_counts = (uint32_t*)(base + kOffCounts);
   p.ord_rank = (uint32_t*)(base + kOffRank);
   p.ord_total = (uint32_t*)(base + kOffTotal);
-  p.ord_binstart = (uint32_t*)(base + kOffBinstart);
   p.order = (uint32_t*)(base + kOffOrder);
   p.max_chunks = kNoAllocMaxBoxes / kChunk;
   p.fs = (uint2*)(base + kOffFs);
@@ -808,5 +806,5 @@ extern "C" fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb,
   p.cand = (PackCand*)(base + kOffCand);
   launch_k(k_noalloc_reset, 1, 256, 0, s, p.ctr, (uint32_t*)p.count, p.ord_total, n);
   return launch_pack_kernels(nullptr, p, d_fa, d_fb, atlas_log2, n_scales, select_mode, min_box, gutter, d_order,
-                             d_place, d_res, s, 0u, nullptr);
+                             d_place, d_res, s, 0u, nullptr, true);
 }

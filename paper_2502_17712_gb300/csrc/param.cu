@@ -287,7 +287,22 @@ struct UvArgs {
   float* uv;
   float* affine;
   DevCounters* ctr;
+  // frame path: placements straight from the selected candidate's records (box b at
+  // sorted position pos_of[b]), and written out to place_out
+  const uint2* cand_xy;
+  const uint2* cand_rec;
+  size_t xy_stride, rec_stride;
+  const uint32_t* pos_of;
+  fa_placement* place_out;
 };
+
+__device__ __forceinline__ fa_placement placement_of(const UvArgs& a, uint32_t c, uint32_t kb) {
+  if (!a.cand_xy) return a.place[c];
+  const uint32_t pos = __ldcg(a.pos_of + c);
+  const uint2 q = __ldcg(a.cand_xy + kb * a.xy_stride + pos);
+  const uint2 r = __ldcg(a.cand_rec + kb * a.rec_stride + pos);
+  return fa_placement{(int32_t)q.x, (int32_t)q.y, (int32_t)(r.x >> 16), (int32_t)(r.y & 0x7FFFFFFFu)};
+}
 
 template <bool DEV_M>
 __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
@@ -303,12 +318,15 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
   g.lo = __fmul_rn(g.lo, inv_n);
   const float gut = (float)a.gutter;
 
-  // per-chart affine (uv = A . ndc + b)
-  if (a.affine) {
+  const uint32_t kb = k - 1u;
+  // per chart: the placement (frame path) and the affine (uv = A . ndc + b)
+  if (a.affine || a.place_out) {
     const uint32_t C = min(__ldcg(a.count), a.max_charts);
     for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+      const fa_placement pl = placement_of(a, c, kb);
+      if (a.place_out) a.place_out[c] = pl;
+      if (!a.affine) continue;
       const float4 bb = reinterpret_cast<const float4*>(a.bbox)[c];
-      const fa_placement pl = a.place[c];
       const DF X = two_sum((float)pl.x, gut), Y = two_sum((float)pl.y, gut);
       const DF agx = df_mul(df_mul_f(alpha, a.hx), g), agy = df_mul(df_mul_f(alpha, a.hy), g);
       const DF gx = df_mul_f(g, a.hx), gy = df_mul_f(g, a.hy);
@@ -339,7 +357,7 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
     const int32_t c = (int32_t)e.y;
     if (c < 0 || (uint32_t)c >= C || t >= a.T) continue;
     const float4 bb = reinterpret_cast<const float4*>(a.bbox)[c];
-    const fa_placement pl = a.place[c];
+    const fa_placement pl = placement_of(a, c, kb);
     const bool r = __ldg(a.rot + c) != 0;
     const DF X = two_sum((float)pl.x, gut), Y = two_sum((float)pl.y, gut);
     const DF wpx = df_mul_f(two_sum(bb.z, -bb.x), a.hx);
@@ -426,7 +444,8 @@ fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, u
 fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H, float ratio,
                     const int32_t* tri_chart, const fa_charts* ch,
                     const fa_placement* place, const fa_pack_result* res, uint32_t atlas_log2,
-                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s, const float* Mdev) {
+                    uint32_t n_scales, float* uv, float* affine, cudaStream_t s, const float* Mdev,
+                    bool from_candidates) {
   UvArgs a;
   a.M = M;
   a.Mdev = Mdev;
@@ -450,6 +469,19 @@ fa_status launch_uv(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
   a.uv = uv;
   a.affine = affine;
   a.ctr = ctx->ctr;
+  a.cand_xy = nullptr;
+  a.cand_rec = nullptr;
+  a.pos_of = nullptr;
+  a.place_out = nullptr;
+  a.xy_stride = a.rec_stride = 0;
+  if (from_candidates) {  // the frame path: no separate placement kernel
+    a.cand_xy = ctx->pack.xy;
+    a.cand_rec = ctx->pack.rec8;
+    a.xy_stride = ctx->pack.max_boxes;
+    a.rec_stride = (size_t)ctx->pack.max_chunks * kChunk;
+    a.pos_of = ctx->pack.ord_rank;
+    a.place_out = const_cast<fa_placement*>(place);
+  }
   mark(ctx, "k_uv", s);
   if (Mdev)
     launch_k(k_uv<true>, grid_for(mesh->T, 256, 152 * 8), 256, 0, s, a);
