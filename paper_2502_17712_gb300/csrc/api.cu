@@ -93,7 +93,7 @@ void fa_destroy(fa_ctx* ctx) {
   if (ctx->prof_on)
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
-  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->bigbits, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
                   ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
@@ -136,7 +136,6 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   if (st == FA_OK) st = alloc(&ptr, (size_t)(n));
   FA_ALLOC(ctx->ctr, 1);
   FA_ALLOC(ctx->zbuf, (uint64_t)c.max_width * c.max_height);
-  FA_ALLOC(ctx->bigbits, (T + 31) / 32);
   FA_ALLOC(ctx->queue, ctx->queue_cap);
   ctx->tile_cap = 4u * ctx->queue_cap;
   FA_ALLOC(ctx->tile_owner, ctx->tile_cap);

@@ -277,57 +277,81 @@ __device__ __forceinline__ uint32_t chart_of_root(const uint32_t* blockcnt, cons
 }
 
 // In-place exclusive scans of the per-block counts a[0..n) and, when given,
-// b[0..n) (one 1024-thread block, both in the same pass); the totals go to a[n],
-// b[n], *ta and *tb.
+// b[0..n) (one 1024-thread block, both at once): thread t owns the `per` consecutive
+// entries from t per (per a multiple of 4, so whole groups move as 16-byte vectors);
+// one block scan of the owners' sums.  The totals go to a[n], b[n], *ta and *tb.
+__device__ __forceinline__ uint4 load4(const uint32_t* a, uint32_t i, uint32_t n) {
+  if (i + 4u <= n) return __ldcg(reinterpret_cast<const uint4*>(a + i));
+  return make_uint4(i < n ? a[i] : 0u, i + 1u < n ? a[i + 1] : 0u, i + 2u < n ? a[i + 2] : 0u,
+                    i + 3u < n ? a[i + 3] : 0u);
+}
+__device__ __forceinline__ void store4(uint32_t* a, uint32_t i, uint32_t n, uint4 v) {
+  if (i + 4u <= n) {
+    *reinterpret_cast<uint4*>(a + i) = v;
+    return;
+  }
+  if (i < n) a[i] = v.x;
+  if (i + 1u < n) a[i + 1] = v.y;
+  if (i + 2u < n) a[i + 2] = v.z;
+}
+__device__ __forceinline__ uint4 excl4(uint4 v, uint32_t& run) {
+  const uint4 o = make_uint4(run, run + v.x, run + v.x + v.y, run + v.x + v.y + v.z);
+  run += v.x + v.y + v.z + v.w;
+  return o;
+}
 __device__ void scan_counts(uint32_t* a, uint32_t* b, uint32_t n, uint32_t* ta, uint32_t* tb) {
   __shared__ uint2 warp_tot[32];
-  __shared__ uint2 carry;
-  if (threadIdx.x == 0) carry = make_uint2(0u, 0u);
-  __syncthreads();
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (uint32_t base = 0; base < n; base += 1024) {
-    const uint32_t i = base + threadIdx.x;
-    const uint2 v = make_uint2(i < n ? a[i] : 0u, (b && i < n) ? b[i] : 0u);
-    uint2 x = v;
+  const uint32_t per = 4u * ((n + 4095u) / 4096u);
+  const uint32_t i0 = threadIdx.x * per;
+  uint2 v = make_uint2(0u, 0u);
+  uint4 a0 = make_uint4(0u, 0u, 0u, 0u), b0 = a0;  // the first group stays in registers
+  for (uint32_t i = i0; i < i0 + per && i < n; i += 4u) {
+    const uint4 x = load4(a, i, n);
+    v.x += x.x + x.y + x.z + x.w;
+    if (i == i0) a0 = x;
+    if (b) {
+      const uint4 y = load4(b, i, n);
+      v.y += y.x + y.y + y.z + y.w;
+      if (i == i0) b0 = y;
+    }
+  }
+  uint2 x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, x.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, x.y, o);
+    if (lane >= (unsigned)o) {
+      x.x += y0;
+      x.y += y1;
+    }
+  }
+  if (lane == 31) warp_tot[wid] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    uint2 t = warp_tot[threadIdx.x];
 #pragma unroll
     for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, x.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, x.y, o);
-      if (lane >= (unsigned)o) {
-        x.x += y0;
-        x.y += y1;
+      const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, t.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, t.y, o);
+      if (threadIdx.x >= (unsigned)o) {
+        t.x += y0;
+        t.y += y1;
       }
     }
-    if (lane == 31) warp_tot[wid] = x;
-    __syncthreads();
-    if (threadIdx.x < 32) {
-      uint2 t = warp_tot[threadIdx.x];
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, t.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, t.y, o);
-        if (threadIdx.x >= (unsigned)o) {
-          t.x += y0;
-          t.y += y1;
-        }
-      }
-      warp_tot[threadIdx.x] = t;
-    }
-    __syncthreads();
-    const uint2 wp = wid ? warp_tot[wid - 1] : make_uint2(0u, 0u);
-    const uint2 cr = carry;
-    if (i < n) {
-      a[i] = cr.x + wp.x + x.x - v.x;
-      if (b) b[i] = cr.y + wp.y + x.y - v.y;
-    }
-    __syncthreads();
-    if (threadIdx.x == 1023) carry = make_uint2(cr.x + wp.x + x.x, cr.y + wp.y + x.y);
-    __syncthreads();
+    warp_tot[threadIdx.x] = t;
   }
-  if (threadIdx.x == 0) {
-    a[n] = carry.x;
-    *ta = carry.x;
+  __syncthreads();
+  const uint2 wp = wid ? warp_tot[wid - 1] : make_uint2(0u, 0u);
+  uint32_t ra = wp.x + x.x - v.x, rb = wp.y + x.y - v.y;
+  for (uint32_t i = i0; i < i0 + per && i < n; i += 4u) {
+    store4(a, i, n, excl4(i == i0 ? a0 : load4(a, i, n), ra));
+    if (b) store4(b, i, n, excl4(i == i0 ? b0 : load4(b, i, n), rb));
+  }
+  if (threadIdx.x == 1023) {
+    a[n] = wp.x + x.x;
+    *ta = wp.x + x.x;
     if (b) {
-      b[n] = carry.y;
-      *tb = carry.y;
+      b[n] = wp.y + x.y;
+      *tb = wp.y + x.y;
     }
   }
   __syncthreads();

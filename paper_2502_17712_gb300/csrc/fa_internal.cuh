@@ -102,7 +102,6 @@ struct fa_ctx {
   // scratch
   fa::DevCounters* ctr;
   uint32_t* zbuf;        // [max_w * max_h]
-  uint32_t* bigbits;     // [ceil(max_tris/32)]
   fa::BigTri* queue;     // [queue_cap]
   uint32_t queue_cap;
   uint32_t* tile_owner;  // [tile_cap] queue record of each 16x16 tile

@@ -353,11 +353,13 @@ __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackA
 // Row push of one candidate per CTA, then the last CTA selects.  The chunks' push
 // records and segment lists are staged into shared memory by bulk asynchronous
 // copies, two chunks in flight; every row segment is processed box-parallel (a
-// group of 32 .. 1 threads per box, by the segment's box count): resting height =
+// group of 32 .. 4 threads per box in segments of at most 256 boxes, else one
+// thread per box): resting height =
 // max of the frontline under the box, then the frontline takes the box top, one
 // barrier per segment.  Segments of one row never overlap in x, so a row may span
 // two chunks.
 constexpr int kPushThreads = 1024;
+constexpr uint32_t kGroupBoxes = 256;  // rows with more boxes take a thread per box
 constexpr uint32_t kStageBytes = kChunk * 8u + kSegStride * 2u;  // records + segment list
 static_assert(kStageBytes % 16u == 0u, "bulk copies move multiples of 16 bytes");
 constexpr unsigned long long kWaitNs = 1000000000ull;  // a second
@@ -475,22 +477,29 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
           const uint32_t j0 = min((uint32_t)s_sg[1 + sgi], kChunk), j1 = min((uint32_t)s_sg[2 + sgi], kChunk);
           const uint32_t nbx = j1 > j0 ? j1 - j0 : 0u;
           bool bad = false;
-          if (nbx > (uint32_t)kPushThreads) {
-            // a thread per box, several boxes per thread
+          if (nbx > kGroupBoxes) {
+            // a thread per box (several boxes per thread past 1024).  Boxes of such rows
+            // are mostly a few texels wide: the first four texels are read with
+            // independent loads before any is used, the rest in a loop.
             for (uint32_t jj = tid; jj < nbx; jj += kPushThreads) {
               const uint2 r = s_rec[j0 + jj];
               const uint32_t xr = r.x & 0xFFFFu, w = r.x >> 16, h = r.y & 0x7FFFFFFFu;
-              const uint32_t x = (r.y >> 31) ? xr : Om - xr - w;
-              uint32_t mx = 0;
-              for (uint32_t u = 0; u < w; ++u) mx = max(mx, F[x + u]);
-              const uint32_t top = mx + h;
-              for (uint32_t u = 0; u < w; ++u) F[x + u] = top;
-              xy[base + j0 + jj] = make_uint2(x, mx);
+              uint32_t* Fx = F + ((r.y >> 31) ? xr : Om - xr - w);
+              uint32_t m0 = w > 0u ? Fx[0] : 0u;
+              const uint32_t m1 = w > 1u ? Fx[1] : 0u, m2 = w > 2u ? Fx[2] : 0u, m3 = w > 3u ? Fx[3] : 0u;
+              for (uint32_t u = 4; u < w; ++u) m0 = max(m0, Fx[u]);
+              const uint32_t mx = max(max(m0, m1), max(m2, m3)), top = mx + h;
+              if (w > 0u) Fx[0] = top;
+              if (w > 1u) Fx[1] = top;
+              if (w > 2u) Fx[2] = top;
+              if (w > 3u) Fx[3] = top;
+              for (uint32_t u = 4; u < w; ++u) Fx[u] = top;
+              xy[base + j0 + jj] = make_uint2((uint32_t)(Fx - F), mx);
               Hloc = max(Hloc, top);
               bad |= top > Om;
             }
           } else {
-            // a group of g threads per box, g = 32 for <= 32 boxes ... 1 for > 512:
+            // a group of g threads per box, g = 32 for <= 32 boxes ... 4 for > 128:
             // 1024 / g >= nbx, so every box has a group.  A box's group reads and then
             // writes only that box's texels, which no other box of the row touches.
             const int lgb = nbx > 1 ? 32 - __clz(nbx - 1) : 0;  // ceil(log2(nbx))

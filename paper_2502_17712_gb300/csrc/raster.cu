@@ -680,51 +680,9 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   }
 }
 
-// Marking pass over the candidate list: a record is visible when one of its samples
-// has key <= the depth buffer; visible bits are OR-ed per VT word and warp.
-__global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
-  pdl_wait();
-  __shared__ uint32_t pre[kMaxFrontBlocks + 1];
-  if (__ldcg(&A.ctr->status) != 0) return;
-  const uint32_t ns = surv_prefix(A, pre);
-  const uint32_t nc = min(__ldcg(&A.ctr->ncand), A.cand_cap - A.clip_base);
-  const uint32_t n = ns + nc;  // survivor records, then the clipped-path records
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
-    const uint32_t k = base + threadIdx.x;
-    bool vis = false;
-    uint32_t t = 0xFFFFFFFFu;
-    if (k < n) {
-      const uint32_t i = k < ns ? surv_slot(A, pre, k, base + (threadIdx.x & ~31u)) : A.clip_base + (k - ns);
-      const float4* s = reinterpret_cast<const float4*>(A.cand + i);
-      const float4 fb = __ldcs(s + 1);
-      const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
-      if (b0 != 0xFFFFFFFFu) {
-        const float4 fa = __ldcs(s), fc = __ldcs(s + 2);
-        const SV a{__float_as_int(fa.x), __float_as_int(fa.y), fc.x};
-        const SV b{__float_as_int(fa.z), __float_as_int(fa.w), fc.y};
-        const SV c{__float_as_int(fb.x), __float_as_int(fb.y), fc.z};
-        t = __float_as_uint(fc.w);
-        const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
-        const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
-        vis = A.cons ? raster_rect<2>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
-                                      (int)(b1 >> 16), A.zbuf, A.W)
-                     : raster_rect<1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
-                                      (int)(b1 >> 16), A.zbuf, A.W);
-      }
-    }
-    const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
-    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, word);
-    const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << (t & 31)) : 0u);
-    if (vis && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicOr(A.vt + word, bits);
-  }
-}
-
-// Large sub-triangles: one warp per 16x16 tile of a queued record.
+// Large sub-triangles: one warp per 16x16 tile of a queued record (grid-stride).
 template <int PASS>
-__global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
-  pdl_wait();
-  if (PASS >= 1 && __ldcg(&A.ctr->status) != 0) return;
+__device__ __forceinline__ void big_tiles(const RasterArgs& A) {
   const uint32_t lane = threadIdx.x & 31;
   const uint64_t warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const uint64_t nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -764,6 +722,54 @@ __global__ void __launch_bounds__(256) k_raster_big(RasterArgs A) {
       if (__any_sync(0xFFFFFFFFu, vis) && lane == 0) atomicOr(A.vt + (q.tri >> 5), 1u << (q.tri & 31));
     }
   }
+}
+
+// Marking pass: first the tiles of the large sub-triangles, then the candidate
+// list (a record is visible when one of its samples has key <= the depth buffer;
+// visible bits are OR-ed per VT word and warp).  One launch for both, so blocks
+// that finish their share of the tiles early take candidate records.
+template <bool CONS>
+__global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
+  pdl_wait();
+  __shared__ uint32_t pre[kMaxFrontBlocks + 1];
+  if (__ldcg(&A.ctr->status) != 0) return;
+  big_tiles<CONS ? 2 : 1>(A);
+  const uint32_t ns = surv_prefix(A, pre);
+  const uint32_t nc = min(__ldcg(&A.ctr->ncand), A.cand_cap - A.clip_base);
+  const uint32_t n = ns + nc;  // survivor records, then the clipped-path records
+  const uint32_t stride = gridDim.x * blockDim.x;
+  for (uint32_t base = blockIdx.x * blockDim.x; base < n; base += stride) {
+    const uint32_t k = base + threadIdx.x;
+    bool vis = false;
+    uint32_t t = 0xFFFFFFFFu;
+    if (k < n) {
+      const uint32_t i = k < ns ? surv_slot(A, pre, k, base + (threadIdx.x & ~31u)) : A.clip_base + (k - ns);
+      const float4* s = reinterpret_cast<const float4*>(A.cand + i);
+      const float4 fb = __ldcs(s + 1);
+      const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
+      if (b0 != 0xFFFFFFFFu) {
+        const float4 fa = __ldcs(s), fc = __ldcs(s + 2);
+        const SV a{__float_as_int(fa.x), __float_as_int(fa.y), fc.x};
+        const SV b{__float_as_int(fa.z), __float_as_int(fa.w), fc.y};
+        const SV c{__float_as_int(fb.x), __float_as_int(fb.y), fc.z};
+        t = __float_as_uint(fc.w);
+        const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
+        const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
+        vis = raster_rect<CONS ? 2 : 1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
+                                        (int)(b1 >> 16), A.zbuf, A.W);
+      }
+    }
+    const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
+    const uint32_t peers = __match_any_sync(0xFFFFFFFFu, word);
+    const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << (t & 31)) : 0u);
+    if (vis && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicOr(A.vt + word, bits);
+  }
+}
+
+// Depth pre-pass of the large sub-triangles.
+__global__ void __launch_bounds__(256) k_raster_depth_big(RasterArgs A) {
+  pdl_wait();
+  big_tiles<0>(A);
 }
 
 }  // namespace
@@ -818,14 +824,12 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   else
     launch_k(k_raster_exact<false>, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_depth_big", s);
-  launch_k(k_raster_big<0>, gb, 256, 0, s, A);
+  launch_k(k_raster_depth_big, gb, 256, 0, s, A);
   mark(ctx, "k_raster_mark", s);
-  launch_k(k_raster_mark, 152 * 8, 256, 0, s, A);
-  mark(ctx, "k_raster_mark_big", s);
   if (cons)
-    launch_k(k_raster_big<2>, gb, 256, 0, s, A);
+    launch_k(k_raster_mark<true>, 152 * 8, 256, 0, s, A);
   else
-    launch_k(k_raster_big<1>, gb, 256, 0, s, A);
+    launch_k(k_raster_mark<false>, 152 * 8, 256, 0, s, A);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
