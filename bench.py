@@ -140,19 +140,39 @@ class Clocks:
 
 
 # algorithmic (compulsory) bytes per launch, by kernel
-def algorithmic_bytes(kernel, T, V, W, H, T_vis, C):
+def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
+    """Compulsory bytes of one launch.  `work` holds the frame's work counts
+    (fa_frame_stats_read): the raster's survivor, clipped-record and large-triangle
+    counts size the kernels after the front end."""
     vt = (T + 31) // 32 * 4
+    w = work or {}
+    n_surv, n_rec = w.get("survivors", 0), w.get("clip_records", 0)
+    n_big, n_tiles = w.get("big_entries", 0), w.get("big_tiles", 0)
+    n_blocks = (T + 1023) // 1024
     table = {
         # read indices + positions once; write the survivors (id + clip coordinates)
         "k_raster_front": 12 * T + 12 * V,
         "k_clear": 4 * W * H + vt,
+        # read each survivor (id + clip coordinates), write its 48-byte record, the
+        # depth buffer written once
+        "k_raster_exact": (4 + 48 + 48) * n_surv + 4 * W * H,
+        # read the queue records and tile owners
+        "k_raster_depth_big": 64 * n_big + 4 * n_tiles,
+        # read every record (survivors, clipped path, queue + owners), the depth
+        # buffer read once, VT written once
+        "k_raster_mark": 48 * (n_surv + n_rec) + 64 * n_big + 4 * n_tiles + 4 * W * H + vt,
+        # per chart: box + full flag read, footprint + rotation written, rank written
+        "k_order_tile": C * (16 + 4 + 12 + 4),
+        # per chart: rank + footprint read, order, sorted footprint and position written
+        "k_order_scatter": C * (4 + 8 + 4 + 8 + 4),
+        # two count arrays read and written
+        "k_scan_blocks": 2 * 2 * 4 * n_blocks,
         "k_uf_local": vt + 12 * T_vis + 4 * T_vis,
         "k_uf_hook": vt + 12 * T_vis + 8 * T_vis,
         "k_uf_flatten": vt + 8 * T_vis,
         "k_tri_chart": vt + 4 * T + 8 * T_vis,
         "k_bbox": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis,
         "k_uv": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis + 24 * T_vis,
-        "k_number": vt + 4 * T_vis,
         # per candidate: read the push record (8 B) and write the resting position (8 B)
         "k_pack_push": 64 * 16 * C,
         # per candidate: read the sorted footprint (8 B) and write the push record (8 B)
@@ -419,6 +439,7 @@ def run_ours(a):
     launches_per_frame = ctx.launches - n0
     C = int(bufs.count[0])
     T_vis = int(np.unpackbits(bufs.vt.cpu().numpy().view(np.uint8)).sum())
+    work = ctx.frame_stats()
 
     # one frame captured as a CUDA graph (the library is allocation- and sync-free);
     # the timed graph records no trace events, a second traced graph gives the
@@ -532,7 +553,7 @@ def run_ours(a):
     roof = None
     if dom:
         avg_ms = tot[dom] / len(per_kernel[dom])
-        ab = algorithmic_bytes(dom, sc.T, sc.V, W, H, T_vis, C)
+        ab = algorithmic_bytes(dom, sc.T, sc.V, W, H, T_vis, C, work)
         traffic = measured_traffic(dom)
         if ab is not None:
             ach = ab / (avg_ms * 1e-3) / 1e9
@@ -549,7 +570,8 @@ def run_ours(a):
             "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "triangles": sc.T, "vertices": sc.V,
-                       "visible_triangles": T_vis, "charts": C, "cuda_graph": graph is not None,
+                       "visible_triangles": T_vis, "charts": C, "raster_survivors": work["survivors"],
+                       "large_subtriangles": work["big_entries"], "cuda_graph": graph is not None,
                        "l2": "flushed between steps (256 MiB write), outside the step events",
                        "parallelism": f"replicas x{world}"},
             "gpu_launches": launches_per_frame * a.steps,

@@ -325,6 +325,22 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out);
  * host-side counter; used to report launches per frame). */
 uint64_t fa_launch_count(const fa_ctx* ctx);
 
+/* Work counts of the last frame (or fa_visibility / fa_chartify call) on this
+ * context, read from its device counters after synchronizing `stream`.  They
+ * describe how much work the data-dependent kernels had (the benchmark derives
+ * their compulsory bytes from them) and change no result.
+ * Errors: FA_E_INVALID_ARG (NULL ctx or out), FA_E_CUDA. */
+typedef struct fa_frame_stats {
+  uint32_t survivors;     /* triangles that passed the raster front end */
+  uint32_t clipped;       /* of those, triangles that needed clipping */
+  uint32_t clip_records;  /* small sub-triangle records of the clipping path */
+  uint32_t big_entries;   /* large sub-triangles queued for tile rasterization */
+  uint64_t big_tiles;     /* their 16x16 tiles */
+  uint32_t visible;       /* entries of the visible-triangle list */
+  uint32_t charts;        /* charts of the last chart pass */
+} fa_frame_stats;
+fa_status fa_frame_stats_read(fa_ctx* ctx, fa_stream_t stream, fa_frame_stats* out);
+
 /* Per-kernel tracing (the paper times its stages per frame, App. B "Timing
  * Methodology"; here every kernel of a public call gets a slot).  When enabled,
  * each public call records a CUDA event on `stream` before each of its kernels

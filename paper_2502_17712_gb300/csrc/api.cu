@@ -141,11 +141,11 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->tile_owner, ctx->tile_cap);
   // survivor regions (one per raster front block, each rounded up to 512 slots) and
   // then the clipped-path candidate records
-  ctx->surv_cap = (uint32_t)(T + 608ull * 512ull);
+  ctx->surv_cap = (uint32_t)(T + (uint64_t)fa::kMaxFrontBlocks * 512ull);
   ctx->cand_cap = ctx->surv_cap + 65536u;
   if (st == FA_OK) st = alloc((unsigned char**)&ctx->cand, (size_t)ctx->cand_cap * 48);
   FA_ALLOC(ctx->surv, ctx->surv_cap);
-  FA_ALLOC(ctx->surv_count, 608);
+  FA_ALLOC(ctx->surv_count, fa::kMaxFrontBlocks);
   if (st == FA_OK) st = alloc((float4**)&ctx->surv_clip, (size_t)ctx->surv_cap * 3);
   FA_ALLOC(ctx->clip, T);
   FA_ALLOC(ctx->label, T + V);
@@ -403,6 +403,28 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {
 }
 
 uint64_t fa_launch_count(const fa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fa_status fa_frame_stats_read(fa_ctx* ctx, fa_stream_t stream, fa_frame_stats* out) {
+  if (!ctx || !out) return FA_E_INVALID_ARG;
+  DeviceGuard g(ctx->device);
+  const cudaStream_t s = (cudaStream_t)stream;
+  fa::DevCounters c{};
+  uint32_t per[fa::kMaxFrontBlocks] = {};
+  const uint32_t nb = ctx->front_blocks < fa::kMaxFrontBlocks ? ctx->front_blocks : fa::kMaxFrontBlocks;
+  FA_CUDA_TRY(cudaMemcpyAsync(&c, ctx->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
+  if (nb) FA_CUDA_TRY(cudaMemcpyAsync(per, ctx->surv_count, nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  FA_CUDA_TRY(cudaStreamSynchronize(s));
+  fa_frame_stats r{};
+  for (uint32_t i = 0; i < nb; ++i) r.survivors += per[i];
+  r.clipped = c.nclip;
+  r.clip_records = c.ncand;
+  r.big_entries = (uint32_t)(c.big >> 40);
+  r.big_tiles = c.big & ((1ull << 40) - 1);
+  r.visible = c.n_vis;
+  r.charts = c.chart_count;
+  *out = r;
+  return FA_OK;
+}
 
 fa_status fa_profile_enable(fa_ctx* ctx, int enable) {
   if (!ctx) return FA_E_INVALID_ARG;

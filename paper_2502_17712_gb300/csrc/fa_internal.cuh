@@ -23,13 +23,14 @@ constexpr uint32_t kLoopCap = 1u << 24;  // device iteration cap (FA_E_TIMEOUT)
 // ----------------------------------------------------------------- device state
 
 // Small counters that live in device memory (one struct per context).
+constexpr uint32_t kMaxFrontBlocks = 152 * 4;  // raster front-end blocks (survivor regions)
+
 struct DevCounters {
   int32_t status;          // sticky fa_status of the context
   uint32_t pad0;
   unsigned long long big;  // big-triangle queue: entries << 40 | tiles
   uint32_t pack_done;      // candidate CTAs finished (last one selects)
   uint32_t ncand;          // small sub-triangles recorded by the depth pre-pass
-  uint32_t nsurv;          // triangles that passed the raster front end
   uint32_t nclip;          // triangles that need clipping
   uint32_t order_tiles;    // tiles of the current order pass
   uint32_t chart_count;    // scratch copy of the frame's chart count
@@ -94,6 +95,7 @@ struct fa_ctx {
   fa_config cfg;
   int device;
   uint64_t launches;
+  uint32_t front_blocks;  // raster front-end blocks of the last visibility pass
   // per-kernel event trace of the last public call (fa_profile_enable)
   int prof_on;
   int prof_n;

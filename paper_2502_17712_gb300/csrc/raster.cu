@@ -213,7 +213,6 @@ struct CandTri {
 static_assert(sizeof(CandTri) == 48, "CandTri is 48 bytes");
 
 constexpr int kFrontThreads = 512;
-constexpr uint32_t kMaxFrontBlocks = 152 * 4;
 
 struct RasterArgs {
   Mat4 M;
@@ -458,7 +457,6 @@ __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __res
     if (reset_status) ctr->status = 0;
     ctr->big = 0ull;
     ctr->ncand = 0u;
-    ctr->nsurv = 0u;
     ctr->nclip = 0u;
   }
   uint4* z4 = reinterpret_cast<uint4*>(zbuf);
@@ -802,6 +800,7 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
     A.surv_per_block = iters * kFrontThreads;
   }
   A.clip_base = A.front_blocks * A.surv_per_block;
+  ctx->front_blocks = A.front_blocks;
   A.surv_clip = reinterpret_cast<float4*>(ctx->surv_clip);
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;

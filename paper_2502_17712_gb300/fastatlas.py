@@ -46,7 +46,7 @@ EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh
            "fa_batch_destroy", "fa_batch_mesh_register", "fa_batch_set_schedule", "fa_batch_get_schedule",
            "fa_atlas_batch", "fa_batch_tune", "fa_batch_launch_count", "fa_server_create", "fa_server_destroy",
            "fa_server_session_open", "fa_server_session_close", "fa_server_submit", "fa_server_poll",
-           "fa_server_stats", "fa_server_now_ms"]
+           "fa_server_stats", "fa_server_now_ms", "fa_frame_stats_read"]
 
 FA_BATCH_ROUND_ROBIN, FA_BATCH_LONGEST_FIRST = 0, 1
 
@@ -83,6 +83,12 @@ class fa_frame_out(ctypes.Structure):
                 ("charts", fa_charts), ("order", ctypes.c_void_p), ("place", ctypes.c_void_p),
                 ("result", ctypes.c_void_p), ("uv", ctypes.c_void_p), ("affine", ctypes.c_void_p),
                 ("partial", ctypes.c_void_p)]
+
+
+class fa_frame_stats(ctypes.Structure):
+    _fields_ = [("survivors", ctypes.c_uint32), ("clipped", ctypes.c_uint32), ("clip_records", ctypes.c_uint32),
+                ("big_entries", ctypes.c_uint32), ("big_tiles", ctypes.c_uint64), ("visible", ctypes.c_uint32),
+                ("charts", ctypes.c_uint32)]
 
 
 class fa_server_done(ctypes.Structure):
@@ -173,6 +179,8 @@ def load(path: str = LIB_PATH):
     lib.fa_last_device_status.restype = st
     lib.fa_launch_count.argtypes = [P]
     lib.fa_launch_count.restype = ctypes.c_uint64
+    lib.fa_frame_stats_read.argtypes = [P, P, ctypes.POINTER(fa_frame_stats)]
+    lib.fa_frame_stats_read.restype = st
     lib.fa_profile_enable.argtypes = [P, ctypes.c_int]
     lib.fa_profile_enable.restype = st
     lib.fa_profile_read.argtypes = [P, ctypes.c_int, ctypes.POINTER(ctypes.c_float),
@@ -299,6 +307,13 @@ def fa_launch_count(ctx) -> int:
     return load().fa_launch_count(ctx)
 
 
+def fa_frame_stats_read(ctx, stream=None) -> dict:
+    """Work counts of the last frame on the context (synchronizes the stream)."""
+    r = fa_frame_stats()
+    _check(load().fa_frame_stats_read(ctx, _stream(stream), ctypes.byref(r)), "fa_frame_stats_read")
+    return {f: int(getattr(r, f)) for f, _ in fa_frame_stats._fields_}
+
+
 def fa_profile_enable(ctx, enable: bool):
     _check(load().fa_profile_enable(ctx, 1 if enable else 0), "fa_profile_enable")
 
@@ -340,6 +355,9 @@ class Context:
     @property
     def launches(self) -> int:
         return fa_launch_count(self.handle)
+
+    def frame_stats(self, stream=None) -> dict:
+        return fa_frame_stats_read(self.handle, stream)
 
 
 class Mesh:

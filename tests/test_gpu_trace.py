@@ -1,0 +1,67 @@
+"""Per-kernel tracing and the work counts of a frame, through the C ABI.
+
+The traced frame is the documented launch sequence; every kernel in it has a
+compulsory-bytes entry in the benchmark's roofline table; the work counts agree
+with the outputs (visible triangles, charts) and with the oracle's visibility.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+from paper_2502_17712_gb300 import scenes as S
+
+pytestmark = pytest.mark.gpu
+
+FRAME_KERNELS = ["k_clear", "k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark",
+                 "k_uf_local", "k_uf_hook", "k_uf_flatten", "k_scan_blocks", "k_tri_chart", "k_bbox",
+                 "k_order_tile", "k_order_scatter", "k_pack_scan", "k_pack_push", "k_uv"]
+
+
+@pytest.fixture(scope="module")
+def F():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.fail("CUDA GPU required for -m gpu tests")
+    from paper_2502_17712_gb300 import build, fastatlas
+    build.build()
+    fastatlas.load()
+    return fastatlas
+
+
+def test_trace_and_work_counts(F):
+    import torch
+    import bench
+    # ~500-pixel triangles: the queued tile rasterizer has work too
+    sc = S.grid_scene(7)
+    W, H = 1920, 1080
+    M = S.spline_cameras(7, 5, W, H)[2]
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 15, max_width=W, max_height=H,
+                    max_atlas_log2=11)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts)
+    F.fa_profile_enable(ctx.handle, True)
+    n0 = ctx.launches
+    F.atlas_frame(ctx, mesh, bufs, M, W, H, 1.0, 11, 0)
+    trace = F.fa_profile_read(ctx.handle)
+    torch.cuda.synchronize()
+    assert ctx.device_status() == 0
+    names = [n for n, _ in trace]
+    assert names == FRAME_KERNELS
+    assert ctx.launches - n0 == len(FRAME_KERNELS)
+    assert all(ms >= 0.0 for _, ms in trace)
+
+    work = ctx.frame_stats()
+    vt = bufs.vt.cpu().numpy().view(np.uint32)
+    assert (vt == O.visibility(M, sc.pos, sc.idx, W, H)).all()
+    T_vis = int(np.unpackbits(vt.view(np.uint8)).sum())
+    C = int(bufs.count[0])
+    assert work["visible"] == T_vis
+    assert work["charts"] == C
+    # a visible triangle passed the front end, directly or through the clipping path
+    assert 0 < T_vis <= work["survivors"] + work["clipped"] <= sc.T
+    assert work["big_entries"] > 0 and work["big_tiles"] >= work["big_entries"]
+    for n in names:
+        assert bench.algorithmic_bytes(n, sc.T, sc.V, W, H, T_vis, C, work) is not None, n
+    F.fa_profile_enable(ctx.handle, False)
+    mesh.close()
+    ctx.close()
