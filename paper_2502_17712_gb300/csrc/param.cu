@@ -319,10 +319,18 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
   const float gut = (float)a.gutter;
 
   const uint32_t kb = k - 1u;
+  // the last blocks take the charts, the others the visible triangles, so that no
+  // thread waits on both chains of dependent loads
+  // (a one-block grid does both)
+  const bool per_chart = a.affine || a.place_out;
+  const uint32_t chart_blocks = (per_chart && a.uv && gridDim.x >= 2u) ? max(gridDim.x / 8u, 1u) : 0u;
+  const uint32_t tri_blocks = gridDim.x - chart_blocks;
   // per chart: the placement (frame path) and the affine (uv = A . ndc + b)
-  if (a.affine || a.place_out) {
+  if (per_chart && (chart_blocks == 0u || blockIdx.x >= tri_blocks)) {
     const uint32_t C = min(__ldcg(a.count), a.max_charts);
-    for (uint32_t c = blockIdx.x * blockDim.x + threadIdx.x; c < C; c += gridDim.x * blockDim.x) {
+    const uint32_t c0 = (chart_blocks ? blockIdx.x - tri_blocks : blockIdx.x) * blockDim.x + threadIdx.x;
+    const uint32_t cstride = (chart_blocks ? chart_blocks : gridDim.x) * blockDim.x;
+    for (uint32_t c = c0; c < C; c += cstride) {
       const fa_placement pl = placement_of(a, c, kb);
       if (a.place_out) a.place_out[c] = pl;
       if (!a.affine) continue;
@@ -348,10 +356,10 @@ __global__ void __launch_bounds__(256) k_uv(UvArgs a) {
       }
     }
   }
-  if (!a.uv) return;
+  if (!a.uv || blockIdx.x >= tri_blocks) return;
   const uint32_t n = __ldcg(&a.ctr->n_vis);
   const uint32_t C = min(__ldcg(a.count), a.max_charts);
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += tri_blocks * blockDim.x) {
     const uint2 e = __ldcg(a.vis + i);
     const uint32_t t = e.x;
     const int32_t c = (int32_t)e.y;
