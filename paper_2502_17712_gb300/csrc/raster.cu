@@ -177,10 +177,77 @@ __device__ __forceinline__ bool sample(const Edges& E, const int64_t* e, const S
 
 // Visit the samples of a sub-triangle over pixel rect [px0..px1] x [py0..py1],
 // stepping the edge functions.  PASS 1 returns true at the first visible sample.
+// sample() on edge values held exactly as floats (integers below 2^24), PASS 0 or 1.
+template <int PASS>
+__device__ __forceinline__ bool sample_f(float e0, float e1, float e2, const bool* tl, float z0, float z1,
+                                         float z2, float invA, uint32_t* __restrict__ z) {
+  const bool in = (e0 > 0.0f || (e0 == 0.0f && tl[0])) && (e1 > 0.0f || (e1 == 0.0f && tl[1])) &&
+                  (e2 > 0.0f || (e2 == 0.0f && tl[2]));
+  if (!in) return false;
+  float s = __fmul_rn(e0, z0);
+  s = __fadd_rn(s, __fmul_rn(e1, z1));
+  s = __fadd_rn(s, __fmul_rn(e2, z2));
+  const float d = __fmul_rn(s, invA);
+  if (!(d >= -1.0f && d <= 1.0f)) return false;
+  const uint32_t key = ordered(d);
+  if (PASS == 0) {
+    atomicMin(z, key);  // result unused: a fire-and-forget reduction
+    return false;
+  }
+  return key <= __ldcg(z);
+}
+
+// raster_rect for boxes whose edge values all stay below 2^24 in magnitude (checked
+// by the caller): those integers are exact in fp32, so the edge functions are kept
+// and stepped as floats (every sum is again such an integer, hence exact), the
+// coverage tests compare the same values and the depth multiplies the same
+// correctly rounded conversions as sample() does: the same samples and keys, with
+// no 64-bit arithmetic or conversion per sample.  PASS 0 or 1.
+template <int PASS>
+__device__ __forceinline__ bool raster_rect_f32(const Edges& E, const SV& a, const SV& b, const SV& c, float invA,
+                                                int px0, int py0, int px1, int py1, uint32_t* __restrict__ zbuf,
+                                                int W) {
+  float er[3], fdx[3], fdy[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) {
+    er[i] = (float)(int32_t)E.e[i];
+    fdx[i] = (float)(int32_t)E.dx[i];
+    fdy[i] = (float)(int32_t)E.dy[i];
+  }
+  bool vis = false;  // PASS 1: no early exit, so the depth loads can overlap
+  for (int py = py0; py <= py1; ++py) {
+    float e0 = er[0], e1 = er[1], e2 = er[2];
+    uint32_t* zrow = zbuf + (size_t)py * W;
+#pragma unroll 2
+    for (int px = px0; px <= px1; ++px) {
+      vis |= sample_f<PASS>(e0, e1, e2, E.tl, a.zn, b.zn, c.zn, invA, zrow + px);
+      e0 = __fadd_rn(e0, fdx[0]);
+      e1 = __fadd_rn(e1, fdx[1]);
+      e2 = __fadd_rn(e2, fdx[2]);
+    }
+    er[0] = __fadd_rn(er[0], fdy[0]);
+    er[1] = __fadd_rn(er[1], fdy[1]);
+    er[2] = __fadd_rn(er[2], fdy[2]);
+  }
+  return vis;
+}
+
 template <int PASS>
 __device__ bool raster_rect(const SV& a, const SV& b, const SV& c, float invA, int px0, int py0,
                             int px1, int py1, uint32_t* __restrict__ zbuf, int W) {
   const Edges E = edges_at(a, b, c, px0, py0);
+  if (PASS != 2 && px1 >= px0 && py1 >= py0) {
+    // |E| over the box <= |E(px0, py0)| + |dx| (px1 - px0) + |dy| (py1 - py0)
+    bool small = true;
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      const int64_t ax = E.dx[i] < 0 ? -E.dx[i] : E.dx[i], ay = E.dy[i] < 0 ? -E.dy[i] : E.dy[i];
+      const int64_t ae = E.e[i] < 0 ? -E.e[i] : E.e[i];
+      small = small && ax < (1ll << 24) && ay < (1ll << 24) &&
+              ae + ax * (int64_t)(px1 - px0) + ay * (int64_t)(py1 - py0) < (1ll << 24);
+    }
+    if (small) return raster_rect_f32<PASS>(E, a, b, c, invA, px0, py0, px1, py1, zbuf, W);
+  }
   const float zmin = fminf(a.zn, fminf(b.zn, c.zn)), zmax = fmaxf(a.zn, fmaxf(b.zn, c.zn));
   int64_t er[3] = {E.e[0], E.e[1], E.e[2]};
   bool vis = false;  // PASS 1: no early exit, so the depth loads can overlap
