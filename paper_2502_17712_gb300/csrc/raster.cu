@@ -225,6 +225,7 @@ __device__ __forceinline__ bool raster_rect_f32(const Edges& E, const SV& a, con
       e1 = __fadd_rn(e1, fdx[1]);
       e2 = __fadd_rn(e2, fdx[2]);
     }
+    if (PASS == 1 && vis) break;
     er[0] = __fadd_rn(er[0], fdy[0]);
     er[1] = __fadd_rn(er[1], fdy[1]);
     er[2] = __fadd_rn(er[2], fdy[2]);
