@@ -221,6 +221,7 @@ __device__ __forceinline__ bool raster_rect_f32(const Edges& E, const SV& a, con
 #pragma unroll 2
     for (int px = px0; px <= px1; ++px) {
       vis |= sample_f<PASS>(e0, e1, e2, E.tl, a.zn, b.zn, c.zn, invA, zrow + px);
+      if (PASS == 1 && vis) break;
       e0 = __fadd_rn(e0, fdx[0]);
       e1 = __fadd_rn(e1, fdx[1]);
       e2 = __fadd_rn(e2, fdx[2]);
