@@ -768,6 +768,8 @@ __device__ __forceinline__ void big_tiles(const RasterArgs& A) {
     const uint32_t ty_n = (uint32_t)((py1 - py0 + kBigTile) / kBigTile);
     const uint64_t local = g - q.tile0;
     if (local >= (uint64_t)tx_n * ty_n) continue;
+    // marking: another tile of the sub-triangle may have marked its triangle already
+    if (PASS >= 1 && ((__ldcg(A.vt + (q.tri >> 5)) >> (q.tri & 31)) & 1u)) continue;
     const int bx = px0 + (int)(local % tx_n) * kBigTile, by = py0 + (int)(local / tx_n) * kBigTile;
     SV a{q.X[0], q.Y[0], q.zn[0]}, b{q.X[1], q.Y[1], q.zn[1]}, c{q.X[2], q.Y[2], q.zn[2]};
     const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
@@ -781,6 +783,7 @@ __device__ __forceinline__ void big_tiles(const RasterArgs& A) {
     for (int py = py_first; py < by + kBigTile; py += 32 / kBigTile) {
       if (px <= px1 && py <= py1)
         vis |= sample<PASS>(E, e, a, b, c, invA, A.zbuf + (size_t)py * A.W + px, zmin, zmax);
+      if (PASS >= 1 && __any_sync(0xFFFFFFFFu, vis)) break;
       e[0] += E.dy[0] * (32 / kBigTile);
       e[1] += E.dy[1] * (32 / kBigTile);
       e[2] += E.dy[2] * (32 / kBigTile);
