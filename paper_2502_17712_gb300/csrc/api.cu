@@ -94,7 +94,7 @@ void fa_destroy(fa_ctx* ctx) {
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
   void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
-                  ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt,
+                  ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt, ctx->tile_flag, ctx->tile_list,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
   for (void* p : ptrs)
@@ -154,6 +154,8 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->viscnt, nblocks + 1);
   FA_ALLOC(ctx->xedge, nblocks * 3072);
   FA_ALLOC(ctx->xcnt, nblocks);
+  FA_ALLOC(ctx->tile_flag, nblocks);
+  FA_ALLOC(ctx->tile_list, nblocks);
   FA_ALLOC(ctx->vis, T);
   FA_ALLOC(ctx->box_enc, 4 * C);
   FA_ALLOC(ctx->box_full, C);
@@ -335,7 +337,8 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s, Md,
                               (p->flags & FA_VIS_CONSERVATIVE) != 0)) != FA_OK)
     return st;
-  if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s)) != FA_OK)
+  if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s,
+                            true)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators
   // the footprints are computed by the first order kernel

@@ -72,6 +72,7 @@ struct UfArgs {
   int32_t* label;
   uint2* xedge;    // per tile: the edges (t, n > t) of its visible triangles that leave it
   uint32_t* xcnt;  // per tile: their count
+  const uint32_t* tile_list;  // tiles with a visible triangle (count in ctr->n_vtiles)
   DevCounters* ctr;
 };
 
@@ -96,11 +97,11 @@ __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
   return cur;
 }
 
-__global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
-  pdl_wait();
+// One tile (all threads of the block; the caller separates tiles by a barrier).
+__device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
   __shared__ int32_t lab[kTile];
   __shared__ uint32_t vis[kTile / 32];
-  const uint32_t base = blockIdx.x * kTile;
+  const uint32_t base = tile * kTile;
   uint32_t v = 0;
   if (threadIdx.x < kTile / 32) {
     const uint32_t w = (base >> 5) + threadIdx.x;
@@ -110,11 +111,11 @@ __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
   __shared__ uint32_t s_xc;
   if (threadIdx.x == 0) s_xc = 0;
   if (!__syncthreads_or(v != 0u)) {  // no visible triangle in this tile
-    if (threadIdx.x == 0) a.xcnt[blockIdx.x] = 0;
+    if (threadIdx.x == 0) a.xcnt[tile] = 0;
     return;
   }
   volatile int32_t* vl = lab;
-  uint2* xe = a.xedge + (size_t)blockIdx.x * kXCap;
+  uint2* xe = a.xedge + (size_t)tile * kXCap;
   // start from the smallest visible neighbour inside the tile (Alg. 1, first loop)
   int32_t nb[kTile / kLocalThreads][3];
 #pragma unroll
@@ -167,7 +168,23 @@ __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
     while ((nx = vl[r]) != r) r = nx;
     a.label[base + i] = (int32_t)base + r;
   }
-  if (threadIdx.x == 0) a.xcnt[blockIdx.x] = s_xc;  // all appends precede the last barrier
+  if (threadIdx.x == 0) a.xcnt[tile] = s_xc;  // all appends precede the last barrier
+}
+
+// Every tile (a block each), or only the tiles that the marking pass listed (a
+// persistent grid over the list).
+template <bool LIST>
+__global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
+  pdl_wait();
+  if (!LIST) {
+    local_tile(a, blockIdx.x);
+    return;
+  }
+  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    __syncthreads();  // the shared memory of the previous tile is free
+    local_tile(a, __ldcg(a.tile_list + i));
+  }
 }
 
 __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
@@ -179,14 +196,24 @@ __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
 // Hooking (Alg. 1, second loop), edge mode: the edges that leave a tile, each once
 // from its lower end, when the other end is visible too (edges inside a tile were
 // joined by k_uf_local).  One block per tile.
-__global__ void __launch_bounds__(128) k_uf_hook(UfArgs a) {
-  pdl_wait();
-  const uint32_t n = min(__ldcg(a.xcnt + blockIdx.x), kXCap);
-  const uint2* xe = a.xedge + (size_t)blockIdx.x * kXCap;
+__device__ __forceinline__ void hook_tile(const UfArgs& a, uint32_t tile) {
+  const uint32_t n = min(__ldcg(a.xcnt + tile), kXCap);
+  const uint2* xe = a.xedge + (size_t)tile * kXCap;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     const uint2 e = __ldcg(xe + i);
     if (e.y < a.T && vt_bit(a.vt, e.y)) unite(a.label, (int32_t)e.x, (int32_t)e.y, a.ctr);
   }
+}
+
+template <bool LIST>
+__global__ void __launch_bounds__(128) k_uf_hook(UfArgs a) {
+  pdl_wait();
+  if (!LIST) {
+    hook_tile(a, blockIdx.x);
+    return;
+  }
+  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) hook_tile(a, __ldcg(a.tile_list + i));
 }
 
 // Vertex mode: every visible triangle joins its three vertex nodes T + v.
@@ -224,9 +251,8 @@ __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* n
 
 // Flatten visible triangles to their root and count roots per block of
 // kPerBlock triangles: warp w of the block owns VT words w, w + 8, w + 16, w + 24.
-__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt, uint32_t* viscnt,
-                                                       uint2* wordroots) {
-  pdl_wait();
+__device__ __forceinline__ void flatten_tile(const UfArgs& a, uint32_t tile, uint32_t* blockcnt,
+                                             uint32_t* viscnt, uint2* wordroots) {
   __shared__ uint32_t wc[kPerBlock / 32], vcnt[kBlock / 32];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
@@ -234,7 +260,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* block
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
     const uint32_t wl = k * (kBlock / 32) + wid;
-    const uint32_t w = blockIdx.x * (kPerBlock / 32) + wl;
+    const uint32_t w = tile * (kPerBlock / 32) + wl;
     const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
     vis += __popc(word);
     bool root = false;
@@ -253,7 +279,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* block
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
     const uint32_t wl = k * (kBlock / 32) + wid;
-    const uint32_t w = blockIdx.x * (kPerBlock / 32) + wl;
+    const uint32_t w = tile * (kPerBlock / 32) + wl;
     if (lane == 0 && w < nwords) {
       uint32_t pre = 0;
       for (uint32_t i = 0; i < wl; ++i) pre += wc[i];
@@ -264,8 +290,25 @@ __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* block
     uint32_t s = 0, v = 0;
     for (int i = 0; i < kPerBlock / 32; ++i) s += wc[i];
     for (int i = 0; i < kBlock / 32; ++i) v += vcnt[i];
-    blockcnt[blockIdx.x] = s;
-    viscnt[blockIdx.x] = v;
+    blockcnt[tile] = s;
+    viscnt[tile] = v;
+  }
+}
+
+// Every counting block (a block each), or only the tiles that the marking pass
+// listed (a persistent grid; the clear zeroed the counts of the others).
+template <bool LIST>
+__global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt, uint32_t* viscnt,
+                                                       uint2* wordroots) {
+  pdl_wait();
+  if (!LIST) {
+    flatten_tile(a, blockIdx.x, blockcnt, viscnt, wordroots);
+    return;
+  }
+  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    __syncthreads();  // the shared memory of the previous tile is free
+    flatten_tile(a, __ldcg(a.tile_list + i), blockcnt, viscnt, wordroots);
   }
 }
 
@@ -489,7 +532,8 @@ __global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wo
 }  // namespace
 
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
-                          int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch, cudaStream_t s) {
+                          int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch, cudaStream_t s,
+                          bool tile_list) {
   UfArgs a;
   a.vt = vt;
   a.idx = mesh->idx;
@@ -499,6 +543,7 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   a.label = ctx->label;
   a.xedge = ctx->xedge;
   a.xcnt = ctx->xcnt;
+  a.tile_list = ctx->tile_list;
   a.ctr = ctx->ctr;
   const int vm = mode == FA_CHARTS_VERTEX;
   const unsigned gw = grid_for((uint64_t)((mesh->T + 31) / 32) * 32, kBlock, 152 * 16);
@@ -506,20 +551,30 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
     mark(ctx, "k_uf_init_v", s);
     launch_k(k_uf_init_v, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, ctx->label, mesh->T, mesh->V);
   }
+  const uint32_t ntiles = (mesh->T + kTile - 1) / kTile;
   mark(ctx, "k_uf_local", s);
-  launch_k(k_uf_local, (mesh->T + kTile - 1) / kTile, kLocalThreads, 0, s, a);
+  if (tile_list)
+    launch_k(k_uf_local<true>, ntiles < 152u * 2u ? ntiles : 152u * 2u, kLocalThreads, 0, s, a);
+  else
+    launch_k(k_uf_local<false>, ntiles, kLocalThreads, 0, s, a);
   mark(ctx, "k_uf_hook", s);
   if (vm)
     launch_k(k_uf_hook_v, gw, kBlock, 0, s, a);
+  else if (tile_list)
+    launch_k(k_uf_hook<true>, ntiles < 152u * 8u ? ntiles : 152u * 8u, 128, 0, s, a);
   else
-    launch_k(k_uf_hook, (mesh->T + kTile - 1) / kTile, 128, 0, s, a);
+    launch_k(k_uf_hook<false>, ntiles, 128, 0, s, a);
   if (!vm && mesh->n_nm) {
     mark(ctx, "k_uf_hook_nm", s);
     launch_k(k_uf_hook_nm, grid_for(mesh->n_nm, 256), 256, 0, s, a, mesh->nm_off, mesh->nm_list, mesh->n_nm);
   }
   const uint32_t nb = (mesh->T + kPerBlock - 1) / kPerBlock;
   mark(ctx, "k_uf_flatten", s);
-  launch_k(k_uf_flatten, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->viscnt, ctx->wordroots);
+  if (tile_list)
+    launch_k(k_uf_flatten<true>, nb < 152u * 8u ? (nb ? nb : 1u) : 152u * 8u, kBlock, 0, s, a, ctx->blockcnt,
+             ctx->viscnt, ctx->wordroots);
+  else
+    launch_k(k_uf_flatten<false>, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->viscnt, ctx->wordroots);
   mark(ctx, "k_scan_blocks", s);
   launch_k(k_scan_blocks, 1, 1024, 0, s, ctx->blockcnt, ctx->viscnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts,
            ctx->ctr);

@@ -37,6 +37,7 @@ struct DevCounters {
   uint32_t n_groups[kMaxScales];
   uint32_t pack_item;      // next (candidate, chunk) item of the width scan
   uint32_t n_vis;          // entries of the visible-triangle list
+  uint32_t n_vtiles;       // 1024-triangle tiles with a visible triangle (listed by the marking pass)
 };
 
 // One queued (large) sub-triangle of the raster: snapped vertices, depths and its
@@ -104,6 +105,8 @@ struct fa_ctx {
   // scratch
   fa::DevCounters* ctr;
   uint32_t* zbuf;        // [max_w * max_h]
+  uint32_t* tile_flag;   // [ceil(max_tris / 1024)] tile has a visible triangle (this frame)
+  uint32_t* tile_list;   // [ceil(max_tris / 1024)] those tiles, in the order the marking found them
   fa::BigTri* queue;     // [queue_cap]
   uint32_t queue_cap;
   uint32_t* tile_owner;  // [tile_cap] queue record of each 16x16 tile
@@ -322,9 +325,12 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                             uint32_t H, uint32_t* vt, bool reset_status, cudaStream_t s,
                             const float* Mdev = nullptr, bool conservative = false);
+// tile_list: the marking pass of the same frame listed the tiles with a visible
+// triangle (and the clear zeroed the per-tile counts), so the union-find passes
+// visit only those
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
-                          cudaStream_t s);
+                          cudaStream_t s, bool tile_list = false);
 // launch_parameterize and launch_uv read the context's visible-triangle list (built
 // by chartify, or by launch_vis_list).
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,

@@ -305,6 +305,8 @@ struct RasterArgs {
   uint32_t front_blocks;
   uint32_t clip_base;  // first candidate slot of the clipped path
   float4* surv_clip;  // [T][3] their clip coordinates
+  uint32_t* tile_flag;  // per 1024-triangle tile: listed in tile_list
+  uint32_t* tile_list;
   uint32_t* clip;  // [T] triangles that need clipping
   DevCounters* ctr;
   uint32_t* vt;
@@ -519,14 +521,24 @@ __device__ __forceinline__ Exact exact_setup(const RasterArgs& A, const float4& 
   return E;
 }
 
+// Clears the depth buffer, VT and counters; also the per-tile flags of the visible-tile
+// list and the per-tile root and visible counts (tiles of 1024 triangles) that the
+// chart passes fill only for listed tiles.
 __global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __restrict__ vt, uint32_t nwords,
-                        DevCounters* ctr, int reset_status) {
+                        DevCounters* ctr, int reset_status, uint32_t* __restrict__ tile_flag,
+                        uint32_t* __restrict__ blockcnt, uint32_t* __restrict__ viscnt, uint32_t ntiles) {
   pdl_wait();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     if (reset_status) ctr->status = 0;
     ctr->big = 0ull;
     ctr->ncand = 0u;
     ctr->nclip = 0u;
+    ctr->n_vtiles = 0u;
+  }
+  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ntiles; i += gridDim.x * blockDim.x) {
+    tile_flag[i] = 0u;
+    blockcnt[i] = 0u;
+    viscnt[i] = 0u;
   }
   uint4* z4 = reinterpret_cast<uint4*>(zbuf);
   const uint4 ff = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
@@ -747,6 +759,12 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
   }
 }
 
+// The marking pass lists each 1024-triangle tile in which it marks a triangle, once.
+__device__ __forceinline__ void note_tile(const RasterArgs& A, uint32_t tile) {
+  if (!__ldcg(A.tile_flag + tile) && atomicExch(A.tile_flag + tile, 1u) == 0u)
+    A.tile_list[atomicAdd(&A.ctr->n_vtiles, 1u)] = tile;
+}
+
 // Large sub-triangles: one warp per 16x16 tile of a queued record (grid-stride).
 template <int PASS>
 __device__ __forceinline__ void big_tiles(const RasterArgs& A) {
@@ -789,7 +807,10 @@ __device__ __forceinline__ void big_tiles(const RasterArgs& A) {
       e[2] += E.dy[2] * (32 / kBigTile);
     }
     if (PASS >= 1) {
-      if (__any_sync(0xFFFFFFFFu, vis) && lane == 0) atomicOr(A.vt + (q.tri >> 5), 1u << (q.tri & 31));
+      if (__any_sync(0xFFFFFFFFu, vis) && lane == 0) {
+        atomicOr(A.vt + (q.tri >> 5), 1u << (q.tri & 31));
+        note_tile(A, q.tri >> 10);
+      }
     }
   }
 }
@@ -832,7 +853,10 @@ __global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
     const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, word);
     const uint32_t bits = __reduce_or_sync(peers, vis ? (1u << (t & 31)) : 0u);
-    if (vis && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) atomicOr(A.vt + word, bits);
+    if (vis && (__ffs(peers) - 1) == (int)(threadIdx.x & 31)) {
+      atomicOr(A.vt + word, bits);
+      note_tile(A, word >> 5);
+    }
   }
 }
 
@@ -874,6 +898,8 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.clip_base = A.front_blocks * A.surv_per_block;
   ctx->front_blocks = A.front_blocks;
   A.surv_clip = reinterpret_cast<float4*>(ctx->surv_clip);
+  A.tile_flag = ctx->tile_flag;
+  A.tile_list = ctx->tile_list;
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;
@@ -881,7 +907,7 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   const uint32_t nwords = (mesh->T + 31) / 32;
   mark(ctx, "k_clear", s);
   launch_k(k_clear, grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s, ctx->zbuf, npix, vt, nwords, ctx->ctr,
-           reset_status ? 1 : 0);
+           reset_status ? 1 : 0, ctx->tile_flag, ctx->blockcnt, ctx->viscnt, (mesh->T + 1023) / 1024);
   const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_front", s);
