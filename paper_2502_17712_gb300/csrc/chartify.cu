@@ -143,6 +143,17 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
     lab[i] = l;
   }
   __syncthreads();
+  // the initial labels form trees (every label is a smaller visible neighbour); a few
+  // rounds of pointer jumping make them shallow before the hooking walks them (a
+  // jump only replaces a label by one of its ancestors, so the rounds need no barrier)
+#pragma unroll
+  for (int k = 0; k < kTile / kLocalThreads; ++k) {
+    const uint32_t i = threadIdx.x + k * kLocalThreads;
+    if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
+#pragma unroll 1
+    for (int r = 0; r < 4; ++r) vl[i] = vl[vl[i]];
+  }
+  __syncthreads();
   // hook every in-tile edge once, from its lower end
 #pragma unroll
   for (int k = 0; k < kTile / kLocalThreads; ++k) {
@@ -164,9 +175,9 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
   __syncthreads();
   for (uint32_t i = threadIdx.x; i < kTile; i += kLocalThreads) {
     if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
-    int32_t r = (int32_t)i, nx;
-    while ((nx = vl[r]) != r) r = nx;
-    a.label[base + i] = (int32_t)base + r;
+    // (path halving: the walks of other threads shorten too; the result goes to the
+    // global labels, so no halving write can overwrite it)
+    a.label[base + i] = (int32_t)base + lfind(vl, (int32_t)i);
   }
   if (threadIdx.x == 0) a.xcnt[tile] = s_xc;  // all appends precede the last barrier
 }
