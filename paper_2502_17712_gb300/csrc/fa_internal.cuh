@@ -296,10 +296,16 @@ inline void trace_end(fa_ctx* ctx, cudaStream_t s) {
 }
 
 // Programmatic dependent launch: every per-frame kernel is launched with
-// programmatic stream serialization, so its blocks may be scheduled while the
-// previous kernel drains; each kernel's first statement waits until the previous
-// grid has completed and its writes are visible (a no-op without the attribute).
-__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+// programmatic stream serialization.  Each kernel's first statement lets the next
+// kernel be scheduled as soon as all of this kernel's blocks have started (so the
+// next kernel's blocks take the resources this one leaves and are resident when it
+// ends; none of this kernel's blocks can be kept out by them), then waits until
+// the previous grid has completed and its writes are visible.  Both are no-ops
+// without the attribute.
+__device__ __forceinline__ void pdl_wait() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
 
 bool pdl_enabled();  // FA_PDL=0 in the environment turns it off
 
