@@ -499,8 +499,13 @@ def run_ours(a):
     if st != 0:
         raise RuntimeError(f"device status {st} in the timed region")
 
-    # end to end through the C ABI with host buffers: H2D positions + matrix from
-    # pinned memory, the frame, D2H of the pack result and the placements
+    # end to end through the C ABI with host buffers: every step copies the mesh
+    # positions host -> device from pinned memory (the matrix travels as a kernel
+    # argument), atlases the frame and copies the pack result and the placements
+    # back.  Double-buffered: two registrations of the mesh take turns, so the copy
+    # of step i + 1's positions (on a copy stream) overlaps step i's frame; each
+    # frame is a replay of a graph captured from fa_atlas_frame.  The L2 flush before
+    # each frame is timed by its own events and not counted.
     e2e = None
     if not a.no_e2e:
         h_pos = torch.as_tensor(sc.pos).pin_memory()
@@ -508,27 +513,55 @@ def run_ours(a):
         h_place = torch.empty(max(C, 1), 4, dtype=torch.int32).pin_memory()
         h2d = h_pos.numel() * 4 + 64
         d2h = h_res.numel() * 4 + h_place.numel() * 4
+        mesh_b = F.Mesh(ctx, sc.pos, sc.idx)
+        meshes = (mesh, mesh_b)
+        egraphs = []
+        for m in meshes:
+            torch.cuda.synchronize()
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr):
+                F.atlas_frame(ctx, m, bufs, M, W, H, a.ratio, L, a.mode)
+            egraphs.append(gr)
+        xs = torch.cuda.Stream()
+        copied = [torch.cuda.Event(), torch.cuda.Event()]
+        released = [torch.cuda.Event(), torch.cuda.Event()]
+        n_e = a.steps
+        fl0 = [torch.cuda.Event(enable_timing=True) for _ in range(n_e + 2)]
+        fl1 = [torch.cuda.Event(enable_timing=True) for _ in range(n_e + 2)]
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        for _ in range(2):
-            mesh.pos.copy_(h_pos, non_blocking=True)
-            frame()
-            h_res.copy_(bufs.result, non_blocking=True)
-            h_place.copy_(bufs.place[:max(C, 1)], non_blocking=True)
+
+        def e2e_steps(first, n):
+            for i in range(first, first + n):
+                b = i & 1
+                xs.wait_event(released[b])  # the frame two steps back has read this buffer
+                with torch.cuda.stream(xs):
+                    meshes[b].pos.copy_(h_pos, non_blocking=True)
+                copied[b].record(xs)
+                fl0[i - first].record(stream)
+                flush.fill_(i)
+                fl1[i - first].record(stream)
+                stream.wait_event(copied[b])
+                egraphs[b].replay()
+                released[b].record(stream)
+                h_res.copy_(bufs.result, non_blocking=True)
+                h_place.copy_(bufs.place[:max(C, 1)], non_blocking=True)
+
+        for b in range(2):
+            released[b].record(stream)
+        e2e_steps(0, 2)
         torch.cuda.synchronize()
-        e_ms = 0.0
-        for i in range(a.steps):
-            flush.fill_(i)
-            e0.record(stream)
-            mesh.pos.copy_(h_pos, non_blocking=True)
-            frame()  # the view matrix travels as a kernel argument (64 B)
-            h_res.copy_(bufs.result, non_blocking=True)
-            h_place.copy_(bufs.place[:max(C, 1)], non_blocking=True)
-            e1.record(stream)
-            e1.synchronize()
-            e_ms += e0.elapsed_time(e1)
+        e0.record(stream)
+        e2e_steps(2, n_e)
+        e1.record(stream)
+        e1.synchronize()
+        e_ms = e0.elapsed_time(e1) - sum(fl0[i].elapsed_time(fl1[i]) for i in range(n_e))
         e_ms = max_over_ranks(e_ms)
+        if int(h_res[3]) != 0:
+            raise RuntimeError(f"pack status {int(h_res[3])} in the end-to-end run")
         e2e = {"value": whole_job_rate(world, a.steps, e_ms), "unit": "frames/s", "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h}
+               "d2h_bytes_per_step": d2h,
+               "pipelining": "double-buffered positions: step i+1's copy overlaps step i's frame"}
+        mesh_b.close()
 
     batched = served = None
     if not (a.no_batched and a.no_served):
