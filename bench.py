@@ -150,8 +150,8 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
     n_big, n_tiles = w.get("big_entries", 0), w.get("big_tiles", 0)
     n_blocks = (T + 1023) // 1024
     table = {
-        # read indices + positions once; write the survivors (id + clip coordinates)
-        "k_raster_front": 12 * T + 12 * V,
+        # read indices + positions once; clear the depth buffer and VT
+        "k_raster_front": 12 * T + 12 * V + 4 * W * H + vt,
         "k_clear": 4 * W * H + vt,
         # read each survivor (id + clip coordinates), write its 48-byte record, the
         # depth buffer written once

@@ -93,7 +93,7 @@ void fa_destroy(fa_ctx* ctx) {
   if (ctx->prof_on)
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
-  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip,
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip, ctx->clip_count,
                   ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt, ctx->tile_flag, ctx->tile_list,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
@@ -147,7 +147,8 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(ctx->surv, ctx->surv_cap);
   FA_ALLOC(ctx->surv_count, fa::kMaxFrontBlocks);
   if (st == FA_OK) st = alloc((float4**)&ctx->surv_clip, (size_t)ctx->surv_cap * 3);
-  FA_ALLOC(ctx->clip, T);
+  FA_ALLOC(ctx->clip, ctx->surv_cap);
+  FA_ALLOC(ctx->clip_count, fa::kMaxFrontBlocks);
   FA_ALLOC(ctx->label, T + V);
   FA_ALLOC(ctx->wordroots, (T + 31) / 32);
   FA_ALLOC(ctx->blockcnt, nblocks + 1);
@@ -412,14 +413,19 @@ fa_status fa_frame_stats_read(fa_ctx* ctx, fa_stream_t stream, fa_frame_stats* o
   DeviceGuard g(ctx->device);
   const cudaStream_t s = (cudaStream_t)stream;
   fa::DevCounters c{};
-  uint32_t per[fa::kMaxFrontBlocks] = {};
+  uint32_t per[fa::kMaxFrontBlocks] = {}, perc[fa::kMaxFrontBlocks] = {};
   const uint32_t nb = ctx->front_blocks < fa::kMaxFrontBlocks ? ctx->front_blocks : fa::kMaxFrontBlocks;
   FA_CUDA_TRY(cudaMemcpyAsync(&c, ctx->ctr, sizeof(c), cudaMemcpyDeviceToHost, s));
-  if (nb) FA_CUDA_TRY(cudaMemcpyAsync(per, ctx->surv_count, nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  if (nb) {
+    FA_CUDA_TRY(cudaMemcpyAsync(per, ctx->surv_count, nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+    FA_CUDA_TRY(cudaMemcpyAsync(perc, ctx->clip_count, nb * sizeof(uint32_t), cudaMemcpyDeviceToHost, s));
+  }
   FA_CUDA_TRY(cudaStreamSynchronize(s));
   fa_frame_stats r{};
-  for (uint32_t i = 0; i < nb; ++i) r.survivors += per[i];
-  r.clipped = c.nclip;
+  for (uint32_t i = 0; i < nb; ++i) {
+    r.survivors += per[i];
+    r.clipped += perc[i];
+  }
   r.clip_records = c.ncand;
   r.big_entries = (uint32_t)(c.big >> 40);
   r.big_tiles = c.big & ((1ull << 40) - 1);

@@ -31,7 +31,6 @@ struct DevCounters {
   unsigned long long big;  // big-triangle queue: entries << 40 | tiles
   uint32_t pack_done;      // candidate CTAs finished (last one selects)
   uint32_t ncand;          // small sub-triangles recorded by the depth pre-pass
-  uint32_t nclip;          // triangles that need clipping
   uint32_t order_tiles;    // tiles of the current order pass
   uint32_t chart_count;    // scratch copy of the frame's chart count
   uint32_t n_groups[kMaxScales];
@@ -117,7 +116,8 @@ struct fa_ctx {
   uint32_t* surv_count;  // [608] survivors of each raster front block
   uint32_t surv_cap;
   void* surv_clip;       // [max_tris][3] float4 clip coordinates of the survivors
-  uint32_t* clip;        // [max_tris] triangles to clip
+  uint32_t* clip;        // [surv_cap] triangles to clip, a region per raster front block
+  uint32_t* clip_count;  // [kMaxFrontBlocks] their count per region
   int32_t* label;        // [max_tris + max_verts]
   uint2* wordroots;      // [ceil(max_tris / 32)] per VT word: root bits, roots before it in its block
   uint32_t* blockcnt;    // [n_blocks + 1]

@@ -307,7 +307,12 @@ struct RasterArgs {
   float4* surv_clip;  // [T][3] their clip coordinates
   uint32_t* tile_flag;  // per 1024-triangle tile: listed in tile_list
   uint32_t* tile_list;
-  uint32_t* clip;  // [T] triangles that need clipping
+  uint32_t* clip_count;  // [front_blocks] clipped triangles per region of `clip`
+  uint32_t* blockcnt;    // per-tile counts of the chart passes (cleared here)
+  uint32_t* viscnt;
+  uint32_t ntiles;
+  int reset_status;      // the front end clears the device status word first
+  uint32_t* clip;  // triangles that need clipping, one region per front block like surv
   DevCounters* ctr;
   uint32_t* vt;
 };
@@ -521,42 +526,39 @@ __device__ __forceinline__ Exact exact_setup(const RasterArgs& A, const float4& 
   return E;
 }
 
-// Clears the depth buffer, VT and counters; also the per-tile flags of the visible-tile
-// list and the per-tile root and visible counts (tiles of 1024 triangles) that the
-// chart passes fill only for listed tiles.
-__global__ void k_clear(uint32_t* __restrict__ zbuf, uint32_t n, uint32_t* __restrict__ vt, uint32_t nwords,
-                        DevCounters* ctr, int reset_status, uint32_t* __restrict__ tile_flag,
-                        uint32_t* __restrict__ blockcnt, uint32_t* __restrict__ viscnt, uint32_t ntiles) {
-  pdl_wait();
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (reset_status) ctr->status = 0;
-    ctr->big = 0ull;
-    ctr->ncand = 0u;
-    ctr->nclip = 0u;
-    ctr->n_vtiles = 0u;
-  }
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < ntiles; i += gridDim.x * blockDim.x) {
-    tile_flag[i] = 0u;
-    blockcnt[i] = 0u;
-    viscnt[i] = 0u;
-  }
-  uint4* z4 = reinterpret_cast<uint4*>(zbuf);
-  const uint4 ff = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
-  const uint32_t n4 = n / 4;
-  const uint32_t stride = gridDim.x * blockDim.x;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n4; i += stride) z4[i] = ff;
-  for (uint32_t i = n4 * 4 + blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) zbuf[i] = 0xFFFFFFFFu;
-  for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nwords; i += stride) vt[i] = 0u;
-}
-
 // Depth pre-pass, front end: one thread per triangle; survivors go to a compact list
 // (warp-aggregated appends) so that the exact set-up runs on full warps.
+// Also clears, for the kernels after it, the depth buffer, VT, the counters and the
+// per-tile flags and counts of the visible-tile list (none of which it reads).
 template <bool DEV_M>
-__global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
+__global__ void __launch_bounds__(kFrontThreads, 2) k_raster_front(RasterArgs A) {
   pdl_wait();
   const Mat4 M = DEV_M ? load_mat(A.Mdev) : A.M;
-  __shared__ uint32_t s_count;
-  if (threadIdx.x == 0) s_count = 0;
+  __shared__ uint32_t s_count, s_nclip;
+  if (threadIdx.x == 0) {
+    s_count = 0;
+    s_nclip = 0;
+    if (blockIdx.x == 0) {
+      if (A.reset_status) A.ctr->status = 0;
+      A.ctr->big = 0ull;
+      A.ctr->ncand = 0u;
+      A.ctr->n_vtiles = 0u;
+    }
+  }
+  {
+    const uint32_t gstride = gridDim.x * blockDim.x, g0 = blockIdx.x * blockDim.x + threadIdx.x;
+    const uint32_t npix = (uint32_t)A.W * (uint32_t)A.H, n4 = npix / 4, nwords = (A.T + 31) / 32;
+    uint4* z4 = reinterpret_cast<uint4*>(A.zbuf);
+    const uint4 ff = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu, 0xFFFFFFFFu);
+    for (uint32_t i = g0; i < n4; i += gstride) z4[i] = ff;
+    for (uint32_t i = n4 * 4 + g0; i < npix; i += gstride) A.zbuf[i] = 0xFFFFFFFFu;
+    for (uint32_t i = g0; i < nwords; i += gstride) A.vt[i] = 0u;
+    for (uint32_t i = g0; i < A.ntiles; i += gstride) {
+      A.tile_flag[i] = 0u;
+      A.blockcnt[i] = 0u;
+      A.viscnt[i] = 0u;
+    }
+  }
   __syncthreads();
   const uint32_t lane = threadIdx.x & 31;
   // block b owns survivor slots [b * surv_per_block, (b + 1) * surv_per_block): it sees
@@ -590,21 +592,24 @@ __global__ void __launch_bounds__(kFrontThreads) k_raster_front(RasterArgs A) {
         sc[2] = c[2];
       }
     }
-    if (b2) {  // rare: one global counter
+    if (b2) {  // rare: the block's clipped region, like the survivors'
       uint32_t o = 0;
-      if (lane == 0) o = atomicAdd(&A.ctr->nclip, (uint32_t)__popc(b2));
+      if (lane == 0) o = atomicAdd(&s_nclip, (uint32_t)__popc(b2));
       o = __shfl_sync(0xFFFFFFFFu, o, 0);
-      if (r == 2) A.clip[o + __popc(b2 & ((1u << lane) - 1u))] = t;
+      if (r == 2) A.clip[region + o + __popc(b2 & ((1u << lane) - 1u))] = t;
     }
   }
   __syncthreads();
-  if (threadIdx.x == 0) A.surv_count[blockIdx.x] = s_count;
+  if (threadIdx.x == 0) {
+    A.surv_count[blockIdx.x] = s_count;
+    A.clip_count[blockIdx.x] = s_nclip;
+  }
 }
 
-// Exclusive prefix of the front blocks' survivor counts into shared memory
-// (front_blocks <= kMaxFrontBlocks); returns the total.  Called by every thread of a
-// block of exactly 256 threads.
-__device__ uint32_t surv_prefix(const RasterArgs& A, uint32_t* pre) {
+// Exclusive prefix of the front blocks' per-region counts (survivors or clipped
+// triangles) into shared memory (front_blocks <= kMaxFrontBlocks); returns the
+// total.  Called by every thread of a block of exactly 256 threads.
+__device__ uint32_t region_prefix(const RasterArgs& A, const uint32_t* counts, uint32_t* pre) {
   constexpr uint32_t kPer = (kMaxFrontBlocks + 255) / 256;
   __shared__ uint32_t s_warp[8];
   const uint32_t nb = A.front_blocks, lane = threadIdx.x & 31, w = threadIdx.x >> 5;
@@ -612,7 +617,7 @@ __device__ uint32_t surv_prefix(const RasterArgs& A, uint32_t* pre) {
 #pragma unroll
   for (uint32_t j = 0; j < kPer; ++j) {
     const uint32_t b = threadIdx.x * kPer + j;
-    c[j] = b < nb ? __ldcg(A.surv_count + b) : 0u;
+    c[j] = b < nb ? __ldcg(counts + b) : 0u;
     sum += c[j];
   }
   uint32_t inc = sum;
@@ -640,9 +645,13 @@ __device__ uint32_t surv_prefix(const RasterArgs& A, uint32_t* pre) {
   __syncthreads();
   return tot;
 }
+__device__ __forceinline__ uint32_t surv_prefix(const RasterArgs& A, uint32_t* pre) {
+  return region_prefix(A, A.surv_count, pre);
+}
 
 // Survivor slot of dense index v: block b with pre[b] <= v < pre[b + 1].
-// Survivor slot of dense index v: block b with pre[b] <= v < pre[b + 1].  vfirst <=
+// Slot of dense index v in the front blocks' regions (survivors or clipped
+// triangles, as pre was built): block b with pre[b] <= v < pre[b + 1].  vfirst <=
 // v is the warp's first index, the same in every lane: its search reads the same
 // shared words in all lanes (broadcasts), and a lane searches on its own only when
 // v lies in a later region than vfirst.
@@ -747,10 +756,11 @@ __global__ void __launch_bounds__(256, 4) k_raster_exact(RasterArgs A) {
       }
     }
   }
-  // then the (rare) triangles that need clipping
-  const uint32_t nc = __ldcg(&A.ctr->nclip);
+  // then the (rare) triangles that need clipping, from the front blocks' regions
+  __syncthreads();  // pre is reused
+  const uint32_t nc = region_prefix(A, A.clip_count, pre);
   for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < nc; i += stride) {
-    const uint32_t t = __ldcg(A.clip + i);
+    const uint32_t t = __ldcg(A.clip + surv_slot(A, pre, i, i));
     const uint32_t* f = A.idx + 3 * (size_t)t;
     const Mat4 M = DEV_M ? load_mat(A.Mdev) : A.M;
     const float4 c0 = load_clip(M, A.pos, __ldg(f)), c1 = load_clip(M, A.pos, __ldg(f + 1)),
@@ -900,15 +910,14 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.surv_clip = reinterpret_cast<float4*>(ctx->surv_clip);
   A.tile_flag = ctx->tile_flag;
   A.tile_list = ctx->tile_list;
+  A.clip_count = ctx->clip_count;
+  A.blockcnt = ctx->blockcnt;
+  A.viscnt = ctx->viscnt;
+  A.ntiles = (mesh->T + 1023) / 1024;
+  A.reset_status = reset_status ? 1 : 0;
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;
-  const uint32_t npix = W * H;
-  const uint32_t nwords = (mesh->T + 31) / 32;
-  mark(ctx, "k_clear", s);
-  launch_k(k_clear, grid_for(npix / 4 + 1, 256, 152 * 4), 256, 0, s, ctx->zbuf, npix, vt, nwords, ctx->ctr,
-           reset_status ? 1 : 0, ctx->tile_flag, ctx->blockcnt, ctx->viscnt, (mesh->T + 1023) / 1024);
-  const unsigned g = grid_for((uint64_t)nwords * 32, 256, 152 * 16);
   const unsigned gb = 152 * 8;
   mark(ctx, "k_raster_front", s);
   if (Mdev)

@@ -12,7 +12,7 @@ from paper_2502_17712_gb300 import scenes as S
 
 pytestmark = pytest.mark.gpu
 
-FRAME_KERNELS = ["k_clear", "k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark",
+FRAME_KERNELS = ["k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark",
                  "k_uf_local", "k_uf_hook", "k_uf_flatten", "k_scan_blocks", "k_tri_chart", "k_bbox",
                  "k_order_tile", "k_order_scatter", "k_pack_scan", "k_pack_push", "k_uv"]
 
