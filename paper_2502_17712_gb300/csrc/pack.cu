@@ -227,6 +227,7 @@ __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackA
   __shared__ unsigned long long ws64[32];
   __shared__ uint32_t ws32[32];
   __shared__ uint32_t s_lastw[kScanThreads / 32];
+  __shared__ uint32_t s_wmax[kScanThreads / 32];
   __shared__ uint32_t s_item;
   __shared__ unsigned long long s_prefix;
   if (__ldcg(&p.ctr->status) != 0) return;
@@ -311,32 +312,67 @@ __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackA
     // previous box's width, for the row test of this thread's first box
     uint32_t wprev = __shfl_up_sync(0xFFFFFFFFu, w[kScanPer - 1], 1);
     if (lane == 0) wprev = wid ? s_lastw[wid - 1] : 0u;
-    unsigned long long P = s_prefix + excl;
+    // the thread's boxes in 32-bit arithmetic relative to its first box: row
+    // q0 + (u >> log2 omega) and offset u & (omega - 1) for u = P - q0 omega (u stays
+    // below 2^28: a box is at most 2^24 wide)
+    const unsigned long long P0 = s_prefix + excl;
+    const unsigned long long q0 = P0 >> a.atlas_log2;
+    const uint32_t q0m3 = (uint32_t)(q0 % 3ull);
+    uint32_t u = (uint32_t)(P0 & (om - 1u));
+    // first box: does a row start here (the previous box begins in an earlier row)?
+    bool first_start = j0 == 0 || ((P0 - wprev) >> a.atlas_log2) != q0;
     uint32_t starts = 0, cnt = 0, mo = 0;
     uint2 r8[kScanPer];
 #pragma unroll
     for (int e = 0; e < kScanPer; ++e) {
       r8[e] = make_uint2(0u, 0u);
       if (j0 + e < n) {
-        const unsigned long long q = P >> a.atlas_log2;
-        const uint32_t xr = (uint32_t)(P & (om - 1u));
-        const uint32_t wp = e ? w[e - 1] : wprev;
-        if (j0 + e == 0 || ((P - wp) >> a.atlas_log2) != q) {
+        const uint32_t dq = u >> a.atlas_log2;
+        const uint32_t xr = u & (om - 1u);
+        const bool st = e ? ((u - w[e - 1]) >> a.atlas_log2) != dq : first_start;
+        if (st) {
           starts |= 1u << e;
           ++cnt;
         }
         if (xr + w[e] > om) mo = max(mo, xr + w[e] - om);
         const uint32_t ws = w[e] < 0xFFFFu ? w[e] : 0xFFFFu;
         const uint32_t hs = h[e] < 0x7FFFFFFFu ? h[e] : 0x7FFFFFFFu;
-        r8[e] = make_uint2(xr | (ws << 16), hs | ((q % 3ull == 0ull) ? 0x80000000u : 0u));
+        r8[e] = make_uint2(xr | (ws << 16), hs | (((q0m3 + dq % 3u) % 3u == 0u) ? 0x80000000u : 0u));
       }
-      P += w[e];
+      u += w[e];
     }
     uint4* o4 = reinterpret_cast<uint4*>(p.rec8 + kidx * rstride + base + j0);
 #pragma unroll
     for (int q = 0; q < kScanPer / 2; ++q) o4[q] = make_uint4(r8[2 * q].x, r8[2 * q].y, r8[2 * q + 1].x, r8[2 * q + 1].y);
-    uint32_t nseg;
-    uint32_t at = block_scan_incl<uint32_t>(cnt, ws32, &nseg) - cnt;
+    // one block pass: the exclusive prefix of the row starts and the largest overflow
+    uint32_t x = cnt, mx = mo;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o), z = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
+      if (lane >= (unsigned)o) x += y;
+      mx = max(mx, z);
+    }
+    if (lane == 31) {
+      ws32[wid] = x;
+      s_wmax[wid] = mx;
+    }
+    __syncthreads();
+    if (wid == 0) {
+      const uint32_t nw = kScanThreads / 32;
+      uint32_t t = lane < nw ? ws32[lane] : 0u, m2 = lane < nw ? s_wmax[lane] : 0u;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o), z = __shfl_xor_sync(0xFFFFFFFFu, m2, o);
+        if (lane >= (unsigned)o) t += y;
+        m2 = max(m2, z);
+      }
+      ws32[lane] = t;
+      if (lane == 0) s_wmax[0] = m2;
+    }
+    __syncthreads();
+    const uint32_t nseg = ws32[31];
+    uint32_t at = x - cnt + (wid ? ws32[wid - 1] : 0u);
+    mo = s_wmax[0];
     uint16_t* sg = p.segs + ((size_t)kidx * p.max_chunks + c) * kSegStride;
 #pragma unroll
     for (int e = 0; e < kScanPer; ++e)
@@ -345,7 +381,6 @@ __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackA
       sg[0] = (uint16_t)nseg;
       sg[1 + nseg] = (uint16_t)n;
     }
-    mo = block_max<uint32_t>(mo, ws32);
     if (tid == 0 && mo) atomicMax(p.m + kidx, mo);
   }
 }
