@@ -148,10 +148,11 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
     w = work or {}
     n_surv, n_rec = w.get("survivors", 0), w.get("clip_records", 0)
     n_big, n_tiles = w.get("big_entries", 0), w.get("big_tiles", 0)
+    n_vtiles = w.get("visible_tiles", (T + 1023) // 1024)
     n_blocks = (T + 1023) // 1024
     table = {
-        # read indices + positions once; clear the depth buffer and VT
-        "k_raster_front": 12 * T + 12 * V + 4 * W * H + vt,
+        # read indices + positions once; clear the depth buffer, VT and tri_chart
+        "k_raster_front": 12 * T + 12 * V + 4 * W * H + vt + 4 * T,
         "k_clear": 4 * W * H + vt,
         # read each survivor (id + clip coordinates), write its 48-byte record, the
         # depth buffer written once
@@ -170,7 +171,8 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
         "k_uf_local": vt + 12 * T_vis + 4 * T_vis,
         "k_uf_hook": vt + 12 * T_vis + 8 * T_vis,
         "k_uf_flatten": vt + 8 * T_vis,
-        "k_tri_chart": vt + 4 * T + 8 * T_vis,
+        # the listed tiles: VT words and chart ids, the visible list
+        "k_tri_chart": n_vtiles * (128 + 4096) + 8 * T_vis,
         "k_bbox": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis,
         "k_uv": vt + 4 * T_vis + 12 * T_vis + 36 * T_vis + 24 * T_vis,
         # per candidate: read the push record (8 B) and write the resting position (8 B)

@@ -338,6 +338,7 @@ typedef struct fa_frame_stats {
   uint64_t big_tiles;     /* their 16x16 tiles */
   uint32_t visible;       /* entries of the visible-triangle list */
   uint32_t charts;        /* charts of the last chart pass */
+  uint32_t visible_tiles; /* tiles of 1024 consecutive triangles holding a visible one */
 } fa_frame_stats;
 fa_status fa_frame_stats_read(fa_ctx* ctx, fa_stream_t stream, fa_frame_stats* out);
 

@@ -335,11 +335,14 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   const float* Md = d_view_proj;
   trace_begin(ctx);
   // k_clear (first kernel of the visibility step) also clears the status word
+  // the raster front end also sets tri_chart to -1 (16-byte stores) when it is
+  // 16-byte aligned; the chart-id pass then writes only the listed tiles
+  const bool tri_init = (reinterpret_cast<uintptr_t>(o->tri_chart) & 15u) == 0;
   if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s, Md,
-                              (p->flags & FA_VIS_CONSERVATIVE) != 0)) != FA_OK)
+                              (p->flags & FA_VIS_CONSERVATIVE) != 0, tri_init ? o->tri_chart : nullptr)) != FA_OK)
     return st;
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s,
-                            true)) != FA_OK)
+                            true, tri_init)) != FA_OK)
     return st;
   // k_number of chartify already reset the chart-box accumulators
   // the footprints are computed by the first order kernel
@@ -431,6 +434,7 @@ fa_status fa_frame_stats_read(fa_ctx* ctx, fa_stream_t stream, fa_frame_stats* o
   r.big_tiles = c.big & ((1ull << 40) - 1);
   r.visible = c.n_vis;
   r.charts = c.chart_count;
+  r.visible_tiles = c.n_vtiles;
   *out = r;
   return FA_OK;
 }

@@ -436,7 +436,8 @@ __global__ void __launch_bounds__(1024) k_scan_vis(uint32_t* viscnt, uint32_t nb
 // triangle order: entry = list start of the block + the visible triangles before
 // it.  words[k] is VT word k * 8 + warp of the block.
 __device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / kBlock], uint32_t start,
-                                            const int32_t (&chart)[kPerBlock / kBlock], uint2* vis) {
+                                            const int32_t (&chart)[kPerBlock / kBlock], uint2* vis,
+                                            uint32_t tile) {
   __shared__ uint32_t wpop[kPerBlock / 32];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
@@ -450,7 +451,7 @@ __device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / 
     uint32_t pre = start;
     for (uint32_t i = 0; i < wl; ++i) pre += wpop[i];
     pre += __popc(words[k] & ((1u << lane) - 1u));
-    const uint32_t t = ((blockIdx.x * (kPerBlock / 32) + wl) << 5) + lane;
+    const uint32_t t = ((tile * (kPerBlock / 32) + wl) << 5) + lane;
     vis[pre] = make_uint2(t, (uint32_t)chart[k]);
   }
 }
@@ -458,19 +459,17 @@ __device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / 
 // Chart id of every triangle (-1 invisible; charts numbered by ascending root) and
 // the visible-triangle list (same blocking as k_uf_flatten); each root records
 // itself as its chart's root and resets the chart's box accumulators.
-__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots,
-                                                      int32_t* tri_chart, uint32_t* roots, uint32_t* box_enc,
-                                                      uint32_t* box_full, uint32_t max_charts,
-                                                      const uint32_t* visstart, uint2* vis) {
-  pdl_wait();
-  if (__ldcg(&a.ctr->status) != 0) return;
+__device__ __forceinline__ void chart_tile(const UfArgs& a, uint32_t tile, const uint32_t* blockcnt,
+                                           const uint2* wordroots, int32_t* tri_chart, uint32_t* roots,
+                                           uint32_t* box_enc, uint32_t* box_full, uint32_t max_charts,
+                                           const uint32_t* visstart, uint2* vis) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
   uint32_t words[kPerBlock / kBlock];
   int32_t chart[kPerBlock / kBlock];
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t w = blockIdx.x * (kPerBlock / 32) + k * (kBlock / 32) + wid;
+    const uint32_t w = tile * (kPerBlock / 32) + k * (kBlock / 32) + wid;
     words[k] = w < nwords ? __ldg(a.vt + w) : 0u;
     const uint32_t t = (w << 5) + lane;
     int32_t out = -1;
@@ -487,7 +486,29 @@ __global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const uint32_t* 
     chart[k] = out;
     if (w < nwords && t < a.T) tri_chart[t] = out;
   }
-  put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis);
+  put_visible(words, __ldcg(visstart + tile), chart, vis, tile);
+}
+
+// Every counting block (a block each; invisible triangles get -1), or, when the
+// raster front end already set tri_chart to -1, only the listed tiles (a persistent
+// grid over the list).
+template <bool LIST>
+__global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots,
+                                                      int32_t* tri_chart, uint32_t* roots, uint32_t* box_enc,
+                                                      uint32_t* box_full, uint32_t max_charts,
+                                                      const uint32_t* visstart, uint2* vis) {
+  pdl_wait();
+  if (__ldcg(&a.ctr->status) != 0) return;
+  if (!LIST) {
+    chart_tile(a, blockIdx.x, blockcnt, wordroots, tri_chart, roots, box_enc, box_full, max_charts, visstart, vis);
+    return;
+  }
+  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
+  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+    __syncthreads();  // the shared memory of the previous tile is free
+    chart_tile(a, __ldcg(a.tile_list + i), blockcnt, wordroots, tri_chart, roots, box_enc, box_full, max_charts,
+               visstart, vis);
+  }
 }
 
 // Standalone path: visible counts per block from a caller's tri_chart ...
@@ -523,7 +544,7 @@ __global__ void __launch_bounds__(kBlock) k_vis_fill(const int32_t* tri_chart, u
     chart[k] = t < T ? tri_chart[t] : -1;
     words[k] = __ballot_sync(0xFFFFFFFFu, chart[k] >= 0);
   }
-  put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis);
+  put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis, blockIdx.x);
 }
 
 __global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots, int32_t* vert_chart,
@@ -544,7 +565,7 @@ __global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wo
 
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch, cudaStream_t s,
-                          bool tile_list) {
+                          bool tile_list, bool tri_chart_cleared) {
   UfArgs a;
   a.vt = vt;
   a.idx = mesh->idx;
@@ -590,8 +611,13 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   launch_k(k_scan_blocks, 1, 1024, 0, s, ctx->blockcnt, ctx->viscnt, nb ? nb : 1, ch->count, ctx->cfg.max_charts,
            ctx->ctr);
   mark(ctx, "k_tri_chart", s);
-  launch_k(k_tri_chart, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->wordroots, tri_chart, ch->root,
-           ctx->box_enc, ctx->box_full, ctx->cfg.max_charts, ctx->viscnt, ctx->vis);
+  if (tile_list && tri_chart_cleared)
+    launch_k(k_tri_chart<true>, nb < 152u * 8u ? (nb ? nb : 1u) : 152u * 8u, kBlock, 0, s, a, ctx->blockcnt,
+             ctx->wordroots, tri_chart, ch->root, ctx->box_enc, ctx->box_full, ctx->cfg.max_charts, ctx->viscnt,
+             ctx->vis);
+  else
+    launch_k(k_tri_chart<false>, nb ? nb : 1, kBlock, 0, s, a, ctx->blockcnt, ctx->wordroots, tri_chart, ch->root,
+             ctx->box_enc, ctx->box_full, ctx->cfg.max_charts, ctx->viscnt, ctx->vis);
   if (vert_chart) {
     mark(ctx, "k_vert_chart", s);
     launch_k(k_vert_chart, grid_for(mesh->V, 256, 152 * 8), 256, 0, s, a, ctx->blockcnt, ctx->wordroots,

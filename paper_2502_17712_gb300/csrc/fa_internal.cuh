@@ -330,13 +330,14 @@ inline void launch_k(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t sme
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,
                             uint32_t H, uint32_t* vt, bool reset_status, cudaStream_t s,
-                            const float* Mdev = nullptr, bool conservative = false);
+                            const float* Mdev = nullptr, bool conservative = false,
+                            int32_t* tri_chart_init = nullptr);
 // tile_list: the marking pass of the same frame listed the tiles with a visible
-// triangle (and the clear zeroed the per-tile counts), so the union-find passes
-// visit only those
+// triangle (and the raster front end zeroed the per-tile counts and set tri_chart
+// to -1), so the union-find and chart-id passes visit only those
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch,
-                          cudaStream_t s, bool tile_list = false);
+                          cudaStream_t s, bool tile_list = false, bool tri_chart_cleared = false);
 // launch_parameterize and launch_uv read the context's visible-triangle list (built
 // by chartify, or by launch_vis_list).
 fa_status launch_parameterize(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W,

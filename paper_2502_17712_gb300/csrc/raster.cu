@@ -312,6 +312,7 @@ struct RasterArgs {
   uint32_t* viscnt;
   uint32_t ntiles;
   int reset_status;      // the front end clears the device status word first
+  int32_t* tri_chart;    // when set, the front end sets it to -1 (the chart pass writes visible ones)
   uint32_t* clip;  // triangles that need clipping, one region per front block like surv
   DevCounters* ctr;
   uint32_t* vt;
@@ -557,6 +558,11 @@ __global__ void __launch_bounds__(kFrontThreads, 2) k_raster_front(RasterArgs A)
       A.tile_flag[i] = 0u;
       A.blockcnt[i] = 0u;
       A.viscnt[i] = 0u;
+    }
+    if (A.tri_chart) {
+      int4* t4 = reinterpret_cast<int4*>(A.tri_chart);
+      for (uint32_t i = g0; i < A.T / 4; i += gstride) t4[i] = make_int4(-1, -1, -1, -1);
+      for (uint32_t i = (A.T / 4) * 4 + g0; i < A.T; i += gstride) A.tri_chart[i] = -1;
     }
   }
   __syncthreads();
@@ -879,7 +885,8 @@ __global__ void __launch_bounds__(256) k_raster_depth_big(RasterArgs A) {
 }  // namespace
 
 fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uint32_t W, uint32_t H,
-                            uint32_t* vt, bool reset_status, cudaStream_t s, const float* Mdev, bool cons) {
+                            uint32_t* vt, bool reset_status, cudaStream_t s, const float* Mdev, bool cons,
+                            int32_t* tri_chart_init) {
   RasterArgs A;
   A.cons = cons ? 1 : 0;
   A.Mdev = Mdev;
@@ -915,6 +922,7 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.viscnt = ctx->viscnt;
   A.ntiles = (mesh->T + 1023) / 1024;
   A.reset_status = reset_status ? 1 : 0;
+  A.tri_chart = tri_chart_init;
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;

@@ -88,7 +88,7 @@ class fa_frame_out(ctypes.Structure):
 class fa_frame_stats(ctypes.Structure):
     _fields_ = [("survivors", ctypes.c_uint32), ("clipped", ctypes.c_uint32), ("clip_records", ctypes.c_uint32),
                 ("big_entries", ctypes.c_uint32), ("big_tiles", ctypes.c_uint64), ("visible", ctypes.c_uint32),
-                ("charts", ctypes.c_uint32)]
+                ("charts", ctypes.c_uint32), ("visible_tiles", ctypes.c_uint32)]
 
 
 class fa_server_done(ctypes.Structure):

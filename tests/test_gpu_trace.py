@@ -60,6 +60,10 @@ def test_trace_and_work_counts(F):
     # a visible triangle passed the front end, directly or through the clipping path
     assert 0 < T_vis <= work["survivors"] + work["clipped"] <= sc.T
     assert work["big_entries"] > 0 and work["big_tiles"] >= work["big_entries"]
+    # the tiles of 1024 triangles that hold a visible one, as the marking pass listed them
+    tiles = np.zeros(((sc.T + 1023) // 1024) * 1024, bool)
+    tiles[:sc.T] = np.unpackbits(vt.view(np.uint8), bitorder="little")[:sc.T].astype(bool)
+    assert work["visible_tiles"] == int(tiles.reshape(-1, 1024).any(1).sum())
     for n in names:
         assert bench.algorithmic_bytes(n, sc.T, sc.V, W, H, T_vis, C, work) is not None, n
     F.fa_profile_enable(ctx.handle, False)
