@@ -69,3 +69,33 @@ def test_trace_and_work_counts(F):
     F.fa_profile_enable(ctx.handle, False)
     mesh.close()
     ctx.close()
+
+
+def test_unaligned_tri_chart_output(F):
+    """A tri_chart buffer that is not 16-byte aligned takes the path that writes every
+    triangle's chart id in the chart pass: same outputs as an aligned buffer."""
+    import torch
+    sc, M, p = S.heightfield_frame(2)
+    W, H = p["width"], p["height"]
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 15, max_width=W, max_height=H,
+                    max_atlas_log2=12)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    outs = []
+    for offset in (0, 1):
+        bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts)
+        big = torch.full((sc.T + 4,), 7, dtype=torch.int32, device="cuda")
+        bufs.tri_chart = big[offset:offset + sc.T]
+        assert (bufs.tri_chart.data_ptr() % 16 == 0) == (offset == 0)
+        F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], p["atlas_log2"], 0)
+        torch.cuda.synchronize()
+        assert ctx.device_status() == 0
+        outs.append({k: getattr(bufs, k).cpu().numpy().view(np.uint8).copy()
+                     for k in ("vt", "tri_chart", "root", "order", "place", "result", "uv")})
+        if offset:  # nothing written outside the view
+            assert int(big[0]) == 7 and (big[offset + sc.T:].cpu().numpy() == 7).all()
+    for k in outs[0]:
+        assert np.array_equal(outs[0][k], outs[1][k]), k
+    fr = O.atlas_frame(M, sc.pos, sc.idx, W, H, p["ratio"], p["atlas_log2"])
+    assert (outs[1]["tri_chart"].view(np.int32) == fr.charts.tri_chart).all()
+    mesh.close()
+    ctx.close()
