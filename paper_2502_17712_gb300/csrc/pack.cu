@@ -165,12 +165,15 @@ __global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, con
   if (i >= C) return;
   const uint32_t bin = height_bin(__ldg(fb + i));
   uint32_t pos = binstart[bin] + p.ord_rank[i];
-  uint32_t t = 0;
-  for (; t + 4 <= blockIdx.x; t += 4) {
+  // the bin's boxes in earlier tiles: sixteen independent loads per round
+  for (uint32_t t = 0; t < blockIdx.x; t += 16) {
     const uint32_t* c = p.ord_counts + (size_t)t * kMaxH + bin;
-    pos += __ldcg(c) + __ldcg(c + kMaxH) + __ldcg(c + 2 * kMaxH) + __ldcg(c + 3 * kMaxH);
+    uint32_t q[16];
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j) q[j] = t + j < blockIdx.x ? __ldcg(c + (size_t)j * kMaxH) : 0u;
+#pragma unroll
+    for (uint32_t j = 0; j < 16; ++j) pos += q[j];
   }
-  for (; t < blockIdx.x; ++t) pos += __ldcg(p.ord_counts + (size_t)t * kMaxH + bin);
   if (pos < C) {
     order[pos] = i;
     p.fs[pos] = make_uint2(__ldg(fa + i), __ldg(fb + i));
