@@ -191,9 +191,16 @@ __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
     local_tile(a, blockIdx.x);
     return;
   }
+  // tiles are handed out by a counter, so that a block that drew light tiles takes
+  // more (their costs differ by an order of magnitude)
   const uint32_t n = __ldcg(&a.ctr->n_vtiles);
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
+  __shared__ uint32_t s_i;
+  for (;;) {
     __syncthreads();  // the shared memory of the previous tile is free
+    if (threadIdx.x == 0) s_i = atomicAdd(&a.ctr->uf_item, 1u);
+    __syncthreads();
+    const uint32_t i = s_i;
+    if (i >= n) break;
     local_tile(a, __ldcg(a.tile_list + i));
   }
 }

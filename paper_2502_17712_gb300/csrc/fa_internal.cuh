@@ -37,6 +37,7 @@ struct DevCounters {
   uint32_t pack_item;      // next (candidate, chunk) item of the width scan
   uint32_t n_vis;          // entries of the visible-triangle list
   uint32_t n_vtiles;       // 1024-triangle tiles with a visible triangle (listed by the marking pass)
+  uint32_t uf_item;        // next listed tile of the local union-find
 };
 
 // One queued (large) sub-triangle of the raster: snapped vertices, depths and its

@@ -544,6 +544,7 @@ __global__ void __launch_bounds__(kFrontThreads, 2) k_raster_front(RasterArgs A)
       A.ctr->big = 0ull;
       A.ctr->ncand = 0u;
       A.ctr->n_vtiles = 0u;
+      A.ctr->uf_item = 0u;
     }
   }
   {
