@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--batch-lanes", type=int, default=16)
     ap.add_argument("--no-served", action="store_true", help="skip the 16-session served measurement")
     ap.add_argument("--served-slots", type=int, default=8)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the small-scene latencies, camera path, ratio sweep and packer stress")
     return ap.parse_args()
 
 
@@ -400,6 +402,97 @@ def run_served(a, F, S, torch):
     return out
 
 
+def run_extras(a, F, S, torch):
+    """The small configurations of the scope (reported as latency, they move < 1 MB)
+    and the packer alone:
+    - the 64x64 heightfield at 480x270 into a 1024^2 atlas: one frame per graph
+      replay and per eager launch sequence (stream), 300 frames each;
+    - the same heightfield along the 300-frame camera path at 1920x1080 into a
+      2048^2 atlas: one graph captured from fa_atlas_frame_dev_matrix, replayed with
+      the next camera copied into the device matrix first;
+    - fa_pack on 10^3, 10^4, 10^5 log-normal boxes into a 4096^2 atlas."""
+    import numpy as np
+    out = {}
+    sc, M, p = S.heightfield_frame(1)
+    W, H, L = p["width"], p["height"], p["atlas_log2"]
+    ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 14, max_width=1920, max_height=1080,
+                    max_atlas_log2=12)
+    mesh = F.Mesh(ctx, sc.pos, sc.idx)
+    bufs = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts)
+    stream = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def timed(fn, n=300):
+        for _ in range(5):
+            fn()
+        torch.cuda.synchronize()
+        t = []
+        for _ in range(n):
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(1e3 * e0.elapsed_time(e1))
+        return {"us_p50": _pct(t, 50), "us_p99": _pct(t, 99), "us_mean": float(np.mean(t))}
+
+    gr = torch.cuda.CUDAGraph()
+    for _ in range(2):
+        F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0)
+    torch.cuda.synchronize()
+    with torch.cuda.graph(gr):
+        F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0)
+    out["small_frame"] = {"workload": "heightfield64_480x270_atlas1024_ratio1", "triangles": sc.T,
+                          "graph": timed(gr.replay),
+                          "stream": timed(lambda: F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0))}
+    del gr
+
+    sc2, cams, p2 = S.camera_path_frames(1, 300)
+    mesh2 = F.Mesh(ctx, sc2.pos, sc2.idx)
+    dm = torch.zeros(16, dtype=torch.float32, device="cuda")
+    h_cams = torch.as_tensor(np.stack([np.asarray(c, np.float32).reshape(16) for c in cams])).pin_memory()
+    dm.copy_(h_cams[0])
+    F.atlas_frame_dev_matrix(ctx, mesh2, bufs, dm, p2["width"], p2["height"], p2["ratio"], p2["atlas_log2"])
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr):
+        F.atlas_frame_dev_matrix(ctx, mesh2, bufs, dm, p2["width"], p2["height"], p2["ratio"], p2["atlas_log2"])
+    t = []
+    for i in range(len(cams)):
+        e0.record(stream)
+        dm.copy_(h_cams[i], non_blocking=True)
+        gr.replay()
+        e1.record(stream)
+        e1.synchronize()
+        t.append(1e3 * e0.elapsed_time(e1))
+    out["camera_path"] = {"workload": "heightfield64_spline300_1920x1080_atlas2048_ratio1", "frames": len(cams),
+                          "us_p50": _pct(t, 50), "us_p99": _pct(t, 99), "us_mean": float(np.mean(t)),
+                          "frames_per_s": 1e6 * len(t) / sum(t)}
+    del gr
+    mesh2.close()
+    mesh.close()
+    ctx.close()
+
+    pk = {}
+    pctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1 << 17, max_width=64, max_height=64,
+                     max_atlas_log2=12)
+    for n in (1000, 10000, 100000):
+        fa, fb = S.lognormal_boxes(3, n, mean_texels=6 if n > 5000 else 12)
+        d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+        d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+        cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+        order = torch.zeros(n, dtype=torch.int32, device="cuda")
+        place = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+        res = torch.zeros(5, dtype=torch.int32, device="cuda")
+        r = timed(lambda: F.fa_pack(pctx.handle, d_fa, d_fb, cnt, 12, 64, 0, order, place, res), n=100)
+        rr = res.cpu().numpy().view(np.uint32)
+        r.update({"k": int(rr[0]), "omega": int(rr[1]), "status": int(rr[3])})
+        pk[str(n)] = r
+    pctx.close()
+    out["packer_stress"] = {"workload": "log-normal boxes (mean 12 texels; 6 for 10^4 and 10^5), 4096^2 atlas, "
+                                        "64 scales", "boxes": pk}
+    return out
+
+
 def run_ours(a):
     import numpy as np
     import torch
@@ -578,14 +671,44 @@ def run_ours(a):
                              "result copy overlap step i's frame"}
         mesh_b.close()
 
+    # the other texel-to-pixel ratios of the 1080p scene (same graph replay and L2
+    # flush as the timed loop, 200 steps each)
+    ratios = None
+    if not a.no_extras:
+        ratios = {}
+        for r in (0.5, 1.0, 2.0):
+            rb = F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts)
+            torch.cuda.synchronize()
+            gr = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(gr):
+                F.atlas_frame(ctx, mesh, rb, M, W, H, r, L, a.mode)
+            for _ in range(3):
+                gr.replay()
+            torch.cuda.synchronize()
+            r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            rms = []
+            for i in range(200):
+                flush.fill_(i)
+                r0.record(stream)
+                gr.replay()
+                r1.record(stream)
+                r1.synchronize()
+                rms.append(r0.elapsed_time(r1))
+            res = rb.result.cpu().numpy().view(np.uint32)
+            ratios[str(r)] = {"frames_per_s": 1e3 * len(rms) / sum(rms), "ms_p50": _pct(rms, 50),
+                              "ms_p99": _pct(rms, 99), "k": int(res[0]), "omega": int(res[1]),
+                              "pack_status": int(res[3])}
+            del gr
+
     batched = served = None
-    if not (a.no_batched and a.no_served):
+    if not (a.no_batched and a.no_served and a.no_extras):
         mesh.close()
         ctx.close()
     if not a.no_batched:
         batched = run_batched(a, F, S, torch)
     if not a.no_served:
         served = run_served(a, F, S, torch)
+    extras = None if a.no_extras else run_extras(a, F, S, torch)
 
     if rank != 0:
         if world > 1:
@@ -627,10 +750,28 @@ def run_ours(a):
             "traced_ms_per_frame": traced_ms / n_traced,
             "ms_p50": srt[len(srt) // 2], "ms_p99": srt[min(len(srt) - 1, (99 * len(srt)) // 100)],
             "roofline": roof, "frame_roofline": frame_roof, "e2e": e2e, "clocks": clk}
+    # stages: the paper's columns (its raster runs in the GL pipeline, so the stages
+    # after it are also given together: the frame with the visible set as input)
+    stage_of = {"raster": ("k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark"),
+                "chartify": ("k_uf_local", "k_uf_hook", "k_uf_flatten", "k_scan_blocks", "k_tri_chart"),
+                "parameterize": ("k_bbox",), "pack": ("k_order_tile", "k_order_scatter", "k_pack_scan",
+                                                      "k_pack_push"), "uv": ("k_uv",)}
+    stages = {}
+    for name, ks in list(stage_of.items()) + [("after_visibility", sum(
+            [v for k_, v in stage_of.items() if k_ != "raster"], ()))]:
+        ms = sum(tot[k] / len(per_kernel[k]) for k in ks if k in tot)
+        ab = sum(algorithmic_bytes(k, sc.T, sc.V, W, H, T_vis, C, work) or 0 for k in ks if k in tot)
+        stages[name] = {"ms": ms, "algorithmic_bytes": ab, "achieved_gbs": ab / (ms * 1e-3) / 1e9 if ms else None,
+                        "frac": ab / (ms * 1e-3) / 1e9 / peak if ms else None}
+    line["stages_traced"] = stages
+    if ratios is not None:
+        line["ratios"] = ratios
     if not a.no_batched:
         line["batched"] = batched
     if not a.no_served:
         line["served"] = served
+    if extras is not None:
+        line.update(extras)
     if world == 1 and not a.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(a, sc, M, p)
     print(json.dumps(line), flush=True)
