@@ -402,6 +402,41 @@ def run_served(a, F, S, torch):
     return out
 
 
+def run_in_flight(a, F, sc, M, W, H, L, torch, lanes=4, views=16):
+    """Throughput of the 1080p scene with several frames in flight: the same view
+    atlased `views` times (own outputs each) by one replay of a batch graph over
+    `lanes` contexts, next to the one-frame-at-a-time rate of the main line."""
+    batch = F.Batch(lanes, max_tris=sc.T, max_verts=sc.V, max_charts=1 << 17, max_width=W, max_height=H,
+                    max_atlas_log2=L)
+    bm = F.BatchMesh(batch, sc.pos, sc.idx)
+    params = [F.frame_params(M, W, H, a.ratio, L, a.mode) for _ in range(views)]
+    bufs = [F.FrameBuffers.allocate(bm.T, bm.V, 1 << 17) for _ in range(views)]
+    meshes = [bm] * views
+    F.atlas_batch(batch, meshes, params, bufs)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        F.atlas_batch(batch, meshes, params, bufs)
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t = []
+    for _ in range(20):
+        e0.record()
+        g.replay()
+        e1.record()
+        e1.synchronize()
+        t.append(e0.elapsed_time(e1))
+    ok = all(int(b.result[3]) == 0 for b in bufs)
+    del g
+    bm.close()
+    batch.close()
+    return {"lanes": lanes, "frames_per_replay": views, "ms_per_replay_p50": _pct(t, 50),
+            "frames_per_s": 1e3 * views * len(t) / sum(t), "all_packed": ok,
+            "l2": "not flushed between replays (each replay moves ~1.6 GB, 12x the L2)"}
+
+
 def run_extras(a, F, S, torch):
     """The small configurations of the scope (reported as latency, they move < 1 MB)
     and the packer alone:
@@ -701,9 +736,12 @@ def run_ours(a):
             del gr
 
     batched = served = None
+    in_flight = None
     if not (a.no_batched and a.no_served and a.no_extras):
         mesh.close()
         ctx.close()
+    if not a.no_extras:
+        in_flight = {str(n): run_in_flight(a, F, sc, M, W, H, L, torch, lanes=n) for n in (2, 4, 8)}
     if not a.no_batched:
         batched = run_batched(a, F, S, torch)
     if not a.no_served:
@@ -766,6 +804,8 @@ def run_ours(a):
     line["stages_traced"] = stages
     if ratios is not None:
         line["ratios"] = ratios
+    if in_flight is not None:
+        line["in_flight"] = in_flight
     if not a.no_batched:
         line["batched"] = batched
     if not a.no_served:
