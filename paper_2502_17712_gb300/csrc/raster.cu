@@ -814,8 +814,13 @@ __device__ __forceinline__ void big_tiles(const RasterArgs& A) {
     const int px = bx + (int)(lane % kBigTile), py_first = by + (int)(lane / kBigTile);
     const Edges E = edges_at(a, b, c, px, py_first);
     int64_t e[3] = {E.e[0], E.e[1], E.e[2]};
+    // only the tile's rows inside the box (the last tile row of a box is often
+    // short); the same trip count in every lane
+    const int rows = min(by + kBigTile - 1, py1) - by + 1;
+    const int steps = (rows + 32 / kBigTile - 1) / (32 / kBigTile);
 #pragma unroll 1
-    for (int py = py_first; py < by + kBigTile; py += 32 / kBigTile) {
+    for (int k = 0; k < steps; ++k) {
+      const int py = py_first + k * (32 / kBigTile);
       if (px <= px1 && py <= py1)
         vis |= sample<PASS>(E, e, a, b, c, invA, A.zbuf + (size_t)py * A.W + px, zmin, zmax);
       if (PASS >= 1 && __any_sync(0xFFFFFFFFu, vis)) break;
