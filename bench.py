@@ -17,6 +17,7 @@ the work per GPU is fixed (weak scaling) and there is no collective on the data 
 from __future__ import annotations
 
 import argparse
+import gc
 import json
 import os
 import subprocess
@@ -373,6 +374,8 @@ def run_served(a, F, S, torch):
         t0 = server.now_ms() + 1.0
         lat, nxt, done, last = [], 0, 0, 0.0
         submit_at = {}
+        gc.collect()
+        gc.disable()  # no collector pause inside the latency measurement
         while done < len(reqs):
             now = server.now_ms() - t0
             while nxt < len(reqs) and reqs[nxt][0] <= now:
@@ -384,6 +387,7 @@ def run_served(a, F, S, torch):
                     lat.append(d["done_ms"] - t0 - submit_at.pop(d["ticket"]))
                     done += 1
                     last = d["done_ms"] - t0
+        gc.enable()
         st = server.stats()
         ok = all(int(b.result[3]) == 0 for b in bufs)
         server.close()
