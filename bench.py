@@ -156,7 +156,6 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
     table = {
         # read indices + positions once; clear the depth buffer, VT and tri_chart
         "k_raster_front": 12 * T + 12 * V + 4 * W * H + vt + 4 * T,
-        "k_clear": 4 * W * H + vt,
         # read each survivor (id + clip coordinates), write its 48-byte record, the
         # depth buffer written once
         "k_raster_exact": (4 + 48 + 48) * n_surv + 4 * W * H,

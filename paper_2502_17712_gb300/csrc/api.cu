@@ -334,9 +334,9 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   const Mat4 M = d_view_proj ? Mat4{} : to_mat(p->view_proj);
   const float* Md = d_view_proj;
   trace_begin(ctx);
-  // k_clear (first kernel of the visibility step) also clears the status word
-  // the raster front end also sets tri_chart to -1 (16-byte stores) when it is
-  // 16-byte aligned; the chart-id pass then writes only the listed tiles
+  // the raster front end (first kernel) clears the status word; it also sets
+  // tri_chart to -1 (16-byte stores) when it is 16-byte aligned, and the chart-id
+  // pass then writes only the listed tiles
   const bool tri_init = (reinterpret_cast<uintptr_t>(o->tri_chart) & 15u) == 0;
   if ((st = launch_visibility(ctx, mesh, M, p->width, p->height, o->vt, true, s, Md,
                               (p->flags & FA_VIS_CONSERVATIVE) != 0, tri_init ? o->tri_chart : nullptr)) != FA_OK)
@@ -344,8 +344,8 @@ fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params*
   if ((st = launch_chartify(ctx, mesh, o->vt, p->chart_mode, o->tri_chart, o->vert_chart, &o->charts, s,
                             true, tri_init)) != FA_OK)
     return st;
-  // k_number of chartify already reset the chart-box accumulators
-  // the footprints are computed by the first order kernel
+  // the chart-id pass already reset the chart-box accumulators; the footprints
+  // are computed by the first order kernel
   if ((st = launch_parameterize(ctx, mesh, M, p->width, p->height, p->ratio, o->tri_chart, &o->charts,
                                 false, p->flags, o->partial, s, Md, false)) != FA_OK)
     return st;

@@ -20,7 +20,8 @@
 //   per candidate (k_pack_push) pushes the rows up against a frontline in shared
 //   memory, with the chunks staged by bulk asynchronous copies; segments of one
 //   row never overlap in x, so a row may span two chunks.  The last CTA to finish
-//   selects the candidate; k_pack_place writes the placements with all CTAs.
+//   selects the candidate.  The placements are written by the UV kernel on the frame
+//   path and by k_pack_place (all CTAs) for a standalone packing.
 #include "fa_internal.cuh"
 
 namespace fa {

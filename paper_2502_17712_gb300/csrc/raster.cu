@@ -11,6 +11,14 @@
 //   ((E0 z0 + E1 z1) + E2 z2) * (1/A), kept when -1 <= d <= 1.
 // Sub-triangles whose clamped pixel box has more than kSmallMaxPix pixels are
 // queued (pass 0) and rasterized by a warp per 16x16 tile in a second kernel.
+//
+// Kernels: k_raster_front (the per-triangle front end above; it also clears the
+// per-frame state for the kernels after it), k_raster_exact (the exact set-up of
+// the survivors; small sub-triangles rasterized in-thread, a 48-byte record kept
+// for the marking pass), k_raster_depth_big (the queued tiles) and k_raster_mark
+// (the queued tiles, then the records; it also lists the 1024-triangle tiles that
+// hold a visible triangle for the chart passes).  Edge values that stay below 2^24
+// over a box are stepped as exact fp32 integers.
 #include "fa_internal.cuh"
 
 namespace fa {
