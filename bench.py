@@ -241,9 +241,25 @@ def run_reference(a):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": workload_name(a), "triangles": sc.T, "parallelism": "host, 1 thread"},
             "cpu_baseline": {"value": v, "unit": "frames/s", "cores": 1, "kind": "oracle",
-                             "sample": f"{a.steps} full frames of the workload"},
+                             "sample": f"{a.steps} full frames of the workload", "host": host_info()},
             "e2e": {"value": v, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def host_info():
+    """The host the oracle ran on: logical cores and CPU model."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "processor\t: ")) and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    if ln.lower().startswith("model name"):
+                        break
+    except OSError:
+        pass
+    import platform
+    return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model or platform.processor()}
 
 
 def cpu_baseline(a, sc, M, p):
@@ -257,7 +273,7 @@ def cpu_baseline(a, sc, M, p):
             break
     dt = time.perf_counter() - t0
     return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
-            "sample": f"{n} full frame(s) of the workload, single-threaded oracle"}
+            "sample": f"{n} full frame(s) of the workload, single-threaded oracle", "host": host_info()}
 
 
 def _pct(v, q):
