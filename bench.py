@@ -252,7 +252,7 @@ def host_info():
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
-                if ln.lower().startswith(("model name", "cpu part", "processor\t: ")) and ":" in ln:
+                if ln.lower().startswith(("model name", "cpu part")) and ":" in ln:
                     model = ln.split(":", 1)[1].strip()
                     if ln.lower().startswith("model name"):
                         break
