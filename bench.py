@@ -376,48 +376,63 @@ def run_served(a, F, S, torch):
             out.append((float(arr[i]), s_, F.frame_params(M, W, H, 1.0, log2)))
         return out
 
-    def serve(n_slots, reqs):
+    def serve(n_slots, runs, trials=3):
+        """One server with n_slots slots and the 16 sessions; every request sequence
+        of `runs` is served `trials` times (the host clock of a shared machine has
+        occasional stalls): the trial with the median p99 is reported, with all
+        trials' p99."""
         server = F.Server(n_slots, 64 << 30, **kw)
         bufs = [F.FrameBuffers.allocate(sc.T, sc.V, kw["max_charts"]) for sc in sessions]
         sids = [server.open_session(sc.pos, sc.idx, b) for sc, b in zip(sessions, bufs)]
-        # warm-up: one request per session
-        for sid in sids:
-            server.submit(sid, reqs[0][2])
-        n = 0
-        while n < len(sids):
-            n += len(server.poll())
-        t0 = server.now_ms() + 1.0
-        lat, nxt, done, last = [], 0, 0, 0.0
-        submit_at = {}
-        gc.collect()
-        gc.disable()  # no collector pause inside the latency measurement
-        while done < len(reqs):
-            now = server.now_ms() - t0
-            while nxt < len(reqs) and reqs[nxt][0] <= now:
-                tk = server.submit(sids[reqs[nxt][1]], reqs[nxt][2])
-                submit_at[tk] = reqs[nxt][0]
-                nxt += 1
-            for d in server.poll():
-                if d["ticket"] in submit_at:
-                    lat.append(d["done_ms"] - t0 - submit_at.pop(d["ticket"]))
-                    done += 1
-                    last = d["done_ms"] - t0
-        gc.enable()
+        # warm-up: one request per session and request shape
+        for r in runs:
+            for _, _, prm in r[:8]:
+                for sid in sids:
+                    server.submit(sid, prm)
+                n = 0
+                while n < len(sids):
+                    n += len(server.poll())
+        results = []
+        for reqs in runs:
+            tr = []
+            for _ in range(trials):
+                gc.collect()
+                gc.disable()  # no collector pause inside the latency measurement
+                t0 = server.now_ms() + 1.0  # arrival times count from here
+                lat, nxt, done, last = [], 0, 0, 0.0
+                submit_at = {}
+                while done < len(reqs):
+                    now = server.now_ms() - t0
+                    while nxt < len(reqs) and reqs[nxt][0] <= now:
+                        tk = server.submit(sids[reqs[nxt][1]], reqs[nxt][2])
+                        submit_at[tk] = reqs[nxt][0]
+                        nxt += 1
+                    for d in server.poll():
+                        if d["ticket"] in submit_at:
+                            lat.append(d["done_ms"] - t0 - submit_at.pop(d["ticket"]))
+                            done += 1
+                            last = d["done_ms"] - t0
+                gc.enable()
+                tr.append({"ms_p50": _pct(lat, 50), "ms_p99": _pct(lat, 99), "ms_mean": float(np.mean(lat)),
+                           "requests_per_s": len(reqs) / ((last - reqs[0][0]) * 1e-3)})
+            med = sorted(tr, key=lambda x: x["ms_p99"])[len(tr) // 2]
+            results.append(dict(med, slots=n_slots, p99_trials=[x["ms_p99"] for x in tr]))
         st = server.stats()
         ok = all(int(b.result[3]) == 0 for b in bufs)
         server.close()
-        return {"ms_p50": _pct(lat, 50), "ms_p99": _pct(lat, 99), "ms_mean": float(np.mean(lat)),
-                "requests_per_s": len(reqs) / ((last - reqs[0][0]) * 1e-3), "slots": n_slots,
-                "max_running": st["max_running"], "last_frames_packed": ok}
+        for r in results:
+            r.update(max_running=st["max_running"], last_frames_packed=ok)
+        return results
 
     out = {"workload": "16 sessions of displaced-icosphere scenes (25-200 spheres, 0.5M-4.1M tris), "
                        "Poisson arrivals, views 1280x720 / 1920x1080 / 2560x1440, atlas 2048 or 4096, ratio 1, "
                        "edge charts, 64 scales",
            "triangles_per_session": [int(sc.T) for sc in sessions]}
-    for name, rate, n in (("rate_240_per_s", 240.0, 480), ("rate_4000_per_s", 4000.0, 1200)):
-        reqs = requests(n, rate, int(rate))
-        out[name] = {"offered_per_s": rate, "requests": n,
-                     "continuous_batching": serve(a.served_slots, reqs), "plain": serve(1, reqs)}
+    rates = (("rate_240_per_s", 240.0, 480), ("rate_4000_per_s", 4000.0, 1200))
+    runs = [requests(n, rate, int(rate)) for _, rate, n in rates]
+    cb, plain = serve(a.served_slots, runs), serve(1, runs)
+    for (name, rate, n), c_, p_ in zip(rates, cb, plain):
+        out[name] = {"offered_per_s": rate, "requests": n, "continuous_batching": c_, "plain": p_}
     return out
 
 
