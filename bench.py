@@ -142,6 +142,14 @@ class Clocks:
         return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# the frame's kernels by stage, in launch order (the paper's columns)
+STAGES = {"raster": ("k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark"),
+          "chartify": ("k_uf_local", "k_uf_hook", "k_uf_flatten", "k_scan_blocks", "k_tri_chart"),
+          "parameterize": ("k_bbox",),
+          "pack": ("k_order_tile", "k_order_scatter", "k_pack_scan", "k_pack_push"),
+          "uv": ("k_uv",)}
+
+
 # algorithmic (compulsory) bytes per launch, by kernel
 def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
     """Compulsory bytes of one launch.  `work` holds the frame's work counts
@@ -824,10 +832,7 @@ def run_ours(a):
             "roofline": roof, "frame_roofline": frame_roof, "e2e": e2e, "clocks": clk}
     # stages: the paper's columns (its raster runs in the GL pipeline, so the stages
     # after it are also given together: the frame with the visible set as input)
-    stage_of = {"raster": ("k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark"),
-                "chartify": ("k_uf_local", "k_uf_hook", "k_uf_flatten", "k_scan_blocks", "k_tri_chart"),
-                "parameterize": ("k_bbox",), "pack": ("k_order_tile", "k_order_scatter", "k_pack_scan",
-                                                      "k_pack_push"), "uv": ("k_uv",)}
+    stage_of = STAGES
     stages = {}
     for name, ks in list(stage_of.items()) + [("after_visibility", sum(
             [v for k_, v in stage_of.items() if k_ != "raster"], ()))]:

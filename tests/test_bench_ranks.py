@@ -74,3 +74,24 @@ def test_frame_algorithmic_bytes():
     vert = bench.frame_algorithmic_bytes(T, V, W, H, Tv, C, 1)
     assert edge - vert == 12 * T  # adjacency is read in edge mode only
     assert 0.15e9 < edge < 0.21e9
+
+
+def test_every_frame_kernel_has_compulsory_bytes():
+    import bench
+    T, V, W, H, Tv, C = 4096000, 2048400, 1920, 1080, 262158, 36112
+    work = {"survivors": 509772, "clip_records": 0, "big_entries": 9483, "big_tiles": 15205,
+            "visible_tiles": 811}
+    kernels = [k for ks in bench.STAGES.values() for k in ks]
+    assert len(kernels) == len(set(kernels)) == 15
+    for k in kernels:
+        b = bench.algorithmic_bytes(k, T, V, W, H, Tv, C, work)
+        assert b is not None and b > 0, k
+    # the front end reads the mesh once and clears the per-frame buffers
+    assert bench.algorithmic_bytes("k_raster_front", T, V, W, H, Tv, C, work) == \
+        12 * T + 12 * V + 4 * W * H + (T + 31) // 32 * 4 + 4 * T
+
+
+def test_host_info():
+    import bench
+    h = bench.host_info()
+    assert h["nproc"] >= 1 and isinstance(h["cpu"], str)

@@ -47,6 +47,7 @@ def test_trace_and_work_counts(F):
     assert ctx.device_status() == 0
     names = [n for n, _ in trace]
     assert names == FRAME_KERNELS
+    assert names == [k for ks in bench.STAGES.values() for k in ks]  # the benchmark's stage table
     assert ctx.launches - n0 == len(FRAME_KERNELS)
     assert all(ms >= 0.0 for _, ms in trace)
 
