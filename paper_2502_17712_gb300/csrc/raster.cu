@@ -921,7 +921,9 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   A.cand_cap = ctx->cand_cap;
   A.surv = ctx->surv;
   A.surv_count = ctx->surv_count;
-  A.front_blocks = grid_for(mesh->T, kFrontThreads, kMaxFrontBlocks);
+  // one wave (two resident blocks per SM): half the survivor regions of two waves,
+  // so the passes that look regions up scan fewer counts
+  A.front_blocks = grid_for(mesh->T, kFrontThreads, 152u * 2u);
   {
     const uint32_t iters = (mesh->T + A.front_blocks * kFrontThreads - 1) / (A.front_blocks * kFrontThreads);
     A.surv_per_block = iters * kFrontThreads;
@@ -954,10 +956,11 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
   mark(ctx, "k_raster_depth_big", s);
   launch_k(k_raster_depth_big, gb, 256, 0, s, A);
   mark(ctx, "k_raster_mark", s);
+  // one wave of four resident blocks per SM: each block scans the region counts once
   if (cons)
-    launch_k(k_raster_mark<true>, 152 * 8, 256, 0, s, A);
+    launch_k(k_raster_mark<true>, 152 * 4, 256, 0, s, A);
   else
-    launch_k(k_raster_mark<false>, 152 * 8, 256, 0, s, A);
+    launch_k(k_raster_mark<false>, 152 * 4, 256, 0, s, A);
   FA_CUDA_TRY(cudaGetLastError());
   return FA_OK;
 }
