@@ -95,3 +95,24 @@ def test_host_info():
     import bench
     h = bench.host_info()
     assert h["nproc"] >= 1 and isinstance(h["cpu"], str)
+
+
+def test_reference_arm_line():
+    """The reference arm times the oracle on the host and prints one contract line
+    (small scene here: 10 spheres, 204,800 triangles)."""
+    import json
+    import subprocess
+    import bench
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "2",
+                        "--warmup", "1", "--spheres", "10"], capture_output=True, text=True, timeout=300, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["metric"] == bench.METRIC and d["unit"] == "frames/s"
+    assert d["higher_is_better"] is True and d["steps"] == 2 and d["warmup"] == 1 and d["n_gpus"] == 1
+    assert d["config"]["workload"].startswith("icospheres10_") and d["config"]["triangles"] == 10 * 20480
+    assert d["value"] > 0 and d["ms_per_step"] == pytest.approx(1e3 / d["value"])
+    cb, e2e = d["cpu_baseline"], d["e2e"]
+    assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
+    assert e2e == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
