@@ -270,18 +270,69 @@ def host_info():
     return {"nproc": os.cpu_count(), "machine": platform.machine(), "cpu": model or platform.processor()}
 
 
-def cpu_baseline(a, sc, M, p):
+def cpu_baseline(a, sc, M, p, gpu=None):
+    """The single-threaded oracle timed on the host on the benchmark frame.  When the
+    GPU frame's outputs are given (copied to the host before the timed loop), the
+    last oracle frame is also compared with them: chart ids, chart count, pack
+    result and placements exactly, and the UVs' largest deviation from the fp64
+    oracle (inside the atlas, where the stated bound is 1e-4 texel, and overall)."""
+    import numpy as np
     import oracle as O
     W, H, L = p["width"], p["height"], p["atlas_log2"]
     n, t0 = 0, time.perf_counter()
     while True:
-        O.atlas_frame(M, sc.pos, sc.idx, W, H, a.ratio, L, mode=a.mode)
+        fr = O.atlas_frame(M, sc.pos, sc.idx, W, H, a.ratio, L, mode=a.mode)
         n += 1
         if time.perf_counter() - t0 > 10.0 or n >= 3:
             break
     dt = time.perf_counter() - t0
-    return {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
+    base = {"value": n / dt, "unit": "frames/s", "cores": 1, "kind": "oracle",
             "sample": f"{n} full frame(s) of the workload, single-threaded oracle", "host": host_info()}
+    parity = None
+    if gpu is not None:
+        C = fr.charts.C
+        res = gpu["result"].view(np.uint32)
+        vis = fr.charts.tri_chart >= 0
+        ou, gu = fr.uv[vis], gpu["uv"].astype(np.float64)[vis]
+        ok = ~np.isnan(ou)
+        err = np.abs(gu[ok] - ou[ok])
+        inside = np.abs(ou[ok]) < float(1 << L)
+        parity = {"against": "fp64 oracle, same frame",
+                  "chart_ids_equal": bool((gpu["tri_chart"] == fr.charts.tri_chart).all()),
+                  "charts_equal": int(gpu["count"][0]) == C,
+                  "pack_equal": (int(res[0]), int(res[1]), int(res[2]), int(res[3])) ==
+                                (fr.pk.k, fr.pk.omega, fr.pk.height, fr.pk.status),
+                  "placements_equal": bool((gpu["place"][:C] == fr.pk.place).all()),
+                  "uv_nan_pattern_equal": bool((np.isnan(gu) == ~ok).all()),
+                  "max_uv_err_texel_inside_atlas": float(err[inside].max()) if inside.any() else 0.0,
+                  "max_uv_err_texel": float(err.max()) if err.size else 0.0,
+                  "uv_components": int(err.size), "uv_components_outside_atlas": int((~inside).sum())}
+    return base, parity
+
+
+def cpu_baseline_batched(views, max_views=32):
+    """The oracle on the batched workload, one thread per view over all host cores
+    (the oracle releases the interpreter lock while it runs): views/s over the first
+    max_views views of the batch (or all of them)."""
+    import concurrent.futures as cf
+    import oracle as O
+    sample = views[:max_views]
+    cores = os.cpu_count() or 1
+
+    def one(v):
+        sc, M, p = v
+        fr = O.atlas_frame(M, sc.pos, sc.idx, p["width"], p["height"], p["ratio"], p["atlas_log2"])
+        return fr.pk.status
+
+    O.build()
+    t0 = time.perf_counter()
+    with cf.ThreadPoolExecutor(max_workers=cores) as ex:
+        st = list(ex.map(one, sample))
+    dt = time.perf_counter() - t0
+    return {"value": len(sample) / dt, "unit": "views/s", "cores": cores, "kind": "oracle",
+            "sample": f"the first {len(sample)} of the {len(views)} views "
+                      f"({sum(v[0].T for v in sample)} triangles), one thread per view",
+            "all_packed": all(x == 0 for x in st), "host": host_info()}
 
 
 def _pct(v, q):
@@ -345,6 +396,9 @@ def run_batched(a, F, S, torch):
     solo.close()
     n = len(views)
     bp50, pp50 = _pct(t_batch, 50), _pct(t_plain, 50)
+    cpu = None
+    if dist_env()[1] == 1 and not a.no_cpu_baseline:
+        cpu = cpu_baseline_batched(views)
     return {"workload": f"{n} views: instanced 64x64 heightfield floors of 50-400 patches, 640x360-2560x1440, "
                         "atlas 1024-4096, ratio 1, edge charts, 64 scales",
             "views": n, "triangles": int(sum(sc.T for sc, _, _ in views)),
@@ -352,7 +406,7 @@ def run_batched(a, F, S, torch):
             "batched_ms_p50": bp50, "batched_ms_p99": _pct(t_batch, 99),
             "batched_views_per_s": n / (bp50 * 1e-3), "batched_gpu_launches": launches,
             "plain_ms_p50": pp50, "plain_ms_p99": _pct(t_plain, 99), "plain_views_per_s": n / (pp50 * 1e-3),
-            "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps}
+            "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps, "cpu_baseline": cpu}
 
 
 def run_served(a, F, S, torch):
@@ -436,7 +490,7 @@ def run_served(a, F, S, torch):
                        "Poisson arrivals, views 1280x720 / 1920x1080 / 2560x1440, atlas 2048 or 4096, ratio 1, "
                        "edge charts, 64 scales",
            "triangles_per_session": [int(sc.T) for sc in sessions]}
-    rates = (("rate_240_per_s", 240.0, 480), ("rate_4000_per_s", 4000.0, 1200))
+    rates = (("rate_30_per_s", 30.0, 90), ("rate_240_per_s", 240.0, 480), ("rate_4000_per_s", 4000.0, 1200))
     runs = [requests(n, rate, int(rate)) for _, rate, n in rates]
     cb, plain = serve(a.served_slots, runs), serve(1, runs)
     for (name, rate, n), c_, p_ in zip(rates, cb, plain):
@@ -612,6 +666,10 @@ def run_ours(a):
     C = int(bufs.count[0])
     T_vis = int(np.unpackbits(bufs.vt.cpu().numpy().view(np.uint8)).sum())
     work = ctx.frame_stats()
+    # the frame's outputs, for the oracle comparison of the CPU-baseline leg
+    gpu_frame = None
+    if world == 1 and not a.no_cpu_baseline:
+        gpu_frame = {k: getattr(bufs, k).cpu().numpy() for k in ("tri_chart", "count", "result", "place", "uv")}
 
     # one frame captured as a CUDA graph (the library is allocation- and sync-free);
     # the timed graph records no trace events, a second traced graph gives the
@@ -673,8 +731,9 @@ def run_ours(a):
 
     # end to end through the C ABI with host buffers: every step copies the mesh
     # positions host -> device from pinned memory (the matrix travels as a kernel
-    # argument), atlases the frame and copies the pack result and the placements
-    # back.  Double-buffered: two registrations of the mesh and two sets of outputs
+    # argument), atlases the frame and copies back what a shading consumer needs:
+    # the pack result, the placements and affines of the charts and the chart id
+    # of every triangle (uv * w = A . (x, y) + b * w with the affine of its chart).  Double-buffered: two registrations of the mesh and two sets of outputs
     # take turns, so the copy of step i + 1's positions and of step i - 1's result (on
     # two copy streams) overlap step i's frame; each frame is a replay of a graph
     # captured from fa_atlas_frame.  The L2 flush before
@@ -684,8 +743,10 @@ def run_ours(a):
         h_pos = torch.as_tensor(sc.pos).pin_memory()
         h_res = torch.empty(5, dtype=torch.int32).pin_memory()
         h_place = torch.empty(max(C, 1), 4, dtype=torch.int32).pin_memory()
+        h_aff = torch.empty(max(C, 1), 6, dtype=torch.float32).pin_memory()
+        h_tc = torch.empty(sc.T, dtype=torch.int32).pin_memory()
         h2d = h_pos.numel() * 4 + 64
-        d2h = h_res.numel() * 4 + h_place.numel() * 4
+        d2h = (h_res.numel() + h_place.numel() + h_aff.numel() + h_tc.numel()) * 4
         mesh_b = F.Mesh(ctx, sc.pos, sc.idx)
         meshes = (mesh, mesh_b)
         ebufs = (bufs, F.FrameBuffers.allocate(mesh.T, mesh.V, ctx.cfg.max_charts))
@@ -726,6 +787,8 @@ def run_ours(a):
                 with torch.cuda.stream(ys):
                     h_res.copy_(ebufs[b].result, non_blocking=True)
                     h_place.copy_(ebufs[b].place[:max(C, 1)], non_blocking=True)
+                    h_aff.copy_(ebufs[b].affine[:max(C, 1)], non_blocking=True)
+                    h_tc.copy_(ebufs[b].tri_chart, non_blocking=True)
                 read[b].record(ys)
 
         for b in range(2):
@@ -742,8 +805,11 @@ def run_ours(a):
         e_ms = max_over_ranks(e_ms)
         if int(h_res[3]) != 0:
             raise RuntimeError(f"pack status {int(h_res[3])} in the end-to-end run")
+        if not (torch.equal(h_tc, bufs.tri_chart.cpu()) and torch.equal(h_place, bufs.place[:max(C, 1)].cpu())):
+            raise RuntimeError("end-to-end outputs differ from the device-resident frame")
         e2e = {"value": whole_job_rate(world, a.steps, e_ms), "unit": "frames/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h,
+               "d2h": "pack result, placements and affines of the charts, chart id of every triangle",
                "pipelining": "double-buffered positions and outputs: step i+1's host copy and step i-1's "
                              "result copy overlap step i's frame"}
         mesh_b.close()
@@ -852,7 +918,7 @@ def run_ours(a):
     if extras is not None:
         line.update(extras)
     if world == 1 and not a.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(a, sc, M, p)
+        line["cpu_baseline"], line["parity"] = cpu_baseline(a, sc, M, p, gpu_frame)
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

@@ -272,7 +272,9 @@ fa_status fa_pack(fa_ctx* ctx, const uint32_t* d_fa, const uint32_t* d_fb, const
  * The first call on a device looks up the array's device address (with that device
  * current) and raises the pack kernel's shared-memory limit; make that first call
  * before any stream capture.  Later calls only launch kernels on `stream`, on the
- * current device.
+ * current device.  The address is kept for the life of the process: resetting the
+ * device (cudaDeviceReset, or tearing down its primary context) afterwards is not
+ * supported.
  * All calls share the one array, and each call leaves its contents behind (the
  * call clears what must start at zero itself); calls whose kernels overlap on the
  * GPU (different streams, or different host threads) race on it and must be
@@ -291,8 +293,10 @@ fa_status fa_pack_noalloc(const uint32_t* d_fa, const uint32_t* d_fb, uint32_t n
  * texels, alpha = omega / Omega, s = ratio * k / n_scales, local = the corner's
  * viewport position relative to the chart box, rotated by +90 degrees for rotated
  * charts (local = (py, Wpx - px)).  Computed from the fp32 clip coordinates with
- * compensated fp32 arithmetic; within 1e-4 texel (plus half an fp32 ulp of the
- * result above 2048) of the exact value.  d_uv float[T][3][2] (NaN for w <= 0,
+ * compensated fp32 arithmetic and rounded once: within 1e-4 texel of the exact
+ * value wherever fp32 can hold it to 1e-4 (|uv| < 2048, every corner inside an
+ * atlas of side <= 2048), else the correctly rounded fp32 value (half an ulp,
+ * plus 2^-30 |uv|).  d_uv float[T][3][2] (NaN for w <= 0,
  * untouched for invisible triangles), d_affine float[C][6] (may be NULL).
  * Skipped when d_res->status != FA_OK.  Errors: FA_E_INVALID_ARG. */
 fa_status fa_uv(fa_ctx* ctx, const fa_mesh* mesh, const float view_proj[16], uint32_t width,
@@ -320,6 +324,24 @@ fa_status fa_atlas_frame_dev_matrix(fa_ctx* ctx, const fa_mesh* mesh, const fa_f
 /* Synchronize `stream`, read the context's sticky device status word into *out
  * and clear it.  Returns FA_E_CUDA if the stream reported a CUDA error. */
 fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out);
+
+/* Limits of the device-side waits in this context's later launches.  The paper
+ * has no failure detection; these bound every loop of the library that waits on
+ * other threads, so that a fault elsewhere cannot hang the GPU.
+ *  loop_cap: CAS retries of one union-find hooking step (Alg. 1's hooking loop)
+ *            and polls of the packing width scan's look-back on one earlier chunk;
+ *  wait_ns:  nanoseconds the packing push waits for a chunk's bulk copy.
+ * When a limit runs out the kernel writes FA_E_TIMEOUT to the device status word,
+ * drops its remaining work (later kernels of the call see the word and skip
+ * theirs; fa_pack_result.status reports it) and returns; copies it started are
+ * still waited for, up to FA_DEFAULT_WAIT_NS, before it exits.  The context stays
+ * usable: the next frame starts from a cleared status word.  The defaults lie far
+ * above what any frame needs; small values exist to exercise the time-out path.
+ * Kernels launched after the call use the new limits (a CUDA graph keeps those of
+ * its capture).  Errors: FA_E_INVALID_ARG (NULL ctx). */
+#define FA_DEFAULT_LOOP_CAP (1u << 24)
+#define FA_DEFAULT_WAIT_NS 1000000000ull
+fa_status fa_set_wait_limits(fa_ctx* ctx, uint32_t loop_cap, uint64_t wait_ns);
 
 /* Number of kernels the library launched on this context since creation (a
  * host-side counter; used to report launches per frame). */

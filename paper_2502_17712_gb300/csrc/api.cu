@@ -124,6 +124,8 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   if (!ctx) return FA_E_OUT_OF_MEMORY;
   ctx->cfg = c;
   ctx->device = c.device;
+  ctx->loop_cap = kLoopCap;
+  ctx->wait_ns = kWaitNs;
   fa_status st = FA_OK;
   const uint64_t T = c.max_tris, V = c.max_verts, C = c.max_charts;
   ctx->queue_cap = (uint32_t)(T < (1u << 20) ? T + 1024 : (1u << 20));
@@ -410,6 +412,13 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {
 }
 
 uint64_t fa_launch_count(const fa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fa_status fa_set_wait_limits(fa_ctx* ctx, uint32_t loop_cap, uint64_t wait_ns) {
+  if (!ctx) return FA_E_INVALID_ARG;
+  ctx->loop_cap = loop_cap;
+  ctx->wait_ns = (unsigned long long)wait_ns;
+  return FA_OK;
+}
 
 fa_status fa_frame_stats_read(fa_ctx* ctx, fa_stream_t stream, fa_frame_stats* out) {
   if (!ctx || !out) return FA_E_INVALID_ARG;

@@ -46,12 +46,12 @@ __device__ __forceinline__ int32_t find_root(const volatile int32_t* label, int3
 }
 
 // Hook the components of a and b: the larger root is CASed onto the smaller.
-__device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevCounters* ctr) {
+__device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevCounters* ctr, uint32_t cap) {
   volatile int32_t* vl = label;
   int32_t ra = find_rep(vl, a), rb = find_rep(vl, b);
   uint32_t guard = 0;
   while (ra != rb) {
-    if (++guard > kLoopCap) {
+    if (++guard > cap) {
       set_status(ctr, FA_E_TIMEOUT);
       return;
     }
@@ -74,6 +74,7 @@ struct UfArgs {
   uint32_t* xcnt;  // per tile: their count
   const uint32_t* tile_list;  // tiles with a visible triangle (count in ctr->n_vtiles)
   DevCounters* ctr;
+  uint32_t loop_cap;  // CAS retries of one hooking step before FA_E_TIMEOUT
 };
 
 // Union of the edges inside one tile of kTile consecutive triangles, in shared
@@ -219,7 +220,7 @@ __device__ __forceinline__ void hook_tile(const UfArgs& a, uint32_t tile) {
   const uint2* xe = a.xedge + (size_t)tile * kXCap;
   for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
     const uint2 e = __ldcg(xe + i);
-    if (e.y < a.T && vt_bit(a.vt, e.y)) unite(a.label, (int32_t)e.x, (int32_t)e.y, a.ctr);
+    if (e.y < a.T && vt_bit(a.vt, e.y)) unite(a.label, (int32_t)e.x, (int32_t)e.y, a.ctr, a.loop_cap);
   }
 }
 
@@ -248,7 +249,7 @@ __global__ void __launch_bounds__(kBlock) k_uf_hook_v(UfArgs a) {
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       uint32_t v = __ldg(a.idx + 3 * (size_t)t + j);
-      unite(a.label, (int32_t)t, (int32_t)(a.T + v), a.ctr);
+      unite(a.label, (int32_t)t, (int32_t)(a.T + v), a.ctr, a.loop_cap);
     }
   }
 }
@@ -261,7 +262,7 @@ __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* n
     for (uint32_t i = nm_off[e]; i < nm_off[e + 1]; ++i) {
       uint32_t t = nm_list[i];
       if (!vt_bit(a.vt, t)) continue;
-      if (prev >= 0 && prev != (int32_t)t) unite(a.label, prev, (int32_t)t, a.ctr);
+      if (prev >= 0 && prev != (int32_t)t) unite(a.label, prev, (int32_t)t, a.ctr, a.loop_cap);
       prev = (int32_t)t;
     }
   }
@@ -584,6 +585,7 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   a.xcnt = ctx->xcnt;
   a.tile_list = ctx->tile_list;
   a.ctr = ctx->ctr;
+  a.loop_cap = ctx->loop_cap;
   const int vm = mode == FA_CHARTS_VERTEX;
   const unsigned gw = grid_for((uint64_t)((mesh->T + 31) / 32) * 32, kBlock, 152 * 16);
   if (vm) {

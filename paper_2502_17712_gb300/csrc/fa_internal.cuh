@@ -18,7 +18,8 @@ constexpr uint32_t kFrontCap = 32768;  // frontline entries per candidate (smem)
 constexpr int kBigTile = 16;        // tile side of the large-triangle raster
 constexpr int kSmallMaxPix = 16;    // in-thread raster when the pixel box has <= this
 constexpr int kOrderTile = 1024;    // boxes per tile of the stable order
-constexpr uint32_t kLoopCap = 1u << 24;  // device iteration cap (FA_E_TIMEOUT)
+constexpr uint32_t kLoopCap = FA_DEFAULT_LOOP_CAP;  // device iteration cap (FA_E_TIMEOUT)
+constexpr unsigned long long kWaitNs = FA_DEFAULT_WAIT_NS;  // device time limit of a bulk-copy wait
 
 // ----------------------------------------------------------------- device state
 
@@ -130,6 +131,9 @@ struct fa_ctx {
   uint32_t* box_full;    // [max_charts]
   fa::PackScratch pack;  // order + pack scratch (count filled per call)
   int pack_smem_set;
+  // limits of the device-side waits of later launches (fa_set_wait_limits)
+  uint32_t loop_cap;
+  unsigned long long wait_ns;
 };
 
 struct fa_mesh {

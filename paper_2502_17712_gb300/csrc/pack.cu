@@ -193,6 +193,8 @@ struct PackArgs {
   uint32_t gutter;
   uint32_t select_mode;
   uint32_t front_cap;
+  uint32_t loop_cap;          // polls of the look-back on one earlier chunk before FA_E_TIMEOUT
+  unsigned long long wait_ns;  // time limit of the push's wait for a staged chunk
   fa_placement* place;
   fa_pack_result* res;
 };
@@ -292,7 +294,7 @@ __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackA
           const int t = jn - (int)lane;
           unsigned long long v = t >= 0 ? ld_relaxed_u64(st + t) : kStInc;
           while (__any_sync(0xFFFFFFFFu, (v >> 62) == 0ull)) {
-            if (++spins > kLoopCap) {
+            if (++spins > a.loop_cap) {
               if (lane == 0) set_status(p.ctr, FA_E_TIMEOUT);
               v = kStInc;
             } else if ((v >> 62) == 0ull) {
@@ -401,7 +403,6 @@ constexpr int kPushThreads = 1024;
 constexpr uint32_t kGroupBoxes = 256;  // rows with more boxes take a thread per box
 constexpr uint32_t kStageBytes = kChunk * 8u + kSegStride * 2u;  // records + segment list
 static_assert(kStageBytes % 16u == 0u, "bulk copies move multiples of 16 bytes");
-constexpr unsigned long long kWaitNs = 1000000000ull;  // a second
 
 __device__ __forceinline__ uint32_t smem_addr(const void* q) { return (uint32_t)__cvta_generic_to_shared(q); }
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -426,13 +427,14 @@ __device__ __forceinline__ bool mbar_try_wait(unsigned long long* bar, uint32_t 
       : "memory");
   return ok != 0u;
 }
-// Waits at most kWaitNs for the phase of the given parity; false on time-out.
-__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity) {
+// Waits at most limit_ns for the phase of the given parity; false on time-out.
+__device__ __forceinline__ bool mbar_wait_bounded(unsigned long long* bar, uint32_t parity,
+                                                  unsigned long long limit_ns) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = global_ns();
   for (;;) {
     if (mbar_try_wait(bar, parity)) return true;
-    if (global_ns() - t0 > kWaitNs) return false;
+    if (global_ns() - t0 > limit_ns) return false;
   }
 }
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, unsigned long long* bar) {
@@ -460,16 +462,17 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
 
   const uint32_t kidx = blockIdx.x;
   const uint32_t tid = threadIdx.x;
+  // an error of an earlier kernel (or of another candidate that already timed out):
+  // no work, but every CTA still publishes and counts itself, so that the last one
+  // selects and resets the counter
   const int32_t st0 = __ldcg(&p.ctr->status);
-  if (st0 != 0) {
-    if (kidx == 0 && tid == 0) *a.res = fa_pack_result{0, 0, 0, st0, 0};
-    return;
-  }
   const uint32_t C = __ldcg(p.count);
   const uint32_t om = 1u << a.atlas_log2;
   int32_t status = FA_OK;
   uint32_t Om = om, H = 0, ok = 0;
-  if (C > p.max_boxes) {
+  if (st0 != 0) {
+    status = st0;
+  } else if (C > p.max_boxes) {
     status = FA_E_CAPACITY;
   } else {
     Om = om + __ldcg(p.m + kidx);
@@ -502,7 +505,7 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
       bool fail = false, timed_out = false;
       for (uint32_t c = 0; c < nchunks; ++c) {
         const uint32_t stg = c & 1u;
-        const bool got = mbar_wait_bounded(&s_bar[stg], (c >> 1) & 1u);
+        const bool got = mbar_wait_bounded(&s_bar[stg], (c >> 1) & 1u, a.wait_ns);
         if (__syncthreads_or(!got)) {
           timed_out = true;
           break;
@@ -582,9 +585,10 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
           ++issued;
         }
       }
-      // copies still in flight land before the CTA leaves
+      // copies still in flight land before the CTA leaves (with the full limit, also
+      // after a time-out: the shared memory they write must outlive them)
       if (tid == 0)
-        for (uint32_t c = consumed; c < issued; ++c) mbar_wait_bounded(&s_bar[c & 1u], (c >> 1) & 1u);
+        for (uint32_t c = consumed; c < issued; ++c) mbar_wait_bounded(&s_bar[c & 1u], (c >> 1) & 1u, kWaitNs);
       if (timed_out) {
         if (tid == 0) set_status(p.ctr, FA_E_TIMEOUT);
         status = FA_E_TIMEOUT;
@@ -641,7 +645,7 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
     if (tid == 0) {
       int32_t pst = est;
       if (pst == FA_OK && bk == 0) pst = FA_E_PACK_FAILED;
-      fa_pack_result r{0, 0, 0, pst, C};
+      fa_pack_result r{0, 0, 0, pst, st0 != 0 ? 0u : C};
       if (pst == FA_OK) {
         r.k = bk;
         r.omega = bOm;
@@ -696,6 +700,8 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   a.select_mode = select_mode;
   const uint32_t om = 1u << atlas_log2;
   a.front_cap = (8u * om < kFrontCap) ? 8u * om : kFrontCap;
+  a.loop_cap = ctx ? ctx->loop_cap : kLoopCap;
+  a.wait_ns = ctx ? ctx->wait_ns : kWaitNs;
   a.place = place;
   a.res = res;
   const uint32_t items = p.max_chunks * n_scales;

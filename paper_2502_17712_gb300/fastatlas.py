@@ -46,7 +46,9 @@ EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh
            "fa_batch_destroy", "fa_batch_mesh_register", "fa_batch_set_schedule", "fa_batch_get_schedule",
            "fa_atlas_batch", "fa_batch_tune", "fa_batch_launch_count", "fa_server_create", "fa_server_destroy",
            "fa_server_session_open", "fa_server_session_close", "fa_server_submit", "fa_server_poll",
-           "fa_server_stats", "fa_server_now_ms", "fa_frame_stats_read"]
+           "fa_server_stats", "fa_server_now_ms", "fa_frame_stats_read", "fa_set_wait_limits"]
+FA_DEFAULT_LOOP_CAP = 1 << 24
+FA_DEFAULT_WAIT_NS = 1_000_000_000
 
 FA_BATCH_ROUND_ROBIN, FA_BATCH_LONGEST_FIRST = 0, 1
 
@@ -179,6 +181,8 @@ def load(path: str = LIB_PATH):
     lib.fa_last_device_status.restype = st
     lib.fa_launch_count.argtypes = [P]
     lib.fa_launch_count.restype = ctypes.c_uint64
+    lib.fa_set_wait_limits.argtypes = [P, u32, ctypes.c_uint64]
+    lib.fa_set_wait_limits.restype = st
     lib.fa_frame_stats_read.argtypes = [P, P, ctypes.POINTER(fa_frame_stats)]
     lib.fa_frame_stats_read.restype = st
     lib.fa_profile_enable.argtypes = [P, ctypes.c_int]
@@ -307,6 +311,10 @@ def fa_launch_count(ctx) -> int:
     return load().fa_launch_count(ctx)
 
 
+def fa_set_wait_limits(ctx, loop_cap=FA_DEFAULT_LOOP_CAP, wait_ns=FA_DEFAULT_WAIT_NS):
+    _check(load().fa_set_wait_limits(ctx, int(loop_cap), int(wait_ns)), "fa_set_wait_limits")
+
+
 def fa_frame_stats_read(ctx, stream=None) -> dict:
     """Work counts of the last frame on the context (synchronizes the stream)."""
     r = fa_frame_stats()
@@ -351,6 +359,9 @@ class Context:
 
     def device_status(self, stream=None) -> int:
         return fa_last_device_status(self.handle, stream)
+
+    def set_wait_limits(self, loop_cap=FA_DEFAULT_LOOP_CAP, wait_ns=FA_DEFAULT_WAIT_NS):
+        fa_set_wait_limits(self.handle, loop_cap, wait_ns)
 
     @property
     def launches(self) -> int:

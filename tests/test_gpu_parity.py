@@ -2,8 +2,11 @@
 
 Bit-exact: VT bits, chart ids, roots, chart count, NDC boxes (fp32 bits),
 footprints, rotations, the packing order, placements and the chosen candidate.
-UVs: |GPU - fp64 oracle| <= 1e-4 texel + half an fp32 ulp of the value (the
-half ulp is the unavoidable final rounding; below 2048 texels it is <= 6.1e-5).
+UVs: |GPU - fp64 oracle| <= 1e-4 texel flat wherever fp32 can hold the value to
+1e-4 (|uv| < 2048 texels, which is every corner inside an atlas of side <= 2048);
+larger values (corners in 4096^2 atlases, off-screen corners of partially visible
+triangles) must be the correctly rounded fp32 value (half an ulp, plus 2^-30 |uv|
+for the compensated arithmetic before the final rounding).
 """
 import numpy as np
 import pytest
@@ -14,6 +17,14 @@ from paper_2502_17712_gb300 import scenes as S
 pytestmark = pytest.mark.gpu
 
 UV_TOL = 1e-4
+
+
+def uv_tolerance(o):
+    """Accepted |GPU - oracle| for UV components whose fp64 oracle value is o."""
+    a = np.abs(np.asarray(o, np.float64))
+    _, e = np.frexp(np.maximum(a, 1.0))
+    half_ulp = np.ldexp(1.0, e - 25)  # half the fp32 spacing in a's binade
+    return np.where(a < 2048.0, UV_TOL, np.maximum(UV_TOL, half_ulp + 2.0 ** -30 * a))
 
 
 @pytest.fixture(scope="module")
@@ -76,9 +87,14 @@ def compare_frame(sc, M, W, H, ratio, log2, bufs, status, mode=0, n_scales=64, s
         gu = u[vis]
         nan = np.isnan(ou)
         assert (np.isnan(gu) == nan).all()
-        tol = UV_TOL + 0.5 * np.spacing(np.abs(ou[~nan]).astype(np.float32)).astype(np.float64)
-        err = np.abs(gu[~nan] - ou[~nan])
-        assert (err <= tol).all(), f"max UV error {err.max():.3g}"
+        o = ou[~nan]
+        err = np.abs(gu[~nan] - o)
+        tol = uv_tolerance(o)
+        assert (err <= tol).all(), f"UV error {err[err > tol].max():.3g} above its tolerance"
+        inside = np.abs(o) < float(1 << log2)
+        fr.uv_err_inside = float(err[inside].max()) if inside.any() else 0.0
+        fr.uv_err_max = float(err.max()) if err.size else 0.0
+        fr.uv_outside = int((~inside).sum())
         ga = to_np(bufs.affine)[:C].astype(np.float64)
         assert np.allclose(ga, fr.affine, rtol=1e-6, atol=2e-4)
     return fr
@@ -275,16 +291,23 @@ def sphere_frame():
     return S.icosphere_frame(1)
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-def test_icosphere_frame_full_size(F, sphere_frame, mode):
+@pytest.mark.parametrize("mode,ratio", [(0, 1.0), (1, 1.0), (0, 0.5), (0, 2.0)])
+def test_icosphere_frame_full_size(F, sphere_frame, mode, ratio):
     """200 icospheres (4,096,000 triangles), 1920x1080, 2048^2 atlas: the whole frame
-    at full size, every output compared (the oracle takes ~10 s here)."""
+    at full size, every output compared (the oracle takes ~10 s here), at the
+    texel-to-pixel ratios 1 (both chart modes), 0.5 and 2 (edge charts; each ratio
+    selects a different candidate, so the push takes a different path)."""
     sc, M, p = sphere_frame
     ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 17, max_width=1920, max_height=1080,
                     max_atlas_log2=11)
     mesh = F.Mesh(ctx, sc.pos, sc.idx)
-    bufs, st = run_gpu(F, ctx, mesh, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], mode)
-    compare_frame(sc, M, p["width"], p["height"], p["ratio"], p["atlas_log2"], bufs, st, mode)
+    bufs, st = run_gpu(F, ctx, mesh, M, p["width"], p["height"], ratio, p["atlas_log2"], mode)
+    fr = compare_frame(sc, M, p["width"], p["height"], ratio, p["atlas_log2"], bufs, st, mode)
+    assert fr.pk.status == 0
+    print(f"ratio {ratio} mode {mode}: k={fr.pk.k} Omega={fr.pk.omega} charts={fr.charts.C} "
+          f"max |duv| inside the atlas {fr.uv_err_inside:.3g} texel, overall {fr.uv_err_max:.3g} "
+          f"({fr.uv_outside} components outside)")
+    assert fr.uv_err_inside <= UV_TOL
     mesh.close()
     ctx.close()
 

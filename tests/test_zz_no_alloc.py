@@ -6,8 +6,10 @@ pack (a host application's frame callback or plugin slot with host-owned device
 memory, or a real-time loop that must not pay cudaMalloc's device
 synchronization); its scratch is a static device array inside the library.  The
 test calls it through the C ABI twice in a row, on different box sets, and compares
-every output with fa_pack's, bit for bit (all outputs are integers).  This file is
-collected last so that a first failure here comes after every other test.
+every output with fa_pack's, bit for bit (all outputs are integers); the second
+call must leave the device's free memory unchanged, and an empty box set must give
+fa_pack's result too.  This file is collected last so that a first failure here
+comes after every other test.
 """
 import numpy as np
 import pytest
@@ -26,11 +28,13 @@ def test_pack_noalloc_matches_pack_twice_in_a_row():
     F.load()
     ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=4096, max_width=64, max_height=64,
                     max_atlas_log2=12)
-    cases = [(3000, 11, 64, 0, 11), (777, 9, 32, 1, 12)]  # n, atlas_log2, n_scales, select, seed
-    for n, log2, ns, sel, seed in cases:
+    cases = [(3000, 11, 64, 0, 11), (777, 9, 32, 1, 12), (0, 10, 64, 0, 13)]  # n, log2, scales, select, seed
+    for i, (n, log2, ns, sel, seed) in enumerate(cases):
         fa, fb = S.lognormal_boxes(seed, n, mean_texels=8)
-        d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
-        d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+        d_fa = torch.zeros(4096, dtype=torch.int32, device="cuda")  # room for 4096 (non-NULL when n = 0)
+        d_fb = torch.zeros(4096, dtype=torch.int32, device="cuda")
+        d_fa[:n] = torch.as_tensor(fa.view(np.int32)).cuda()
+        d_fb[:n] = torch.as_tensor(fb.view(np.int32)).cuda()
         cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
         want_order = torch.zeros(4096, dtype=torch.int32, device="cuda")
         want_place = torch.zeros(4096, 4, dtype=torch.int32, device="cuda")
@@ -39,8 +43,12 @@ def test_pack_noalloc_matches_pack_twice_in_a_row():
         got_order = torch.full((4096,), -1, dtype=torch.int32, device="cuda")
         got_place = torch.full((4096, 4), -1, dtype=torch.int32, device="cuda")
         got_res = torch.full((5,), -1, dtype=torch.int32, device="cuda")
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         F.fa_pack_noalloc(d_fa, d_fb, n, log2, ns, sel, 2, 0, got_order, got_place, got_res)
         torch.cuda.synchronize()
+        if i > 0:  # after the first call's one-time set-up: no device memory taken
+            assert torch.cuda.mem_get_info()[0] == free0
         assert int(want_res[3]) == F.FA_OK
         assert torch.equal(got_res, want_res)
         assert torch.equal(got_order[:n], want_order[:n])
