@@ -236,7 +236,12 @@ __global__ void __launch_bounds__(kScanThreads) k_pack_scan(PackScratch p, PackA
   __shared__ uint32_t s_wmax[kScanThreads / 32];
   __shared__ uint32_t s_item;
   __shared__ unsigned long long s_prefix;
-  if (__ldcg(&p.ctr->status) != 0) return;
+  __shared__ int32_t s_status;
+  // one read of the status word for the whole CTA (another CTA's time-out can set
+  // it meanwhile, and every thread must take the same branch before the barriers)
+  if (threadIdx.x == 0) s_status = __ldcg(&p.ctr->status);
+  __syncthreads();
+  if (s_status != 0) return;
   const uint32_t C = __ldcg(p.count);
   if (C > p.max_boxes || C == 0) return;
   const uint32_t nch = (C + kChunk - 1) / kChunk;
@@ -459,13 +464,16 @@ __global__ void __launch_bounds__(kPushThreads) k_pack_push(PackScratch p, PackA
   __shared__ __align__(8) unsigned long long s_bar[2];
   __shared__ uint32_t ws32[32];
   __shared__ uint32_t s_last;
-
+  __shared__ int32_t s_st0;
   const uint32_t kidx = blockIdx.x;
   const uint32_t tid = threadIdx.x;
   // an error of an earlier kernel (or of another candidate that already timed out):
   // no work, but every CTA still publishes and counts itself, so that the last one
-  // selects and resets the counter
-  const int32_t st0 = __ldcg(&p.ctr->status);
+  // selects and resets the counter.  One read for the whole CTA: every thread must
+  // take the same branch before the barriers below.
+  if (tid == 0) s_st0 = __ldcg(&p.ctr->status);
+  __syncthreads();
+  const int32_t st0 = s_st0;
   const uint32_t C = __ldcg(p.count);
   const uint32_t om = 1u << a.atlas_log2;
   int32_t status = FA_OK;
