@@ -1,522 +1,77 @@
-// Charts: connected components of the visible triangles (Sec. 5.1) by union-find
-// with pointer hooking in the style of ECL-CC (App. A "GPU Union Find", Alg. 1):
-// initialise each visible triangle to the smallest visible neighbour, hook roots
-// with atomicCAS so the larger root always points to the smaller one, then flatten.
-// The root of a component is therefore its smallest triangle id.  Charts are
-// numbered by ascending root: the flatten pass counts the roots per 1024-triangle
-// block and records each VT word's root bits, a scan gives each block's first chart,
-// and a root's chart is that plus the roots before it inside its block.
-//
-// Edge mode joins triangles across shared edges (the adjacency built at mesh
-// registration, plus the incidence lists of non-manifold edges).  Vertex mode
-// (the vertex merge of App. A) joins each visible triangle with its three vertices:
-// vertices are extra nodes T + v, so every component's smallest node is a triangle.
-//
-// Visible triangles are found from the VT words: a warp owns 32 consecutive
-// triangles and skips the whole word when it is zero.
-#include "fa_internal.cuh"
+// Chart kernels (Sec. 5.1; App. A "GPU Union Find", Alg. 1): the launch wrappers
+// of the stage bodies in chartify.cuh, the standalone visible-list kernels and the
+// launch sequence of one chart pass.
+#include "chartify.cuh"
 
 namespace fa {
 namespace {
 
-constexpr int kBlock = 256;
-constexpr int kPerBlock = 1024;  // triangles per counting block (4 per thread)
+using cf::UfArgs;
+using cf::kBlock;
+using cf::kPerBlock;
+using cf::kLocalThreads;
+using cf::kTile;
 
-// Representative with path halving (labels only decrease; parents are smaller).
-__device__ __forceinline__ int32_t find_rep(volatile int32_t* label, int32_t x) {
-  int32_t cur = label[x];
-  if (cur != x) {
-    int32_t prev = x, next;
-    while (cur > (next = label[cur])) {
-      label[prev] = next;
-      prev = cur;
-      cur = next;
-    }
-  }
-  return cur;
-}
-
-// Root without writing: used once hooking is over.  (Path halving here would race
-// with the final store of another thread: a halving write can replace a label that
-// was just set to the root by a non-root ancestor.)
-__device__ __forceinline__ int32_t find_root(const volatile int32_t* label, int32_t x) {
-  int32_t cur = x, next;
-  while ((next = label[cur]) != cur) cur = next;
-  return cur;
-}
-
-// Hook the components of a and b: the larger root is CASed onto the smaller.
-__device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevCounters* ctr, uint32_t cap) {
-  volatile int32_t* vl = label;
-  int32_t ra = find_rep(vl, a), rb = find_rep(vl, b);
-  uint32_t guard = 0;
-  while (ra != rb) {
-    if (++guard > cap) {
-      set_status(ctr, FA_E_TIMEOUT);
-      return;
-    }
-    int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
-    int32_t old = atomicCAS(label + hi, hi, lo);
-    if (old == hi) return;
-    // hi stopped being a root; retry from the current representatives
-    ra = find_rep(vl, old);
-    rb = find_rep(vl, lo);
-  }
-}
-
-struct UfArgs {
-  const uint32_t* vt;
-  const uint32_t* idx;
-  const int32_t* adj;
-  uint32_t T, V;
-  int32_t* label;
-  uint2* xedge;    // per tile: the edges (t, n > t) of its visible triangles that leave it
-  uint32_t* xcnt;  // per tile: their count
-  const uint32_t* tile_list;  // tiles with a visible triangle (count in ctr->n_vtiles)
-  DevCounters* ctr;
-  uint32_t loop_cap;  // CAS retries of one hooking step before FA_E_TIMEOUT
-};
-
-// Union of the edges inside one tile of kTile consecutive triangles, in shared
-// memory, then label[t] = the tile-local root (its smallest triangle).  Replaces the
-// global init: afterwards every visible triangle points to a root, and only edges that
-// leave the tile remain for the global hooking.
-constexpr int kTile = 1024;
-constexpr int kLocalThreads = 1024;  // one triangle of the tile per thread
-constexpr uint32_t kXCap = 3 * kTile;  // cross-tile edge slots per tile
-
-__device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
-  int32_t cur = lab[x];
-  if (cur != x) {
-    int32_t prev = x, next;
-    while (cur > (next = lab[cur])) {
-      lab[prev] = next;
-      prev = cur;
-      cur = next;
-    }
-  }
-  return cur;
-}
-
-// One tile (all threads of the block; the caller separates tiles by a barrier).
-__device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
-  __shared__ int32_t lab[kTile];
-  __shared__ uint32_t vis[kTile / 32];
-  const uint32_t base = tile * kTile;
-  uint32_t v = 0;
-  if (threadIdx.x < kTile / 32) {
-    const uint32_t w = (base >> 5) + threadIdx.x;
-    v = w < ((a.T + 31) >> 5) ? __ldg(a.vt + w) : 0u;
-    vis[threadIdx.x] = v;
-  }
-  __shared__ uint32_t s_xc;
-  if (threadIdx.x == 0) s_xc = 0;
-  if (!__syncthreads_or(v != 0u)) {  // no visible triangle in this tile
-    if (threadIdx.x == 0) a.xcnt[tile] = 0;
-    return;
-  }
-  volatile int32_t* vl = lab;
-  uint2* xe = a.xedge + (size_t)tile * kXCap;
-  // start from the smallest visible neighbour inside the tile (Alg. 1, first loop)
-  int32_t nb[kTile / kLocalThreads][3];
-#pragma unroll
-  for (int k = 0; k < kTile / kLocalThreads; ++k) {
-    const uint32_t i = threadIdx.x + k * kLocalThreads;
-    int32_t l = (int32_t)i;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) nb[k][j] = -1;
-    if ((vis[i >> 5] >> (i & 31)) & 1u) {
-      const uint32_t t = base + i;
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        const int32_t n = __ldg(a.adj + 3 * (size_t)t + j);
-        if (n < (int32_t)base || (uint32_t)n >= base + kTile) {
-          // leaves the tile: hooked globally (once, from the lower end) if n is visible
-          if (n > (int32_t)t) xe[atomicAdd(&s_xc, 1u)] = make_uint2(t, (uint32_t)n);
-          continue;
-        }
-        const uint32_t ni = (uint32_t)n - base;
-        if (!((vis[ni >> 5] >> (ni & 31)) & 1u)) continue;
-        nb[k][j] = (int32_t)ni;
-        if ((int32_t)ni < l) l = (int32_t)ni;
-      }
-    }
-    lab[i] = l;
-  }
-  __syncthreads();
-  // the initial labels form trees (every label is a smaller visible neighbour); a few
-  // rounds of pointer jumping make them shallow before the hooking walks them (a
-  // jump only replaces a label by one of its ancestors, so the rounds need no barrier)
-#pragma unroll
-  for (int k = 0; k < kTile / kLocalThreads; ++k) {
-    const uint32_t i = threadIdx.x + k * kLocalThreads;
-    if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
-#pragma unroll 1
-    for (int r = 0; r < 4; ++r) vl[i] = vl[vl[i]];
-  }
-  __syncthreads();
-  // hook every in-tile edge once, from its lower end
-#pragma unroll
-  for (int k = 0; k < kTile / kLocalThreads; ++k) {
-    const int32_t i = (int32_t)(threadIdx.x + k * kLocalThreads);
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      const int32_t ni = nb[k][j];
-      if (ni <= i) continue;
-      int32_t ra = lfind(vl, i), rb = lfind(vl, ni);
-      while (ra != rb) {
-        const int32_t hi = ra > rb ? ra : rb, lo = ra > rb ? rb : ra;
-        const int32_t old = atomicCAS(lab + hi, hi, lo);
-        if (old == hi) break;
-        ra = lfind(vl, old);
-        rb = lfind(vl, lo);
-      }
-    }
-  }
-  __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kTile; i += kLocalThreads) {
-    if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
-    // (path halving: the walks of other threads shorten too; the result goes to the
-    // global labels, so no halving write can overwrite it)
-    a.label[base + i] = (int32_t)base + lfind(vl, (int32_t)i);
-  }
-  if (threadIdx.x == 0) a.xcnt[tile] = s_xc;  // all appends precede the last barrier
-}
-
-// Every tile (a block each), or only the tiles that the marking pass listed (a
-// persistent grid over the list).
 template <bool LIST>
 __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
   pdl_wait();
-  if (!LIST) {
-    local_tile(a, blockIdx.x);
-    return;
-  }
-  // tiles are handed out by a counter, so that a block that drew light tiles takes
-  // more (their costs differ by an order of magnitude)
-  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
-  __shared__ uint32_t s_i;
-  for (;;) {
-    __syncthreads();  // the shared memory of the previous tile is free
-    if (threadIdx.x == 0) s_i = atomicAdd(&a.ctr->uf_item, 1u);
-    __syncthreads();
-    const uint32_t i = s_i;
-    if (i >= n) break;
-    local_tile(a, __ldcg(a.tile_list + i));
-  }
+  cf::local_body<LIST>(a, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
   pdl_wait();
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < V; v += gridDim.x * blockDim.x)
-    label[T + v] = (int32_t)(T + v);
-}
-
-// Hooking (Alg. 1, second loop), edge mode: the edges that leave a tile, each once
-// from its lower end, when the other end is visible too (edges inside a tile were
-// joined by k_uf_local).  One block per tile.
-__device__ __forceinline__ void hook_tile(const UfArgs& a, uint32_t tile) {
-  const uint32_t n = min(__ldcg(a.xcnt + tile), kXCap);
-  const uint2* xe = a.xedge + (size_t)tile * kXCap;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
-    const uint2 e = __ldcg(xe + i);
-    if (e.y < a.T && vt_bit(a.vt, e.y)) unite(a.label, (int32_t)e.x, (int32_t)e.y, a.ctr, a.loop_cap);
-  }
+  cf::init_v_body(label, T, V, blockIdx.x, gridDim.x);
 }
 
 template <bool LIST>
 __global__ void __launch_bounds__(128) k_uf_hook(UfArgs a) {
   pdl_wait();
-  if (!LIST) {
-    hook_tile(a, blockIdx.x);
-    return;
-  }
-  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) hook_tile(a, __ldcg(a.tile_list + i));
+  cf::hook_body<LIST>(a, blockIdx.x, gridDim.x);
 }
 
-// Vertex mode: every visible triangle joins its three vertex nodes T + v.
 __global__ void __launch_bounds__(kBlock) k_uf_hook_v(UfArgs a) {
   pdl_wait();
-  const uint32_t lane = threadIdx.x & 31;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  for (uint32_t w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; w < nwords;
-       w += (gridDim.x * blockDim.x) >> 5) {
-    const uint32_t word = __ldg(a.vt + w);
-    if (word == 0) continue;
-    const uint32_t t = (w << 5) + lane;
-    if (!((word >> lane) & 1u)) continue;
-#pragma unroll
-    for (int j = 0; j < 3; ++j) {
-      uint32_t v = __ldg(a.idx + 3 * (size_t)t + j);
-      unite(a.label, (int32_t)t, (int32_t)(a.T + v), a.ctr, a.loop_cap);
-    }
-  }
+  cf::hook_v_body(a, blockIdx.x, gridDim.x);
 }
 
-// Non-manifold edges: join consecutive visible triangles of each incidence list.
 __global__ void k_uf_hook_nm(UfArgs a, const uint32_t* nm_off, const uint32_t* nm_list, uint32_t n_nm) {
   pdl_wait();
-  for (uint32_t e = blockIdx.x * blockDim.x + threadIdx.x; e < n_nm; e += gridDim.x * blockDim.x) {
-    int32_t prev = -1;
-    for (uint32_t i = nm_off[e]; i < nm_off[e + 1]; ++i) {
-      uint32_t t = nm_list[i];
-      if (!vt_bit(a.vt, t)) continue;
-      if (prev >= 0 && prev != (int32_t)t) unite(a.label, prev, (int32_t)t, a.ctr, a.loop_cap);
-      prev = (int32_t)t;
-    }
-  }
+  cf::hook_nm_body(a, nm_off, nm_list, n_nm, blockIdx.x, gridDim.x);
 }
 
-// Flatten visible triangles to their root and count roots per block of
-// kPerBlock triangles: warp w of the block owns VT words w, w + 8, w + 16, w + 24.
-__device__ __forceinline__ void flatten_tile(const UfArgs& a, uint32_t tile, uint32_t* blockcnt,
-                                             uint32_t* viscnt, uint2* wordroots) {
-  __shared__ uint32_t wc[kPerBlock / 32], vcnt[kBlock / 32];
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  uint32_t vis = 0, rb[kPerBlock / kBlock];
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t wl = k * (kBlock / 32) + wid;
-    const uint32_t w = tile * (kPerBlock / 32) + wl;
-    const uint32_t word = w < nwords ? __ldg(a.vt + w) : 0u;
-    vis += __popc(word);
-    bool root = false;
-    if ((word >> lane) & 1u) {
-      const uint32_t t = (w << 5) + lane;
-      const int32_t r = find_root(a.label, (int32_t)t);
-      a.label[t] = r;
-      root = r == (int32_t)t;
-    }
-    rb[k] = __ballot_sync(0xFFFFFFFFu, root);
-    if (lane == 0) wc[wl] = __popc(rb[k]);
-  }
-  if (lane == 0) vcnt[wid] = vis;  // every lane counted the same words
-  __syncthreads();
-  // per VT word: its root bits and the roots of the block's earlier words
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t wl = k * (kBlock / 32) + wid;
-    const uint32_t w = tile * (kPerBlock / 32) + wl;
-    if (lane == 0 && w < nwords) {
-      uint32_t pre = 0;
-      for (uint32_t i = 0; i < wl; ++i) pre += wc[i];
-      wordroots[w] = make_uint2(rb[k], pre);
-    }
-  }
-  if (threadIdx.x == 0) {
-    uint32_t s = 0, v = 0;
-    for (int i = 0; i < kPerBlock / 32; ++i) s += wc[i];
-    for (int i = 0; i < kBlock / 32; ++i) v += vcnt[i];
-    blockcnt[tile] = s;
-    viscnt[tile] = v;
-  }
-}
-
-// Every counting block (a block each), or only the tiles that the marking pass
-// listed (a persistent grid; the clear zeroed the counts of the others).
 template <bool LIST>
 __global__ void __launch_bounds__(kBlock) k_uf_flatten(UfArgs a, uint32_t* blockcnt, uint32_t* viscnt,
                                                        uint2* wordroots) {
   pdl_wait();
-  if (!LIST) {
-    flatten_tile(a, blockIdx.x, blockcnt, viscnt, wordroots);
-    return;
-  }
-  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
-    __syncthreads();  // the shared memory of the previous tile is free
-    flatten_tile(a, __ldcg(a.tile_list + i), blockcnt, viscnt, wordroots);
-  }
+  cf::flatten_body<LIST, kBlock>(a, blockcnt, viscnt, wordroots, blockIdx.x, gridDim.x);
 }
 
-// Chart of root triangle r: the roots before its block (scanned block counts),
-// before its word inside the block, and before it inside its word.
-__device__ __forceinline__ uint32_t chart_of_root(const uint32_t* blockcnt, const uint2* wordroots, uint32_t r) {
-  const uint2 wr = __ldcg(wordroots + (r >> 5));
-  return __ldcg(blockcnt + r / kPerBlock) + wr.y + __popc(wr.x & ((1u << (r & 31)) - 1u));
-}
-
-// In-place exclusive scans of the per-block counts a[0..n) and, when given,
-// b[0..n) (one 1024-thread block, both at once): thread t owns the `per` consecutive
-// entries from t per (per a multiple of 4, so whole groups move as 16-byte vectors);
-// one block scan of the owners' sums.  The totals go to a[n], b[n], *ta and *tb.
-__device__ __forceinline__ uint4 load4(const uint32_t* a, uint32_t i, uint32_t n) {
-  if (i + 4u <= n) return __ldcg(reinterpret_cast<const uint4*>(a + i));
-  return make_uint4(i < n ? a[i] : 0u, i + 1u < n ? a[i + 1] : 0u, i + 2u < n ? a[i + 2] : 0u,
-                    i + 3u < n ? a[i + 3] : 0u);
-}
-__device__ __forceinline__ void store4(uint32_t* a, uint32_t i, uint32_t n, uint4 v) {
-  if (i + 4u <= n) {
-    *reinterpret_cast<uint4*>(a + i) = v;
-    return;
-  }
-  if (i < n) a[i] = v.x;
-  if (i + 1u < n) a[i + 1] = v.y;
-  if (i + 2u < n) a[i + 2] = v.z;
-}
-__device__ __forceinline__ uint4 excl4(uint4 v, uint32_t& run) {
-  const uint4 o = make_uint4(run, run + v.x, run + v.x + v.y, run + v.x + v.y + v.z);
-  run += v.x + v.y + v.z + v.w;
-  return o;
-}
-__device__ void scan_counts(uint32_t* a, uint32_t* b, uint32_t n, uint32_t* ta, uint32_t* tb) {
-  __shared__ uint2 warp_tot[32];
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t per = 4u * ((n + 4095u) / 4096u);
-  const uint32_t i0 = threadIdx.x * per;
-  uint2 v = make_uint2(0u, 0u);
-  uint4 a0 = make_uint4(0u, 0u, 0u, 0u), b0 = a0;  // the first group stays in registers
-  for (uint32_t i = i0; i < i0 + per && i < n; i += 4u) {
-    const uint4 x = load4(a, i, n);
-    v.x += x.x + x.y + x.z + x.w;
-    if (i == i0) a0 = x;
-    if (b) {
-      const uint4 y = load4(b, i, n);
-      v.y += y.x + y.y + y.z + y.w;
-      if (i == i0) b0 = y;
-    }
-  }
-  uint2 x = v;
-#pragma unroll
-  for (int o = 1; o < 32; o <<= 1) {
-    const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, x.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, x.y, o);
-    if (lane >= (unsigned)o) {
-      x.x += y0;
-      x.y += y1;
-    }
-  }
-  if (lane == 31) warp_tot[wid] = x;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    uint2 t = warp_tot[threadIdx.x];
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y0 = __shfl_up_sync(0xFFFFFFFFu, t.x, o), y1 = __shfl_up_sync(0xFFFFFFFFu, t.y, o);
-      if (threadIdx.x >= (unsigned)o) {
-        t.x += y0;
-        t.y += y1;
-      }
-    }
-    warp_tot[threadIdx.x] = t;
-  }
-  __syncthreads();
-  const uint2 wp = wid ? warp_tot[wid - 1] : make_uint2(0u, 0u);
-  uint32_t ra = wp.x + x.x - v.x, rb = wp.y + x.y - v.y;
-  for (uint32_t i = i0; i < i0 + per && i < n; i += 4u) {
-    store4(a, i, n, excl4(i == i0 ? a0 : load4(a, i, n), ra));
-    if (b) store4(b, i, n, excl4(i == i0 ? b0 : load4(b, i, n), rb));
-  }
-  if (threadIdx.x == 1023) {
-    a[n] = wp.x + x.x;
-    *ta = wp.x + x.x;
-    if (b) {
-      b[n] = wp.y + x.y;
-      *tb = wp.y + x.y;
-    }
-  }
-  __syncthreads();
-}
-
-// Exclusive scans of the per-block root counts (chart numbering) and visible
-// counts (the visible-triangle list); writes the chart count.
 __global__ void __launch_bounds__(1024) k_scan_blocks(uint32_t* blockcnt, uint32_t* viscnt, uint32_t nblocks,
                                                       uint32_t* count_out, uint32_t max_charts,
                                                       DevCounters* ctr) {
   pdl_wait();
-  __shared__ uint32_t charts;
-  scan_counts(blockcnt, viscnt, nblocks, &charts, &ctr->n_vis);
-  if (threadIdx.x == 0) {
-    ctr->chart_count = charts;
-    *count_out = charts;
-    if (charts > max_charts) set_status(ctr, FA_E_CAPACITY);
-  }
+  cf::scan_blocks_body(blockcnt, viscnt, nblocks, count_out, max_charts, ctr);
 }
 
-// Scan of the visible counts alone (the standalone box / UV calls).
 __global__ void __launch_bounds__(1024) k_scan_vis(uint32_t* viscnt, uint32_t nblocks, DevCounters* ctr) {
   pdl_wait();
-  scan_counts(viscnt, nullptr, nblocks, &ctr->n_vis, nullptr);
+  cf::scan_vis_body(viscnt, nblocks, ctr);
 }
 
-// The entries of one 1024-triangle block's visible triangles in the list, in
-// triangle order: entry = list start of the block + the visible triangles before
-// it.  words[k] is VT word k * 8 + warp of the block.
-__device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / kBlock], uint32_t start,
-                                            const int32_t (&chart)[kPerBlock / kBlock], uint2* vis,
-                                            uint32_t tile) {
-  __shared__ uint32_t wpop[kPerBlock / 32];
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k)
-    if (lane == 0) wpop[k * (kBlock / 32) + wid] = __popc(words[k]);
-  __syncthreads();
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t wl = k * (kBlock / 32) + wid;
-    if (!((words[k] >> lane) & 1u)) continue;
-    uint32_t pre = start;
-    for (uint32_t i = 0; i < wl; ++i) pre += wpop[i];
-    pre += __popc(words[k] & ((1u << lane) - 1u));
-    const uint32_t t = ((tile * (kPerBlock / 32) + wl) << 5) + lane;
-    vis[pre] = make_uint2(t, (uint32_t)chart[k]);
-  }
-}
-
-// Chart id of every triangle (-1 invisible; charts numbered by ascending root) and
-// the visible-triangle list (same blocking as k_uf_flatten); each root records
-// itself as its chart's root and resets the chart's box accumulators.
-__device__ __forceinline__ void chart_tile(const UfArgs& a, uint32_t tile, const uint32_t* blockcnt,
-                                           const uint2* wordroots, int32_t* tri_chart, uint32_t* roots,
-                                           uint32_t* box_enc, uint32_t* box_full, uint32_t max_charts,
-                                           const uint32_t* visstart, uint2* vis) {
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  const uint32_t nwords = (a.T + 31) >> 5;
-  uint32_t words[kPerBlock / kBlock];
-  int32_t chart[kPerBlock / kBlock];
-#pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / kBlock; ++k) {
-    const uint32_t w = tile * (kPerBlock / 32) + k * (kBlock / 32) + wid;
-    words[k] = w < nwords ? __ldg(a.vt + w) : 0u;
-    const uint32_t t = (w << 5) + lane;
-    int32_t out = -1;
-    if ((words[k] >> lane) & 1u) {
-      const uint32_t r = (uint32_t)__ldcg(a.label + t);
-      const uint32_t c = chart_of_root(blockcnt, wordroots, r);
-      out = (int32_t)c;
-      if (r == t && c < max_charts) {
-        roots[c] = t;
-        reinterpret_cast<uint4*>(box_enc)[c] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
-        box_full[c] = 0u;
-      }
-    }
-    chart[k] = out;
-    if (w < nwords && t < a.T) tri_chart[t] = out;
-  }
-  put_visible(words, __ldcg(visstart + tile), chart, vis, tile);
-}
-
-// Every counting block (a block each; invisible triangles get -1), or, when the
-// raster front end already set tri_chart to -1, only the listed tiles (a persistent
-// grid over the list).
 template <bool LIST>
 __global__ void __launch_bounds__(kBlock) k_tri_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots,
                                                       int32_t* tri_chart, uint32_t* roots, uint32_t* box_enc,
                                                       uint32_t* box_full, uint32_t max_charts,
                                                       const uint32_t* visstart, uint2* vis) {
   pdl_wait();
-  if (__ldcg(&a.ctr->status) != 0) return;
-  if (!LIST) {
-    chart_tile(a, blockIdx.x, blockcnt, wordroots, tri_chart, roots, box_enc, box_full, max_charts, visstart, vis);
-    return;
-  }
-  const uint32_t n = __ldcg(&a.ctr->n_vtiles);
-  for (uint32_t i = blockIdx.x; i < n; i += gridDim.x) {
-    __syncthreads();  // the shared memory of the previous tile is free
-    chart_tile(a, __ldcg(a.tile_list + i), blockcnt, wordroots, tri_chart, roots, box_enc, box_full, max_charts,
-               visstart, vis);
-  }
+  cf::tri_chart_body<LIST, kBlock>(a, blockcnt, wordroots, tri_chart, roots, box_enc, box_full, max_charts,
+                                   visstart, vis, blockIdx.x, gridDim.x);
+}
+
+__global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots, int32_t* vert_chart,
+                             int vertex_mode) {
+  pdl_wait();
+  cf::vert_chart_body(a, blockcnt, wordroots, vert_chart, vertex_mode, blockIdx.x, gridDim.x);
 }
 
 // Standalone path: visible counts per block from a caller's tri_chart ...
@@ -552,21 +107,7 @@ __global__ void __launch_bounds__(kBlock) k_vis_fill(const int32_t* tri_chart, u
     chart[k] = t < T ? tri_chart[t] : -1;
     words[k] = __ballot_sync(0xFFFFFFFFu, chart[k] >= 0);
   }
-  put_visible(words, __ldcg(visstart + blockIdx.x), chart, vis, blockIdx.x);
-}
-
-__global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wordroots, int32_t* vert_chart,
-                             int vertex_mode) {
-  pdl_wait();
-  if (__ldcg(&a.ctr->status) != 0) return;
-  for (uint32_t v = blockIdx.x * blockDim.x + threadIdx.x; v < a.V; v += gridDim.x * blockDim.x) {
-    int32_t out = -1;
-    if (vertex_mode) {
-      int32_t r = find_root(a.label, (int32_t)(a.T + v));
-      if (r < (int32_t)a.T) out = (int32_t)chart_of_root(blockcnt, wordroots, (uint32_t)r);
-    }
-    vert_chart[v] = out;
-  }
+  cf::put_visible<kBlock>(words, __ldcg(visstart + blockIdx.x), chart, vis, blockIdx.x);
 }
 
 }  // namespace
@@ -574,18 +115,7 @@ __global__ void k_vert_chart(UfArgs a, const uint32_t* blockcnt, const uint2* wo
 fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, uint32_t mode,
                           int32_t* tri_chart, int32_t* vert_chart, const fa_charts* ch, cudaStream_t s,
                           bool tile_list, bool tri_chart_cleared) {
-  UfArgs a;
-  a.vt = vt;
-  a.idx = mesh->idx;
-  a.adj = mesh->adj;
-  a.T = mesh->T;
-  a.V = mesh->V;
-  a.label = ctx->label;
-  a.xedge = ctx->xedge;
-  a.xcnt = ctx->xcnt;
-  a.tile_list = ctx->tile_list;
-  a.ctr = ctx->ctr;
-  a.loop_cap = ctx->loop_cap;
+  const UfArgs a = cf::make_uf_args(ctx, mesh, vt);
   const int vm = mode == FA_CHARTS_VERTEX;
   const unsigned gw = grid_for((uint64_t)((mesh->T + 31) / 32) * 32, kBlock, 152 * 16);
   if (vm) {

@@ -266,7 +266,7 @@ __device__ __forceinline__ void set_status(DevCounters* c, int32_t s) {
 }
 
 __device__ __forceinline__ bool vt_bit(const uint32_t* vt, uint32_t t) {
-  return (__ldg(vt + (t >> 5)) >> (t & 31)) & 1u;
+  return (__ldcg(vt + (t >> 5)) >> (t & 31)) & 1u;
 }
 
 inline unsigned grid_for(uint64_t n, unsigned block, unsigned cap = 152u * 16u) {
