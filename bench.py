@@ -390,6 +390,18 @@ def run_batched(a, F, S, torch):
     F.atlas_batch(batch, mb, params, out)
     torch.cuda.synchronize()
     launches = batch.launches - n0
+    del g
+    # the same batch as one launch of the persistent frame kernel (a batch plan),
+    # its schedule autotuned first
+    plan = F.BatchPlan(batch, mb, params, out)
+    p_lanes, p_pol, p_pct, _ = plan.tune(reps=2)
+    t_plan = timed(plan.launch)
+    plan_ok = all(int(b.result[3]) == 0 for b in out)
+    n0 = batch.launches
+    plan.launch()
+    torch.cuda.synchronize()
+    plan_launches = batch.launches - n0
+    plan.close()
     for m in mb + ms:
         m.close()
     batch.close()
@@ -406,7 +418,13 @@ def run_batched(a, F, S, torch):
             "batched_ms_p50": bp50, "batched_ms_p99": _pct(t_batch, 99),
             "batched_views_per_s": n / (bp50 * 1e-3), "batched_gpu_launches": launches,
             "plain_ms_p50": pp50, "plain_ms_p99": _pct(t_plain, 99), "plain_views_per_s": n / (pp50 * 1e-3),
-            "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps, "cpu_baseline": cpu}
+            "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps,
+            "persistent_plan": {"launches_per_batch": plan_launches, "lanes": p_lanes,
+                                "policy": "longest_first" if p_pol else "round_robin", "worker_pct": p_pct,
+                                "ms_p50": _pct(t_plan, 50), "ms_p99": _pct(t_plan, 99),
+                                "views_per_s": n / (_pct(t_plan, 50) * 1e-3),
+                                "speedup_p50_vs_plain": pp50 / _pct(t_plan, 50), "all_views_packed": plan_ok},
+            "cpu_baseline": cpu}
 
 
 def run_served(a, F, S, torch):
@@ -576,6 +594,17 @@ def run_extras(a, F, S, torch):
                           "graph": timed(gr.replay),
                           "stream": timed(lambda: F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0))}
     del gr
+    # the same frame as one launch of the persistent frame kernel (FA_FRAME_PERSISTENT)
+    pf = F.FA_FRAME_PERSISTENT
+    F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0, flags=pf)
+    torch.cuda.synchronize()
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr):
+        F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0, flags=pf)
+    out["small_frame"]["persistent"] = {
+        "graph": timed(gr.replay), "stream": timed(lambda: F.atlas_frame(ctx, mesh, bufs, M, W, H, p["ratio"], L, 0,
+                                                                         flags=pf)), "launches_per_frame": 1}
+    del gr
 
     sc2, cams, p2 = S.camera_path_frames(1, 300)
     mesh2 = F.Mesh(ctx, sc2.pos, sc2.idx)
@@ -587,17 +616,30 @@ def run_extras(a, F, S, torch):
     gr = torch.cuda.CUDAGraph()
     with torch.cuda.graph(gr):
         F.atlas_frame_dev_matrix(ctx, mesh2, bufs, dm, p2["width"], p2["height"], p2["ratio"], p2["atlas_log2"])
-    t = []
-    for i in range(len(cams)):
-        e0.record(stream)
-        dm.copy_(h_cams[i], non_blocking=True)
-        gr.replay()
-        e1.record(stream)
-        e1.synchronize()
-        t.append(1e3 * e0.elapsed_time(e1))
+    def path(graph):
+        t = []
+        for i in range(len(cams)):
+            e0.record(stream)
+            dm.copy_(h_cams[i], non_blocking=True)
+            graph.replay()
+            e1.record(stream)
+            e1.synchronize()
+            t.append(1e3 * e0.elapsed_time(e1))
+        return t
+
+    t = path(gr)
     out["camera_path"] = {"workload": "heightfield64_spline300_1920x1080_atlas2048_ratio1", "frames": len(cams),
                           "us_p50": _pct(t, 50), "us_p99": _pct(t, 99), "us_mean": float(np.mean(t)),
                           "frames_per_s": 1e6 * len(t) / sum(t)}
+    del gr
+    dm.copy_(h_cams[0])
+    gr = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(gr):
+        F.atlas_frame_dev_matrix(ctx, mesh2, bufs, dm, p2["width"], p2["height"], p2["ratio"], p2["atlas_log2"],
+                                 flags=F.FA_FRAME_PERSISTENT)
+    t = path(gr)
+    out["camera_path"]["persistent"] = {"us_p50": _pct(t, 50), "us_p99": _pct(t, 99),
+                                        "frames_per_s": 1e6 * len(t) / sum(t), "launches_per_frame": 1}
     del gr
     mesh2.close()
     mesh.close()

@@ -112,7 +112,8 @@ typedef struct {
   uint32_t chart_mode;  /* fa_chart_mode                                           */
   uint32_t n_scales;    /* candidate scales k / n, k = 1..n; n in {1,2,4,...,64}   */
   uint32_t select_mode; /* fa_select_mode                                          */
-  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE | FA_LOWRES(d) */
+  uint32_t flags;       /* FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE | FA_LOWRES(d) |
+                           FA_FRAME_PERSISTENT */
 } fa_frame_params;
 
 /* fa_frame_params.flags / fa_parameterize flags.  FA_BOX_FRUSTUM_CLIP: a visible
@@ -140,6 +141,16 @@ typedef struct {
  * share no texel of the scaled atlas.  Needs a context gutter > 0.  The scaled
  * atlas's UVs are the UVs times 2^-d (exact in fp32). */
 #define FA_LOWRES(d) ((((uint32_t)(d)) & 7u) << 8)
+
+/* fa_frame_params.flags: run the whole frame as ONE launch of the persistent frame
+ * kernel instead of the 15-launch sequence.  A cooperative grid of one CTA per SM
+ * takes (stage, worker) items in order from a device queue; a stage starts when the
+ * stage before it has finished (a device counter instead of a kernel boundary).
+ * The stages run the same code as the separate kernels, so the results are
+ * identical; on small frames the launch and drain of every kernel of the sequence
+ * dominate, and this removes them.  Works with every other flag, chart mode and
+ * output, in fa_atlas_frame, fa_atlas_frame_dev_matrix, batches and the server. */
+#define FA_FRAME_PERSISTENT (1u << 12)
 
 /* All outputs of fa_atlas_frame (caller-owned device memory). */
 typedef struct {
@@ -431,6 +442,63 @@ fa_status fa_batch_tune(fa_batch* batch, uint32_t n_views, const fa_mesh* const*
 
 /* Kernels launched by all lanes since creation. */
 uint64_t fa_batch_launch_count(const fa_batch* batch);
+
+/* Batch plans: the views of a batch atlased by ONE launch of the persistent frame
+ * kernel (see FA_FRAME_PERSISTENT).  The launch is a cooperative grid of one
+ * 1024-thread CTA per SM that drains a device work queue of (view, stage, worker)
+ * items: a stage is one step of the per-frame path (raster front end, exact
+ * set-up, large-triangle tiles, marking, the union-find passes, chart ids, boxes,
+ * order, width scan, push, UVs), its workers are the virtual blocks of that step's
+ * kernel.  Items are claimed in a fixed order: round by round (the r-th view of
+ * every lane), stage by stage, lane by lane; an item waits until the stage before
+ * it has finished (and a view's first stage until the lane's previous view has).
+ * While one view's latency-bound stages leave SMs idle, the other views' stages run
+ * there.  Results equal fa_atlas_frame's for every view.  A plan is set-up work:
+ * creating or rescheduling it builds and uploads the views' arguments and
+ * synchronizes the device; launching it only enqueues the one kernel, so a CUDA
+ * graph captured from fa_batch_plan_launch atlases the batch in one kernel node.
+ * The views' matrices are params[i].view_proj, or read on the device when the
+ * kernel runs from d_view_proj[i] (16 floats, 16-byte aligned) when d_view_proj is
+ * given, so a captured launch can serve new cameras.  Meshes, outputs and matrix
+ * buffers must stay alive and in place while the plan is used. */
+typedef struct fa_batch_plan fa_batch_plan;
+
+#define FA_PLAN_MAX_VIEWS 4096u
+
+/* Schedule of a plan; it changes timing only, never results. */
+typedef struct {
+  uint32_t lanes;      /* lanes (contexts) used, 1 .. the batch's n_lanes; a lane's views run in turn */
+  uint32_t policy;     /* fa_batch_policy: views to lanes */
+  uint32_t worker_pct; /* workers per data-sized stage, percent of the default counts (10 .. 1000) */
+} fa_plan_schedule;
+
+/* Plan n_views views (as fa_atlas_batch) on all of the batch's lanes, longest
+ * first, default worker counts.  d_view_proj may be NULL.
+ * Errors: FA_E_INVALID_ARG (a view fails fa_atlas_frame's checks, n_views 0 or above
+ * FA_PLAN_MAX_VIEWS), FA_E_OUT_OF_MEMORY, FA_E_CUDA. */
+fa_status fa_batch_plan_create(fa_batch* batch, uint32_t n_views, const fa_mesh* const* meshes,
+                               const fa_frame_params* params, const float* const* d_view_proj,
+                               const fa_frame_out* outs, fa_batch_plan** out);
+
+/* One launch of the persistent kernel for every view of the plan on `stream`.  Each
+ * view's status lands in its result record (FA_E_TIMEOUT for every view if a wait
+ * of the launch ran out).  Launches of one plan must not overlap on the GPU.
+ * Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_batch_plan_launch(fa_batch_plan* plan, fa_stream_t stream);
+
+/* Read / change the schedule (changing it rebuilds the plan; synchronizes). */
+fa_status fa_batch_plan_get_schedule(const fa_batch_plan* plan, fa_plan_schedule* schedule);
+fa_status fa_batch_plan_set_schedule(fa_batch_plan* plan, const fa_plan_schedule* schedule);
+
+/* Schedule autotuner: lanes in {1, 2, 4, .., n_lanes} x both policies x worker
+ * counts at 50 / 100 / 200 %; each schedule is launched once, then `reps` launches
+ * are timed (CUDA events, best of); the fastest is kept.  Runs the views (outputs
+ * are overwritten) and synchronizes; not for use inside a capture.  *best_ms (may
+ * be NULL) receives its time.  Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
+fa_status fa_batch_plan_tune(fa_batch_plan* plan, uint32_t reps, float* best_ms);
+
+/* Synchronizes the device and frees the plan.  NULL is ignored. */
+void fa_batch_plan_destroy(fa_batch_plan* plan);
 
 /* ------------------------------------------------------------------ serving
  *

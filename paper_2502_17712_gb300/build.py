@@ -14,7 +14,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libfastatlas.so")
-SOURCES = ["api.cu", "raster.cu", "chartify.cu", "param.cu", "pack.cu", "mesh.cu", "batch.cu", "server.cu"]
+SOURCES = ["api.cu", "raster.cu", "chartify.cu", "param.cu", "pack.cu", "mesh.cu", "batch.cu", "server.cu",
+           "persist.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVFLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
            "--expt-relaxed-constexpr"]

@@ -96,7 +96,7 @@ void fa_destroy(fa_ctx* ctx) {
   void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip, ctx->clip_count,
                   ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt, ctx->tile_flag, ctx->tile_list,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total,
-                  p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand};
+                  p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand, ctx->psched};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   std::free(ctx);
@@ -173,11 +173,13 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   FA_ALLOC(pk.m, kMaxScales);
   FA_ALLOC(pk.xy, (uint64_t)kMaxScales * C);
   FA_ALLOC(pk.cand, kMaxScales);
+  FA_ALLOC(ctx->psched, kPschedWords);
 #undef FA_ALLOC
   pk.ctr = ctx->ctr;
   pk.count = nullptr;
   if (st == FA_OK && cudaMemset(ctx->ctr, 0, sizeof(DevCounters)) != cudaSuccess) st = FA_E_CUDA;
   if (st == FA_OK && cudaMemset(pk.ord_total, 0, kMaxH * sizeof(uint32_t)) != cudaSuccess) st = FA_E_CUDA;
+  if (st == FA_OK && cudaMemset(ctx->psched, 0, kPschedWords * sizeof(uint32_t)) != cudaSuccess) st = FA_E_CUDA;
   if (st == FA_OK && cudaDeviceSynchronize() != cudaSuccess) st = FA_E_CUDA;
   if (st != FA_OK) {
     fa_destroy(ctx);
@@ -323,7 +325,8 @@ fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_par
   if (st == FA_OK) st = check_pack(ctx, p->atlas_log2, p->n_scales, p->select_mode);
   if (st != FA_OK) return st;
   if (p->chart_mode > FA_CHARTS_VERTEX || !(p->ratio > 0.0f && p->ratio <= 64.0f)) return FA_E_INVALID_ARG;
-  if (p->flags & ~(FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE | FA_LOWRES(7))) return FA_E_INVALID_ARG;
+  if (p->flags & ~(FA_BOX_FRUSTUM_CLIP | FA_VIS_CONSERVATIVE | FA_LOWRES(7) | FA_FRAME_PERSISTENT))
+    return FA_E_INVALID_ARG;
   if (d_view_proj && (reinterpret_cast<uintptr_t>(d_view_proj) & 15u)) return FA_E_INVALID_ARG;
   return FA_OK;
 }
@@ -332,6 +335,7 @@ fa_status check_frame(const fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_par
 // matrix is p->view_proj, or read on the device from d_view_proj.
 fa_status enqueue_frame(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, const float* d_view_proj,
                         const fa_frame_out* o, cudaStream_t s) {
+  if (p->flags & FA_FRAME_PERSISTENT) return enqueue_frame_persistent(ctx, mesh, p, d_view_proj, o, s);
   fa_status st;
   const Mat4 M = d_view_proj ? Mat4{} : to_mat(p->view_proj);
   const float* Md = d_view_proj;

@@ -13,17 +13,6 @@
 
 #include "fa_internal.cuh"
 
-struct fa_batch {
-  fa_config cfg;
-  int device = 0;
-  uint32_t active = 1;  // lanes in use
-  uint32_t policy = FA_BATCH_ROUND_ROBIN;
-  std::vector<fa_ctx*> ctx;
-  std::vector<cudaStream_t> stream;
-  std::vector<cudaEvent_t> join;
-  cudaEvent_t fork = nullptr;
-};
-
 namespace {
 
 struct Guard {

@@ -219,24 +219,30 @@ __device__ __forceinline__ void init_v_body(int32_t* label, uint32_t T, uint32_t
 // Hooking (Alg. 1, second loop), edge mode: the edges that leave a tile, each once
 // from its lower end, when the other end is visible too (edges inside a tile were
 // joined by k_uf_local).  One block per tile.
-__device__ __forceinline__ void hook_tile(const UfArgs& a, uint32_t tile) {
+// t0 / nt: this thread's index in the group of threads that hooks the tile, and the
+// group's size (the block, or a slice of it).
+__device__ __forceinline__ void hook_tile(const UfArgs& a, uint32_t tile, uint32_t t0, uint32_t nt) {
   const uint32_t n = min(__ldcg(a.xcnt + tile), kXCap);
   const uint2* xe = a.xedge + (size_t)tile * kXCap;
-  for (uint32_t i = threadIdx.x; i < n; i += blockDim.x) {
+  for (uint32_t i = t0; i < n; i += nt) {
     const uint2 e = __ldcg(xe + i);
     if (e.y < a.T && vt_bit(a.vt, e.y)) unite(a.label, (int32_t)e.x, (int32_t)e.y, a.ctr, a.loop_cap);
   }
 }
 
-template <bool LIST>
+// Each tile is hooked by a group of GT threads (GT divides the block; no barriers),
+// so that a large block hooks several tiles at once.
+template <bool LIST, uint32_t GT = 0>
 __device__ __forceinline__ void hook_body(const UfArgs& a, uint32_t bid, uint32_t nblk) {
+  const uint32_t gt = GT ? GT : blockDim.x, per = blockDim.x / gt;
+  const uint32_t grp = bid * per + threadIdx.x / gt, ngrp = nblk * per, t0 = threadIdx.x % gt;
   if (!LIST) {
     const uint32_t ntiles = (a.T + kTile - 1) / kTile;
-    for (uint32_t t = bid; t < ntiles; t += nblk) hook_tile(a, t);
+    for (uint32_t t = grp; t < ntiles; t += ngrp) hook_tile(a, t, t0, gt);
     return;
   }
   const uint32_t n = __ldcg(&a.ctr->n_vtiles);
-  for (uint32_t i = bid; i < n; i += nblk) hook_tile(a, __ldcg(a.tile_list + i));
+  for (uint32_t i = grp; i < n; i += ngrp) hook_tile(a, __ldcg(a.tile_list + i), t0, gt);
 }
 
 // Vertex mode: every visible triangle joins its three vertex nodes T + v.

@@ -4,6 +4,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <vector>
+
 #include "../../include/fastatlas.h"
 
 namespace fa {
@@ -25,6 +27,7 @@ constexpr unsigned long long kWaitNs = FA_DEFAULT_WAIT_NS;  // device time limit
 
 // Small counters that live in device memory (one struct per context).
 constexpr uint32_t kMaxFrontBlocks = 152 * 4;  // raster front-end blocks (survivor regions)
+constexpr uint32_t kPschedWords = 64;          // schedule state of a single-view persistent launch
 
 struct DevCounters {
   int32_t status;          // sticky fa_status of the context
@@ -134,6 +137,22 @@ struct fa_ctx {
   // limits of the device-side waits of later launches (fa_set_wait_limits)
   uint32_t loop_cap;
   unsigned long long wait_ns;
+  // schedule state of the persistent frame kernel (FA_FRAME_PERSISTENT): work-item
+  // counter, exit counter, abort flag and one completion counter per stage group;
+  // zero between launches
+  uint32_t* psched;
+};
+
+// A batch: lanes (contexts of one configuration), each with its own stream.
+struct fa_batch {
+  fa_config cfg;
+  int device = 0;
+  uint32_t active = 1;  // lanes in use
+  uint32_t policy = FA_BATCH_ROUND_ROBIN;
+  std::vector<fa_ctx*> ctx;
+  std::vector<cudaStream_t> stream;
+  std::vector<cudaEvent_t> join;
+  cudaEvent_t fork = nullptr;
 };
 
 struct fa_mesh {
@@ -374,5 +393,9 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
                               uint32_t gutter, uint32_t* order, fa_placement* place, fa_pack_result* res,
                               cudaStream_t s, uint32_t lowres_log2, const FootArgs* foot, bool write_place);
 fa_status pack_set_smem_limit();
+// fa_atlas_frame with FA_FRAME_PERSISTENT: the checked frame as one launch of the
+// persistent frame kernel (persist.cu).
+fa_status enqueue_frame_persistent(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p,
+                                   const float* d_view_proj, const fa_frame_out* o, cudaStream_t s);
 
 }  // namespace fa

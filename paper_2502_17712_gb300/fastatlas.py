@@ -33,6 +33,7 @@ FA_SELECT_EFFECTIVE = 0
 FA_SELECT_LARGEST_K = 1
 FA_BOX_FRUSTUM_CLIP = 1
 FA_VIS_CONSERVATIVE = 2
+FA_FRAME_PERSISTENT = 1 << 12
 
 
 def FA_LOWRES(d):
@@ -46,7 +47,9 @@ EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh
            "fa_batch_destroy", "fa_batch_mesh_register", "fa_batch_set_schedule", "fa_batch_get_schedule",
            "fa_atlas_batch", "fa_batch_tune", "fa_batch_launch_count", "fa_server_create", "fa_server_destroy",
            "fa_server_session_open", "fa_server_session_close", "fa_server_submit", "fa_server_poll",
-           "fa_server_stats", "fa_server_now_ms", "fa_frame_stats_read", "fa_set_wait_limits"]
+           "fa_server_stats", "fa_server_now_ms", "fa_frame_stats_read", "fa_set_wait_limits",
+           "fa_batch_plan_create", "fa_batch_plan_launch", "fa_batch_plan_get_schedule",
+           "fa_batch_plan_set_schedule", "fa_batch_plan_tune", "fa_batch_plan_destroy"]
 FA_DEFAULT_LOOP_CAP = 1 << 24
 FA_DEFAULT_WAIT_NS = 1_000_000_000
 
@@ -91,6 +94,10 @@ class fa_frame_stats(ctypes.Structure):
     _fields_ = [("survivors", ctypes.c_uint32), ("clipped", ctypes.c_uint32), ("clip_records", ctypes.c_uint32),
                 ("big_entries", ctypes.c_uint32), ("big_tiles", ctypes.c_uint64), ("visible", ctypes.c_uint32),
                 ("charts", ctypes.c_uint32), ("visible_tiles", ctypes.c_uint32)]
+
+
+class fa_plan_schedule(ctypes.Structure):
+    _fields_ = [("lanes", ctypes.c_uint32), ("policy", ctypes.c_uint32), ("worker_pct", ctypes.c_uint32)]
 
 
 class fa_server_done(ctypes.Structure):
@@ -156,6 +163,19 @@ def load(path: str = LIB_PATH):
     lib.fa_batch_tune.argtypes = [P, u32, ctypes.POINTER(P), ctypes.POINTER(fa_frame_params),
                                   ctypes.POINTER(fa_frame_out), u32, ctypes.POINTER(f32)]
     lib.fa_batch_tune.restype = st
+    lib.fa_batch_plan_create.argtypes = [P, u32, ctypes.POINTER(P), ctypes.POINTER(fa_frame_params),
+                                         ctypes.POINTER(P), ctypes.POINTER(fa_frame_out), ctypes.POINTER(P)]
+    lib.fa_batch_plan_create.restype = st
+    lib.fa_batch_plan_launch.argtypes = [P, P]
+    lib.fa_batch_plan_launch.restype = st
+    lib.fa_batch_plan_get_schedule.argtypes = [P, ctypes.POINTER(fa_plan_schedule)]
+    lib.fa_batch_plan_get_schedule.restype = st
+    lib.fa_batch_plan_set_schedule.argtypes = [P, ctypes.POINTER(fa_plan_schedule)]
+    lib.fa_batch_plan_set_schedule.restype = st
+    lib.fa_batch_plan_tune.argtypes = [P, u32, ctypes.POINTER(f32)]
+    lib.fa_batch_plan_tune.restype = st
+    lib.fa_batch_plan_destroy.argtypes = [P]
+    lib.fa_batch_plan_destroy.restype = None
     lib.fa_batch_launch_count.argtypes = [P]
     lib.fa_batch_launch_count.restype = ctypes.c_uint64
     lib.fa_server_create.argtypes = [ctypes.POINTER(P), ctypes.POINTER(fa_config), u32, ctypes.c_uint64,
@@ -452,11 +472,11 @@ def atlas_frame(ctx: Context, mesh: Mesh, bufs: FrameBuffers, M, width, height, 
 
 def atlas_frame_dev_matrix(ctx: Context, mesh: Mesh, bufs: FrameBuffers, d_view_proj, width, height, ratio,
                            atlas_log2, chart_mode=FA_CHARTS_EDGE, n_scales=64, select_mode=FA_SELECT_EFFECTIVE,
-                           stream=None):
+                           stream=None, flags=0):
     """fa_atlas_frame_dev_matrix: the matrix is the device tensor ``d_view_proj``
     (16 float32, row-major), read when the kernels run."""
     p = frame_params(np.eye(4, dtype=np.float32), width, height, ratio, atlas_log2, chart_mode, n_scales,
-                     select_mode)
+                     select_mode, flags)
     fa_atlas_frame_dev_matrix(ctx.handle, mesh.handle, p, d_view_proj, bufs.c_out(), stream)
 
 
@@ -538,6 +558,53 @@ def batch_tune(batch: Batch, meshes, params, bufs, reps=3):
     _check(load().fa_batch_tune(batch.handle, n, mh, pa, oa, reps, ctypes.byref(ms)), "fa_batch_tune")
     lanes, pol = batch.schedule()
     return lanes, pol, ms.value
+
+
+class BatchPlan:
+    """An fa_batch_plan: the views of a batch atlased by one launch of the persistent
+    frame kernel.  ``d_view_proj`` (optional) is a list of device tensors of 16
+    float32 each, read when the kernel runs (the views' params matrices are then
+    ignored)."""
+
+    def __init__(self, batch: Batch, meshes, params, bufs, d_view_proj=None):
+        n, mh, pa, oa = _batch_arrays(meshes, params, bufs)
+        dm = None
+        if d_view_proj is not None:
+            dm = (ctypes.c_void_p * n)(*[_ptr(t) for t in d_view_proj])
+        h = ctypes.c_void_p()
+        _check(load().fa_batch_plan_create(batch.handle, n, mh, pa, dm, oa, ctypes.byref(h)),
+               "fa_batch_plan_create")
+        self.handle = h.value
+        self._keep = (batch, meshes, bufs, d_view_proj, mh, pa, oa)
+
+    def launch(self, stream=None):
+        _check(load().fa_batch_plan_launch(self.handle, _stream(stream)), "fa_batch_plan_launch")
+
+    def schedule(self):
+        s = fa_plan_schedule()
+        _check(load().fa_batch_plan_get_schedule(self.handle, ctypes.byref(s)), "fa_batch_plan_get_schedule")
+        return s.lanes, s.policy, s.worker_pct
+
+    def set_schedule(self, lanes, policy=FA_BATCH_LONGEST_FIRST, worker_pct=100):
+        s = fa_plan_schedule(lanes, policy, worker_pct)
+        _check(load().fa_batch_plan_set_schedule(self.handle, ctypes.byref(s)), "fa_batch_plan_set_schedule")
+
+    def tune(self, reps=3):
+        """fa_batch_plan_tune; returns (lanes, policy, worker_pct, best_ms)."""
+        ms = ctypes.c_float()
+        _check(load().fa_batch_plan_tune(self.handle, reps, ctypes.byref(ms)), "fa_batch_plan_tune")
+        return (*self.schedule(), ms.value)
+
+    def close(self):
+        if self.handle:
+            load().fa_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 # ------------------------------------------------------------------ serving
