@@ -378,6 +378,11 @@ def run_batched(a, F, S, torch):
         return t
 
     t_plain = timed(plain)
+    # the plain path again with the raster schedule for mid-size triangles on (a
+    # schedule knob the tuners below search; it changes no result)
+    solo.set_raster_schedule(64)
+    t_plain_mid = timed(plain)
+    solo.set_raster_schedule()
     lanes, policy, _ = F.batch_tune(batch, mb, params, out, reps=2)
     F.atlas_batch(batch, mb, params, out)
     torch.cuda.synchronize()
@@ -394,7 +399,7 @@ def run_batched(a, F, S, torch):
     # the same batch as one launch of the persistent frame kernel (a batch plan),
     # its schedule autotuned first
     plan = F.BatchPlan(batch, mb, params, out)
-    p_lanes, p_pol, p_pct, _ = plan.tune(reps=2)
+    p_lanes, p_pol, p_pct, p_mid, _ = plan.tune(reps=2)
     t_plan = timed(plan.launch)
     plan_ok = all(int(b.result[3]) == 0 for b in out)
     n0 = batch.launches
@@ -418,9 +423,11 @@ def run_batched(a, F, S, torch):
             "batched_ms_p50": bp50, "batched_ms_p99": _pct(t_batch, 99),
             "batched_views_per_s": n / (bp50 * 1e-3), "batched_gpu_launches": launches,
             "plain_ms_p50": pp50, "plain_ms_p99": _pct(t_plain, 99), "plain_views_per_s": n / (pp50 * 1e-3),
+            "plain_raster_mid64_ms_p50": _pct(t_plain_mid, 50),
             "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps,
             "persistent_plan": {"launches_per_batch": plan_launches, "lanes": p_lanes,
                                 "policy": "longest_first" if p_pol else "round_robin", "worker_pct": p_pct,
+                                "raster_mid_max_pix": p_mid,
                                 "ms_p50": _pct(t_plan, 50), "ms_p99": _pct(t_plan, 99),
                                 "views_per_s": n / (_pct(t_plan, 50) * 1e-3),
                                 "speedup_p50_vs_plain": pp50 / _pct(t_plan, 50), "all_views_packed": plan_ok},

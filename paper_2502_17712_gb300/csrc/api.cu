@@ -126,6 +126,7 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   ctx->device = c.device;
   ctx->loop_cap = kLoopCap;
   ctx->wait_ns = kWaitNs;
+  ctx->mid_max_pix = FA_RASTER_MID_OFF;
   fa_status st = FA_OK;
   const uint64_t T = c.max_tris, V = c.max_verts, C = c.max_charts;
   ctx->queue_cap = (uint32_t)(T < (1u << 20) ? T + 1024 : (1u << 20));
@@ -416,6 +417,12 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {
 }
 
 uint64_t fa_launch_count(const fa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix) {
+  if (!ctx || mid_max_pix < FA_RASTER_MID_OFF || mid_max_pix > FA_RASTER_MID_MAX) return FA_E_INVALID_ARG;
+  ctx->mid_max_pix = mid_max_pix;
+  return FA_OK;
+}
 
 fa_status fa_set_wait_limits(fa_ctx* ctx, uint32_t loop_cap, uint64_t wait_ns) {
   if (!ctx) return FA_E_INVALID_ARG;

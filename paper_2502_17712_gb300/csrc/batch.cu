@@ -189,13 +189,17 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
   for (uint32_t l = 1; l < max_lanes; l <<= 1) cand.push_back(l);
   cand.push_back(max_lanes);
   float best = -1.0f;
-  uint32_t best_l = b->active, best_p = b->policy;
+  uint32_t best_l = b->active, best_p = b->policy, best_m = b->ctx[0]->mid_max_pix;
+  const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
   fa_status st = FA_OK;
   for (uint32_t l : cand) {
-    for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST && st == FA_OK; ++pol) {
+    for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST && st == FA_OK; ++pol)
+    for (uint32_t mid : mids) {
+      if (st != FA_OK) break;
       if (l == 1 && pol == FA_BATCH_LONGEST_FIRST) continue;  // same schedule as round robin
       b->active = l;
       b->policy = pol;
+      for (fa_ctx* c : b->ctx) c->mid_max_pix = mid;
       // time the schedule as the caller would run it: one captured graph per batch
       cudaGraph_t graph = nullptr;
       cudaGraphExec_t exec = nullptr;
@@ -231,6 +235,7 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
         best = ms;
         best_l = l;
         best_p = pol;
+        best_m = mid;
       }
     }
     if (st != FA_OK) break;
@@ -241,6 +246,7 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
   cudaEventDestroy(e1);
   b->active = best_l;
   b->policy = best_p;
+  for (fa_ctx* c : b->ctx) c->mid_max_pix = best_m;
   if (best_ms) *best_ms = best;
   return st;
 }

@@ -19,6 +19,11 @@ constexpr int kMaxScales = 64;      // candidate scales (Sec. 4.2)
 constexpr uint32_t kFrontCap = 32768;  // frontline entries per candidate (smem)
 constexpr int kBigTile = 16;        // tile side of the large-triangle raster
 constexpr int kSmallMaxPix = 16;    // in-thread raster when the pixel box has <= this
+// boxes of up to mid_max_pix pixels (a per-context schedule knob, fa_set_raster_schedule)
+// are also rasterized in-thread when that costs the warp less than the tiles:
+constexpr uint32_t kMidSampleCost = 2;  // relative cost of one in-thread sample
+constexpr uint32_t kMidStepCost = 3;    // of one warp step of a tile
+constexpr uint32_t kMidTriCost = 10;    // of one queued triangle's record and set-up
 constexpr int kOrderTile = 1024;    // boxes per tile of the stable order
 constexpr uint32_t kLoopCap = FA_DEFAULT_LOOP_CAP;  // device iteration cap (FA_E_TIMEOUT)
 constexpr unsigned long long kWaitNs = FA_DEFAULT_WAIT_NS;  // device time limit of a bulk-copy wait
@@ -137,6 +142,7 @@ struct fa_ctx {
   // limits of the device-side waits of later launches (fa_set_wait_limits)
   uint32_t loop_cap;
   unsigned long long wait_ns;
+  uint32_t mid_max_pix;  // fa_set_raster_schedule
   // schedule state of the persistent frame kernel (FA_FRAME_PERSISTENT): work-item
   // counter, exit counter, abort flag and one completion counter per stage group;
   // zero between launches

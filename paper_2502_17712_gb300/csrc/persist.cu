@@ -553,6 +553,7 @@ fa_status plan_build(fa_batch_plan* pl) {
     for (uint32_t i : assign[l]) {
       fa::build_view(b->ctx[l], pl->meshes[i], &pl->params[i], pl->dmat[i], &pl->outs[i], pl->G,
                      pl->sched.worker_pct, &vps[i]);
+      vps[i].va.ra.mid_max_pix = pl->sched.mid_max_pix;
       va[i] = vps[i].va;
       front_cap = std::max(front_cap, vps[i].front_cap);
     }
@@ -637,6 +638,7 @@ fa_status fa_batch_plan_create(fa_batch* b, uint32_t n_views, const fa_mesh* con
   pl->sched.lanes = (uint32_t)b->ctx.size();
   pl->sched.policy = FA_BATCH_LONGEST_FIRST;
   pl->sched.worker_pct = 100;
+  pl->sched.mid_max_pix = b->ctx[0]->mid_max_pix;
   pl->max_groups = n_views * (uint32_t)fa::kMaxStages;
   fa_status st = fa::persist_grid(b->device, &pl->G);
   if (st == FA_OK && (cudaMalloc(&pl->d_views, n_views * sizeof(fa::ViewArgs)) != cudaSuccess ||
@@ -690,7 +692,8 @@ fa_status fa_batch_plan_get_schedule(const fa_batch_plan* pl, fa_plan_schedule* 
 
 fa_status fa_batch_plan_set_schedule(fa_batch_plan* pl, const fa_plan_schedule* s) {
   if (!pl || !s || s->lanes == 0 || s->lanes > pl->batch->ctx.size() || s->policy > FA_BATCH_LONGEST_FIRST ||
-      s->worker_pct < 10 || s->worker_pct > 1000)
+      s->worker_pct < 10 || s->worker_pct > 1000 || s->mid_max_pix < FA_RASTER_MID_OFF ||
+      s->mid_max_pix > FA_RASTER_MID_MAX)
     return FA_E_INVALID_ARG;
   int prev = -1;
   cudaGetDevice(&prev);
@@ -725,15 +728,17 @@ fa_status fa_batch_plan_tune(fa_batch_plan* pl, uint32_t reps, float* best_ms) {
   for (uint32_t l = 1; l < max_lanes; l <<= 1) lanes.push_back(l);
   lanes.push_back(max_lanes);
   const uint32_t pcts[] = {50, 100, 200};
+  const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
   fa_plan_schedule best = pl->sched;
   float best_t = -1.0f;
   fa_status st = FA_OK;
   for (uint32_t l : lanes)
     for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST && st == FA_OK; ++pol)
-      for (uint32_t pct : pcts) {
+      for (uint32_t pct : pcts)
+        for (uint32_t mid : mids) {
         if (st != FA_OK) break;
         if (l == 1 && pol == FA_BATCH_LONGEST_FIRST) continue;  // the same order as round robin
-        fa_plan_schedule c{l, pol, pct};
+        fa_plan_schedule c{l, pol, pct, mid};
         st = fa_batch_plan_set_schedule(pl, &c);
         if (st != FA_OK) break;
         float ms = 0.0f;

@@ -324,6 +324,7 @@ struct RasterArgs {
   int reset_status;      // the front end clears the device status word first
   int32_t* tri_chart;    // when set, the front end sets it to -1 (the chart pass writes visible ones)
   uint32_t* partial_clear;  // when set, the front end also clears these ceil(T/32) words
+  uint32_t mid_max_pix;     // boxes up to this size may be rasterized in-thread (<= kSmallMaxPix: off)
   uint32_t* clip;  // triangles that need clipping, one region per front block like surv
   DevCounters* ctr;
   uint32_t* vt;
@@ -710,6 +711,8 @@ __device__ __forceinline__ void exact_body(const RasterArgs& A, uint32_t bid, ui
     Exact E;
     uint32_t t = 0, tiles = 0;
     int kind = 0;  // 0 nothing, 1 small, 2 large
+    bool mid = false;  // large, but at most kMidMaxPix pixels
+    uint32_t mid_pix = 0, mid_cost = 0;
     if (v < n) {
       const float4* sc = A.surv_clip + 3 * (size_t)i;
       t = __ldcg(A.surv + i);
@@ -719,9 +722,29 @@ __device__ __forceinline__ void exact_body(const RasterArgs& A, uint32_t bid, ui
         if (w * h > kSmallMaxPix) {
           kind = 2;
           tiles = (uint32_t)(((w + kBigTile - 1) / kBigTile) * ((h + kBigTile - 1) / kBigTile));
+          mid = w * h <= (int)A.mid_max_pix;
+          if (mid) {
+            mid_pix = (uint32_t)(w * h);
+            // the tile path: two rows per warp step in each 16-pixel-wide tile
+            // column, plus the queue record and its set-up
+            mid_cost = kMidStepCost * (uint32_t)((w + kBigTile - 1) / kBigTile) * (uint32_t)((h + 1) / 2) +
+                       kMidTriCost;
+          }
         } else {
           kind = 1;
         }
+      }
+    }
+    // Mid-size boxes are rasterized in-thread when that is cheaper for the warp: the
+    // in-thread loop lasts as long as the warp's largest box (the small boxes' 16
+    // samples are paid anyway), the tile path costs each such triangle its tile
+    // steps and its queue record.  Either way the same samples get the same keys.
+    {
+      const uint32_t smax = __reduce_max_sync(0xFFFFFFFFu, mid_pix);
+      const uint32_t tsum = __reduce_add_sync(0xFFFFFFFFu, mid_cost);
+      if (mid && (smax - (uint32_t)kSmallMaxPix) * kMidSampleCost < tsum) {
+        kind = 1;
+        tiles = 0;
       }
     }
     // large triangles of the warp reserve queue records and tiles with one atomic
@@ -944,6 +967,7 @@ inline RasterArgs make_raster_args(fa_ctx* ctx, const fa_mesh* mesh, const Mat4&
   A.reset_status = reset_status ? 1 : 0;
   A.tri_chart = tri_chart_init;
   A.partial_clear = nullptr;
+  A.mid_max_pix = ctx->mid_max_pix;
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;
