@@ -31,7 +31,7 @@ __global__ void __launch_bounds__(pk::kScanThreads) k_pack_scan(PackScratch p, P
 __global__ void __launch_bounds__(pk::kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
   pdl_wait();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  pk::push_body(p, a, blockIdx.x, gridDim.x, smem_raw);
+  pk::push_body<pk::kPushThreads>(p, a, blockIdx.x, gridDim.x, smem_raw);
 }
 
 __global__ void __launch_bounds__(256) k_pack_place(PackScratch p, PackArgs a) {

@@ -406,8 +406,7 @@ __device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackA
 // max of the frontline under the box, then the frontline takes the box top, one
 // barrier per segment.  Segments of one row never overlap in x, so a row may span
 // two chunks.
-constexpr int kPushThreads = 1024;
-constexpr uint32_t kGroupBoxes = 256;  // rows with more boxes take a thread per box
+constexpr int kPushThreads = 1024;  // threads of a candidate's CTA (the separate push kernel)
 constexpr uint32_t kStageBytes = kChunk * 8u + kSegStride * 2u;  // records + segment list
 static_assert(kStageBytes % 16u == 0u, "bulk copies move multiples of 16 bytes");
 
@@ -463,6 +462,8 @@ __device__ __forceinline__ bool better_cand(uint32_t k1, uint32_t o1, uint32_t k
 }
 
 // smem_raw: push_smem_bytes(a.front_cap) bytes of shared memory (128-byte aligned).
+// NT: threads of the CTA (a power of two, 64 .. 1024).
+template <int NT>
 __device__ __forceinline__ void push_body(const PackScratch& p, const PackArgs& a, uint32_t bid, uint32_t nblk,
                                           unsigned char* smem_raw) {
   uint32_t* F = reinterpret_cast<uint32_t*>(smem_raw + 2 * kStageBytes);  // [front_cap]
@@ -505,7 +506,7 @@ __device__ __forceinline__ void push_body(const PackScratch& p, const PackArgs& 
         bulk_g2s(dst, rec + (size_t)c * kChunk, rbytes, &s_bar[c & 1u]);
         bulk_g2s(dst + kChunk * 8u, sgg + (size_t)c * kSegStride, kSegStride * 2u, &s_bar[c & 1u]);
       };
-      for (uint32_t x = tid; x < Om; x += kPushThreads) F[x] = 0;
+      for (uint32_t x = tid; x < Om; x += NT) F[x] = 0;
       if (tid == 0) {
         mbar_init(&s_bar[0], 1);
         mbar_init(&s_bar[1], 1);
@@ -532,11 +533,11 @@ __device__ __forceinline__ void push_body(const PackScratch& p, const PackArgs& 
           const uint32_t j0 = min((uint32_t)s_sg[1 + sgi], kChunk), j1 = min((uint32_t)s_sg[2 + sgi], kChunk);
           const uint32_t nbx = j1 > j0 ? j1 - j0 : 0u;
           bool bad = false;
-          if (nbx > kGroupBoxes) {
-            // a thread per box (several boxes per thread past 1024).  Boxes of such rows
+          if (nbx > (uint32_t)NT / 4u) {
+            // a thread per box (several boxes per thread past NT).  Boxes of such rows
             // are mostly a few texels wide: the first four texels are read with
             // independent loads before any is used, the rest in a loop.
-            for (uint32_t jj = tid; jj < nbx; jj += kPushThreads) {
+            for (uint32_t jj = tid; jj < nbx; jj += NT) {
               const uint2 r = s_rec[j0 + jj];
               const uint32_t xr = r.x & 0xFFFFu, w = r.x >> 16, h = r.y & 0x7FFFFFFFu;
               uint32_t* Fx = F + ((r.y >> 31) ? xr : Om - xr - w);
@@ -554,11 +555,11 @@ __device__ __forceinline__ void push_body(const PackScratch& p, const PackArgs& 
               bad |= top > Om;
             }
           } else {
-            // a group of g threads per box, g = 32 for <= 32 boxes ... 4 for > 128:
-            // 1024 / g >= nbx, so every box has a group.  A box's group reads and then
+            // a group of g threads per box, g = min(32, NT / 2^ceil(log2 nbx)) >= 2:
+            // NT / g >= nbx, so every box has a group.  A box's group reads and then
             // writes only that box's texels, which no other box of the row touches.
             const int lgb = nbx > 1 ? 32 - __clz(nbx - 1) : 0;  // ceil(log2(nbx))
-            const int lg = min(max(10 - lgb, 0), 5);
+            const int lg = min(max((31 - __clz(NT)) - lgb, 0), 5);
             const uint32_t g = 1u << lg;
             const uint32_t jj = tid >> lg, li = tid & (g - 1u);
             uint32_t mx = 0, x = 0, w = 0, h = 0;

@@ -173,7 +173,7 @@ __device__ __noinline__ void st_pack_scan(const ViewArgs& v, uint32_t j) {
   pk::pack_scan_body<kPT>(v.ps, v.pa, v.n_scales, j);
 }
 __device__ __noinline__ void st_push(const ViewArgs& v, uint32_t j, uint32_t n, unsigned char* smem) {
-  pk::push_body(v.ps, v.pa, j, n, smem);
+  pk::push_body<kPT>(v.ps, v.pa, j, n, smem);
 }
 __device__ __noinline__ void st_place(const ViewArgs& v, uint32_t j, uint32_t n) { pk::pack_place_body(v.ps, v.pa, j, n); }
 template <bool DEV_M>
