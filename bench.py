@@ -143,7 +143,7 @@ class Clocks:
 
 
 # the frame's kernels by stage, in launch order (the paper's columns)
-STAGES = {"raster": ("k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_mark"),
+STAGES = {"raster": ("k_raster_front", "k_raster_exact", "k_raster_depth_big", "k_raster_zmax", "k_raster_mark"),
           "chartify": ("k_uf_local", "k_uf_hook", "k_uf_flatten", "k_scan_blocks", "k_tri_chart"),
           "parameterize": ("k_bbox",),
           "pack": ("k_order_tile", "k_order_scatter", "k_pack_scan", "k_pack_push"),
@@ -169,6 +169,8 @@ def algorithmic_bytes(kernel, T, V, W, H, T_vis, C, work=None):
         "k_raster_exact": (4 + 48 + 48) * n_surv + 4 * W * H,
         # read the queue records and tile owners
         "k_raster_depth_big": 64 * n_big + 4 * n_tiles,
+        # read the depth buffer once, write the largest key of each 16x16 tile
+        "k_raster_zmax": 4 * W * H + 4 * ((W + 15) // 16) * ((H + 15) // 16),
         # read every record (survivors, clipped path, queue + owners), the depth
         # buffer read once, VT written once
         "k_raster_mark": 48 * (n_surv + n_rec) + 64 * n_big + 4 * n_tiles + 4 * W * H + vt,
@@ -378,9 +380,10 @@ def run_batched(a, F, S, torch):
         return t
 
     t_plain = timed(plain)
-    # the plain path again with the raster schedule for mid-size triangles on (a
-    # schedule knob the tuners below search; it changes no result)
-    solo.set_raster_schedule(64)
+    # the plain path again with the raster schedule for mid-size triangles and the
+    # tile-depth marking on (schedule knobs the tuners below search; they change no
+    # result)
+    solo.set_raster_schedule(64, F.FA_RASTER_HIZ)
     t_plain_mid = timed(plain)
     solo.set_raster_schedule()
     lanes, policy, _ = F.batch_tune(batch, mb, params, out, reps=2)
@@ -399,7 +402,7 @@ def run_batched(a, F, S, torch):
     # the same batch as one launch of the persistent frame kernel (a batch plan),
     # its schedule autotuned first
     plan = F.BatchPlan(batch, mb, params, out)
-    p_lanes, p_pol, p_pct, p_mid, _ = plan.tune(reps=2)
+    p_lanes, p_pol, p_pct, p_mid, p_rfl, _ = plan.tune(reps=2)
     t_plan = timed(plan.launch)
     plan_ok = all(int(b.result[3]) == 0 for b in out)
     n0 = batch.launches
@@ -423,11 +426,11 @@ def run_batched(a, F, S, torch):
             "batched_ms_p50": bp50, "batched_ms_p99": _pct(t_batch, 99),
             "batched_views_per_s": n / (bp50 * 1e-3), "batched_gpu_launches": launches,
             "plain_ms_p50": pp50, "plain_ms_p99": _pct(t_plain, 99), "plain_views_per_s": n / (pp50 * 1e-3),
-            "plain_raster_mid64_ms_p50": _pct(t_plain_mid, 50),
+            "plain_raster_mid64_hiz_ms_p50": _pct(t_plain_mid, 50),
             "speedup_p50": pp50 / bp50, "all_views_packed": ok, "reps": reps,
             "persistent_plan": {"launches_per_batch": plan_launches, "lanes": p_lanes,
                                 "policy": "longest_first" if p_pol else "round_robin", "worker_pct": p_pct,
-                                "raster_mid_max_pix": p_mid,
+                                "raster_mid_max_pix": p_mid, "raster_hiz": bool(p_rfl),
                                 "ms_p50": _pct(t_plan, 50), "ms_p99": _pct(t_plan, 99),
                                 "views_per_s": n / (_pct(t_plan, 50) * 1e-3),
                                 "speedup_p50_vs_plain": pp50 / _pct(t_plan, 50), "all_views_packed": plan_ok},

@@ -355,18 +355,28 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out);
 fa_status fa_set_wait_limits(fa_ctx* ctx, uint32_t loop_cap, uint64_t wait_ns);
 
 /* Raster schedule of this context's later frames (changes timing only, never
- * results).  A sub-triangle whose pixel box has at most 16 pixels is rasterized by
- * one thread; larger ones are split into 16x16 tiles, one warp per tile.  With
- * mid_max_pix > 16, boxes of up to mid_max_pix pixels are also rasterized in-thread
- * when, for the warp that set them up, that costs less than the tiles (the warp's
- * largest such box against the summed tile steps).  That pays on views of many
- * mid-size triangles (high resolutions, dense meshes seen close up); on views of
- * mostly tiny triangles the tiles stay cheaper, hence the default
- * FA_RASTER_MID_OFF.  Both ways the same samples get the same depth keys.
- * Errors: FA_E_INVALID_ARG (NULL ctx, mid_max_pix outside [16, 256]). */
+ * results).
+ *  mid_max_pix: a sub-triangle whose pixel box has at most 16 pixels is rasterized
+ *    by one thread; larger ones are split into 16x16 tiles, one warp per tile.
+ *    With mid_max_pix > 16, boxes of up to mid_max_pix pixels are also rasterized
+ *    in-thread when, for the warp that set them up, that costs less than the tiles
+ *    (the warp's largest such box against the summed tile steps).  That pays on
+ *    views of many mid-size triangles (high resolutions, dense meshes seen close
+ *    up); on views of mostly tiny triangles the tiles stay cheaper, hence the
+ *    default FA_RASTER_MID_OFF.
+ *  flags: FA_RASTER_HIZ adds a pass that takes the largest depth of every 16x16
+ *    pixel tile of the final depth buffer; the marking pass then skips a
+ *    sub-triangle (or a tile of one) whose smallest possible sample depth, less a
+ *    bound on the depth's rounding error, is above the largest depth of every tile
+ *    it touches.  That pays where most hidden triangles lie behind fully covered
+ *    tiles (large overlapping surfaces); off by default.
+ * Both ways the same samples get the same depth keys and the same triangles are
+ * marked.  Errors: FA_E_INVALID_ARG (NULL ctx, mid_max_pix outside [16, 256],
+ * unknown flags). */
 #define FA_RASTER_MID_OFF 16u
 #define FA_RASTER_MID_MAX 256u
-fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix);
+#define FA_RASTER_HIZ 1u
+fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix, uint32_t flags);
 
 /* Number of kernels the library launched on this context since creation (a
  * host-side counter; used to report launches per frame). */
@@ -445,10 +455,11 @@ fa_status fa_batch_get_schedule(const fa_batch* batch, uint32_t* lanes, uint32_t
 fa_status fa_atlas_batch(fa_batch* batch, uint32_t n_views, const fa_mesh* const* meshes,
                          const fa_frame_params* params, const fa_frame_out* outs, fa_stream_t stream);
 
-/* Schedule autotuner: for lanes in {1, 2, 4, .., n_lanes}, both policies and the
- * raster schedule FA_RASTER_MID_OFF or 64 (set on every lane's context), capture
- * the batch into a CUDA graph, launch it once, time `reps` launches (CUDA events,
- * best of) and keep the fastest schedule; *best_ms (may be NULL)
+/* Schedule autotuner: first the raster schedule of every lane's context (mid-size
+ * limit 16 or 64, with and without FA_RASTER_HIZ, at the current lanes), then lanes
+ * in {1, 2, 4, .., n_lanes} x both policies: each schedule's batch is captured into
+ * a CUDA graph, launched once, `reps` launches are timed (CUDA events, best of) and
+ * the fastest schedule is kept; *best_ms (may be NULL)
  * receives its time.  Runs the views (outputs are overwritten) and synchronizes;
  * not for use inside a capture.  Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
 fa_status fa_batch_tune(fa_batch* batch, uint32_t n_views, const fa_mesh* const* meshes,
@@ -486,6 +497,7 @@ typedef struct {
   uint32_t policy;      /* fa_batch_policy: views to lanes */
   uint32_t worker_pct;  /* workers per data-sized stage, percent of the default counts (10 .. 1000) */
   uint32_t mid_max_pix; /* raster schedule of every view (see fa_set_raster_schedule) */
+  uint32_t raster_flags;
 } fa_plan_schedule;
 
 /* Plan n_views views (as fa_atlas_batch) on all of the batch's lanes, longest
@@ -507,9 +519,10 @@ fa_status fa_batch_plan_get_schedule(const fa_batch_plan* plan, fa_plan_schedule
 fa_status fa_batch_plan_set_schedule(fa_batch_plan* plan, const fa_plan_schedule* schedule);
 
 /* Schedule autotuner: lanes in {1, 2, 4, .., n_lanes} x both policies x worker
- * counts at 50 / 100 / 200 % x raster schedule FA_RASTER_MID_OFF or 64; each
- * schedule is launched once, then `reps` launches are timed (CUDA events, best of);
- * the fastest is kept.  Runs the views (outputs
+ * counts at 50 / 100 / 200 %, after the raster schedule (mid-size limit 16 or 64,
+ * with and without FA_RASTER_HIZ) was picked on all lanes; each schedule is
+ * launched once, then `reps` launches are timed (CUDA events, best of); the
+ * fastest is kept.  Runs the views (outputs
  * are overwritten) and synchronizes; not for use inside a capture.  *best_ms (may
  * be NULL) receives its time.  Errors: FA_E_INVALID_ARG, FA_E_CUDA. */
 fa_status fa_batch_plan_tune(fa_batch_plan* plan, uint32_t reps, float* best_ms);

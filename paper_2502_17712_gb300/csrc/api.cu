@@ -93,7 +93,7 @@ void fa_destroy(fa_ctx* ctx) {
   if (ctx->prof_on)
     for (int i = 0; i <= kMaxProf; ++i) cudaEventDestroy(ctx->prof_ev[i]);
   const PackScratch& p = ctx->pack;
-  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip, ctx->clip_count,
+  void* ptrs[] = {ctx->ctr, ctx->zbuf, ctx->zmax, ctx->queue, ctx->tile_owner, ctx->cand, ctx->surv, ctx->surv_count, ctx->surv_clip, ctx->clip, ctx->clip_count,
                   ctx->label, ctx->wordroots, ctx->blockcnt, ctx->viscnt, ctx->vis, ctx->xedge, ctx->xcnt, ctx->tile_flag, ctx->tile_list,
                   ctx->box_enc, ctx->box_full, p.ord_counts, p.ord_rank, p.ord_total,
                   p.order, p.fs, p.rec8, p.segs, p.scan_state, p.m, p.xy, p.cand, ctx->psched};
@@ -139,6 +139,7 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   if (st == FA_OK) st = alloc(&ptr, (size_t)(n));
   FA_ALLOC(ctx->ctr, 1);
   FA_ALLOC(ctx->zbuf, (uint64_t)c.max_width * c.max_height);
+  FA_ALLOC(ctx->zmax, (uint64_t)((c.max_width + 15) / 16) * ((c.max_height + 15) / 16));
   FA_ALLOC(ctx->queue, ctx->queue_cap);
   ctx->tile_cap = 4u * ctx->queue_cap;
   FA_ALLOC(ctx->tile_owner, ctx->tile_cap);
@@ -418,9 +419,11 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {
 
 uint64_t fa_launch_count(const fa_ctx* ctx) { return ctx ? ctx->launches : 0; }
 
-fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix) {
-  if (!ctx || mid_max_pix < FA_RASTER_MID_OFF || mid_max_pix > FA_RASTER_MID_MAX) return FA_E_INVALID_ARG;
+fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix, uint32_t flags) {
+  if (!ctx || mid_max_pix < FA_RASTER_MID_OFF || mid_max_pix > FA_RASTER_MID_MAX || (flags & ~FA_RASTER_HIZ))
+    return FA_E_INVALID_ARG;
   ctx->mid_max_pix = mid_max_pix;
+  ctx->raster_flags = flags;
   return FA_OK;
 }
 

@@ -189,64 +189,77 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
   for (uint32_t l = 1; l < max_lanes; l <<= 1) cand.push_back(l);
   cand.push_back(max_lanes);
   float best = -1.0f;
-  uint32_t best_l = b->active, best_p = b->policy, best_m = b->ctx[0]->mid_max_pix;
-  const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
+  uint32_t best_l = b->active, best_p = b->policy, best_m = b->ctx[0]->mid_max_pix,
+           best_f = b->ctx[0]->raster_flags;
   fa_status st = FA_OK;
-  for (uint32_t l : cand) {
-    for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST && st == FA_OK; ++pol)
-    for (uint32_t mid : mids) {
-      if (st != FA_OK) break;
-      if (l == 1 && pol == FA_BATCH_LONGEST_FIRST) continue;  // same schedule as round robin
-      b->active = l;
-      b->policy = pol;
-      for (fa_ctx* c : b->ctx) c->mid_max_pix = mid;
-      // time the schedule as the caller would run it: one captured graph per batch
-      cudaGraph_t graph = nullptr;
-      cudaGraphExec_t exec = nullptr;
-      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-        st = FA_E_CUDA;
-        break;
-      }
-      fa_status est = enqueue_batch(b, n_views, meshes, params, outs, s);
-      cudaError_t ce = cudaStreamEndCapture(s, &graph);
-      if (est != FA_OK || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
-        if (graph) cudaGraphDestroy(graph);
-        cudaGetLastError();
-        st = est != FA_OK ? est : FA_E_CUDA;
-        break;
-      }
-      float ms = 0.0f;
-      bool ok = cudaGraphLaunch(exec, s) == cudaSuccess;  // warm-up
-      for (uint32_t r = 0; ok && r < reps; ++r) {
-        float t = 0.0f;
-        ok = cudaEventRecord(e0, s) == cudaSuccess && cudaGraphLaunch(exec, s) == cudaSuccess &&
-             cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-             cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
-        if (ok && (r == 0 || t < ms)) ms = t;
-      }
-      cudaGraphExecDestroy(exec);
-      cudaGraphDestroy(graph);
-      if (!ok) {
-        cudaGetLastError();
-        st = FA_E_CUDA;
-        break;
-      }
-      if (best < 0.0f || ms < best) {
-        best = ms;
-        best_l = l;
-        best_p = pol;
-        best_m = mid;
-      }
+  // one schedule: capture the batch as the caller would run it (one graph), time it
+  auto trial = [&](uint32_t l, uint32_t pol, uint32_t mid, uint32_t fl) {
+    if (st != FA_OK) return;
+    b->active = l;
+    b->policy = pol;
+    for (fa_ctx* c : b->ctx) {
+      c->mid_max_pix = mid;
+      c->raster_flags = fl;
     }
-    if (st != FA_OK) break;
-  }
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+      st = FA_E_CUDA;
+      return;
+    }
+    fa_status est = enqueue_batch(b, n_views, meshes, params, outs, s);
+    cudaError_t ce = cudaStreamEndCapture(s, &graph);
+    if (est != FA_OK || ce != cudaSuccess || cudaGraphInstantiate(&exec, graph, 0) != cudaSuccess) {
+      if (graph) cudaGraphDestroy(graph);
+      cudaGetLastError();
+      st = est != FA_OK ? est : FA_E_CUDA;
+      return;
+    }
+    float ms = 0.0f;
+    bool ok = cudaGraphLaunch(exec, s) == cudaSuccess;  // warm-up
+    for (uint32_t r = 0; ok && r < reps; ++r) {
+      float t = 0.0f;
+      ok = cudaEventRecord(e0, s) == cudaSuccess && cudaGraphLaunch(exec, s) == cudaSuccess &&
+           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+      if (ok && (r == 0 || t < ms)) ms = t;
+    }
+    cudaGraphExecDestroy(exec);
+    cudaGraphDestroy(graph);
+    if (!ok) {
+      cudaGetLastError();
+      st = FA_E_CUDA;
+      return;
+    }
+    if (best < 0.0f || ms < best) {
+      best = ms;
+      best_l = l;
+      best_p = pol;
+      best_m = mid;
+      best_f = fl;
+    }
+  };
+  // the raster schedule first (at the current lanes and policy), then lanes x policy
+  const uint32_t l0 = b->active, p0 = b->policy;
+  const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
+  for (uint32_t mid : mids)
+    for (uint32_t fl = 0; fl <= FA_RASTER_HIZ; ++fl) trial(l0, p0, mid, fl);
+  const uint32_t rm = best_m, rf = best_f;
+  for (uint32_t l : cand)
+    for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST; ++pol) {
+      if (l == 1 && pol == FA_BATCH_LONGEST_FIRST) continue;  // same schedule as round robin
+      trial(l, pol, rm, rf);
+    }
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   b->active = best_l;
   b->policy = best_p;
-  for (fa_ctx* c : b->ctx) c->mid_max_pix = best_m;
+  for (fa_ctx* c : b->ctx) {
+    c->mid_max_pix = best_m;
+    c->raster_flags = best_f;
+  }
   if (best_ms) *best_ms = best;
   return st;
 }

@@ -114,6 +114,7 @@ struct fa_ctx {
   // scratch
   fa::DevCounters* ctr;
   uint32_t* zbuf;        // [max_w * max_h]
+  uint32_t* zmax;        // [ceil(max_w / 16) * ceil(max_h / 16)] largest depth key per 16x16 tile
   uint32_t* tile_flag;   // [ceil(max_tris / 1024)] tile has a visible triangle (this frame)
   uint32_t* tile_list;   // [ceil(max_tris / 1024)] those tiles, in the order the marking found them
   fa::BigTri* queue;     // [queue_cap]
@@ -143,6 +144,7 @@ struct fa_ctx {
   uint32_t loop_cap;
   unsigned long long wait_ns;
   uint32_t mid_max_pix;  // fa_set_raster_schedule
+  uint32_t raster_flags;
   // schedule state of the persistent frame kernel (FA_FRAME_PERSISTENT): work-item
   // counter, exit counter, abort flag and one completion counter per stage group;
   // zero between launches

@@ -36,7 +36,7 @@ constexpr int kMaxStages = 24;      // stages of one view (at most 20 are used)
 constexpr int kInlineGroups = 24;   // stage groups of a single-view launch (kernel parameter)
 
 enum Stage : uint8_t {
-  S_FRONT, S_EXACT, S_DEPTH_BIG, S_MARK, S_INIT_V, S_LOCAL, S_HOOK, S_HOOK_V, S_HOOK_NM, S_FLATTEN, S_SCAN,
+  S_FRONT, S_EXACT, S_DEPTH_BIG, S_ZMAX, S_MARK, S_INIT_V, S_LOCAL, S_HOOK, S_HOOK_V, S_HOOK_NM, S_FLATTEN, S_SCAN,
   S_TRI_CHART, S_VERT_CHART, S_BBOX, S_ORDER_TILE, S_ORDER_SCATTER, S_PACK_SCAN, S_PUSH, S_PLACE, S_UV
 };
 
@@ -127,6 +127,7 @@ __device__ __noinline__ void st_exact(const ViewArgs& v, uint32_t j, uint32_t n)
   rs::exact_body<DEV_M, kPT>(v.ra, j, n);
 }
 __device__ __noinline__ void st_depth_big(const ViewArgs& v, uint32_t j, uint32_t n) { rs::depth_big_body(v.ra, j, n); }
+__device__ __noinline__ void st_zmax(const ViewArgs& v, uint32_t j, uint32_t n) { rs::zmax_body(v.ra, j, n); }
 template <bool CONS>
 __device__ __noinline__ void st_mark(const ViewArgs& v, uint32_t j, uint32_t n) {
   rs::mark_body<CONS, kPT>(v.ra, j, n);
@@ -201,6 +202,7 @@ __device__ void run_stage(const ViewArgs& v, uint32_t stage, uint32_t j, uint32_
     case S_FRONT: v.devm ? st_front<true>(v, j, n) : st_front<false>(v, j, n); break;
     case S_EXACT: v.devm ? st_exact<true>(v, j, n) : st_exact<false>(v, j, n); break;
     case S_DEPTH_BIG: st_depth_big(v, j, n); break;
+    case S_ZMAX: st_zmax(v, j, n); break;
     case S_MARK: v.cons ? st_mark<true>(v, j, n) : st_mark<false>(v, j, n); break;
     case S_INIT_V: st_init_v(v, j, n); break;
     case S_LOCAL: st_local(v, j, n); break;
@@ -382,6 +384,7 @@ void build_view(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, cons
   add(S_FRONT, n_front);
   add(S_EXACT, n_tri);
   add(S_DEPTH_BIG, n_pix);
+  if (v.ra.zmax) add(S_ZMAX, wk(pix, 8192));
   add(S_MARK, std::max(n_tri, n_pix));
   if (vm) add(S_INIT_V, wk(mesh->V, 128));
   add(S_LOCAL, n_tiles);
@@ -554,6 +557,29 @@ fa_status plan_build(fa_batch_plan* pl) {
       fa::build_view(b->ctx[l], pl->meshes[i], &pl->params[i], pl->dmat[i], &pl->outs[i], pl->G,
                      pl->sched.worker_pct, &vps[i]);
       vps[i].va.ra.mid_max_pix = pl->sched.mid_max_pix;
+      if (!(pl->sched.raster_flags & FA_RASTER_HIZ)) {
+        vps[i].va.ra.zmax = nullptr;  // and no tile-depth stage
+        uint32_t k = 0;
+        for (uint32_t q = 0; q < vps[i].n_stages; ++q)
+          if (vps[i].stage[q] != fa::S_ZMAX) {
+            vps[i].stage[k] = vps[i].stage[q];
+            vps[i].workers[k] = vps[i].workers[q];
+            ++k;
+          }
+        vps[i].n_stages = k;
+      } else if (!vps[i].va.ra.zmax) {
+        vps[i].va.ra.zmax = b->ctx[l]->zmax;  // and a tile-depth stage before the marking
+        uint32_t q = 0;
+        while (q < vps[i].n_stages && vps[i].stage[q] != fa::S_MARK) ++q;
+        for (uint32_t k = vps[i].n_stages; k > q; --k) {
+          vps[i].stage[k] = vps[i].stage[k - 1];
+          vps[i].workers[k] = vps[i].workers[k - 1];
+        }
+        const uint64_t pix = (uint64_t)pl->params[i].width * pl->params[i].height;
+        vps[i].stage[q] = fa::S_ZMAX;
+        vps[i].workers[q] = (uint32_t)std::min<uint64_t>(pl->G, std::max<uint64_t>(1, (pix + 8191) / 8192));
+        ++vps[i].n_stages;
+      }
       va[i] = vps[i].va;
       front_cap = std::max(front_cap, vps[i].front_cap);
     }
@@ -639,6 +665,7 @@ fa_status fa_batch_plan_create(fa_batch* b, uint32_t n_views, const fa_mesh* con
   pl->sched.policy = FA_BATCH_LONGEST_FIRST;
   pl->sched.worker_pct = 100;
   pl->sched.mid_max_pix = b->ctx[0]->mid_max_pix;
+  pl->sched.raster_flags = b->ctx[0]->raster_flags;
   pl->max_groups = n_views * (uint32_t)fa::kMaxStages;
   fa_status st = fa::persist_grid(b->device, &pl->G);
   if (st == FA_OK && (cudaMalloc(&pl->d_views, n_views * sizeof(fa::ViewArgs)) != cudaSuccess ||
@@ -693,7 +720,7 @@ fa_status fa_batch_plan_get_schedule(const fa_batch_plan* pl, fa_plan_schedule* 
 fa_status fa_batch_plan_set_schedule(fa_batch_plan* pl, const fa_plan_schedule* s) {
   if (!pl || !s || s->lanes == 0 || s->lanes > pl->batch->ctx.size() || s->policy > FA_BATCH_LONGEST_FIRST ||
       s->worker_pct < 10 || s->worker_pct > 1000 || s->mid_max_pix < FA_RASTER_MID_OFF ||
-      s->mid_max_pix > FA_RASTER_MID_MAX)
+      s->mid_max_pix > FA_RASTER_MID_MAX || (s->raster_flags & ~FA_RASTER_HIZ))
     return FA_E_INVALID_ARG;
   int prev = -1;
   cudaGetDevice(&prev);
@@ -727,38 +754,46 @@ fa_status fa_batch_plan_tune(fa_batch_plan* pl, uint32_t reps, float* best_ms) {
   std::vector<uint32_t> lanes;
   for (uint32_t l = 1; l < max_lanes; l <<= 1) lanes.push_back(l);
   lanes.push_back(max_lanes);
-  const uint32_t pcts[] = {50, 100, 200};
-  const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
   fa_plan_schedule best = pl->sched;
   float best_t = -1.0f;
   fa_status st = FA_OK;
+  auto trial = [&](const fa_plan_schedule& c) {
+    if (st != FA_OK) return;
+    st = fa_batch_plan_set_schedule(pl, &c);
+    if (st != FA_OK) return;
+    float ms = 0.0f;
+    bool ok = fa_batch_plan_launch(pl, s) == FA_OK;  // warm-up
+    for (uint32_t r = 0; ok && r < reps; ++r) {
+      float t = 0.0f;
+      ok = cudaEventRecord(e0, s) == cudaSuccess && fa_batch_plan_launch(pl, s) == FA_OK &&
+           cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
+           cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
+      if (ok && (r == 0 || t < ms)) ms = t;
+    }
+    if (!ok) {
+      cudaGetLastError();
+      st = FA_E_CUDA;
+      return;
+    }
+    if (best_t < 0.0f || ms < best_t) {
+      best_t = ms;
+      best = c;
+    }
+  };
+  // the raster schedule first (at the plan's lanes, policy and worker counts), then
+  // lanes x policy x worker counts with the best raster schedule
+  const fa_plan_schedule start = pl->sched;
+  const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
+  for (uint32_t mid : mids)
+    for (uint32_t fl = 0; fl <= FA_RASTER_HIZ; ++fl) trial(fa_plan_schedule{start.lanes, start.policy,
+                                                                             start.worker_pct, mid, fl});
+  const uint32_t best_mid = best.mid_max_pix, best_fl = best.raster_flags;
+  const uint32_t pcts[] = {50, 100, 200};
   for (uint32_t l : lanes)
-    for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST && st == FA_OK; ++pol)
-      for (uint32_t pct : pcts)
-        for (uint32_t mid : mids) {
-        if (st != FA_OK) break;
+    for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST; ++pol)
+      for (uint32_t pct : pcts) {
         if (l == 1 && pol == FA_BATCH_LONGEST_FIRST) continue;  // the same order as round robin
-        fa_plan_schedule c{l, pol, pct, mid};
-        st = fa_batch_plan_set_schedule(pl, &c);
-        if (st != FA_OK) break;
-        float ms = 0.0f;
-        bool ok = fa_batch_plan_launch(pl, s) == FA_OK;  // warm-up
-        for (uint32_t r = 0; ok && r < reps; ++r) {
-          float t = 0.0f;
-          ok = cudaEventRecord(e0, s) == cudaSuccess && fa_batch_plan_launch(pl, s) == FA_OK &&
-               cudaEventRecord(e1, s) == cudaSuccess && cudaEventSynchronize(e1) == cudaSuccess &&
-               cudaEventElapsedTime(&t, e0, e1) == cudaSuccess;
-          if (ok && (r == 0 || t < ms)) ms = t;
-        }
-        if (!ok) {
-          cudaGetLastError();
-          st = FA_E_CUDA;
-          break;
-        }
-        if (best_t < 0.0f || ms < best_t) {
-          best_t = ms;
-          best = c;
-        }
+        trial(fa_plan_schedule{l, pol, pct, best_mid, best_fl});
       }
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);

@@ -25,6 +25,11 @@ __global__ void __launch_bounds__(256) k_raster_depth_big(RasterArgs A) {
   rs::depth_big_body(A, blockIdx.x, gridDim.x);
 }
 
+__global__ void __launch_bounds__(256) k_raster_zmax(RasterArgs A) {
+  pdl_wait();
+  rs::zmax_body(A, blockIdx.x, gridDim.x);
+}
+
 template <bool CONS>
 __global__ void __launch_bounds__(256, 4) k_raster_mark(RasterArgs A) {
   pdl_wait();
@@ -55,6 +60,10 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
     launch_k(k_raster_exact<false>, 152 * 8, 256, 0, s, A);
   mark(ctx, "k_raster_depth_big", s);
   launch_k(k_raster_depth_big, gb, 256, 0, s, A);
+  if (A.zmax) {
+    mark(ctx, "k_raster_zmax", s);
+    launch_k(k_raster_zmax, grid_for((uint64_t)A.ztx * ((H + 15) / 16) * 32, 256, 152 * 8), 256, 0, s, A);
+  }
   mark(ctx, "k_raster_mark", s);
   // one wave of four resident blocks per SM: each block scans the region counts once
   if (cons)

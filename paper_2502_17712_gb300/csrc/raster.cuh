@@ -325,6 +325,9 @@ struct RasterArgs {
   int32_t* tri_chart;    // when set, the front end sets it to -1 (the chart pass writes visible ones)
   uint32_t* partial_clear;  // when set, the front end also clears these ceil(T/32) words
   uint32_t mid_max_pix;     // boxes up to this size may be rasterized in-thread (<= kSmallMaxPix: off)
+  uint32_t* zmax;           // [ztx * ceil(H / 16)] largest depth key of each 16x16 pixel tile, or
+                            // null: no tile-depth pass (FA_RASTER_HIZ off)
+  int ztx;                  // tiles per row, ceil(W / 16)
   uint32_t* clip;  // triangles that need clipping, one region per front block like surv
   DevCounters* ctr;
   uint32_t* vt;
@@ -812,6 +815,50 @@ __device__ __forceinline__ void exact_body(const RasterArgs& A, uint32_t bid, ui
   }
 }
 
+// Occlusion test of the marking pass on the final depth buffer (exact): a
+// sub-triangle whose every sample depth is above the largest depth key of every
+// 16x16 tile that its pixel box [px0, px1] x [py0, py1] touches cannot mark.  A
+// sample depth is the rounded barycentric combination of the vertex depths; it
+// lies within 7 * 2^-24 * max |z| of the exact value (three rounded terms, their
+// two sums, 1 / A and the product), which lies in [zmin, zmax] (the clamped depth
+// of conservative marking too), so zmin - 1e-6 max |z|, rounded down, bounds it
+// from below.
+__device__ __forceinline__ bool hidden_by_tiles(const RasterArgs& A, float z0, float z1, float z2, int px0, int py0,
+                                                int px1, int py1) {
+  if (!A.zmax) return false;
+  const float zmin = fminf(z0, fminf(z1, z2));
+  const float zabs = fmaxf(fabsf(z0), fmaxf(fabsf(z1), fabsf(z2)));
+  const float lo = __fsub_rd(zmin, __fmaf_ru(zabs, 1e-6f, 1e-37f));
+  const uint32_t klo = ordered(lo);
+  uint32_t zm = 0u;
+  for (int ty = py0 >> 4; ty <= (py1 >> 4); ++ty)
+    for (int tx = px0 >> 4; tx <= (px1 >> 4); ++tx) zm = max(zm, __ldcg(A.zmax + ty * A.ztx + tx));
+  return klo > zm;
+}
+
+// The largest depth key of each 16x16 pixel tile of the final depth buffer: a
+// warp per tile, a half warp per row.
+__device__ __forceinline__ void zmax_body(const RasterArgs& A, uint32_t bid, uint32_t nblk) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t zty = (uint32_t)((A.H + 15) / 16), ntile = (uint32_t)A.ztx * zty;
+  const uint32_t nwarps = (nblk * blockDim.x) >> 5;
+  for (uint32_t g = (bid * blockDim.x + threadIdx.x) >> 5; g < ntile; g += nwarps) {
+    const int x = (int)(g % (uint32_t)A.ztx) * 16 + (int)(lane & 15);
+    const int y0 = (int)(g / (uint32_t)A.ztx) * 16 + (int)(lane >> 4);
+    uint32_t m = 0u;
+    uint32_t k[8];
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+      const int y = y0 + 2 * r;
+      k[r] = (x < A.W && y < A.H) ? __ldcg(A.zbuf + (size_t)y * A.W + x) : 0u;
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) m = max(m, k[r]);
+    m = __reduce_max_sync(0xFFFFFFFFu, m);
+    if (lane == 0) A.zmax[g] = m;
+  }
+}
+
 // The marking pass lists each 1024-triangle tile in which it marks a triangle, once.
 __device__ __forceinline__ void note_tile(const RasterArgs& A, uint32_t tile) {
   if (!__ldcg(A.tile_flag + tile) && atomicExch(A.tile_flag + tile, 1u) == 0u)
@@ -842,6 +889,9 @@ __device__ __forceinline__ void big_tiles(const RasterArgs& A, uint32_t bid, uin
     // marking: another tile of the sub-triangle may have marked its triangle already
     if (PASS >= 1 && ((__ldcg(A.vt + (q.tri >> 5)) >> (q.tri & 31)) & 1u)) continue;
     const int bx = px0 + (int)(local % tx_n) * kBigTile, by = py0 + (int)(local / tx_n) * kBigTile;
+    if (PASS >= 1 && hidden_by_tiles(A, q.zn[0], q.zn[1], q.zn[2], bx, by, min(bx + kBigTile - 1, px1),
+                                     min(by + kBigTile - 1, py1)))
+      continue;
     SV a{q.X[0], q.Y[0], q.zn[0]}, b{q.X[1], q.Y[1], q.zn[1]}, c{q.X[2], q.Y[2], q.zn[2]};
     const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
     const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
@@ -904,10 +954,12 @@ __device__ __forceinline__ void mark_body(const RasterArgs& A, uint32_t bid, uin
         const SV b{__float_as_int(fa.z), __float_as_int(fa.w), fc.y};
         const SV c{__float_as_int(fb.x), __float_as_int(fb.y), fc.z};
         t = __float_as_uint(fc.w);
-        const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
-        const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
-        vis = raster_rect<CONS ? 2 : 1>(a, b, c, invA, (int)(b0 & 0xFFFFu), (int)(b0 >> 16), (int)(b1 & 0xFFFFu),
-                                        (int)(b1 >> 16), A.zbuf, A.W);
+        const int px0 = (int)(b0 & 0xFFFFu), py0 = (int)(b0 >> 16), px1 = (int)(b1 & 0xFFFFu), py1 = (int)(b1 >> 16);
+        if (!hidden_by_tiles(A, fc.x, fc.y, fc.z, px0, py0, px1, py1)) {
+          const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
+          const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
+          vis = raster_rect<CONS ? 2 : 1>(a, b, c, invA, px0, py0, px1, py1, A.zbuf, A.W);
+        }
       }
     }
     const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
@@ -968,6 +1020,8 @@ inline RasterArgs make_raster_args(fa_ctx* ctx, const fa_mesh* mesh, const Mat4&
   A.tri_chart = tri_chart_init;
   A.partial_clear = nullptr;
   A.mid_max_pix = ctx->mid_max_pix;
+  A.zmax = (ctx->raster_flags & FA_RASTER_HIZ) ? ctx->zmax : nullptr;
+  A.ztx = (int)((W + 15) / 16);
   A.clip = ctx->clip;
   A.ctr = ctx->ctr;
   A.vt = vt;

@@ -52,6 +52,7 @@ EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh
            "fa_batch_plan_set_schedule", "fa_batch_plan_tune", "fa_batch_plan_destroy", "fa_set_raster_schedule"]
 FA_RASTER_MID_OFF = 16
 FA_RASTER_MID_MAX = 256
+FA_RASTER_HIZ = 1
 FA_DEFAULT_LOOP_CAP = 1 << 24
 FA_DEFAULT_WAIT_NS = 1_000_000_000
 
@@ -100,7 +101,7 @@ class fa_frame_stats(ctypes.Structure):
 
 class fa_plan_schedule(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("policy", ctypes.c_uint32), ("worker_pct", ctypes.c_uint32),
-                ("mid_max_pix", ctypes.c_uint32)]
+                ("mid_max_pix", ctypes.c_uint32), ("raster_flags", ctypes.c_uint32)]
 
 
 class fa_server_done(ctypes.Structure):
@@ -204,7 +205,7 @@ def load(path: str = LIB_PATH):
     lib.fa_last_device_status.restype = st
     lib.fa_launch_count.argtypes = [P]
     lib.fa_launch_count.restype = ctypes.c_uint64
-    lib.fa_set_raster_schedule.argtypes = [P, u32]
+    lib.fa_set_raster_schedule.argtypes = [P, u32, u32]
     lib.fa_set_raster_schedule.restype = st
     lib.fa_set_wait_limits.argtypes = [P, u32, ctypes.c_uint64]
     lib.fa_set_wait_limits.restype = st
@@ -388,8 +389,8 @@ class Context:
     def set_wait_limits(self, loop_cap=FA_DEFAULT_LOOP_CAP, wait_ns=FA_DEFAULT_WAIT_NS):
         fa_set_wait_limits(self.handle, loop_cap, wait_ns)
 
-    def set_raster_schedule(self, mid_max_pix=FA_RASTER_MID_OFF):
-        _check(load().fa_set_raster_schedule(self.handle, int(mid_max_pix)), "fa_set_raster_schedule")
+    def set_raster_schedule(self, mid_max_pix=FA_RASTER_MID_OFF, flags=0):
+        _check(load().fa_set_raster_schedule(self.handle, int(mid_max_pix), int(flags)), "fa_set_raster_schedule")
 
     @property
     def launches(self) -> int:
@@ -591,14 +592,15 @@ class BatchPlan:
     def schedule(self):
         s = fa_plan_schedule()
         _check(load().fa_batch_plan_get_schedule(self.handle, ctypes.byref(s)), "fa_batch_plan_get_schedule")
-        return s.lanes, s.policy, s.worker_pct, s.mid_max_pix
+        return s.lanes, s.policy, s.worker_pct, s.mid_max_pix, s.raster_flags
 
-    def set_schedule(self, lanes, policy=FA_BATCH_LONGEST_FIRST, worker_pct=100, mid_max_pix=FA_RASTER_MID_OFF):
-        s = fa_plan_schedule(lanes, policy, worker_pct, mid_max_pix)
+    def set_schedule(self, lanes, policy=FA_BATCH_LONGEST_FIRST, worker_pct=100, mid_max_pix=FA_RASTER_MID_OFF,
+                     raster_flags=0):
+        s = fa_plan_schedule(lanes, policy, worker_pct, mid_max_pix, raster_flags)
         _check(load().fa_batch_plan_set_schedule(self.handle, ctypes.byref(s)), "fa_batch_plan_set_schedule")
 
     def tune(self, reps=3):
-        """fa_batch_plan_tune; returns (lanes, policy, worker_pct, mid_max_pix, best_ms)."""
+        """fa_batch_plan_tune; returns (lanes, policy, worker_pct, mid_max_pix, raster_flags, best_ms)."""
         ms = ctypes.c_float()
         _check(load().fa_batch_plan_tune(self.handle, reps, ctypes.byref(ms)), "fa_batch_plan_tune")
         return (*self.schedule(), ms.value)

@@ -54,7 +54,7 @@ def test_host_side_argument_errors(lib):
     assert h.value is None
     assert lib.fa_launch_count(None) == 0
     assert lib.fa_set_wait_limits(None, 0, 0) == F.FA_E_INVALID_ARG
-    assert lib.fa_set_raster_schedule(None, 64) == F.FA_E_INVALID_ARG
+    assert lib.fa_set_raster_schedule(None, 64, 0) == F.FA_E_INVALID_ARG
     lib.fa_destroy(None)
     lib.fa_mesh_release(None)
     out = ctypes.c_int32()

@@ -524,17 +524,18 @@ def test_chart_count_one_above_capacity(F, small_ctx):
 
 # ---------------------------------------------------------------- raster schedule
 
-@pytest.mark.parametrize("mid", [64, 256])
-def test_raster_schedule_changes_no_result(F, small_ctx, mid):
-    """Mid-size sub-triangles rasterized in-thread instead of in 16x16 tiles
-    (fa_set_raster_schedule) give the same frame, bit for bit, and the oracle's."""
+@pytest.mark.parametrize("mid,flags", [(64, 0), (256, 0), (16, 1), (64, 1)])
+def test_raster_schedule_changes_no_result(F, small_ctx, mid, flags):
+    """Mid-size sub-triangles rasterized in-thread instead of in 16x16 tiles, and the
+    marking pass skipping what the tile depths show hidden (fa_set_raster_schedule),
+    give the same frame, bit for bit, and the oracle's."""
     import torch
     cases = [(S.grid_scene(7), S.spline_cameras(7, 5, 1920, 1080)[2], 1920, 1080, 11),
              (S.instanced_grid_scene(11, 8, n=24), S.hemisphere_camera(11, 1280, 720, radius=4.0), 1280, 720, 11)]
     for sc, M, W, H, L in cases:
         mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
         a, sa = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, L)
-        small_ctx.set_raster_schedule(mid)
+        small_ctx.set_raster_schedule(mid, flags)
         try:
             b, sb = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, L)
         finally:

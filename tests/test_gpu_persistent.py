@@ -198,8 +198,8 @@ def test_batch_plan_equals_solo(F):
 
     plan.launch()
     check()
-    for lanes, pol, pct, mid in [(1, 0, 100, 16), (2, 1, 50, 64), (4, 0, 200, 256), (3, 1, 100, 16)]:
-        plan.set_schedule(lanes, pol, pct, mid)
+    for lanes, pol, pct, mid, rfl in [(1, 0, 100, 16, 0), (2, 1, 50, 64, 1), (4, 0, 200, 256, 0), (3, 1, 100, 16, 1)]:
+        plan.set_schedule(lanes, pol, pct, mid, rfl)
         plan.launch()
         check()
     g = torch.cuda.CUDAGraph()
@@ -208,8 +208,8 @@ def test_batch_plan_equals_solo(F):
         plan.launch()
     g.replay()
     check()
-    lanes, pol, pct, mid, ms = plan.tune(reps=1)
-    assert 1 <= lanes <= 4 and ms > 0 and mid in (16, 64)
+    lanes, pol, pct, mid, rfl, ms = plan.tune(reps=1)
+    assert 1 <= lanes <= 4 and ms > 0 and mid in (16, 64) and rfl in (0, F.FA_RASTER_HIZ)
     plan.launch()
     check()
     del g

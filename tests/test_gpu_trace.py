@@ -47,9 +47,19 @@ def test_trace_and_work_counts(F):
     assert ctx.device_status() == 0
     names = [n for n, _ in trace]
     assert names == FRAME_KERNELS
-    assert names == [k for ks in bench.STAGES.values() for k in ks]  # the benchmark's stage table
+    # the benchmark's stage table (which also lists the optional tile-depth pass)
+    assert names == [k for ks in bench.STAGES.values() for k in ks if k != "k_raster_zmax"]
     assert ctx.launches - n0 == len(FRAME_KERNELS)
     assert all(ms >= 0.0 for _, ms in trace)
+    # with the tile-depth marking on, that pass runs right before the marking pass
+    ctx.set_raster_schedule(16, F.FA_RASTER_HIZ)
+    ref_vt = bufs.vt.clone()
+    F.atlas_frame(ctx, mesh, bufs, M, W, H, 1.0, 11, 0)
+    hiz_names = [n for n, _ in F.fa_profile_read(ctx.handle)]
+    ctx.set_raster_schedule()
+    assert hiz_names == [k for ks in bench.STAGES.values() for k in ks]
+    assert torch.equal(bufs.vt, ref_vt) and ctx.device_status() == 0
+    F.atlas_frame(ctx, mesh, bufs, M, W, H, 1.0, 11, 0)
 
     work = ctx.frame_stats()
     vt = bufs.vt.cpu().numpy().view(np.uint32)
