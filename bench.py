@@ -51,6 +51,9 @@ def parse():
     ap.add_argument("--served-slots", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the small-scene latencies, camera path, ratio sweep and packer stress")
+    ap.add_argument("--write-traffic", metavar="NCU_CSV",
+                    help="write profiles/traffic.json from an ncu --csv log of dram__bytes_read.sum and "
+                         "dram__bytes_write.sum (one launch per kernel), with the current source hashes, and exit")
     return ap.parse_args()
 
 
@@ -207,24 +210,71 @@ def frame_algorithmic_bytes(T, V, W, H, T_vis, C, mode):
     return b
 
 
+# the source file of each per-frame kernel (its body is in the .cuh of the same name)
+KERNEL_SOURCE = {"k_raster": "raster.cu", "k_uf_": "chartify.cu", "k_scan_blocks": "chartify.cu",
+                 "k_tri_chart": "chartify.cu", "k_bbox": "param.cu", "k_uv": "param.cu", "k_order": "pack.cu",
+                 "k_pack": "pack.cu"}
+
+
+def kernel_source(kernel):
+    for prefix, src in KERNEL_SOURCE.items():
+        if kernel.startswith(prefix):
+            return src
+    return None
+
+
+def source_hash(source):
+    """First 16 hex digits of the SHA-256 of a kernel's .cu, its .cuh and fa_internal.cuh."""
+    import hashlib
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2502_17712_gb300", "csrc")
+    for name in (source, source[:-3] + ".cuh", "fa_internal.cuh"):
+        path = os.path.join(csrc, name)
+        if os.path.exists(path):
+            with open(path, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def measured_traffic(kernel):
     """DRAM bytes per launch from the committed ncu capture, or None when the
     kernel's source has changed since the counters were taken."""
-    import hashlib
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
-        if rec is None:
-            return None
-        h = hashlib.sha256()
-        for name in (rec["source"], "fa_internal.cuh"):
-            with open(os.path.join(ROOT, "paper_2502_17712_gb300", "csrc", name), "rb") as f:
-                h.update(f.read())
-        if h.hexdigest()[:16] != rec["source_sha256_16"]:
+        if rec is None or source_hash(rec["source"]) != rec["source_sha256_16"]:
             return None
         return rec["dram_bytes_per_launch"]
     except Exception:
         return None
+
+
+def write_traffic(csv_path):
+    """profiles/traffic.json from an ncu --csv log (one row per launch and metric):
+    per kernel the read + write DRAM bytes of its first captured launch."""
+    import csv
+    import re
+    with open(csv_path) as f:
+        lines = f.read().splitlines()
+    start = next(i for i, ln in enumerate(lines) if ln.startswith('"ID"'))
+    scale = {"byte": 1, "Kbyte": 1e3, "Mbyte": 1e6, "Gbyte": 1e9, "KB": 1024, "MB": 1 << 20, "GB": 1 << 30}
+    per_launch = {}
+    for r in csv.DictReader(lines[start:]):
+        m = re.search(r"\bk_[a-z0-9_]+", r["Kernel Name"])
+        if not m or r["Metric Name"] not in ("dram__bytes_read.sum", "dram__bytes_write.sum"):
+            continue
+        v = float(r["Metric Value"].replace(",", "")) * scale.get(r["Metric Unit"], 1)
+        key = (int(r["ID"]), m.group(0))
+        per_launch[key] = per_launch.get(key, 0.0) + v
+    out = {}
+    for (_, k), b in sorted(per_launch.items()):
+        src = kernel_source(k)
+        if src and k not in out:
+            out[k] = {"dram_bytes_per_launch": int(round(b)), "source": src, "source_sha256_16": source_hash(src)}
+    with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
+        json.dump(out, f, indent=1)
+        f.write("\n")
+    print(json.dumps({k: v["dram_bytes_per_launch"] for k, v in out.items()}))
 
 
 def run_reference(a):
@@ -979,7 +1029,9 @@ def run_ours(a):
 
 def main():
     a = parse()
-    if a.impl == "reference":
+    if a.write_traffic:
+        write_traffic(a.write_traffic)
+    elif a.impl == "reference":
         run_reference(a)
     else:
         run_ours(a)

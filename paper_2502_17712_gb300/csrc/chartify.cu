@@ -15,7 +15,7 @@ using cf::kTile;
 template <bool LIST>
 __global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
   pdl_wait();
-  cf::local_body<LIST>(a, blockIdx.x, gridDim.x);
+  cf::local_body<LIST, kLocalThreads>(a, blockIdx.x, gridDim.x);
 }
 
 __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
@@ -125,7 +125,7 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   const uint32_t ntiles = (mesh->T + kTile - 1) / kTile;
   mark(ctx, "k_uf_local", s);
   if (tile_list)
-    launch_k(k_uf_local<true>, ntiles < 152u * 2u ? ntiles : 152u * 2u, kLocalThreads, 0, s, a);
+    launch_k(k_uf_local<true>, std::min(ntiles, 152u * (2048u / kLocalThreads)), kLocalThreads, 0, s, a);
   else
     launch_k(k_uf_local<false>, ntiles, kLocalThreads, 0, s, a);
   mark(ctx, "k_uf_hook", s);

@@ -84,7 +84,7 @@ struct UfArgs {
 // global init: afterwards every visible triangle points to a root, and only edges that
 // leave the tile remain for the global hooking.
 constexpr int kTile = 1024;
-constexpr int kLocalThreads = 1024;  // one triangle of the tile per thread
+constexpr int kLocalThreads = 1024;  // threads of the local union-find kernel (kTile / kLocalThreads triangles each)
 constexpr uint32_t kXCap = 3 * kTile;  // cross-tile edge slots per tile
 
 __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
@@ -101,7 +101,12 @@ __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {
 }
 
 // One tile (all threads of the block; the caller separates tiles by a barrier).
+// NT: the threads that take triangles (kTile / NT each); threads past NT of a larger
+// block only pass the barriers.
+template <int NT>
 __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
+  static_assert(kTile % NT == 0 && NT >= 32, "whole triangles per thread");
+  const bool act = threadIdx.x < (uint32_t)NT;
   __shared__ int32_t lab[kTile];
   __shared__ uint32_t vis[kTile / 32];
   const uint32_t base = tile * kTile;
@@ -120,10 +125,11 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
   volatile int32_t* vl = lab;
   uint2* xe = a.xedge + (size_t)tile * kXCap;
   // start from the smallest visible neighbour inside the tile (Alg. 1, first loop)
-  int32_t nb[kTile / kLocalThreads][3];
+  int32_t nb[kTile / NT][3];
 #pragma unroll
-  for (int k = 0; k < kTile / kLocalThreads; ++k) {
-    const uint32_t i = threadIdx.x + k * kLocalThreads;
+  for (int k = 0; k < kTile / NT; ++k) {
+    if (!act) break;
+    const uint32_t i = threadIdx.x + k * NT;
     int32_t l = (int32_t)i;
 #pragma unroll
     for (int j = 0; j < 3; ++j) nb[k][j] = -1;
@@ -150,8 +156,9 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
   // rounds of pointer jumping make them shallow before the hooking walks them (a
   // jump only replaces a label by one of its ancestors, so the rounds need no barrier)
 #pragma unroll
-  for (int k = 0; k < kTile / kLocalThreads; ++k) {
-    const uint32_t i = threadIdx.x + k * kLocalThreads;
+  for (int k = 0; k < kTile / NT; ++k) {
+    if (!act) break;
+    const uint32_t i = threadIdx.x + k * NT;
     if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
 #pragma unroll 1
     for (int r = 0; r < 4; ++r) vl[i] = vl[vl[i]];
@@ -159,8 +166,9 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
   __syncthreads();
   // hook every in-tile edge once, from its lower end
 #pragma unroll
-  for (int k = 0; k < kTile / kLocalThreads; ++k) {
-    const int32_t i = (int32_t)(threadIdx.x + k * kLocalThreads);
+  for (int k = 0; k < kTile / NT; ++k) {
+    if (!act) break;
+    const int32_t i = (int32_t)(threadIdx.x + k * NT);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
       const int32_t ni = nb[k][j];
@@ -176,7 +184,7 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
     }
   }
   __syncthreads();
-  for (uint32_t i = threadIdx.x; i < kTile; i += kLocalThreads) {
+  for (uint32_t i = threadIdx.x; act && i < kTile; i += NT) {
     if (!((vis[i >> 5] >> (i & 31)) & 1u)) continue;
     // (path halving: the walks of other threads shorten too; the result goes to the
     // global labels, so no halving write can overwrite it)
@@ -187,13 +195,13 @@ __device__ __forceinline__ void local_tile(const UfArgs& a, uint32_t tile) {
 
 // Every tile (a block each), or only the tiles that the marking pass listed (a
 // persistent grid over the list).
-template <bool LIST>
+template <bool LIST, int NT>
 __device__ __forceinline__ void local_body(const UfArgs& a, uint32_t bid, uint32_t nblk) {
   if (!LIST) {
     const uint32_t ntiles = (a.T + kTile - 1) / kTile;
     for (uint32_t t = bid; t < ntiles; t += nblk) {
       __syncthreads();  // the shared memory of the previous tile is free
-      local_tile(a, t);
+      local_tile<NT>(a, t);
     }
     return;
   }
@@ -207,7 +215,7 @@ __device__ __forceinline__ void local_body(const UfArgs& a, uint32_t bid, uint32
     __syncthreads();
     const uint32_t i = s_i;
     if (i >= n) break;
-    local_tile(a, __ldcg(a.tile_list + i));
+    local_tile<NT>(a, __ldcg(a.tile_list + i));
   }
 }
 

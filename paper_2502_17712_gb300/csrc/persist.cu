@@ -135,7 +135,7 @@ __device__ __noinline__ void st_mark(const ViewArgs& v, uint32_t j, uint32_t n) 
 __device__ __noinline__ void st_init_v(const ViewArgs& v, uint32_t j, uint32_t n) {
   cf::init_v_body(v.uf.label, v.uf.T, v.uf.V, j, n);
 }
-__device__ __noinline__ void st_local(const ViewArgs& v, uint32_t j, uint32_t n) { cf::local_body<true>(v.uf, j, n); }
+__device__ __noinline__ void st_local(const ViewArgs& v, uint32_t j, uint32_t n) { cf::local_body<true, kPT>(v.uf, j, n); }
 __device__ __noinline__ void st_hook(const ViewArgs& v, uint32_t j, uint32_t n) {
   cf::hook_body<true, 128>(v.uf, j, n);  // eight tiles at a time per CTA
 }

@@ -116,3 +116,32 @@ def test_reference_arm_line():
     cb, e2e = d["cpu_baseline"], d["e2e"]
     assert cb["kind"] == "oracle" and cb["cores"] == 1 and cb["value"] == d["value"] and cb["sample"]
     assert e2e == {"value": d["value"], "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_traffic_table_round_trip(tmp_path, monkeypatch):
+    """bench.py --write-traffic: every per-frame kernel has a source file; the table
+    written from an ncu CSV log (thousands separators, scaled units, other metrics)
+    is read back while the sources are unchanged."""
+    import bench
+    for k in [k for ks in bench.STAGES.values() for k in ks]:
+        assert bench.kernel_source(k) is not None, k
+    log = tmp_path / "traffic.csv"
+    hdr = ('"ID","Process ID","Process Name","Host Name","Kernel Name","Context","Stream","Block Size",'
+           '"Grid Size","Device","CC","Section Name","Metric Name","Metric Unit","Metric Value"')
+    rows = [("0", "void fa::(anonymous namespace)::k_raster_front<false>(RasterArgs)", "dram__bytes_read.sum",
+             "byte", "73,751,296"),
+            ("0", "void fa::(anonymous namespace)::k_raster_front<false>(RasterArgs)", "dram__bytes_write.sum",
+             "Mbyte", "26.0"),
+            ("1", "k_uv<false>", "gpu__time_duration.sum", "usecond", "18.5"),
+            ("1", "k_uv<false>", "dram__bytes_read.sum", "Kbyte", "1,500")]
+    body = "\n".join(",".join(f'"{x}"' for x in (i, "1", "python", "h", k, "1", "7", "(1,1,1)", "(1,1,1)", "0",
+                                                  "10.3", "s", m, u, v)) for i, k, m, u, v in rows)
+    log.write_text("==PROF== Connected\n" + hdr + "\n" + body + "\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    (tmp_path / "profiles").mkdir()
+    real = __import__("os").path.dirname(bench.__file__)
+    (tmp_path / "paper_2502_17712_gb300").symlink_to(__import__("os").path.join(real, "paper_2502_17712_gb300"))
+    bench.write_traffic(str(log))
+    assert bench.measured_traffic("k_raster_front") == 73751296 + 26000000
+    assert bench.measured_traffic("k_uv") == 1500000
+    assert bench.measured_traffic("k_pack_push") is None
