@@ -437,6 +437,7 @@ def run_batched(a, F, S, torch):
     t_plain_mid = timed(plain)
     solo.set_raster_schedule()
     lanes, policy, _ = F.batch_tune(batch, mb, params, out, reps=2)
+    ksched = batch.kernel_schedule()
     F.atlas_batch(batch, mb, params, out)
     torch.cuda.synchronize()
     g = torch.cuda.CUDAGraph()
@@ -472,7 +473,7 @@ def run_batched(a, F, S, torch):
     return {"workload": f"{n} views: instanced 64x64 heightfield floors of 50-400 patches, 640x360-2560x1440, "
                         "atlas 1024-4096, ratio 1, edge charts, 64 scales",
             "views": n, "triangles": int(sum(sc.T for sc, _, _ in views)),
-            "lanes": lanes, "policy": "longest_first" if policy else "round_robin",
+            "lanes": lanes, "policy": "longest_first" if policy else "round_robin", "kernel_schedule": ksched,
             "batched_ms_p50": bp50, "batched_ms_p99": _pct(t_batch, 99),
             "batched_views_per_s": n / (bp50 * 1e-3), "batched_gpu_launches": launches,
             "plain_ms_p50": pp50, "plain_ms_p99": _pct(t_plain, 99), "plain_views_per_s": n / (pp50 * 1e-3),

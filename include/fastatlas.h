@@ -378,6 +378,29 @@ fa_status fa_set_wait_limits(fa_ctx* ctx, uint32_t loop_cap, uint64_t wait_ns);
 #define FA_RASTER_HIZ 1u
 fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix, uint32_t flags);
 
+/* Kernel shapes of the chart and packing passes on this context, a schedule knob
+ * like the raster one: every value gives the same results, only the timing differs.
+ *   uf_threads    threads per 1024-triangle tile of the local union-find of the chart
+ *                 pass (App. A "GPU Union Find"): 256, 512 or 1024 (4, 2 or 1
+ *                 triangles per thread; 8, 4 or 2 tiles resident per SM);
+ *   push_threads  threads of the CTA that pushes one scale candidate's rows onto its
+ *                 frontline (Sec. 4.3): 256, 512 or 1024.
+ * Defaults 1024 and 512 (the fastest on one large frame).  fa_batch_tune searches both.
+ * The persistent frame kernel (FA_FRAME_PERSISTENT, batch plans) runs its own
+ * 1024-thread CTAs and ignores them.
+ * Errors: FA_E_INVALID_ARG (NULL ctx, any other value). */
+fa_status fa_set_chart_pack_schedule(fa_ctx* ctx, uint32_t uf_threads, uint32_t push_threads);
+
+/* The schedule knobs of a context (fa_set_raster_schedule, fa_set_chart_pack_schedule).
+ * Errors: FA_E_INVALID_ARG (NULL ctx or out). */
+typedef struct fa_kernel_schedule {
+  uint32_t mid_max_pix;
+  uint32_t raster_flags;
+  uint32_t uf_threads;
+  uint32_t push_threads;
+} fa_kernel_schedule;
+fa_status fa_get_kernel_schedule(const fa_ctx* ctx, fa_kernel_schedule* out);
+
 /* Number of kernels the library launched on this context since creation (a
  * host-side counter; used to report launches per frame). */
 uint64_t fa_launch_count(const fa_ctx* ctx);
@@ -456,8 +479,9 @@ fa_status fa_atlas_batch(fa_batch* batch, uint32_t n_views, const fa_mesh* const
                          const fa_frame_params* params, const fa_frame_out* outs, fa_stream_t stream);
 
 /* Schedule autotuner: first the raster schedule of every lane's context (mid-size
- * limit 16 or 64, with and without FA_RASTER_HIZ, at the current lanes), then lanes
- * in {1, 2, 4, .., n_lanes} x both policies: each schedule's batch is captured into
+ * limit 16 or 64, with and without FA_RASTER_HIZ, at the current lanes), then the
+ * chart/pack kernel shapes (uf_threads x push_threads in {256, 512, 1024}^2), then
+ * lanes in {1, 2, 4, .., n_lanes} x both policies: each schedule's batch is captured into
  * a CUDA graph, launched once, `reps` launches are timed (CUDA events, best of) and
  * the fastest schedule is kept; *best_ms (may be NULL)
  * receives its time.  Runs the views (outputs are overwritten) and synchronizes;
@@ -465,6 +489,9 @@ fa_status fa_atlas_batch(fa_batch* batch, uint32_t n_views, const fa_mesh* const
 fa_status fa_batch_tune(fa_batch* batch, uint32_t n_views, const fa_mesh* const* meshes,
                         const fa_frame_params* params, const fa_frame_out* outs, uint32_t reps,
                         float* best_ms);
+
+/* The kernel schedule of the batch's lanes (all lanes share it; the tuner sets it). */
+fa_status fa_batch_get_kernel_schedule(const fa_batch* batch, fa_kernel_schedule* out);
 
 /* Kernels launched by all lanes since creation. */
 uint64_t fa_batch_launch_count(const fa_batch* batch);

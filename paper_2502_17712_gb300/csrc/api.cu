@@ -127,6 +127,8 @@ fa_status fa_create(fa_ctx** out, const fa_config* cfg) {
   ctx->loop_cap = kLoopCap;
   ctx->wait_ns = kWaitNs;
   ctx->mid_max_pix = FA_RASTER_MID_OFF;
+  ctx->uf_threads = 1024;
+  ctx->push_threads = kDefaultPushThreads;
   fa_status st = FA_OK;
   const uint64_t T = c.max_tris, V = c.max_verts, C = c.max_charts;
   ctx->queue_cap = (uint32_t)(T < (1u << 20) ? T + 1024 : (1u << 20));
@@ -418,6 +420,21 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out) {
 }
 
 uint64_t fa_launch_count(const fa_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+static bool schedule_threads_ok(uint32_t n) { return n == 256 || n == 512 || n == 1024; }
+
+fa_status fa_set_chart_pack_schedule(fa_ctx* ctx, uint32_t uf_threads, uint32_t push_threads) {
+  if (!ctx || !schedule_threads_ok(uf_threads) || !schedule_threads_ok(push_threads)) return FA_E_INVALID_ARG;
+  ctx->uf_threads = uf_threads;
+  ctx->push_threads = push_threads;
+  return FA_OK;
+}
+
+fa_status fa_get_kernel_schedule(const fa_ctx* ctx, fa_kernel_schedule* out) {
+  if (!ctx || !out) return FA_E_INVALID_ARG;
+  *out = fa_kernel_schedule{ctx->mid_max_pix, ctx->raster_flags, ctx->uf_threads, ctx->push_threads};
+  return FA_OK;
+}
 
 fa_status fa_set_raster_schedule(fa_ctx* ctx, uint32_t mid_max_pix, uint32_t flags) {
   if (!ctx || mid_max_pix < FA_RASTER_MID_OFF || mid_max_pix > FA_RASTER_MID_MAX || (flags & ~FA_RASTER_HIZ))

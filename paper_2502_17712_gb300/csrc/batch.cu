@@ -190,16 +190,18 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
   cand.push_back(max_lanes);
   float best = -1.0f;
   uint32_t best_l = b->active, best_p = b->policy, best_m = b->ctx[0]->mid_max_pix,
-           best_f = b->ctx[0]->raster_flags;
+           best_f = b->ctx[0]->raster_flags, best_u = b->ctx[0]->uf_threads, best_q = b->ctx[0]->push_threads;
   fa_status st = FA_OK;
   // one schedule: capture the batch as the caller would run it (one graph), time it
-  auto trial = [&](uint32_t l, uint32_t pol, uint32_t mid, uint32_t fl) {
+  auto trial = [&](uint32_t l, uint32_t pol, uint32_t mid, uint32_t fl, uint32_t uf, uint32_t pu) {
     if (st != FA_OK) return;
     b->active = l;
     b->policy = pol;
     for (fa_ctx* c : b->ctx) {
       c->mid_max_pix = mid;
       c->raster_flags = fl;
+      c->uf_threads = uf;
+      c->push_threads = pu;
     }
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
@@ -237,18 +239,26 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
       best_p = pol;
       best_m = mid;
       best_f = fl;
+      best_u = uf;
+      best_q = pu;
     }
   };
-  // the raster schedule first (at the current lanes and policy), then lanes x policy
-  const uint32_t l0 = b->active, p0 = b->policy;
+  // the raster schedule first (at the current lanes, policy and kernel shapes), then
+  // the chart/pack kernel shapes, then lanes x policy
+  const uint32_t l0 = b->active, p0 = b->policy, u0 = best_u, q0 = best_q;
   const uint32_t mids[] = {FA_RASTER_MID_OFF, 64};
   for (uint32_t mid : mids)
-    for (uint32_t fl = 0; fl <= FA_RASTER_HIZ; ++fl) trial(l0, p0, mid, fl);
+    for (uint32_t fl = 0; fl <= FA_RASTER_HIZ; ++fl) trial(l0, p0, mid, fl, u0, q0);
   const uint32_t rm = best_m, rf = best_f;
+  const uint32_t shapes[] = {256, 512, 1024};
+  for (uint32_t uf : shapes)
+    for (uint32_t pu : shapes)
+      if (uf != u0 || pu != q0) trial(l0, p0, rm, rf, uf, pu);
+  const uint32_t ru = best_u, rq = best_q;
   for (uint32_t l : cand)
     for (uint32_t pol = FA_BATCH_ROUND_ROBIN; pol <= FA_BATCH_LONGEST_FIRST; ++pol) {
       if (l == 1 && pol == FA_BATCH_LONGEST_FIRST) continue;  // same schedule as round robin
-      trial(l, pol, rm, rf);
+      trial(l, pol, rm, rf, ru, rq);
     }
   cudaStreamSynchronize(s);
   cudaStreamDestroy(s);
@@ -259,9 +269,16 @@ fa_status fa_batch_tune(fa_batch* b, uint32_t n_views, const fa_mesh* const* mes
   for (fa_ctx* c : b->ctx) {
     c->mid_max_pix = best_m;
     c->raster_flags = best_f;
+    c->uf_threads = best_u;
+    c->push_threads = best_q;
   }
   if (best_ms) *best_ms = best;
   return st;
+}
+
+fa_status fa_batch_get_kernel_schedule(const fa_batch* b, fa_kernel_schedule* out) {
+  if (!b || !out || b->ctx.empty()) return FA_E_INVALID_ARG;
+  return fa_get_kernel_schedule(b->ctx[0], out);
 }
 
 uint64_t fa_batch_launch_count(const fa_batch* b) {

@@ -1,6 +1,8 @@
 // Chart kernels (Sec. 5.1; App. A "GPU Union Find", Alg. 1): the launch wrappers
 // of the stage bodies in chartify.cuh, the standalone visible-list kernels and the
 // launch sequence of one chart pass.
+#include <algorithm>
+
 #include "chartify.cuh"
 
 namespace fa {
@@ -9,13 +11,25 @@ namespace {
 using cf::UfArgs;
 using cf::kBlock;
 using cf::kPerBlock;
-using cf::kLocalThreads;
 using cf::kTile;
 
-template <bool LIST>
-__global__ void __launch_bounds__(kLocalThreads) k_uf_local(UfArgs a) {
+template <bool LIST, int NT>
+__global__ void __launch_bounds__(NT) k_uf_local(UfArgs a) {
   pdl_wait();
-  cf::local_body<LIST, kLocalThreads>(a, blockIdx.x, gridDim.x);
+  cf::local_body<LIST, NT>(a, blockIdx.x, gridDim.x);
+}
+
+// The local union-find with the context's tile shape (NT threads per tile; listed
+// tiles: a grid of the resident blocks, 2048 / NT per SM).
+template <bool LIST>
+void launch_local(uint32_t nt, uint32_t ntiles, cudaStream_t s, const UfArgs& a) {
+  auto grid = [&](uint32_t per_sm) { return LIST ? std::min(ntiles, 152u * per_sm) : ntiles; };
+  if (nt == 256)
+    launch_k(k_uf_local<LIST, 256>, grid(8), 256, 0, s, a);
+  else if (nt == 512)
+    launch_k(k_uf_local<LIST, 512>, grid(4), 512, 0, s, a);
+  else
+    launch_k(k_uf_local<LIST, 1024>, grid(2), 1024, 0, s, a);
 }
 
 __global__ void k_uf_init_v(int32_t* label, uint32_t T, uint32_t V) {
@@ -125,9 +139,9 @@ fa_status launch_chartify(fa_ctx* ctx, const fa_mesh* mesh, const uint32_t* vt, 
   const uint32_t ntiles = (mesh->T + kTile - 1) / kTile;
   mark(ctx, "k_uf_local", s);
   if (tile_list)
-    launch_k(k_uf_local<true>, std::min(ntiles, 152u * (2048u / kLocalThreads)), kLocalThreads, 0, s, a);
+    launch_local<true>(ctx->uf_threads, ntiles, s, a);
   else
-    launch_k(k_uf_local<false>, ntiles, kLocalThreads, 0, s, a);
+    launch_local<false>(ctx->uf_threads, ntiles, s, a);
   mark(ctx, "k_uf_hook", s);
   if (vm)
     launch_k(k_uf_hook_v, gw, kBlock, 0, s, a);

@@ -84,7 +84,6 @@ struct UfArgs {
 // global init: afterwards every visible triangle points to a root, and only edges that
 // leave the tile remain for the global hooking.
 constexpr int kTile = 1024;
-constexpr int kLocalThreads = 1024;  // threads of the local union-find kernel (kTile / kLocalThreads triangles each)
 constexpr uint32_t kXCap = 3 * kTile;  // cross-tile edge slots per tile
 
 __device__ __forceinline__ int32_t lfind(volatile int32_t* lab, int32_t x) {

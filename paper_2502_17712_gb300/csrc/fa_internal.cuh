@@ -32,6 +32,7 @@ constexpr unsigned long long kWaitNs = FA_DEFAULT_WAIT_NS;  // device time limit
 
 // Small counters that live in device memory (one struct per context).
 constexpr uint32_t kMaxFrontBlocks = 152 * 4;  // raster front-end blocks (survivor regions)
+constexpr uint32_t kDefaultPushThreads = 512;  // threads of a candidate's push CTA (fa_set_chart_pack_schedule)
 constexpr uint32_t kPschedWords = 64;          // schedule state of a single-view persistent launch
 
 struct DevCounters {
@@ -145,6 +146,8 @@ struct fa_ctx {
   unsigned long long wait_ns;
   uint32_t mid_max_pix;  // fa_set_raster_schedule
   uint32_t raster_flags;
+  uint32_t uf_threads;    // fa_set_chart_pack_schedule: threads per tile of the local union-find
+  uint32_t push_threads;  // threads of each candidate's push CTA
   // schedule state of the persistent frame kernel (FA_FRAME_PERSISTENT): work-item
   // counter, exit counter, abort flag and one completion counter per stage group;
   // zero between launches

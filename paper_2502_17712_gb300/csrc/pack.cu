@@ -28,10 +28,11 @@ __global__ void __launch_bounds__(pk::kScanThreads) k_pack_scan(PackScratch p, P
   pk::pack_scan_body<pk::kScanThreads>(p, a, n_scales, blockIdx.x);
 }
 
-__global__ void __launch_bounds__(pk::kPushThreads) k_pack_push(PackScratch p, PackArgs a) {
+template <int NT>
+__global__ void __launch_bounds__(NT) k_pack_push(PackScratch p, PackArgs a) {
   pdl_wait();
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  pk::push_body<pk::kPushThreads>(p, a, blockIdx.x, gridDim.x, smem_raw);
+  pk::push_body<NT>(p, a, blockIdx.x, gridDim.x, smem_raw);
 }
 
 __global__ void __launch_bounds__(256) k_pack_place(PackScratch p, PackArgs a) {
@@ -60,7 +61,16 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
   if (ctx) mark(ctx, "k_pack_scan", s);
   launch_k(k_pack_scan, g2, pk::kScanThreads, 0, s, p, a, n_scales);
   if (ctx) mark(ctx, "k_pack_push", s);
-  launch_k(k_pack_push, n_scales, pk::kPushThreads, pk::push_smem_bytes(a.front_cap), s, p, a);
+  // one CTA per candidate, of the context's push shape (the allocation-free entry,
+  // without a context, takes the default)
+  const uint32_t pt = ctx ? ctx->push_threads : (uint32_t)pk::kPushThreads;
+  const size_t psm = pk::push_smem_bytes(a.front_cap);
+  if (pt == 256)
+    launch_k(k_pack_push<256>, n_scales, 256, psm, s, p, a);
+  else if (pt == 512)
+    launch_k(k_pack_push<512>, n_scales, 512, psm, s, p, a);
+  else
+    launch_k(k_pack_push<1024>, n_scales, 1024, psm, s, p, a);
   if (write_place) {
     if (ctx) mark(ctx, "k_pack_place", s);
     launch_k(k_pack_place, 152 * 2, 256, 0, s, p, a);
@@ -70,7 +80,11 @@ fa_status launch_pack_kernels(fa_ctx* ctx, const PackScratch& p, const uint32_t*
 }
 
 fa_status pack_set_smem_limit() {
-  FA_CUDA_TRY(cudaFuncSetAttribute(k_pack_push, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  FA_CUDA_TRY(cudaFuncSetAttribute(k_pack_push<256>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)pk::push_smem_bytes(kFrontCap)));
+  FA_CUDA_TRY(cudaFuncSetAttribute(k_pack_push<512>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   (int)pk::push_smem_bytes(kFrontCap)));
+  FA_CUDA_TRY(cudaFuncSetAttribute(k_pack_push<1024>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    (int)pk::push_smem_bytes(kFrontCap)));
   return FA_OK;
 }

@@ -406,7 +406,7 @@ __device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackA
 // max of the frontline under the box, then the frontline takes the box top, one
 // barrier per segment.  Segments of one row never overlap in x, so a row may span
 // two chunks.
-constexpr int kPushThreads = 1024;  // threads of a candidate's CTA (the separate push kernel)
+constexpr int kPushThreads = (int)kDefaultPushThreads;  // the push kernel's CTA without a context
 constexpr uint32_t kStageBytes = kChunk * 8u + kSegStride * 2u;  // records + segment list
 static_assert(kStageBytes % 16u == 0u, "bulk copies move multiples of 16 bytes");
 

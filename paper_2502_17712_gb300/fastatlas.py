@@ -49,7 +49,8 @@ EXPORTS = ["fa_version", "fa_status_string", "fa_create", "fa_destroy", "fa_mesh
            "fa_server_session_open", "fa_server_session_close", "fa_server_submit", "fa_server_poll",
            "fa_server_stats", "fa_server_now_ms", "fa_frame_stats_read", "fa_set_wait_limits",
            "fa_batch_plan_create", "fa_batch_plan_launch", "fa_batch_plan_get_schedule",
-           "fa_batch_plan_set_schedule", "fa_batch_plan_tune", "fa_batch_plan_destroy", "fa_set_raster_schedule"]
+           "fa_batch_plan_set_schedule", "fa_batch_plan_tune", "fa_batch_plan_destroy", "fa_set_raster_schedule",
+           "fa_set_chart_pack_schedule", "fa_get_kernel_schedule", "fa_batch_get_kernel_schedule"]
 FA_RASTER_MID_OFF = 16
 FA_RASTER_MID_MAX = 256
 FA_RASTER_HIZ = 1
@@ -102,6 +103,14 @@ class fa_frame_stats(ctypes.Structure):
 class fa_plan_schedule(ctypes.Structure):
     _fields_ = [("lanes", ctypes.c_uint32), ("policy", ctypes.c_uint32), ("worker_pct", ctypes.c_uint32),
                 ("mid_max_pix", ctypes.c_uint32), ("raster_flags", ctypes.c_uint32)]
+
+
+class fa_kernel_schedule(ctypes.Structure):
+    _fields_ = [("mid_max_pix", ctypes.c_uint32), ("raster_flags", ctypes.c_uint32),
+                ("uf_threads", ctypes.c_uint32), ("push_threads", ctypes.c_uint32)]
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k, _ in self._fields_}
 
 
 class fa_server_done(ctypes.Structure):
@@ -207,6 +216,12 @@ def load(path: str = LIB_PATH):
     lib.fa_launch_count.restype = ctypes.c_uint64
     lib.fa_set_raster_schedule.argtypes = [P, u32, u32]
     lib.fa_set_raster_schedule.restype = st
+    lib.fa_set_chart_pack_schedule.argtypes = [P, u32, u32]
+    lib.fa_set_chart_pack_schedule.restype = st
+    lib.fa_get_kernel_schedule.argtypes = [P, ctypes.POINTER(fa_kernel_schedule)]
+    lib.fa_get_kernel_schedule.restype = st
+    lib.fa_batch_get_kernel_schedule.argtypes = [P, ctypes.POINTER(fa_kernel_schedule)]
+    lib.fa_batch_get_kernel_schedule.restype = st
     lib.fa_set_wait_limits.argtypes = [P, u32, ctypes.c_uint64]
     lib.fa_set_wait_limits.restype = st
     lib.fa_frame_stats_read.argtypes = [P, P, ctypes.POINTER(fa_frame_stats)]
@@ -392,6 +407,15 @@ class Context:
     def set_raster_schedule(self, mid_max_pix=FA_RASTER_MID_OFF, flags=0):
         _check(load().fa_set_raster_schedule(self.handle, int(mid_max_pix), int(flags)), "fa_set_raster_schedule")
 
+    def set_chart_pack_schedule(self, uf_threads=1024, push_threads=512):
+        _check(load().fa_set_chart_pack_schedule(self.handle, int(uf_threads), int(push_threads)),
+               "fa_set_chart_pack_schedule")
+
+    def kernel_schedule(self) -> dict:
+        out = fa_kernel_schedule()
+        _check(load().fa_get_kernel_schedule(self.handle, ctypes.byref(out)), "fa_get_kernel_schedule")
+        return out.as_dict()
+
     @property
     def launches(self) -> int:
         return fa_launch_count(self.handle)
@@ -522,6 +546,11 @@ class Batch:
         _check(load().fa_batch_get_schedule(self.handle, ctypes.byref(lanes), ctypes.byref(pol)),
                "fa_batch_get_schedule")
         return lanes.value, pol.value
+
+    def kernel_schedule(self) -> dict:
+        out = fa_kernel_schedule()
+        _check(load().fa_batch_get_kernel_schedule(self.handle, ctypes.byref(out)), "fa_batch_get_kernel_schedule")
+        return out.as_dict()
 
     @property
     def launches(self) -> int:

@@ -55,6 +55,10 @@ def test_host_side_argument_errors(lib):
     assert lib.fa_launch_count(None) == 0
     assert lib.fa_set_wait_limits(None, 0, 0) == F.FA_E_INVALID_ARG
     assert lib.fa_set_raster_schedule(None, 64, 0) == F.FA_E_INVALID_ARG
+    assert lib.fa_set_chart_pack_schedule(None, 1024, 1024) == F.FA_E_INVALID_ARG
+    ks = F.fa_kernel_schedule()
+    assert lib.fa_get_kernel_schedule(None, ctypes.byref(ks)) == F.FA_E_INVALID_ARG
+    assert lib.fa_batch_get_kernel_schedule(None, ctypes.byref(ks)) == F.FA_E_INVALID_ARG
     lib.fa_destroy(None)
     lib.fa_mesh_release(None)
     out = ctypes.c_int32()

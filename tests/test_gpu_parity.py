@@ -546,3 +546,49 @@ def test_raster_schedule_changes_no_result(F, small_ctx, mid, flags):
         assert torch.equal(torch.nan_to_num(a.uv, 7.0), torch.nan_to_num(b.uv, 7.0))
         compare_frame(sc, M, W, H, 1.0, L, b, sb)
         mesh.close()
+
+
+@pytest.mark.parametrize("uf,push", [(256, 256), (512, 512), (256, 1024), (1024, 1024)])
+def test_chart_pack_schedule_changes_no_result(F, small_ctx, uf, push):
+    """Other tile shapes of the local union-find and CTA sizes of the push
+    (fa_set_chart_pack_schedule) give the same frame, bit for bit, and the oracle's;
+    so does fa_pack alone on 40,000 boxes."""
+    import torch
+    with pytest.raises(F.FastAtlasError):
+        small_ctx.set_chart_pack_schedule(128, 1024)
+    assert small_ctx.kernel_schedule()["uf_threads"] == 1024
+    cases = [(S.grid_scene(7), S.spline_cameras(7, 5, 1920, 1080)[2], 1920, 1080, 11),
+             (S.instanced_grid_scene(11, 8, n=24), S.hemisphere_camera(11, 1280, 720, radius=4.0), 1280, 720, 11)]
+    for sc, M, W, H, L in cases:
+        mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+        a, sa = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, L)
+        small_ctx.set_chart_pack_schedule(uf, push)
+        try:
+            assert small_ctx.kernel_schedule() == {"mid_max_pix": F.FA_RASTER_MID_OFF, "raster_flags": 0,
+                                                   "uf_threads": uf, "push_threads": push}
+            b, sb = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, L)
+        finally:
+            small_ctx.set_chart_pack_schedule()
+        assert sa == sb == 0
+        for name in ("vt", "tri_chart", "place", "result", "bbox"):
+            assert torch.equal(getattr(a, name), getattr(b, name)), name
+        assert torch.equal(torch.nan_to_num(a.uv, 7.0), torch.nan_to_num(b.uv, 7.0))
+        compare_frame(sc, M, W, H, 1.0, L, b, sb)
+        mesh.close()
+    n, log2 = 40000, 12
+    fa, fb = S.lognormal_boxes(6, n, mean_texels=6)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1 << 16, max_width=64, max_height=64,
+                    max_atlas_log2=12)
+    ctx.set_chart_pack_schedule(uf, push)
+    place = torch.zeros(1 << 16, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    F.fa_pack(ctx.handle, d_fa, d_fb, cnt, log2, 64, 0, None, place, res)
+    torch.cuda.synchronize()
+    pk = O.pack(fa, fb, log2)
+    r = res.cpu().numpy().view(np.uint32)
+    assert (int(r[0]), int(r[1]), int(r[2]), int(r[3])) == (pk.k, pk.omega, pk.height, 0)
+    assert (place[:n].cpu().numpy() == pk.place).all()
+    ctx.close()
