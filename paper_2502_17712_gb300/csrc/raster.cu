@@ -1,6 +1,8 @@
 // Visibility kernels (Sec. 5.1; App. A "Detecting Visible Triangles"): the launch
 // wrappers of the stage bodies in raster.cuh and the launch sequence of one
 // visibility pass.
+#include <algorithm>
+
 #include "raster.cuh"
 
 namespace fa {
@@ -43,7 +45,9 @@ fa_status launch_visibility(fa_ctx* ctx, const fa_mesh* mesh, const Mat4& M, uin
                             int32_t* tri_chart_init) {
   // one wave (two resident blocks per SM): half the survivor regions of two waves,
   // so the passes that look regions up scan fewer counts
-  const uint32_t fb = grid_for(mesh->T, rs::kFrontThreads, 152u * 2u);
+  // (and enough blocks for the clears: at most 16 depth-buffer pixels per thread)
+  const uint32_t fb = std::max(grid_for(mesh->T, rs::kFrontThreads, 152u * 2u),
+                               grid_for((uint64_t)W * H, rs::kFrontThreads * 16u, 152u * 2u));
   const RasterArgs A = rs::make_raster_args(ctx, mesh, M, W, H, vt, reset_status, Mdev, cons, tri_chart_init, fb,
                                             rs::kFrontThreads);
   ctx->front_blocks = A.front_blocks;
