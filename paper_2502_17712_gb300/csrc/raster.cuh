@@ -702,16 +702,65 @@ __device__ __forceinline__ uint32_t surv_slot(const RasterArgs& A, const uint32_
 // Depth pre-pass, exact part: survivors of the front end.  Survivor i writes its
 // candidate record (or an empty marker) at slot i, so no counter is needed; clipped
 // triangles append theirs after slot T.
+// The samples of one sub-triangle per group of kRasterGroup lanes: the group's
+// leader (its first lane) holds the snapped vertices, area and pixel box, and `go`;
+// every lane of the group takes the box's samples sub, sub + kRasterGroup, ...  PASS
+// as in sample(): 0 writes the depth keys; 1 and 2 return whether a sample of the
+// leader's sub-triangle passed the depth test (in every lane of the group).  All
+// lanes of the warp call it.
+constexpr uint32_t kRasterGroup = 16;
+template <int PASS>
+__device__ __forceinline__ bool group_raster(const SV& a0, const SV& b0, const SV& c0, int64_t A0, int qx0, int qy0,
+                                             int qx1, int qy1, bool go0, uint32_t* __restrict__ zbuf, int W) {
+  const uint32_t lane = threadIdx.x & 31, src = lane & ~(kRasterGroup - 1u), sub = lane - src;
+  // every lane of the warp takes part in every shuffle (the groups' leaders differ in
+  // `go`, so no shuffle may sit under it)
+  const bool go = __shfl_sync(0xFFFFFFFFu, go0, src);
+  const SV a{__shfl_sync(0xFFFFFFFFu, (int32_t)a0.X, src), __shfl_sync(0xFFFFFFFFu, (int32_t)a0.Y, src),
+             __shfl_sync(0xFFFFFFFFu, a0.zn, src)};
+  const SV b{__shfl_sync(0xFFFFFFFFu, (int32_t)b0.X, src), __shfl_sync(0xFFFFFFFFu, (int32_t)b0.Y, src),
+             __shfl_sync(0xFFFFFFFFu, b0.zn, src)};
+  const SV c{__shfl_sync(0xFFFFFFFFu, (int32_t)c0.X, src), __shfl_sync(0xFFFFFFFFu, (int32_t)c0.Y, src),
+             __shfl_sync(0xFFFFFFFFu, c0.zn, src)};
+  const int64_t Ar = (int64_t)(((uint64_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)((uint64_t)A0 >> 32), src) << 32) |
+                               (uint64_t)__shfl_sync(0xFFFFFFFFu, (uint32_t)A0, src));
+  const int px0 = __shfl_sync(0xFFFFFFFFu, qx0, src), py0 = __shfl_sync(0xFFFFFFFFu, qy0, src);
+  const int px1 = __shfl_sync(0xFFFFFFFFu, qx1, src), py1 = __shfl_sync(0xFFFFFFFFu, qy1, src);
+  bool vis = false;
+  if (go) {
+    const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
+    const float zmin = fminf(a.zn, fminf(b.zn, c.zn)), zmax = fmaxf(a.zn, fmaxf(b.zn, c.zn));
+    const int w = px1 - px0 + 1, npix = w * (py1 - py0 + 1);
+    for (int s = (int)sub; s < npix; s += (int)kRasterGroup) {
+      const int px = px0 + s % w, py = py0 + s / w;
+      const Edges E = edges_at(a, b, c, px, py);
+      vis |= sample<PASS>(E, E.e, a, b, c, invA, zbuf + (size_t)py * W + px, zmin, zmax);
+    }
+  }
+  if (PASS == 0) return false;
+  const uint32_t gmask = ((1u << kRasterGroup) - 1u) << src;
+  return (__ballot_sync(0xFFFFFFFFu, vis) & gmask) != 0u;
+}
+
 template <bool DEV_M, int NT>
 __device__ __forceinline__ void exact_body(const RasterArgs& A, uint32_t bid, uint32_t nblk) {
   __shared__ uint32_t pre[kMaxFrontBlocks + 1];
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t n = surv_prefix<NT>(A, pre);
   const uint32_t stride = nblk * blockDim.x;
-  for (uint32_t wbase = bid * blockDim.x + (threadIdx.x & ~31u); wbase < n; wbase += stride) {
-    const uint32_t v = wbase + lane;
-    const uint32_t i = v < n ? surv_slot(A, pre, v, wbase) : 0u;
-    Exact E;
+  // Few survivors for the grid (a small frame): each gets a group of kRasterGroup
+  // lanes, its leader doing the set-up and the group sharing the box's samples, so
+  // that the grid's warps are not each waiting on one thread's sample loop.  The
+  // same samples get the same keys either way.
+  const bool grouped = (uint64_t)n * kRasterGroup <= (uint64_t)stride;
+  const uint32_t sub = lane & (kRasterGroup - 1u);
+  for (uint32_t wbase = bid * blockDim.x + (threadIdx.x & ~31u); (grouped ? wbase / kRasterGroup : wbase) < n;
+       wbase += stride) {
+    const uint32_t vfirst = grouped ? wbase / kRasterGroup : wbase;
+    // (in a group only the leader sets up; the others take no survivor here)
+    const uint32_t v = grouped ? (sub == 0u ? vfirst + lane / kRasterGroup : n) : wbase + lane;
+    const uint32_t i = v < n ? surv_slot(A, pre, v, vfirst) : 0u;
+    Exact E = {};
     uint32_t t = 0, tiles = 0;
     int kind = 0;  // 0 nothing, 1 small, 2 large
     bool mid = false;  // large, but at most kMidMaxPix pixels
@@ -794,13 +843,16 @@ __device__ __forceinline__ void exact_body(const RasterArgs& A, uint32_t bid, ui
     }
     if (v < n) {
       if (kind == 1) {
-        const float invA = __fdiv_rn(1.0f, ll2float_rn(E.s.A));
-        raster_rect<0>(E.a, E.b, E.c, invA, E.s.px0, E.s.py0, E.s.px1, E.s.py1, A.zbuf, A.W);
+        if (!grouped) {
+          const float invA = __fdiv_rn(1.0f, ll2float_rn(E.s.A));
+          raster_rect<0>(E.a, E.b, E.c, invA, E.s.px0, E.s.py0, E.s.px1, E.s.py1, A.zbuf, A.W);
+        }
         store_cand(A, i, make_cand(E.a, E.b, E.c, E.s, t));
       } else {
         reinterpret_cast<uint32_t*>(A.cand + i)[6] = 0xFFFFFFFFu;  // empty: px0 = py0 = 0xFFFF
       }
     }
+    if (grouped) group_raster<0>(E.a, E.b, E.c, E.s.A, E.s.px0, E.s.py0, E.s.px1, E.s.py1, kind == 1, A.zbuf, A.W);
   }
   // then the (rare) triangles that need clipping, from the front blocks' regions
   __syncthreads();  // pre is reused
@@ -939,12 +991,21 @@ __device__ __forceinline__ void mark_body(const RasterArgs& A, uint32_t bid, uin
   const uint32_t nc = min(__ldcg(&A.ctr->ncand), A.cand_cap - A.clip_base);
   const uint32_t n = ns + nc;  // survivor records, then the clipped-path records
   const uint32_t stride = nblk * blockDim.x;
-  for (uint32_t base = bid * blockDim.x; base < n; base += stride) {
-    const uint32_t k = base + threadIdx.x;
-    bool vis = false;
+  // few records for the grid: a group of kRasterGroup lanes per record (as in the
+  // exact pass), its samples tested together instead of one after the other
+  const bool grouped = (uint64_t)n * kRasterGroup <= (uint64_t)stride;
+  const uint32_t sub = threadIdx.x & (kRasterGroup - 1u);
+  for (uint32_t base = bid * blockDim.x; (grouped ? base / kRasterGroup : base) < n; base += stride) {
+    const uint32_t wb = base + (threadIdx.x & ~31u);  // the warp's first thread
+    const uint32_t kfirst = grouped ? wb / kRasterGroup : wb;
+    const uint32_t k = grouped ? (sub == 0u ? kfirst + (threadIdx.x & 31u) / kRasterGroup : n) : base + threadIdx.x;
+    bool vis = false, go = false;
     uint32_t t = 0xFFFFFFFFu;
+    SV ga{0, 0, 0.0f}, gb{0, 0, 0.0f}, gc{0, 0, 0.0f};
+    int64_t gA = 0;
+    int gx0 = 0, gy0 = 0, gx1 = -1, gy1 = -1;
     if (k < n) {
-      const uint32_t i = k < ns ? surv_slot(A, pre, k, base + (threadIdx.x & ~31u)) : A.clip_base + (k - ns);
+      const uint32_t i = k < ns ? surv_slot(A, pre, k, kfirst) : A.clip_base + (k - ns);
       const float4* s = reinterpret_cast<const float4*>(A.cand + i);
       const float4 fb = __ldcs(s + 1);
       const uint32_t b0 = __float_as_uint(fb.z), b1 = __float_as_uint(fb.w);
@@ -957,10 +1018,26 @@ __device__ __forceinline__ void mark_body(const RasterArgs& A, uint32_t bid, uin
         const int px0 = (int)(b0 & 0xFFFFu), py0 = (int)(b0 >> 16), px1 = (int)(b1 & 0xFFFFu), py1 = (int)(b1 >> 16);
         if (!hidden_by_tiles(A, fc.x, fc.y, fc.z, px0, py0, px1, py1)) {
           const int64_t Ar = (b.X - a.X) * (c.Y - a.Y) - (c.X - a.X) * (b.Y - a.Y);
-          const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
-          vis = raster_rect<CONS ? 2 : 1>(a, b, c, invA, px0, py0, px1, py1, A.zbuf, A.W);
+          if (grouped) {
+            go = true;
+            ga = a;
+            gb = b;
+            gc = c;
+            gA = Ar;
+            gx0 = px0;
+            gy0 = py0;
+            gx1 = px1;
+            gy1 = py1;
+          } else {
+            const float invA = __fdiv_rn(1.0f, ll2float_rn(Ar));
+            vis = raster_rect<CONS ? 2 : 1>(a, b, c, invA, px0, py0, px1, py1, A.zbuf, A.W);
+          }
         }
       }
+    }
+    if (grouped) {
+      const bool gv = group_raster<CONS ? 2 : 1>(ga, gb, gc, gA, gx0, gy0, gx1, gy1, go, A.zbuf, A.W);
+      vis = sub == 0u && k < n && gv;
     }
     const uint32_t word = vis ? (t >> 5) : 0xFFFFFFFFu;
     const uint32_t peers = __match_any_sync(0xFFFFFFFFu, word);
