@@ -400,9 +400,9 @@ __device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackA
 
 // Row push of one candidate per CTA, then the last CTA selects.  The chunks' push
 // records and segment lists are staged into shared memory by bulk asynchronous
-// copies, two chunks in flight; every row segment is processed box-parallel (a
-// group of 32 .. 4 threads per box in segments of at most 256 boxes, else one
-// thread per box): resting height =
+// copies, two chunks in flight; every row segment is processed box-parallel (with NT
+// threads: a group of 2 .. 32 threads per box in segments of at most NT / 4 boxes,
+// else one thread per box): resting height =
 // max of the frontline under the box, then the frontline takes the box top, one
 // barrier per segment.  Segments of one row never overlap in x, so a row may span
 // two chunks.

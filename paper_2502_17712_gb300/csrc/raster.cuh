@@ -14,11 +14,12 @@
 //
 // Kernels: k_raster_front (the per-triangle front end above; it also clears the
 // per-frame state for the kernels after it), k_raster_exact (the exact set-up of
-// the survivors; small sub-triangles rasterized in-thread, a 48-byte record kept
-// for the marking pass), k_raster_depth_big (the queued tiles) and k_raster_mark
-// (the queued tiles, then the records; it also lists the 1024-triangle tiles that
-// hold a visible triangle for the chart passes).  Edge values that stay below 2^24
-// over a box are stepped as exact fp32 integers.
+// the survivors; small sub-triangles rasterized in-thread, or by a group of 16
+// lanes each when the survivors are few for the grid, a 48-byte record kept for the
+// marking pass), k_raster_depth_big (the queued tiles) and k_raster_mark (the queued
+// tiles, then the records, grouped in the same way; it also lists the 1024-triangle
+// tiles that hold a visible triangle for the chart passes).  Edge values that stay
+// below 2^24 over a box are stepped as exact fp32 integers.
 #pragma once
 #include "fa_internal.cuh"
 
@@ -224,7 +225,7 @@ __device__ __forceinline__ bool raster_rect_f32(const Edges& E, const SV& a, con
     fdx[i] = (float)(int32_t)E.dx[i];
     fdy[i] = (float)(int32_t)E.dy[i];
   }
-  bool vis = false;  // PASS 1: no early exit, so the depth loads can overlap
+  bool vis = false;  // PASS 1 stops at the first sample that passes the depth test
   for (int py = py0; py <= py1; ++py) {
     float e0 = er[0], e1 = er[1], e2 = er[2];
     uint32_t* zrow = zbuf + (size_t)py * W;
