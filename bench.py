@@ -224,15 +224,20 @@ def kernel_source(kernel):
 
 
 def source_hash(source):
-    """First 16 hex digits of the SHA-256 of a kernel's .cu, its .cuh and fa_internal.cuh."""
+    """First 16 hex digits of the SHA-256 of the code of a kernel's .cu, its .cuh and
+    fa_internal.cuh, comments and whitespace removed (they change no counter)."""
     import hashlib
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2502_17712_gb300", "csrc")
     for name in (source, source[:-3] + ".cuh", "fa_internal.cuh"):
         path = os.path.join(csrc, name)
         if os.path.exists(path):
-            with open(path, "rb") as f:
-                h.update(f.read())
+            with open(path) as f:
+                text = f.read()
+            text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+            text = re.sub(r"//[^\n]*", " ", text)
+            h.update(" ".join(text.split()).encode())
     return h.hexdigest()[:16]
 
 

@@ -700,9 +700,6 @@ __device__ __forceinline__ uint32_t surv_slot(const RasterArgs& A, const uint32_
   return lo * A.surv_per_block + (v - pre[lo]);
 }
 
-// Depth pre-pass, exact part: survivors of the front end.  Survivor i writes its
-// candidate record (or an empty marker) at slot i, so no counter is needed; clipped
-// triangles append theirs after slot T.
 // The samples of one sub-triangle per group of kRasterGroup lanes: the group's
 // leader (its first lane) holds the snapped vertices, area and pixel box, and `go`;
 // every lane of the group takes the box's samples sub, sub + kRasterGroup, ...  PASS
@@ -743,6 +740,9 @@ __device__ __forceinline__ bool group_raster(const SV& a0, const SV& b0, const S
   return (__ballot_sync(0xFFFFFFFFu, vis) & gmask) != 0u;
 }
 
+// Depth pre-pass, exact part: survivors of the front end.  Survivor i writes its
+// candidate record (or an empty marker) at slot i, so no counter is needed; clipped
+// triangles append theirs after slot T.
 template <bool DEV_M, int NT>
 __device__ __forceinline__ void exact_body(const RasterArgs& A, uint32_t bid, uint32_t nblk) {
   __shared__ uint32_t pre[kMaxFrontBlocks + 1];
