@@ -592,3 +592,26 @@ def test_chart_pack_schedule_changes_no_result(F, small_ctx, uf, push):
     assert (int(r[0]), int(r[1]), int(r[2]), int(r[3])) == (pk.k, pk.omega, pk.height, 0)
     assert (place[:n].cpu().numpy() == pk.place).all()
     ctx.close()
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_grouped_raster_random_views(F, small_ctx, seed):
+    """Small meshes (a few thousand survivors: the exact and marking passes give each
+    survivor a group of lanes) under seeded views, resolutions and raster options:
+    conservative marking, mid-size boxes in-thread, tile-depth marking.  Every frame
+    equals the oracle's."""
+    rng = np.random.default_rng([seed, 0x6A0])
+    n_inst = int(rng.integers(1, 5))
+    sc = S.instanced_grid_scene(100 + seed, n_inst, n=int(rng.choice([16, 24, 32])), half=2.0)
+    W, H = [(640, 360), (1280, 720), (1920, 1080), (480, 270)][seed % 4]
+    M = S.hemisphere_camera(200 + seed, W, H, radius=float(rng.uniform(1.5, 4.0)))
+    flags = F.FA_VIS_CONSERVATIVE if seed % 2 else 0
+    mid, hiz = [(16, 0), (64, 0), (256, F.FA_RASTER_HIZ)][seed % 3]
+    mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
+    small_ctx.set_raster_schedule(mid, hiz)
+    try:
+        bufs, st = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, 11, flags=flags)
+    finally:
+        small_ctx.set_raster_schedule()
+    compare_frame(sc, M, W, H, 1.0, 11, bufs, st, flags=flags)
+    mesh.close()
