@@ -382,10 +382,13 @@ void build_view(fa_ctx* ctx, const fa_mesh* mesh, const fa_frame_params* p, cons
     ++n;
   };
   add(S_FRONT, n_front);
-  add(S_EXACT, n_tri);
+  // (twice the front end's workers: a small frame's survivors then get the raster's
+  // lane groups, one group per survivor)
+  const uint32_t n_rast = wk(T, 64);
+  add(S_EXACT, n_rast);
   add(S_DEPTH_BIG, n_pix);
   if (v.ra.zmax) add(S_ZMAX, wk(pix, 8192));
-  add(S_MARK, std::max(n_tri, n_pix));
+  add(S_MARK, std::max(n_rast, n_pix));
   if (vm) add(S_INIT_V, wk(mesh->V, 128));
   add(S_LOCAL, n_tiles);
   add(vm ? S_HOOK_V : S_HOOK, vm ? n_tri : clampu((ntiles + 7) / 8, 1, G));
