@@ -530,11 +530,17 @@ def test_raster_schedule_changes_no_result(F, small_ctx, mid, flags):
     marking pass skipping what the tile depths show hidden (fa_set_raster_schedule),
     give the same frame, bit for bit, and the oracle's."""
     import torch
+    # (the third scene has more survivors than the raster's lane groups take: its
+    # mid-size boxes go to whole warps)
     cases = [(S.grid_scene(7), S.spline_cameras(7, 5, 1920, 1080)[2], 1920, 1080, 11),
-             (S.instanced_grid_scene(11, 8, n=24), S.hemisphere_camera(11, 1280, 720, radius=4.0), 1280, 720, 11)]
-    for sc, M, W, H, L in cases:
+             (S.instanced_grid_scene(11, 8, n=24), S.hemisphere_camera(11, 1280, 720, radius=4.0), 1280, 720, 11),
+             (S.instanced_grid_scene(13, 24, n=32, half=3.0), S.hemisphere_camera(13, 1920, 1080, radius=4.0),
+              1920, 1080, 11)]
+    for ci, (sc, M, W, H, L) in enumerate(cases):
         mesh = F.Mesh(small_ctx, sc.pos, sc.idx)
         a, sa = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, L)
+        if ci == 2:
+            assert small_ctx.frame_stats()["survivors"] > 9728
         small_ctx.set_raster_schedule(mid, flags)
         try:
             b, sb = run_gpu(F, small_ctx, mesh, M, W, H, 1.0, L)
