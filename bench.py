@@ -51,13 +51,28 @@ def parse():
     ap.add_argument("--served-slots", type=int, default=8)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the small-scene latencies, camera path, ratio sweep and packer stress")
+    ap.add_argument("--scene", choices=["icospheres", "heightfield"], default="icospheres",
+                    help="the frame measured: the 4.1M-triangle icosphere scene at 1080p (default), or the "
+                         "64x64 heightfield at 480x270 into a 1024^2 atlas (the small frame, for profiles)")
     ap.add_argument("--write-traffic", metavar="NCU_CSV",
                     help="write profiles/traffic.json from an ncu --csv log of dram__bytes_read.sum and "
-                         "dram__bytes_write.sum (one launch per kernel), with the current source hashes, and exit")
+                         "dram__bytes_write.sum (one launch per kernel) of the workload the other options name, "
+                         "with the current source hashes, and exit")
     return ap.parse_args()
 
 
+def frame_scene(a):
+    """The measured frame's scene, view matrix and parameters."""
+    from paper_2502_17712_gb300 import scenes as S
+    if a.scene == "heightfield":
+        return S.heightfield_frame(a.seed)
+    return S.icosphere_frame(a.seed, a.spheres, a.ratio)
+
+
 def workload_name(a):
+    if a.scene == "heightfield":
+        return (f"heightfield64_480x270_atlas1024_ratio{a.ratio:g}_"
+                f"{'vertex' if a.mode else 'edge'}charts_64scales")
     return (f"icospheres{a.spheres}_sub5_1920x1080_atlas2048_ratio{a.ratio:g}_"
             f"{'vertex' if a.mode else 'edge'}charts_64scales")
 
@@ -241,22 +256,25 @@ def source_hash(source):
     return h.hexdigest()[:16]
 
 
-def measured_traffic(kernel):
+def measured_traffic(kernel, workload):
     """DRAM bytes per launch from the committed ncu capture, or None when the
-    kernel's source has changed since the counters were taken."""
+    capture was of another workload or the kernel's source has changed since
+    the counters were taken."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
             rec = json.load(f).get(kernel)
-        if rec is None or source_hash(rec["source"]) != rec["source_sha256_16"]:
+        if rec is None or rec.get("workload") != workload \
+                or source_hash(rec["source"]) != rec["source_sha256_16"]:
             return None
         return rec["dram_bytes_per_launch"]
     except Exception:
         return None
 
 
-def write_traffic(csv_path):
-    """profiles/traffic.json from an ncu --csv log (one row per launch and metric):
-    per kernel the read + write DRAM bytes of its first captured launch."""
+def write_traffic(csv_path, workload):
+    """profiles/traffic.json from an ncu --csv log (one row per launch and metric)
+    of the named workload: per kernel the read + write DRAM bytes of its first
+    captured launch."""
     import csv
     import re
     with open(csv_path) as f:
@@ -275,7 +293,8 @@ def write_traffic(csv_path):
     for (_, k), b in sorted(per_launch.items()):
         src = kernel_source(k)
         if src and k not in out:
-            out[k] = {"dram_bytes_per_launch": int(round(b)), "source": src, "source_sha256_16": source_hash(src)}
+            out[k] = {"dram_bytes_per_launch": int(round(b)), "workload": workload,
+                      "source": src, "source_sha256_16": source_hash(src)}
     with open(os.path.join(ROOT, "profiles", "traffic.json"), "w") as f:
         json.dump(out, f, indent=1)
         f.write("\n")
@@ -288,7 +307,7 @@ def run_reference(a):
         return
     import oracle as O
     from paper_2502_17712_gb300 import scenes as S
-    sc, M, p = S.icosphere_frame(a.seed, a.spheres, a.ratio)
+    sc, M, p = frame_scene(a)
     W, H, L = p["width"], p["height"], p["atlas_log2"]
 
     def frame():
@@ -749,7 +768,7 @@ def run_ours(a):
     if world > 1:
         dist.barrier()
     F.load()
-    sc, M, p = S.icosphere_frame(a.seed, a.spheres, a.ratio)
+    sc, M, p = frame_scene(a)
     W, H, L = p["width"], p["height"], p["atlas_log2"]
     ctx = F.Context(max_tris=sc.T, max_verts=sc.V, max_charts=1 << 17, max_width=W, max_height=H,
                     max_atlas_log2=L, device=local)
@@ -979,7 +998,7 @@ def run_ours(a):
     if dom:
         avg_ms = tot[dom] / len(per_kernel[dom])
         ab = algorithmic_bytes(dom, sc.T, sc.V, W, H, T_vis, C, work)
-        traffic = measured_traffic(dom)
+        traffic = measured_traffic(dom, workload_name(a))
         if ab is not None:
             ach = ab / (avg_ms * 1e-3) / 1e9
             roof = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
@@ -1036,7 +1055,7 @@ def run_ours(a):
 def main():
     a = parse()
     if a.write_traffic:
-        write_traffic(a.write_traffic)
+        write_traffic(a.write_traffic, workload_name(a))
     elif a.impl == "reference":
         run_reference(a)
     else:

@@ -121,7 +121,7 @@ def test_reference_arm_line():
 def test_traffic_table_round_trip(tmp_path, monkeypatch):
     """bench.py --write-traffic: every per-frame kernel has a source file; the table
     written from an ncu CSV log (thousands separators, scaled units, other metrics)
-    is read back while the sources are unchanged."""
+    is read back for the workload it was captured on while the sources are unchanged."""
     import bench
     for k in [k for ks in bench.STAGES.values() for k in ks]:
         assert bench.kernel_source(k) is not None, k
@@ -141,7 +141,8 @@ def test_traffic_table_round_trip(tmp_path, monkeypatch):
     (tmp_path / "profiles").mkdir()
     real = __import__("os").path.dirname(bench.__file__)
     (tmp_path / "paper_2502_17712_gb300").symlink_to(__import__("os").path.join(real, "paper_2502_17712_gb300"))
-    bench.write_traffic(str(log))
-    assert bench.measured_traffic("k_raster_front") == 73751296 + 26000000
-    assert bench.measured_traffic("k_uv") == 1500000
-    assert bench.measured_traffic("k_pack_push") is None
+    bench.write_traffic(str(log), "frame_a")
+    assert bench.measured_traffic("k_raster_front", "frame_a") == 73751296 + 26000000
+    assert bench.measured_traffic("k_uv", "frame_a") == 1500000
+    assert bench.measured_traffic("k_pack_push", "frame_a") is None
+    assert bench.measured_traffic("k_uv", "frame_b") is None
