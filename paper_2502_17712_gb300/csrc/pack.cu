@@ -23,9 +23,9 @@ __global__ void __launch_bounds__(kOrderTile) k_order_scatter(PackScratch p, con
   pk::order_scatter_body(p, fa, fb, order, blockIdx.x, binstart);
 }
 
-__global__ void __launch_bounds__(pk::kScanThreads) k_pack_scan(PackScratch p, PackArgs a, uint32_t n_scales) {
+__global__ void __launch_bounds__(pk::kScanThreads, 2) k_pack_scan(PackScratch p, PackArgs a, uint32_t n_scales) {
   pdl_wait();
-  pk::pack_scan_body<pk::kScanThreads>(p, a, n_scales, blockIdx.x);
+  pk::pack_scan_body<pk::kScanThreads>(p, a, n_scales, blockIdx.x, gridDim.x);
 }
 
 template <int NT>

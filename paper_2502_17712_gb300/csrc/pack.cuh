@@ -200,11 +200,11 @@ struct PackArgs {
   fa_pack_result* res;
 };
 
-// Width scan: one work item per (candidate, chunk of kChunk boxes), handed out in
-// increasing order by a counter, so the chunks before an item are always held by
+// Width scan: one work item per (KC candidates, chunk of kChunk boxes), handed out
+// in increasing order by a counter, so the chunks before an item are always held by
 // running CTAs.  Each item computes the scaled boxes (Sec. 4.2), scans the widths,
 // and takes its chunk's offset P by a decoupled look-back over the preceding chunks'
-// published sums.  It then writes, per box, the push record
+// published sums (one warp per candidate).  It then writes, per box, the push record
 //   x: xr = P mod omega (bits 0-15) | w (bits 16-31)
 //   y: h (bits 0-30) | row runs left to right (bit 31: row q = P / omega, q mod 3 == 0)
 // (w and h saturate; a candidate whose box exceeds 16 bits of width has Omega above
@@ -225,29 +225,68 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long* q, unsigned l
   asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(q), "l"(v) : "memory");
 }
 
-template <int NT>
-__device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackArgs& a, uint32_t n_scales,
-                                               uint32_t bid) {
-  constexpr int kScanPer = kChunk / NT;  // consecutive boxes per thread
-  // the order's bin totals were last read by k_order_scatter: clear them for the next call
-  if (bid == 0)
-    for (uint32_t b = threadIdx.x; b < kMaxH; b += blockDim.x) p.ord_total[b] = 0u;
-  __shared__ unsigned long long ws64[32];
-  __shared__ uint32_t ws32[32];
-  __shared__ uint32_t s_lastw[NT / 32];
-  __shared__ uint32_t s_wmax[NT / 32];
-  __shared__ uint32_t s_item;
-  __shared__ unsigned long long s_prefix;
-  __shared__ int32_t s_status;
-  // one read of the status word for the whole CTA (another CTA's time-out can set
-  // it meanwhile, and every thread must take the same branch before the barriers)
-  if (threadIdx.x == 0) s_status = __ldcg(&p.ctr->status);
+// Block-wide inclusive scans of KC values at once (warp q scans the warp sums of
+// value q); total[q] is value q's block total.
+template <int KC>
+__device__ __forceinline__ void block_scan_incl_n(const unsigned long long (&v)[KC], unsigned long long (*warp_sums)[32],
+                                                  unsigned long long (&incl)[KC], unsigned long long (&total)[KC]) {
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  unsigned long long x[KC];
+#pragma unroll
+  for (int q = 0; q < KC; ++q) x[q] = v[q];
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, x[q], o);
+      if (lane >= (unsigned)o) x[q] += y;
+    }
+  }
+  if (lane == 31)
+#pragma unroll
+    for (int q = 0; q < KC; ++q) warp_sums[q][wid] = x[q];
   __syncthreads();
-  if (s_status != 0) return;
-  const uint32_t C = __ldcg(p.count);
-  if (C > p.max_boxes || C == 0) return;
+  const uint32_t nw = blockDim.x >> 5;
+  if (wid < (uint32_t)KC) {
+    unsigned long long t = lane < nw ? warp_sums[wid][lane] : 0ull;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const unsigned long long y = __shfl_up_sync(0xFFFFFFFFu, t, o);
+      if (lane >= (unsigned)o) t += y;
+    }
+    warp_sums[wid][lane] = t;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int q = 0; q < KC; ++q) {
+    incl[q] = x[q] + (wid ? warp_sums[q][wid - 1] : 0ull);
+    total[q] = warp_sums[q][31];
+  }
+}
+
+// Scaled width and height of a footprint for candidate k (Sec. 4.2).
+__device__ __forceinline__ uint32_t scaled_side(unsigned long long k, uint32_t f, const PackArgs& a,
+                                                unsigned long long d) {
+  const uint32_t s = (uint32_t)((k * f + d) >> a.shift);
+  return (s > a.min_box ? s : a.min_box) + 2u * a.gutter;
+}
+
+// The items of C boxes with KC candidates each.  KC = 2: the candidates of item
+// (g, c) are k = 2g + 1 and 2g + 2, so one item loads its chunk's footprints once
+// for both, and twice as many chunks fit one wave of the grid; each candidate keeps
+// its own scan state.
+template <int NT, int KC>
+__device__ __forceinline__ void pack_scan_items(const PackScratch& p, const PackArgs& a, uint32_t n_scales,
+                                                uint32_t C) {
+  constexpr int kScanPer = kChunk / NT;  // consecutive boxes per thread
+  __shared__ unsigned long long ws64[KC][32];
+  __shared__ uint32_t ws32[KC][32];
+  __shared__ uint32_t s_lastw[KC][NT / 32];
+  __shared__ uint32_t s_wmax[KC][NT / 32];
+  __shared__ uint32_t s_item;
+  __shared__ unsigned long long s_prefix[KC];
   const uint32_t nch = (C + kChunk - 1) / kChunk;
-  const uint32_t items = nch * n_scales;
+  const uint32_t items = nch * ((n_scales + KC - 1) / KC);
   const uint32_t om = 1u << a.atlas_log2;
   const unsigned long long d = (1ull << a.shift) - 1ull;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
@@ -257,44 +296,46 @@ __device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackA
     __syncthreads();
     const uint32_t item = s_item;
     if (item >= items) break;
-    const uint32_t kidx = item / nch, c = item % nch;
-    const unsigned long long k = kidx + 1;
+    const uint32_t grp = item / nch, c = item % nch;
     const uint32_t base = c * kChunk, n = min(C - base, kChunk);
     const uint32_t j0 = tid * kScanPer;
-    // this thread's boxes (the footprint array is padded to whole chunks)
+    // this thread's footprints (the footprint array is padded to whole chunks)
     const uint4* f4 = reinterpret_cast<const uint4*>(p.fs + base + j0);
-    uint32_t w[kScanPer], h[kScanPer];
-    unsigned long long sum = 0;
+    uint32_t fa[kScanPer], fb[kScanPer];
 #pragma unroll
     for (int q = 0; q < kScanPer / 2; ++q) {
       const uint4 v = __ldcg(f4 + q);
-      const uint32_t fa2[2] = {v.x, v.z}, fb2[2] = {v.y, v.w};
-#pragma unroll
-      for (int e2 = 0; e2 < 2; ++e2) {
-        const int e = 2 * q + e2;
-        if (j0 + e < n) {
-          const uint32_t sw = (uint32_t)((k * fa2[e2] + d) >> a.shift);
-          const uint32_t sh = (uint32_t)((k * fb2[e2] + d) >> a.shift);
-          w[e] = (sw > a.min_box ? sw : a.min_box) + 2u * a.gutter;
-          h[e] = (sh > a.min_box ? sh : a.min_box) + 2u * a.gutter;
-        } else {
-          w[e] = 0;
-          h[e] = 0;
-        }
-        sum += w[e];
-      }
+      fa[2 * q] = v.x;
+      fb[2 * q] = v.y;
+      fa[2 * q + 1] = v.z;
+      fb[2 * q + 1] = v.w;
     }
-    if (lane == 31) s_lastw[wid] = w[kScanPer - 1];
-    unsigned long long tot;
-    const unsigned long long excl = block_scan_incl<unsigned long long>(sum, ws64, &tot) - sum;
-    // chunk offset by decoupled look-back (warp 0)
-    if (wid == 0) {
+    unsigned long long sum[KC], incl[KC], tot[KC];
+#pragma unroll
+    for (int q = 0; q < KC; ++q) {
+      const unsigned long long k = (unsigned long long)grp * KC + q + 1;
+      sum[q] = 0;
+      uint32_t w = 0;
+#pragma unroll
+      for (int e = 0; e < kScanPer; ++e) {
+        w = j0 + e < n ? scaled_side(k, fa[e], a, d) : 0u;
+        sum[q] += w;
+      }
+      if (lane == 31) s_lastw[q][wid] = w;
+    }
+    block_scan_incl_n<KC>(sum, ws64, incl, tot);
+    // chunk offsets by decoupled look-back (warp q for the item's candidate q)
+    if (wid < (uint32_t)KC && grp * KC + wid < n_scales) {
+      const uint32_t kidx = grp * KC + wid;
       unsigned long long* st = p.scan_state + (size_t)kidx * p.max_chunks;
-      unsigned long long prefix = 0;
+      unsigned long long prefix = 0, tq = 0;
+#pragma unroll
+      for (int q = 0; q < KC; ++q)
+        if (wid == (uint32_t)q) tq = tot[q];
       if (c == 0) {
-        if (lane == 0) st_relaxed_u64(st, kStInc | tot);
+        if (lane == 0) st_relaxed_u64(st, kStInc | tq);
       } else {
-        if (lane == 0) st_relaxed_u64(st + c, kStAgg | tot);
+        if (lane == 0) st_relaxed_u64(st + c, kStAgg | tq);
         int jn = (int)c - 1;  // nearest chunk not yet folded in
         uint32_t spins = 0;
         for (;;) {
@@ -317,85 +358,136 @@ __device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackA
           if (inc) break;
           jn -= 32;
         }
-        if (lane == 0) st_relaxed_u64(st + c, kStInc | ((prefix + tot) & kStVal));
+        if (lane == 0) st_relaxed_u64(st + c, kStInc | ((prefix + tq) & kStVal));
       }
-      if (lane == 0) s_prefix = prefix;
+      if (lane == 0) s_prefix[wid] = prefix;
     }
     __syncthreads();
-    // previous box's width, for the row test of this thread's first box
-    uint32_t wprev = __shfl_up_sync(0xFFFFFFFFu, w[kScanPer - 1], 1);
-    if (lane == 0) wprev = wid ? s_lastw[wid - 1] : 0u;
-    // the thread's boxes in 32-bit arithmetic relative to its first box: row
-    // q0 + (u >> log2 omega) and offset u & (omega - 1) for u = P - q0 omega (u stays
-    // below 2^28: a box is at most 2^24 wide)
-    const unsigned long long P0 = s_prefix + excl;
-    const unsigned long long q0 = P0 >> a.atlas_log2;
-    const uint32_t q0m3 = (uint32_t)(q0 % 3ull);
-    uint32_t u = (uint32_t)(P0 & (om - 1u));
-    // first box: does a row start here (the previous box begins in an earlier row)?
-    bool first_start = j0 == 0 || ((P0 - wprev) >> a.atlas_log2) != q0;
-    uint32_t starts = 0, cnt = 0, mo = 0;
-    uint2 r8[kScanPer];
+    // the item's candidates side by side: push records, row starts and overflow
+    uint32_t u[KC], starts[KC], cnt[KC], mo[KC], wlast[KC], q0m3[KC];
+    bool first_start[KC];
 #pragma unroll
-    for (int e = 0; e < kScanPer; ++e) {
-      r8[e] = make_uint2(0u, 0u);
-      if (j0 + e < n) {
-        const uint32_t dq = u >> a.atlas_log2;
-        const uint32_t xr = u & (om - 1u);
-        const bool st = e ? ((u - w[e - 1]) >> a.atlas_log2) != dq : first_start;
-        if (st) {
-          starts |= 1u << e;
-          ++cnt;
+    for (int q = 0; q < KC; ++q) {
+      const unsigned long long k = (unsigned long long)grp * KC + q + 1;
+      // previous box's width, for the row test of this thread's first box
+      uint32_t wprev = __shfl_up_sync(0xFFFFFFFFu, j0 + kScanPer - 1 < n ? scaled_side(k, fa[kScanPer - 1], a, d) : 0u, 1);
+      if (lane == 0) wprev = wid ? s_lastw[q][wid - 1] : 0u;
+      // the thread's boxes in 32-bit arithmetic relative to its first box: row
+      // q0 + (u >> log2 omega) and offset u & (omega - 1) for u = P - q0 omega (u stays
+      // below 2^28: a box is at most 2^24 wide)
+      const unsigned long long P0 = s_prefix[q] + incl[q] - sum[q];
+      const unsigned long long q0 = P0 >> a.atlas_log2;
+      q0m3[q] = (uint32_t)(q0 % 3ull);
+      u[q] = (uint32_t)(P0 & (om - 1u));
+      // first box: does a row start here (the previous box begins in an earlier row)?
+      first_start[q] = j0 == 0 || ((P0 - wprev) >> a.atlas_log2) != q0;
+      starts[q] = cnt[q] = mo[q] = wlast[q] = 0u;
+    }
+#pragma unroll
+    for (int e2 = 0; e2 < kScanPer / 2; ++e2) {
+#pragma unroll
+      for (int q = 0; q < KC; ++q) {
+        const uint32_t kidx = grp * KC + q;
+        if (kidx >= n_scales) break;  // (the same for the whole CTA)
+        const unsigned long long k = kidx + 1;
+        uint32_t r[4] = {0u, 0u, 0u, 0u};
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+          const int e = 2 * e2 + h2;
+          uint32_t w = 0;
+          if (j0 + e < n) {
+            w = scaled_side(k, fa[e], a, d);
+            const uint32_t h = scaled_side(k, fb[e], a, d);
+            const uint32_t dq = u[q] >> a.atlas_log2;
+            const uint32_t xr = u[q] & (om - 1u);
+            const bool st = e ? ((u[q] - wlast[q]) >> a.atlas_log2) != dq : first_start[q];
+            if (st) {
+              starts[q] |= 1u << e;
+              ++cnt[q];
+            }
+            if (xr + w > om) mo[q] = max(mo[q], xr + w - om);
+            const uint32_t ws = w < 0xFFFFu ? w : 0xFFFFu;
+            const uint32_t hs = h < 0x7FFFFFFFu ? h : 0x7FFFFFFFu;
+            r[2 * h2] = xr | (ws << 16);
+            r[2 * h2 + 1] = hs | (((q0m3[q] + dq % 3u) % 3u == 0u) ? 0x80000000u : 0u);
+          }
+          u[q] += w;
+          wlast[q] = w;
         }
-        if (xr + w[e] > om) mo = max(mo, xr + w[e] - om);
-        const uint32_t ws = w[e] < 0xFFFFu ? w[e] : 0xFFFFu;
-        const uint32_t hs = h[e] < 0x7FFFFFFFu ? h[e] : 0x7FFFFFFFu;
-        r8[e] = make_uint2(xr | (ws << 16), hs | (((q0m3 + dq % 3u) % 3u == 0u) ? 0x80000000u : 0u));
+        reinterpret_cast<uint4*>(p.rec8 + kidx * rstride + base + j0)[e2] = make_uint4(r[0], r[1], r[2], r[3]);
       }
-      u += w[e];
     }
-    uint4* o4 = reinterpret_cast<uint4*>(p.rec8 + kidx * rstride + base + j0);
+    // one block pass for all of them: the exclusive prefix of the row starts and the
+    // largest overflow
+    uint32_t x[KC], mx[KC];
 #pragma unroll
-    for (int q = 0; q < kScanPer / 2; ++q) o4[q] = make_uint4(r8[2 * q].x, r8[2 * q].y, r8[2 * q + 1].x, r8[2 * q + 1].y);
-    // one block pass: the exclusive prefix of the row starts and the largest overflow
-    uint32_t x = cnt, mx = mo;
+    for (int q = 0; q < KC; ++q) {
+      x[q] = cnt[q];
+      mx[q] = mo[q];
 #pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o), z = __shfl_xor_sync(0xFFFFFFFFu, mx, o);
-      if (lane >= (unsigned)o) x += y;
-      mx = max(mx, z);
-    }
-    if (lane == 31) {
-      ws32[wid] = x;
-      s_wmax[wid] = mx;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x[q], o), z = __shfl_xor_sync(0xFFFFFFFFu, mx[q], o);
+        if (lane >= (unsigned)o) x[q] += y;
+        mx[q] = max(mx[q], z);
+      }
+      if (lane == 31) {
+        ws32[q][wid] = x[q];
+        s_wmax[q][wid] = mx[q];
+      }
     }
     __syncthreads();
-    if (wid == 0) {
+    if (wid < (uint32_t)KC) {
       const uint32_t nw = NT / 32;
-      uint32_t t = lane < nw ? ws32[lane] : 0u, m2 = lane < nw ? s_wmax[lane] : 0u;
+      uint32_t t = lane < nw ? ws32[wid][lane] : 0u, m2 = lane < nw ? s_wmax[wid][lane] : 0u;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
         const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, t, o), z = __shfl_xor_sync(0xFFFFFFFFu, m2, o);
         if (lane >= (unsigned)o) t += y;
         m2 = max(m2, z);
       }
-      ws32[lane] = t;
-      if (lane == 0) s_wmax[0] = m2;
+      ws32[wid][lane] = t;
+      if (lane == 0) s_wmax[wid][0] = m2;
     }
     __syncthreads();
-    const uint32_t nseg = ws32[31];
-    uint32_t at = x - cnt + (wid ? ws32[wid - 1] : 0u);
-    mo = s_wmax[0];
-    uint16_t* sg = p.segs + ((size_t)kidx * p.max_chunks + c) * kSegStride;
 #pragma unroll
-    for (int e = 0; e < kScanPer; ++e)
-      if (starts & (1u << e)) sg[1 + at++] = (uint16_t)(j0 + e);
-    if (tid == 0) {
-      sg[0] = (uint16_t)nseg;
-      sg[1 + nseg] = (uint16_t)n;
+    for (int q = 0; q < KC; ++q) {
+      const uint32_t kidx = grp * KC + q;
+      if (kidx >= n_scales) break;
+      const uint32_t nseg = ws32[q][31];
+      uint32_t at = x[q] - cnt[q] + (wid ? ws32[q][wid - 1] : 0u);
+      uint16_t* sg = p.segs + ((size_t)kidx * p.max_chunks + c) * kSegStride;
+#pragma unroll
+      for (int e = 0; e < kScanPer; ++e)
+        if (starts[q] & (1u << e)) sg[1 + at++] = (uint16_t)(j0 + e);
+      if (tid == 0) {
+        sg[0] = (uint16_t)nseg;
+        sg[1 + nseg] = (uint16_t)n;
+        if (s_wmax[q][0]) atomicMax(p.m + kidx, s_wmax[q][0]);
+      }
     }
-    if (tid == 0 && mo) atomicMax(p.m + kidx, mo);
   }
+}
+
+// nblk: the CTAs that take items.  PAIRS: two candidates per item where one per item
+// would take more than one wave of them.
+template <int NT, bool PAIRS = true>
+__device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackArgs& a, uint32_t n_scales,
+                                               uint32_t bid, uint32_t nblk) {
+  // the order's bin totals were last read by k_order_scatter: clear them for the next call
+  if (bid == 0)
+    for (uint32_t b = threadIdx.x; b < kMaxH; b += blockDim.x) p.ord_total[b] = 0u;
+  __shared__ int32_t s_status;
+  // one read of the status word for the whole CTA (another CTA's time-out can set
+  // it meanwhile, and every thread must take the same branch before the barriers)
+  if (threadIdx.x == 0) s_status = __ldcg(&p.ctr->status);
+  __syncthreads();
+  if (s_status != 0) return;
+  const uint32_t C = __ldcg(p.count);
+  if (C > p.max_boxes || C == 0) return;
+  if (PAIRS && (unsigned long long)((C + kChunk - 1) / kChunk) * n_scales > nblk)
+    pack_scan_items<NT, 2>(p, a, n_scales, C);
+  else
+    pack_scan_items<NT, 1>(p, a, n_scales, C);
 }
 
 // Row push of one candidate per CTA, then the last CTA selects.  The chunks' push

@@ -171,7 +171,7 @@ __device__ __noinline__ void st_order_scatter(const ViewArgs& v, uint32_t j, uns
   pk::order_scatter_body(v.ps, v.fa, v.fb, v.order, j, reinterpret_cast<uint32_t*>(smem));
 }
 __device__ __noinline__ void st_pack_scan(const ViewArgs& v, uint32_t j) {
-  pk::pack_scan_body<kPT>(v.ps, v.pa, v.n_scales, j);
+  pk::pack_scan_body<kPT, false>(v.ps, v.pa, v.n_scales, j, 0u);  // one candidate per item
 }
 __device__ __noinline__ void st_push(const ViewArgs& v, uint32_t j, uint32_t n, unsigned char* smem) {
   pk::push_body<kPT>(v.ps, v.pa, j, n, smem);

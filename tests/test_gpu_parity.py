@@ -232,6 +232,61 @@ def test_pack_matches_oracle(F, n, log2, seed):
     ctx.close()
 
 
+@pytest.mark.parametrize("n_scales,mean_texels,fits", [(1, 5, True), (1, 16, False), (2, 16, True),
+                                                      (4, 16, True), (8, 16, True)])
+def test_pack_few_scales_matches_oracle(F, n_scales, mean_texels, fits):
+    """Short scale ladders (Sec. 4.2: candidates k / n, k = 1..n), on three 4096-box
+    chunks and a ragged tail: the width scan takes two candidates per work item, so
+    n = 1 leaves the second slot of its only item empty.  At 16 texels per box the
+    largest candidates overflow (the oracle picks k = 1, 2, 5 of 2, 4, 8) and the
+    single candidate of n = 1 fails."""
+    import torch
+    n, log2 = 13001, 11
+    ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1 << 16, max_width=64, max_height=64,
+                    max_atlas_log2=12)
+    fa, fb = S.lognormal_boxes(40 + n_scales, n, mean_texels=mean_texels)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    place = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    for sel in (0, 1):
+        F.fa_pack(ctx.handle, d_fa, d_fb, cnt, log2, n_scales, sel, None, place, res)
+        torch.cuda.synchronize()
+        pk = O.pack(fa, fb, log2, n_scales, select_mode=sel)
+        r = to_np(res).view(np.uint32)
+        assert int(r[3]) == pk.status
+        assert (pk.status == 0) == fits
+        if fits:
+            assert (int(r[0]), int(r[1]), int(r[2])) == (pk.k, pk.omega, pk.height)
+            assert (to_np(place) == pk.place).all()
+    ctx.close()
+
+
+def test_pack_one_scale_past_one_wave(F):
+    """One candidate (n = 1) on 305 chunks of 4096 boxes plus a ragged tail: more
+    chunks than the width scan's CTAs, so the scan pairs candidates per work item and
+    every item's second slot is empty."""
+    import torch
+    n, log2 = 305 * 4096 + 77, 12
+    ctx = F.Context(max_tris=64, max_verts=64, max_charts=1 << 21, max_atlas_log2=log2)
+    fa, fb = S.lognormal_boxes(77, n, mean_texels=1)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    place = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    for sel in (0, 1):
+        F.fa_pack(ctx.handle, d_fa, d_fb, cnt, log2, 1, sel, None, place, res)
+        torch.cuda.synchronize()
+        pk = O.pack(fa, fb, log2, 1, select_mode=sel)
+        r = to_np(res).view(np.uint32)
+        assert pk.status == 0 and int(r[3]) == 0
+        assert (int(r[0]), int(r[1]), int(r[2]), int(r[4])) == (pk.k, pk.omega, pk.height, n)
+        assert (to_np(place) == pk.place).all()
+    ctx.close()
+
+
 def test_pack_failure_and_capacity(F):
     import torch
     ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1024, max_width=64, max_height=64,
