@@ -204,17 +204,17 @@ __device__ __forceinline__ void local_body(const UfArgs& a, uint32_t bid, uint32
     }
     return;
   }
-  // tiles are handed out by a counter, so that a block that drew light tiles takes
-  // more (their costs differ by an order of magnitude)
+  // the first tile by block index, the others handed out by a counter, so that a
+  // block that drew light tiles takes more (their costs differ by an order of
+  // magnitude) and the blocks do not all queue on the counter at once
   const uint32_t n = __ldcg(&a.ctr->n_vtiles);
   __shared__ uint32_t s_i;
-  for (;;) {
-    __syncthreads();  // the shared memory of the previous tile is free
-    if (threadIdx.x == 0) s_i = atomicAdd(&a.ctr->uf_item, 1u);
-    __syncthreads();
-    const uint32_t i = s_i;
-    if (i >= n) break;
+  for (uint32_t i = bid; i < n;) {
     local_tile<NT>(a, __ldcg(a.tile_list + i));
+    __syncthreads();  // the shared memory of this tile is free, and s_i was read
+    if (threadIdx.x == 0) s_i = nblk + atomicAdd(&a.ctr->uf_item, 1u);
+    __syncthreads();
+    i = s_i;
   }
 }
 
