@@ -339,8 +339,10 @@ fa_status fa_last_device_status(fa_ctx* ctx, fa_stream_t stream, int32_t* out);
 /* Limits of the device-side waits in this context's later launches.  The paper
  * has no failure detection; these bound every loop of the library that waits on
  * other threads, so that a fault elsewhere cannot hang the GPU.
- *  loop_cap: CAS retries of one union-find hooking step (Alg. 1's hooking loop)
- *            and polls of the packing width scan's look-back on one earlier chunk;
+ *  loop_cap: CAS retries of one union-find hooking step (Alg. 1's hooking loop);
+ *            also caps the polls (at most 256) of the packing width scan's
+ *            look-back on an earlier chunk that has published nothing, after which
+ *            the scan sums that chunk's widths itself (it never runs out);
  *  wait_ns:  nanoseconds the packing push waits for a chunk's bulk copy.
  * When a limit runs out the kernel writes FA_E_TIMEOUT to the device status word,
  * drops its remaining work (later kernels of the call see the word and skip

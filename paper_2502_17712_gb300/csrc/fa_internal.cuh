@@ -44,7 +44,6 @@ struct DevCounters {
   uint32_t order_tiles;    // tiles of the current order pass
   uint32_t chart_count;    // scratch copy of the frame's chart count
   uint32_t n_groups[kMaxScales];
-  uint32_t pack_item;      // next (candidate, chunk) item of the width scan
   uint32_t n_vis;          // entries of the visible-triangle list
   uint32_t n_vtiles;       // 1024-triangle tiles with a visible triangle (listed by the marking pass)
   uint32_t uf_item;        // next listed tile of the local union-find

@@ -138,7 +138,6 @@ __device__ __forceinline__ void order_scatter_body(const PackScratch& p, const u
   if (bid == 0) {  // also with no boxes: the push reads the overflows
     for (uint32_t i = threadIdx.x; i < kMaxScales * p.max_chunks; i += blockDim.x) p.scan_state[i] = 0ull;
     if (threadIdx.x < kMaxScales) p.m[threadIdx.x] = 0u;
-    if (threadIdx.x == 0) p.ctr->pack_item = 0u;
   }
   if (bid * kOrderTile >= C) return;
   constexpr uint32_t kPer = kMaxH / kOrderTile;
@@ -200,11 +199,13 @@ struct PackArgs {
   fa_pack_result* res;
 };
 
-// Width scan: one work item per (KC candidates, chunk of kChunk boxes), handed out
-// in increasing order by a counter, so the chunks before an item are always held by
-// running CTAs.  Each item computes the scaled boxes (Sec. 4.2), scans the widths,
-// and takes its chunk's offset P by a decoupled look-back over the preceding chunks'
-// published sums (one warp per candidate).  It then writes, per box, the push record
+// Width scan: one work item per (KC candidates, chunk of kChunk boxes), taken by CTA
+// index (items bid, bid + nblk, ...).  Each item computes the scaled boxes (Sec.
+// 4.2), scans the widths, and takes its chunk's offset P by a decoupled look-back
+// over the preceding chunks' published sums (one warp per candidate); an earlier
+// chunk that has published nothing after a few polls is summed by the looking warp
+// itself, so no item waits on a CTA that may not be resident.  It then writes, per
+// box, the push record
 //   x: xr = P mod omega (bits 0-15) | w (bits 16-31)
 //   y: h (bits 0-30) | row runs left to right (bit 31: row q = P / omega, q mod 3 == 0)
 // (w and h saturate; a candidate whose box exceeds 16 bits of width has Omega above
@@ -271,19 +272,42 @@ __device__ __forceinline__ uint32_t scaled_side(unsigned long long k, uint32_t f
   return (s > a.min_box ? s : a.min_box) + 2u * a.gutter;
 }
 
+// Polls of an unpublished earlier chunk before the look-back sums it itself (the
+// context's loop_cap, if lower).
+constexpr uint32_t kLookbackPolls = 256;
+
+// Sum of candidate k's scaled widths over chunk j (one warp; the look-back's
+// fallback when chunk j's item has published nothing).
+__device__ __forceinline__ unsigned long long chunk_width_sum(const PackScratch& p, const PackArgs& a, uint32_t C,
+                                                              uint32_t j, unsigned long long k,
+                                                              unsigned long long d) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t base = j * kChunk, n = min(C - base, kChunk);
+  const uint4* f4 = reinterpret_cast<const uint4*>(p.fs + base);  // padded to whole chunks
+  unsigned long long s = 0;
+#pragma unroll 4
+  for (uint32_t i = lane; i < kChunk / 2; i += 32) {
+    const uint4 v = __ldcg(f4 + i);
+    if (2u * i < n) s += scaled_side(k, v.x, a, d);
+    if (2u * i + 1u < n) s += scaled_side(k, v.z, a, d);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xFFFFFFFFu, s, o);
+  return s;
+}
+
 // The items of C boxes with KC candidates each.  KC = 2: the candidates of item
 // (g, c) are k = 2g + 1 and 2g + 2, so one item loads its chunk's footprints once
 // for both, and twice as many chunks fit one wave of the grid; each candidate keeps
 // its own scan state.
 template <int NT, int KC>
 __device__ __forceinline__ void pack_scan_items(const PackScratch& p, const PackArgs& a, uint32_t n_scales,
-                                                uint32_t C) {
+                                                uint32_t C, uint32_t bid, uint32_t nblk) {
   constexpr int kScanPer = kChunk / NT;  // consecutive boxes per thread
   __shared__ unsigned long long ws64[KC][32];
   __shared__ uint32_t ws32[KC][32];
   __shared__ uint32_t s_lastw[KC][NT / 32];
   __shared__ uint32_t s_wmax[KC][NT / 32];
-  __shared__ uint32_t s_item;
   __shared__ unsigned long long s_prefix[KC];
   const uint32_t nch = (C + kChunk - 1) / kChunk;
   const uint32_t items = nch * ((n_scales + KC - 1) / KC);
@@ -291,11 +315,8 @@ __device__ __forceinline__ void pack_scan_items(const PackScratch& p, const Pack
   const unsigned long long d = (1ull << a.shift) - 1ull;
   const uint32_t tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const size_t rstride = (size_t)p.max_chunks * kChunk;
-  for (;;) {
-    if (tid == 0) s_item = atomicAdd(&p.ctr->pack_item, 1u);
-    __syncthreads();
-    const uint32_t item = s_item;
-    if (item >= items) break;
+  for (uint32_t item = bid; item < items; item += nblk) {
+    __syncthreads();  // the shared memory of the previous item is free
     const uint32_t grp = item / nch, c = item % nch;
     const uint32_t base = c * kChunk, n = min(C - base, kChunk);
     const uint32_t j0 = tid * kScanPer;
@@ -337,26 +358,33 @@ __device__ __forceinline__ void pack_scan_items(const PackScratch& p, const Pack
       } else {
         if (lane == 0) st_relaxed_u64(st + c, kStAgg | tq);
         int jn = (int)c - 1;  // nearest chunk not yet folded in
-        uint32_t spins = 0;
+        const uint32_t max_polls = min(a.loop_cap, kLookbackPolls);
+        uint32_t polls = 0;
         for (;;) {
           const int t = jn - (int)lane;
-          unsigned long long v = t >= 0 ? ld_relaxed_u64(st + t) : kStInc;
-          while (__any_sync(0xFFFFFFFFu, (v >> 62) == 0ull)) {
-            if (++spins > a.loop_cap) {
-              if (lane == 0) set_status(p.ctr, FA_E_TIMEOUT);
-              v = kStInc;
-            } else if ((v >> 62) == 0ull) {
-              v = ld_relaxed_u64(st + t);
-            }
-          }
+          const unsigned long long v = t >= 0 ? ld_relaxed_u64(st + t) : kStInc;
           const uint32_t inc = __ballot_sync(0xFFFFFFFFu, (v >> 62) == 2ull);
-          const uint32_t upto = inc ? (uint32_t)(__ffs(inc) - 1) : 31u;
-          unsigned long long x = lane <= upto ? (v & kStVal) : 0ull;
+          const uint32_t none = __ballot_sync(0xFFFFFFFFu, (v >> 62) == 0ull);
+          const uint32_t ui = inc ? (uint32_t)(__ffs(inc) - 1) : 32u;
+          const uint32_t un = none ? (uint32_t)(__ffs(none) - 1) : 32u;
+          // fold in the sums before the first unpublished chunk, up to and with the
+          // first inclusive prefix
+          const uint32_t upto = ui < un ? ui + 1u : un;
+          unsigned long long x = lane < upto ? (v & kStVal) : 0ull;
 #pragma unroll
           for (int o = 16; o > 0; o >>= 1) x += __shfl_xor_sync(0xFFFFFFFFu, x, o);
           prefix += x;
-          if (inc) break;
-          jn -= 32;
+          if (ui < un) break;
+          jn -= (int)upto;
+          if (upto) polls = 0;
+          if (un == 32u) continue;
+          // chunk jn has published nothing yet: poll it again, or (its item may not
+          // have started: CTAs need not be resident together) sum its widths here
+          if (++polls > max_polls) {
+            prefix += chunk_width_sum(p, a, C, (uint32_t)jn, kidx + 1ull, d);
+            jn -= 1;
+            polls = 0;
+          }
         }
         if (lane == 0) st_relaxed_u64(st + c, kStInc | ((prefix + tq) & kStVal));
       }
@@ -485,9 +513,9 @@ __device__ __forceinline__ void pack_scan_body(const PackScratch& p, const PackA
   const uint32_t C = __ldcg(p.count);
   if (C > p.max_boxes || C == 0) return;
   if (PAIRS && (unsigned long long)((C + kChunk - 1) / kChunk) * n_scales > nblk)
-    pack_scan_items<NT, 2>(p, a, n_scales, C);
+    pack_scan_items<NT, 2>(p, a, n_scales, C, bid, nblk);
   else
-    pack_scan_items<NT, 1>(p, a, n_scales, C);
+    pack_scan_items<NT, 1>(p, a, n_scales, C, bid, nblk);
 }
 
 // Row push of one candidate per CTA, then the last CTA selects.  The chunks' push

@@ -170,8 +170,8 @@ __device__ __noinline__ void st_order_tile(const ViewArgs& v, uint32_t j, unsign
 __device__ __noinline__ void st_order_scatter(const ViewArgs& v, uint32_t j, unsigned char* smem) {
   pk::order_scatter_body(v.ps, v.fa, v.fb, v.order, j, reinterpret_cast<uint32_t*>(smem));
 }
-__device__ __noinline__ void st_pack_scan(const ViewArgs& v, uint32_t j) {
-  pk::pack_scan_body<kPT, false>(v.ps, v.pa, v.n_scales, j, 0u);  // one candidate per item
+__device__ __noinline__ void st_pack_scan(const ViewArgs& v, uint32_t j, uint32_t n) {
+  pk::pack_scan_body<kPT, false>(v.ps, v.pa, v.n_scales, j, n);  // one candidate per item
 }
 __device__ __noinline__ void st_push(const ViewArgs& v, uint32_t j, uint32_t n, unsigned char* smem) {
   pk::push_body<kPT>(v.ps, v.pa, j, n, smem);
@@ -216,7 +216,7 @@ __device__ void run_stage(const ViewArgs& v, uint32_t stage, uint32_t j, uint32_
     case S_BBOX: v.devm ? st_bbox<true>(v, j, n) : st_bbox<false>(v, j, n); break;
     case S_ORDER_TILE: st_order_tile(v, j, smem); break;
     case S_ORDER_SCATTER: st_order_scatter(v, j, smem); break;
-    case S_PACK_SCAN: st_pack_scan(v, j); break;
+    case S_PACK_SCAN: st_pack_scan(v, j, n); break;
     case S_PUSH: st_push(v, j, n, smem); break;
     case S_PLACE: st_place(v, j, n); break;
     case S_UV: v.devm ? st_uv<true>(v, j, n) : st_uv<false>(v, j, n); break;

@@ -6,10 +6,12 @@ same context is clean and equals the oracle.
 The limits are lowered on purpose here.  With a hooking cap of 0, the first
 union-find hooking step that finds two different roots gives up: on the
 heightfield frame the visible patch spans several 1024-triangle tiles, so the
-cross-tile hooking always meets such a step.  The packing look-back and the
-push's bulk-copy wait are run with limits of 0 as well; whether they run out
-depends on timing, so that case checks that the outcome is one of the two
-consistent ones and that the context recovers.
+cross-tile hooking always meets such a step.  The push's bulk-copy wait is run
+with a limit of 0 as well; whether it runs out depends on timing, so that case
+checks that the outcome is one of the two consistent ones and that the context
+recovers.  The packing width scan's look-back never gives up: with a poll limit
+of 0 every item sums the earlier chunks that have not published yet itself, and
+the packing still equals the oracle.
 """
 import numpy as np
 import pytest
@@ -74,4 +76,33 @@ def test_pack_waits_with_zero_limits_stay_consistent_and_recover(F):
     r = res.cpu().numpy().view(np.uint32)
     assert (int(r[0]), int(r[1]), int(r[2]), int(r[3])) == (pk.k, pk.omega, pk.height, 0)
     assert (place[:n].cpu().numpy() == pk.place).all()
+    ctx.close()
+
+
+@pytest.mark.parametrize("n", [12000, 40000])
+def test_scan_look_back_sums_unpublished_chunks_itself(F, n):
+    """loop_cap = 0: the width scan polls no earlier chunk, so each item adds up the
+    widths of the chunks before it that have published nothing yet (the fallback
+    that lets the scan finish whichever of its CTAs are resident).  12,000 boxes are
+    3 chunks (one candidate per item, one wave); 40,000 are 10 chunks (two
+    candidates per item, and some CTAs take a second item)."""
+    import torch
+    log2 = 12
+    fa, fb = S.lognormal_boxes(6, n, mean_texels=6)
+    ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1 << 16, max_width=64, max_height=64,
+                    max_atlas_log2=12)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    place = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    ctx.set_wait_limits(loop_cap=0)
+    for sel in (0, 1):
+        pk = O.pack(fa, fb, log2, select_mode=sel)
+        F.fa_pack(ctx.handle, d_fa, d_fb, cnt, log2, 64, sel, None, place, res)
+        torch.cuda.synchronize()
+        assert ctx.device_status() == F.FA_OK
+        r = res.cpu().numpy().view(np.uint32)
+        assert (int(r[0]), int(r[1]), int(r[2]), int(r[3])) == (pk.k, pk.omega, pk.height, 0)
+        assert (place.cpu().numpy() == pk.place).all()
     ctx.close()
