@@ -12,9 +12,9 @@
 //   (deterministic, identical for identical frames).
 //
 // Pack: candidates k / n, k = 1..n (Sec. 4.2).  k_order_scatter also writes the
-//   footprints in box order.  k_pack_scan takes (candidate, 4096-box chunk) work
-//   items: scaled integer boxes, the exclusive prefix P of the widths (chunk-local
-//   scan plus a decoupled look-back over the preceding chunks), the largest
+//   footprints in box order.  k_pack_scan takes (one or two candidates, 4096-box
+//   chunk) work items: scaled integer boxes, the exclusive prefix P of the widths
+//   (chunk-local scan plus a decoupled look-back over the preceding chunks), the largest
 //   overflow m past omega (Sec. 4.3), and per box a push-ready record (x inside the
 //   row, w, h, row direction) plus per chunk the list of row segments.  Then one CTA
 //   per candidate (k_pack_push) pushes the rows up against a frontline in shared
