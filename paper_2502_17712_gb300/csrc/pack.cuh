@@ -125,8 +125,8 @@ __device__ __forceinline__ void order_tile_body(const PackScratch& p, const uint
 
 // Each block scans the bin totals itself (exclusive, in shared memory), then places
 // its boxes: bin start + the bin's boxes in earlier tiles + the rank in the tile.
-// Block 0 also clears the width scan's look-back state, work counter and overflows
-// (k_pack_scan runs next; it clears the bin totals for the next call).
+// Block 0 also clears the width scan's look-back state and overflows (k_pack_scan
+// runs next; it clears the bin totals for the next call).
 // binstart: kMaxH words of shared memory.
 __device__ __forceinline__ void order_scatter_body(const PackScratch& p, const uint32_t* __restrict__ fa,
                                                    const uint32_t* __restrict__ fb, uint32_t* order, uint32_t bid,
@@ -193,7 +193,8 @@ struct PackArgs {
   uint32_t gutter;
   uint32_t select_mode;
   uint32_t front_cap;
-  uint32_t loop_cap;          // polls of the look-back on one earlier chunk before FA_E_TIMEOUT
+  uint32_t loop_cap;          // polls (at most kLookbackPolls) of an unpublished earlier chunk before
+                              // the look-back sums that chunk itself
   unsigned long long wait_ns;  // time limit of the push's wait for a staged chunk
   fa_placement* place;
   fa_pack_result* res;
