@@ -287,6 +287,32 @@ def test_pack_one_scale_past_one_wave(F):
     ctx.close()
 
 
+@pytest.mark.parametrize("n,log2,mean_texels,seed", [(1, 1, 1, 0), (2, 1, 1, 1), (1, 2, 1, 2), (40, 3, 1, 3),
+                                                       (60000, 14, 800, 4)])
+def test_pack_extreme_atlas_sizes(F, n, log2, mean_texels, seed):
+    """The smallest atlases (2^1 .. 2^3 texels: one box fits a 2x2 atlas, two do not)
+    and the largest one (2^14, with boxes so large that only k = 6 of 64 fits and the
+    frontline spans 16,479 texels)."""
+    import torch
+    ctx = F.Context(max_tris=64, max_verts=64, max_charts=1 << 16, max_atlas_log2=14)
+    fa, fb = S.lognormal_boxes(seed, n, mean_texels=mean_texels)
+    d_fa = torch.as_tensor(fa.view(np.int32)).cuda()
+    d_fb = torch.as_tensor(fb.view(np.int32)).cuda()
+    cnt = torch.tensor([n], dtype=torch.int32, device="cuda")
+    place = torch.zeros(n, 4, dtype=torch.int32, device="cuda")
+    res = torch.zeros(5, dtype=torch.int32, device="cuda")
+    for sel in (0, 1):
+        F.fa_pack(ctx.handle, d_fa, d_fb, cnt, log2, 64, sel, None, place, res)
+        torch.cuda.synchronize()
+        pk = O.pack(fa, fb, log2, select_mode=sel)
+        r = to_np(res).view(np.uint32)
+        assert int(r[3]) == pk.status
+        if pk.status == 0:
+            assert (int(r[0]), int(r[1]), int(r[2])) == (pk.k, pk.omega, pk.height)
+            assert (to_np(place) == pk.place).all()
+    ctx.close()
+
+
 def test_pack_failure_and_capacity(F):
     import torch
     ctx = F.Context(max_tris=1024, max_verts=1024, max_charts=1024, max_width=64, max_height=64,
