@@ -291,19 +291,47 @@ __device__ __forceinline__ void flatten_tile(const UfArgs& a, uint32_t tile, uin
   __shared__ uint32_t wc[kPerBlock / 32], vcnt[NT / 32];
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
-  uint32_t vis = 0, rb[kPerBlock / NT];
+  constexpr uint32_t kK = kPerBlock / NT;
+  uint32_t vis = 0, rb[kK], words[kK];
+  int32_t cur[kK];
+  // the thread's kK triangles walk to their roots side by side, one round of
+  // independent label loads per step (every label read on the way is an ancestor on
+  // the same path: the only writes meanwhile are other walks' compressions to roots)
 #pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / NT; ++k) {
+  for (uint32_t k = 0; k < kK; ++k) {
+    const uint32_t w = tile * (kPerBlock / 32) + k * (NT / 32) + wid;
+    words[k] = w < nwords ? __ldcg(a.vt + w) : 0u;
+    vis += __popc(words[k]);
+  }
+  uint32_t walking = 0;  // bit k: triangle k has not reached its root yet
+#pragma unroll
+  for (uint32_t k = 0; k < kK; ++k) {
+    const uint32_t t = ((tile * (kPerBlock / 32) + k * (NT / 32) + wid) << 5) + lane;
+    cur[k] = -1;
+    if ((words[k] >> lane) & 1u) {
+      cur[k] = __ldcg(a.label + t);
+      if (cur[k] != (int32_t)t) walking |= 1u << k;
+    }
+  }
+  while (walking) {
+    int32_t nxt[kK];
+#pragma unroll
+    for (uint32_t k = 0; k < kK; ++k) nxt[k] = (walking >> k) & 1u ? __ldcg(a.label + cur[k]) : cur[k];
+#pragma unroll
+    for (uint32_t k = 0; k < kK; ++k) {
+      if (!((walking >> k) & 1u)) continue;
+      if (nxt[k] == cur[k]) walking &= ~(1u << k);
+      else cur[k] = nxt[k];
+    }
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kK; ++k) {
     const uint32_t wl = k * (NT / 32) + wid;
-    const uint32_t w = tile * (kPerBlock / 32) + wl;
-    const uint32_t word = w < nwords ? __ldcg(a.vt + w) : 0u;
-    vis += __popc(word);
+    const uint32_t t = ((tile * (kPerBlock / 32) + wl) << 5) + lane;
     bool root = false;
-    if ((word >> lane) & 1u) {
-      const uint32_t t = (w << 5) + lane;
-      const int32_t r = find_root(a.label, (int32_t)t);
-      a.label[t] = r;
-      root = r == (int32_t)t;
+    if ((words[k] >> lane) & 1u) {
+      a.label[t] = cur[k];
+      root = cur[k] == (int32_t)t;
     }
     rb[k] = __ballot_sync(0xFFFFFFFFu, root);
     if (lane == 0) wc[wl] = __popc(rb[k]);
@@ -483,26 +511,35 @@ __device__ __forceinline__ void chart_tile(const UfArgs& a, uint32_t tile, const
                                            const uint32_t* visstart, uint2* vis) {
   const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   const uint32_t nwords = (a.T + 31) >> 5;
-  uint32_t words[kPerBlock / NT];
-  int32_t chart[kPerBlock / NT];
+  constexpr uint32_t kK = kPerBlock / NT;
+  uint32_t words[kK], rt[kK];
+  int32_t chart[kK];
+  // the loads of the thread's kK triangles in rounds (VT words, roots, the roots'
+  // counts), each round independent, before any store
 #pragma unroll
-  for (uint32_t k = 0; k < kPerBlock / NT; ++k) {
+  for (uint32_t k = 0; k < kK; ++k) {
     const uint32_t w = tile * (kPerBlock / 32) + k * (NT / 32) + wid;
     words[k] = w < nwords ? __ldcg(a.vt + w) : 0u;
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kK; ++k) {
+    const uint32_t t = ((tile * (kPerBlock / 32) + k * (NT / 32) + wid) << 5) + lane;
+    rt[k] = (words[k] >> lane) & 1u ? (uint32_t)__ldcg(a.label + t) : 0u;
+  }
+#pragma unroll
+  for (uint32_t k = 0; k < kK; ++k)
+    chart[k] = (words[k] >> lane) & 1u ? (int32_t)chart_of_root(blockcnt, wordroots, rt[k]) : -1;
+#pragma unroll
+  for (uint32_t k = 0; k < kK; ++k) {
+    const uint32_t w = tile * (kPerBlock / 32) + k * (NT / 32) + wid;
     const uint32_t t = (w << 5) + lane;
-    int32_t out = -1;
-    if ((words[k] >> lane) & 1u) {
-      const uint32_t r = (uint32_t)__ldcg(a.label + t);
-      const uint32_t c = chart_of_root(blockcnt, wordroots, r);
-      out = (int32_t)c;
-      if (r == t && c < max_charts) {
-        roots[c] = t;
-        reinterpret_cast<uint4*>(box_enc)[c] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
-        box_full[c] = 0u;
-      }
+    if (chart[k] >= 0 && rt[k] == t && (uint32_t)chart[k] < max_charts) {
+      const uint32_t c = (uint32_t)chart[k];
+      roots[c] = t;
+      reinterpret_cast<uint4*>(box_enc)[c] = make_uint4(0xFFFFFFFFu, 0xFFFFFFFFu, 0u, 0u);
+      box_full[c] = 0u;
     }
-    chart[k] = out;
-    if (w < nwords && t < a.T) tri_chart[t] = out;
+    if (w < nwords && t < a.T) tri_chart[t] = chart[k];
   }
   put_visible<NT>(words, __ldcg(visstart + tile), chart, vis, tile);
 }
