@@ -338,23 +338,30 @@ __device__ __forceinline__ void flatten_tile(const UfArgs& a, uint32_t tile, uin
   }
   if (lane == 0) vcnt[wid] = vis;  // every lane counted the same words
   __syncthreads();
+  // the exclusive prefix of the words' root counts (one warp scan)
+  if (wid == 0) {
+    const uint32_t c = wc[lane];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= (unsigned)o) x += y;
+    }
+    wc[lane] = x - c;
+    if (lane == 31) {
+      uint32_t v = 0;
+      for (int i = 0; i < NT / 32; ++i) v += vcnt[i];
+      blockcnt[tile] = x;
+      viscnt[tile] = v;
+    }
+  }
+  __syncthreads();
   // per VT word: its root bits and the roots of the block's earlier words
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / NT; ++k) {
     const uint32_t wl = k * (NT / 32) + wid;
     const uint32_t w = tile * (kPerBlock / 32) + wl;
-    if (lane == 0 && w < nwords) {
-      uint32_t pre = 0;
-      for (uint32_t i = 0; i < wl; ++i) pre += wc[i];
-      wordroots[w] = make_uint2(rb[k], pre);
-    }
-  }
-  if (threadIdx.x == 0) {
-    uint32_t s = 0, v = 0;
-    for (int i = 0; i < kPerBlock / 32; ++i) s += wc[i];
-    for (int i = 0; i < NT / 32; ++i) v += vcnt[i];
-    blockcnt[tile] = s;
-    viscnt[tile] = v;
+    if (lane == 0 && w < nwords) wordroots[w] = make_uint2(rb[k], wc[wl]);
   }
 }
 
@@ -489,13 +496,22 @@ __device__ __forceinline__ void put_visible(const uint32_t (&words)[kPerBlock / 
   for (uint32_t k = 0; k < kPerBlock / NT; ++k)
     if (lane == 0) wpop[k * (NT / 32) + wid] = __popc(words[k]);
   __syncthreads();
+  if (wid == 0) {  // the exclusive prefix of the words' visible counts
+    const uint32_t c = wpop[lane];
+    uint32_t x = c;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xFFFFFFFFu, x, o);
+      if (lane >= (unsigned)o) x += y;
+    }
+    wpop[lane] = x - c;
+  }
+  __syncthreads();
 #pragma unroll
   for (uint32_t k = 0; k < kPerBlock / NT; ++k) {
     const uint32_t wl = k * (NT / 32) + wid;
     if (!((words[k] >> lane) & 1u)) continue;
-    uint32_t pre = start;
-    for (uint32_t i = 0; i < wl; ++i) pre += wpop[i];
-    pre += __popc(words[k] & ((1u << lane) - 1u));
+    const uint32_t pre = start + wpop[wl] + __popc(words[k] & ((1u << lane) - 1u));
     const uint32_t t = ((tile * (kPerBlock / 32) + wl) << 5) + lane;
     vis[pre] = make_uint2(t, (uint32_t)chart[k]);
   }
