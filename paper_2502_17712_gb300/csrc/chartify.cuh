@@ -24,18 +24,35 @@ namespace {
 constexpr int kBlock = 256;
 constexpr int kPerBlock = 1024;  // triangles per counting block (4 per thread)
 
-// Representative with path halving (labels only decrease; parents are smaller).
-__device__ __forceinline__ int32_t find_rep(volatile int32_t* label, int32_t x) {
-  int32_t cur = label[x];
-  if (cur != x) {
-    int32_t prev = x, next;
-    while (cur > (next = label[cur])) {
-      label[prev] = next;
-      prev = cur;
-      cur = next;
+// The representatives of a and of b, walked side by side (each step loads both next
+// labels at once) with path halving (labels only decrease: parents are smaller, and
+// a label only ever moves to an ancestor).
+__device__ __forceinline__ void find_rep2(volatile int32_t* label, int32_t a, int32_t b, int32_t& ra, int32_t& rb) {
+  int32_t ca = label[a], cb = label[b], pa = a, pb = b;
+  bool wa = ca != a, wb = cb != b;  // still walking
+  while (wa || wb) {
+    const int32_t na = wa ? label[ca] : ca, nb = wb ? label[cb] : cb;
+    if (wa) {
+      if (ca > na) {
+        label[pa] = na;
+        pa = ca;
+        ca = na;
+      } else {
+        wa = false;
+      }
+    }
+    if (wb) {
+      if (cb > nb) {
+        label[pb] = nb;
+        pb = cb;
+        cb = nb;
+      } else {
+        wb = false;
+      }
     }
   }
-  return cur;
+  ra = ca;
+  rb = cb;
 }
 
 // Root without writing: used once hooking is over.  (Path halving here would race
@@ -50,7 +67,8 @@ __device__ __forceinline__ int32_t find_root(const volatile int32_t* label, int3
 // Hook the components of a and b: the larger root is CASed onto the smaller.
 __device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevCounters* ctr, uint32_t cap) {
   volatile int32_t* vl = label;
-  int32_t ra = find_rep(vl, a), rb = find_rep(vl, b);
+  int32_t ra, rb;
+  find_rep2(vl, a, b, ra, rb);
   uint32_t guard = 0;
   while (ra != rb) {
     if (++guard > cap) {
@@ -61,8 +79,7 @@ __device__ __forceinline__ void unite(int32_t* label, int32_t a, int32_t b, DevC
     int32_t old = atomicCAS(label + hi, hi, lo);
     if (old == hi) return;
     // hi stopped being a root; retry from the current representatives
-    ra = find_rep(vl, old);
-    rb = find_rep(vl, lo);
+    find_rep2(vl, old, lo, ra, rb);
   }
 }
 
